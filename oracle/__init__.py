@@ -1,0 +1,132 @@
+"""CPU oracle for the pressure-Poisson hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 (also long double / __float128) C++ implementation of the exact solution of the
+7-point staggered Poisson equation (eq. poi) reached by eigenfunction expansion in x and y and a
+Thomas solve along z (eq. poi_reduced), with dense closed-form eigenbases instead of FFTs.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
+package.  The product path never does: it shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.cpp")
+
+BC_P, BC_NN, BC_DD = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (OpenMP, libquadmath).  Returns the path."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", "-o", _SO + ".tmp", _SRC, "-lquadmath"]
+        subprocess.check_call(cmd)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.oracle_poisson_solve.argtypes = [ctypes.c_int, ip, dp, ip, dp, dp, dp, ctypes.c_int]
+        L.oracle_apply_laplacian.argtypes = [ctypes.c_int, ip, dp, ip, dp, dp, dp, ctypes.c_int]
+        L.oracle_eigenbasis.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        L.oracle_z_rows.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
+        L.oracle_set_fault.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _dz(n, dzf):
+    if dzf is None:
+        return np.full(n[2], 1.0 / n[2])
+    dzf = np.ascontiguousarray(dzf, dtype=np.float64)
+    assert dzf.shape == (n[2],)
+    return dzf
+
+
+def poisson_solve(f, bc, length_xy=(1.0, 1.0), dzf=None, prec=64, nthreads=0):
+    """p with L_h p = f.  f has shape (nz, ny, nx) (x fastest).  Singular cases: zero-mean p."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    nz, ny, nx = f.shape
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    b = np.array(bc, dtype=np.int32)
+    L = np.array(length_xy, dtype=np.float64)
+    dz = _dz(n, dzf)
+    p = np.empty_like(f)
+    rc = lib().oracle_poisson_solve(prec, _i(n), _d(L), _i(b), _d(dz), _d(f), _d(p), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_poisson_solve rejected its arguments (rc={rc})")
+    return p
+
+
+def apply_laplacian(p, bc, length_xy=(1.0, 1.0), dzf=None, prec=64, nthreads=0):
+    """L_h p (eq. poi with a non-uniform z grid)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    nz, ny, nx = p.shape
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    b = np.array(bc, dtype=np.int32)
+    L = np.array(length_xy, dtype=np.float64)
+    dz = _dz(n, dzf)
+    out = np.empty_like(p)
+    rc = lib().oracle_apply_laplacian(prec, _i(n), _d(L), _i(b), _d(dz), _d(p), _d(out), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_apply_laplacian rejected its arguments (rc={rc})")
+    return out
+
+
+def eigenbasis(bc, n):
+    """(E, lam): orthonormal eigenvectors (columns) and unit-spacing eigenvalues of the 1-D operator."""
+    E = np.empty((n, n))
+    lam = np.empty(n)
+    if lib().oracle_eigenbasis(int(bc), int(n), _d(E), _d(lam)) != 0:
+        raise ValueError("bad eigenbasis arguments")
+    return E, lam
+
+
+def z_rows(bc_z, dzf):
+    dzf = np.ascontiguousarray(dzf, dtype=np.float64)
+    nz = dzf.shape[0]
+    a, b, c = np.empty(nz), np.empty(nz), np.empty(nz)
+    if lib().oracle_z_rows(int(bc_z), nz, _d(dzf), _d(a), _d(b), _d(c)) != 0:
+        raise ValueError("bad z_rows arguments")
+    return a, b, c
+
+
+def thomas(a, b, c, d):
+    a, b, c, d = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, c, d))
+    x = np.empty_like(d)
+    lib().oracle_thomas(d.shape[0], _d(a), _d(b), _d(c), _d(d), _d(x))
+    return x
+
+
+def set_fault(mode: int) -> None:
+    """Plant one deliberate mistake (mutation tests only); 0 restores the correct oracle."""
+    lib().oracle_set_fault(int(mode))
+
+
+def relative_residual(p, f, bc, length_xy=(1.0, 1.0), dzf=None, nthreads=0):
+    r = apply_laplacian(p, bc, length_xy, dzf, nthreads=nthreads) - f
+    return float(np.linalg.norm(r) / np.linalg.norm(f))

@@ -1,0 +1,446 @@
+// Test infrastructure -- NOT part of the product path.
+//
+// A plain, slow, obviously correct CPU implementation of what the pressure-Poisson hot path computes:
+// the exact solution of the second-order, 7-point, staggered finite-difference Poisson equation
+// (eq. poi, "FFT-based Poisson solver" subsection of Numerical method) reached the way the paper
+// describes it (eq. poi_reduced): diagonalise the x and y operators with their eigenvectors, then
+// solve one tridiagonal system along z per (x, y) mode by Gauss elimination.
+//
+// The eigenvectors are written out as dense orthonormal bases (closed-form cos/sin columns), and the
+// transforms are dense matrix products -- no FFT, no Makhoul tricks, no blocking.  Every routine is a
+// template over the scalar type so the same source runs in double, long double and __float128.
+//
+// Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this library.
+// It shares no code with the CUDA path.
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <quadmath.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2 };
+
+// Deliberate-mistake switch used only by the mutation tests (tests/test_oracle_mutations.py): each
+// value plants one plausible error so the tests can show that some pin catches it.  0 = correct.
+int g_fault = 0;
+
+typedef __float128 quad;
+
+// ---- scalar helpers for the three precisions --------------------------------------------------
+inline double sin_(double x) { return std::sin(x); }
+inline long double sin_(long double x) { return sinl(x); }
+inline quad sin_(quad x) { return sinq(x); }
+inline double cos_(double x) { return std::cos(x); }
+inline long double cos_(long double x) { return cosl(x); }
+inline quad cos_(quad x) { return cosq(x); }
+inline double sqrt_(double x) { return std::sqrt(x); }
+inline long double sqrt_(long double x) { return sqrtl(x); }
+inline quad sqrt_(quad x) { return sqrtq(x); }
+template <typename T> T pi_();
+template <> double pi_<double>() { return 3.14159265358979323846264338327950288; }
+template <> long double pi_<long double>() { return 3.14159265358979323846264338327950288L; }
+template <> quad pi_<quad>() { return acosq((quad)-1); }
+
+// ---- grid (Validation section: x, y uniform; z cell widths dzf may be non-uniform) ---------------
+// z centres sit half-way between faces; dzc[k+1] is the centre-to-centre distance between cells k
+// and k+1 (stored with an offset of one so that dzc[0] is the wall ghost distance below cell 0 and
+// dzc[nz] the one above cell nz-1).  At a wall the ghost cell mirrors the first interior cell, so
+// the ghost distance equals the wall cell's width.  A periodic z wraps.
+template <typename T>
+struct ZGrid {
+  int nz, bc;
+  std::vector<T> dzf, dzc;  // dzf[k], k=0..nz-1; dzc[k], k=0..nz (see above)
+  ZGrid(int nz_, int bc_, const double* dzf_in) : nz(nz_), bc(bc_), dzf(nz_), dzc(nz_ + 1) {
+    for (int k = 0; k < nz; ++k) dzf[k] = (T)dzf_in[k];
+    for (int k = 1; k < nz; ++k) dzc[k] = (dzf[k - 1] + dzf[k]) / 2;
+    if (bc == BC_P) {
+      dzc[0] = dzc[nz] = (dzf[nz - 1] + dzf[0]) / 2;
+    } else {
+      dzc[0] = dzf[0];
+      dzc[nz] = dzf[nz - 1];
+    }
+  }
+};
+
+// ---- the operator L_h of eq. poi, with the ghost rules of each boundary condition -----------------
+// One direction, uniform spacing h: (q[i-1] - 2 q[i] + q[i+1]) / h^2 with ghosts:
+// periodic wraps; Neumann-Neumann q[-1] = q[0]; Dirichlet-Dirichlet q[-1] = -q[0] (wall half-way
+// between ghost and first cell), likewise at the far end.
+template <typename T>
+inline T ghost(int bc, T inner, T wrap) {
+  if (bc == BC_P) return wrap;
+  if (bc == BC_NN) return inner;
+  return -inner;
+}
+
+template <typename T>
+void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const ZGrid<T>& zg, const T* p, T* out,
+                     int nthreads) {
+  const int nx = n[0], ny = n[1], nz = n[2];
+  const T dx = len_xy[0] / nx, dy = len_xy[1] / ny;
+  const T idx2 = 1 / (dx * dx), idy2 = 1 / (dy * dy);
+  const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int k = 0; k < nz; ++k) {
+    for (int j = 0; j < ny; ++j) {
+      for (int i = 0; i < nx; ++i) {
+        const size_t c = i * sx + j * sy + k * sz;
+        const T pc = p[c];
+        const T xm = (i > 0) ? p[c - sx] : ghost<T>(bc[0], pc, p[c + (nx - 1) * sx]);
+        const T xp = (i < nx - 1) ? p[c + sx] : ghost<T>(bc[0], pc, p[c - (nx - 1) * sx]);
+        const T ym = (j > 0) ? p[c - sy] : ghost<T>(bc[1], pc, p[c + (ny - 1) * sy]);
+        const T yp = (j < ny - 1) ? p[c + sy] : ghost<T>(bc[1], pc, p[c - (ny - 1) * sy]);
+        const T zm = (k > 0) ? p[c - sz] : ghost<T>(bc[2], pc, p[c + (nz - 1) * sz]);
+        const T zp = (k < nz - 1) ? p[c + sz] : ghost<T>(bc[2], pc, p[c - (nz - 1) * sz]);
+        const T lx = (xm - 2 * pc + xp) * idx2;
+        const T ly = (ym - 2 * pc + yp) * idy2;
+        // z: (1/dzf_k) [ (p_{k+1}-p_k)/dzc_{k+1/2} - (p_k-p_{k-1})/dzc_{k-1/2} ]  (non-uniform z)
+        T up = (zp - pc) / zg.dzc[k + 1];
+        T dn = (pc - zm) / zg.dzc[k];
+        if (g_fault == 1) dn = (pc - zm) / zg.dzc[k + 1];  // planted: wrong metric index
+        const T lz = (up - dn) / zg.dzf[k];
+        out[c] = lx + ly + lz;
+      }
+    }
+  }
+}
+
+// ---- orthonormal eigenbases of the 1-D operators (the discrete operator F of eq. poi_reduced) -----
+// Column m of E is an eigenvector of the 1-D second-difference operator of that boundary condition
+// (unit spacing) with eigenvalue lam[m]; E is stored row-major, E[i*n + m].
+//   periodic : 1/sqrt(n); sqrt(2/n) cos(2 pi k i/n), sqrt(2/n) sin(2 pi k i/n) for 1 <= k < n/2
+//              (columns 2k-1 and 2k); (-1)^i/sqrt(n) if n is even (last column).
+//              lam = -4 sin^2(pi k/n), which equals 2(cos(2 pi k/n) - 1).
+//   Neumann  : sqrt(2/n) c_m cos(pi m (i+1/2)/n), c_0 = 1/sqrt(2); lam = -4 sin^2(pi m/(2n)).
+//   Dirichlet: sqrt(2/n) c_m sin(pi (m+1)(i+1/2)/n), c_{n-1} = 1/sqrt(2); lam = -4 sin^2(pi (m+1)/(2n)).
+template <typename T>
+void eigenbasis(int bc, int n, std::vector<T>& E, std::vector<T>& lam) {
+  E.assign((size_t)n * n, T(0));
+  lam.assign(n, T(0));
+  const T pi = pi_<T>();
+  const T s2n = sqrt_(T(2) / n), s1n = sqrt_(T(1) / n);
+  if (bc == BC_P) {
+    for (int i = 0; i < n; ++i) E[(size_t)i * n + 0] = s1n;
+    lam[0] = 0;
+    const int kmax = (n % 2 == 0) ? n / 2 - 1 : (n - 1) / 2;
+    for (int k = 1; k <= kmax; ++k) {
+      for (int i = 0; i < n; ++i) {
+        const T th = 2 * pi * T(k) * T(i) / T(n);
+        E[(size_t)i * n + 2 * k - 1] = s2n * cos_(th);
+        E[(size_t)i * n + 2 * k] = s2n * sin_(th);
+      }
+      const T s = sin_(pi * T(k) / T(n));
+      lam[2 * k - 1] = lam[2 * k] = -4 * s * s;
+    }
+    if (n % 2 == 0) {
+      for (int i = 0; i < n; ++i) E[(size_t)i * n + n - 1] = (i % 2 == 0) ? s1n : -s1n;
+      lam[n - 1] = -4;
+    }
+  } else if (bc == BC_NN) {
+    for (int m = 0; m < n; ++m) {
+      const T cm = (m == 0) ? sqrt_(T(0.5)) : T(1);
+      for (int i = 0; i < n; ++i) E[(size_t)i * n + m] = s2n * cm * cos_(pi * T(m) * (T(i) + T(0.5)) / T(n));
+      const T s = sin_(pi * T(m) / (2 * T(n)));
+      lam[m] = -4 * s * s;
+    }
+  } else {
+    for (int m = 0; m < n; ++m) {
+      const T cm = (m == n - 1) ? sqrt_(T(0.5)) : T(1);
+      for (int i = 0; i < n; ++i) E[(size_t)i * n + m] = s2n * cm * sin_(pi * T(m + 1) * (T(i) + T(0.5)) / T(n));
+      const T s = sin_(pi * T(m + 1) / (2 * T(n)));
+      lam[m] = -4 * s * s;
+    }
+  }
+  if (g_fault == 2) {  // planted: eigenvalue of the neighbouring mode
+    std::vector<T> l2(lam);
+    for (int m = 0; m + 1 < n; ++m) lam[m] = l2[m + 1];
+  }
+}
+
+// ---- z tridiagonal rows of L_h for one (x, y) mode: a_k p_{k-1} + b_k p_k + c_k p_{k+1} ------------
+template <typename T>
+void z_rows(const ZGrid<T>& zg, std::vector<T>& a, std::vector<T>& b, std::vector<T>& c) {
+  const int nz = zg.nz;
+  a.assign(nz, T(0));
+  b.assign(nz, T(0));
+  c.assign(nz, T(0));
+  for (int k = 0; k < nz; ++k) {
+    a[k] = 1 / (zg.dzf[k] * zg.dzc[k]);
+    c[k] = 1 / (zg.dzf[k] * zg.dzc[k + 1]);
+    b[k] = -(a[k] + c[k]);
+  }
+  if (zg.bc == BC_NN) {  // ghost equals the wall cell: that flux vanishes
+    b[0] += a[0];
+    b[nz - 1] += c[nz - 1];
+  } else if (zg.bc == BC_DD) {  // ghost is minus the wall cell
+    b[0] -= a[0];
+    b[nz - 1] -= c[nz - 1];
+  }
+  if (zg.bc != BC_P) {
+    a[0] = 0;
+    c[nz - 1] = 0;
+  }
+}
+
+// Plain Gauss elimination without pivoting (Thomas) for a_k x_{k-1} + b_k x_k + c_k x_{k+1} = d_k.
+template <typename T>
+void thomas(int n, const T* a, const T* b, const T* c, const T* d, T* x) {
+  std::vector<T> cp(n), dp(n);
+  cp[0] = c[0] / b[0];
+  dp[0] = d[0] / b[0];
+  for (int k = 1; k < n; ++k) {
+    const T m = b[k] - a[k] * cp[k - 1];
+    cp[k] = c[k] / m;
+    dp[k] = (d[k] - a[k] * dp[k - 1]) / m;
+  }
+  x[n - 1] = dp[n - 1];
+  for (int k = n - 2; k >= 0; --k) x[k] = dp[k] - cp[k] * x[k + 1];
+}
+
+// ---- the direct solver (eq. poi_reduced) ---------------------------------------------------------
+// fhat = (Ex^T (x) Ey^T) f;  for every (mx, my): (A_z + mu I) phat = fhat with
+// mu = lam_x/dx^2 + lam_y/dy^2;  p = (Ex (x) Ey) phat.
+// If z is periodic (uniform only) the z direction is diagonalised too.
+// Singular case (x, y, z all periodic or Neumann): the (0,0) z-system is singular; its last equation
+// is dropped with phat_{nz-1} = 0, and the result is shifted to zero dzf-weighted mean, which makes
+// the cell-volume-weighted mean of p zero.
+template <typename T>
+int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGrid<T>& zg, const T* f, T* p,
+                  int nthreads) {
+  const int nx = n[0], ny = n[1], nz = n[2];
+  const size_t plane = (size_t)nx * ny;
+  std::vector<T> Ex, lx, Ey, ly, Ez, lz;
+  eigenbasis<T>(bc[0], nx, Ex, lx);
+  eigenbasis<T>(bc[1], ny, Ey, ly);
+  const T dx = len_xy[0] / nx, dy = len_xy[1] / ny;
+  std::vector<T> hat(plane * nz);
+
+  // forward: per z-plane, hat = Ey^T F Ex with F the [ny][nx] plane
+#pragma omp parallel num_threads(nthreads)
+  {
+    std::vector<T> tmp(plane);
+#pragma omp for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+      const T* F = f + k * plane;
+      std::fill(tmp.begin(), tmp.end(), T(0));
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const T s = F[(size_t)j * nx + i];
+          const T* e = &Ex[(size_t)i * nx];
+          T* t = &tmp[(size_t)j * nx];
+          for (int m = 0; m < nx; ++m) t[m] += s * e[m];
+        }
+      T* H = hat.data() + k * plane;
+      std::fill(H, H + plane, T(0));
+      for (int my = 0; my < ny; ++my)
+        for (int j = 0; j < ny; ++j) {
+          const T s = Ey[(size_t)j * ny + my];
+          const T* t = &tmp[(size_t)j * nx];
+          T* h = &H[(size_t)my * nx];
+          for (int m = 0; m < nx; ++m) h[m] += s * t[m];
+        }
+    }
+  }
+
+  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+  if (bc[2] == BC_P) {
+    // uniform periodic z: diagonalise z as well (checked by the caller)
+    eigenbasis<T>(BC_P, nz, Ez, lz);
+    const T dz = zg.dzf[0];
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (long long col = 0; col < (long long)plane; ++col) {
+      const int mx = (int)(col % nx), my = (int)(col / nx);
+      const T mu = lx[mx] / (dx * dx) + ly[my] / (dy * dy);
+      std::vector<T> g(nz), q(nz, T(0));
+      for (int k = 0; k < nz; ++k) g[k] = hat[col + k * plane];
+      for (int mz = 0; mz < nz; ++mz) {
+        T s = 0;
+        for (int k = 0; k < nz; ++k) s += Ez[(size_t)k * nz + mz] * g[k];
+        const T den = mu + lz[mz] / (dz * dz);
+        q[mz] = (singular && mx == 0 && my == 0 && mz == 0) ? T(0) : s / den;
+      }
+      for (int k = 0; k < nz; ++k) {
+        T s = 0;
+        for (int mz = 0; mz < nz; ++mz) s += Ez[(size_t)k * nz + mz] * q[mz];
+        hat[col + k * plane] = s;
+      }
+    }
+  } else {
+    std::vector<T> a, b, c;
+    z_rows<T>(zg, a, b, c);
+    T wsum = 0;
+    for (int k = 0; k < nz; ++k) wsum += zg.dzf[k];
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (long long col = 0; col < (long long)plane; ++col) {
+      const int mx = (int)(col % nx), my = (int)(col / nx);
+      const T mu = lx[mx] / (dx * dx) + ly[my] / (dy * dy);
+      std::vector<T> bb(nz), d(nz), x(nz);
+      for (int k = 0; k < nz; ++k) {
+        bb[k] = b[k] + mu;
+        d[k] = hat[col + k * plane];
+      }
+      if (singular && mx == 0 && my == 0) {
+        x[nz - 1] = 0;
+        if (nz > 1) thomas<T>(nz - 1, a.data(), bb.data(), c.data(), d.data(), x.data());
+        T m = 0;
+        for (int k = 0; k < nz; ++k) m += zg.dzf[k] * x[k];
+        m /= wsum;
+        for (int k = 0; k < nz; ++k) x[k] -= m;
+      } else {
+        thomas<T>(nz, a.data(), bb.data(), c.data(), d.data(), x.data());
+      }
+      for (int k = 0; k < nz; ++k) hat[col + k * plane] = x[k];
+    }
+  }
+
+  // inverse: per z-plane, P = Ey H Ex^T
+#pragma omp parallel num_threads(nthreads)
+  {
+    std::vector<T> tmp(plane);
+#pragma omp for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+      const T* H = hat.data() + k * plane;
+      std::fill(tmp.begin(), tmp.end(), T(0));
+      for (int j = 0; j < ny; ++j)
+        for (int my = 0; my < ny; ++my) {
+          const T s = Ey[(size_t)j * ny + my];
+          const T* h = &H[(size_t)my * nx];
+          T* t = &tmp[(size_t)j * nx];
+          for (int m = 0; m < nx; ++m) t[m] += s * h[m];
+        }
+      T* P = p + k * plane;
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const T* e = &Ex[(size_t)i * nx];
+          const T* t = &tmp[(size_t)j * nx];
+          T s = 0;
+          if (g_fault == 3) {  // planted: transposed basis on the way back
+            for (int m = 0; m < nx; ++m) s += Ex[(size_t)m * nx + i] * t[m];
+          } else {
+            for (int m = 0; m < nx; ++m) s += e[m] * t[m];
+          }
+          P[(size_t)j * nx + i] = s;
+        }
+    }
+  }
+  return 0;
+}
+
+int check_args(const int n[3], const int bc[3], const double* dzf) {
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1) return -1;
+    if (bc[d] < 0 || bc[d] > 2) return -1;
+  }
+  for (int k = 0; k < n[2]; ++k)
+    if (!(dzf[k] > 0) || !std::isfinite(dzf[k])) return -1;
+  if (bc[2] == BC_P)
+    for (int k = 1; k < n[2]; ++k)
+      if (dzf[k] != dzf[0]) return -2;  // periodic z must be uniform
+  return 0;
+}
+
+template <typename T>
+int solve_t(const int n[3], const double len_xy[2], const int bc[3], const double* dzf, const double* f, double* p,
+            int nthreads) {
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  std::vector<T> ft(N), pt(N);
+  for (size_t i = 0; i < N; ++i) ft[i] = (T)f[i];
+  const T L[2] = {(T)len_xy[0], (T)len_xy[1]};
+  ZGrid<T> zg(n[2], bc[2], dzf);
+  int rc = poisson_solve<T>(n, L, bc, zg, ft.data(), pt.data(), nthreads);
+  for (size_t i = 0; i < N; ++i) p[i] = (double)pt[i];
+  return rc;
+}
+
+template <typename T>
+int apply_t(const int n[3], const double len_xy[2], const int bc[3], const double* dzf, const double* p, double* out,
+            int nthreads) {
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  std::vector<T> pt(N), ot(N);
+  for (size_t i = 0; i < N; ++i) pt[i] = (T)p[i];
+  const T L[2] = {(T)len_xy[0], (T)len_xy[1]};
+  ZGrid<T> zg(n[2], bc[2], dzf);
+  apply_laplacian<T>(n, L, bc, zg, pt.data(), ot.data(), nthreads);
+  for (size_t i = 0; i < N; ++i) out[i] = (double)ot[i];
+  return 0;
+}
+
+int nthreads_or_default(int nthreads) {
+#ifdef _OPENMP
+  return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
+}  // namespace
+
+extern "C" {
+
+// prec_bits: 64 = double, 80 = long double, 128 = __float128.  Inputs and outputs are double;
+// the arithmetic runs in the requested precision.  Returns 0 on success, <0 on bad arguments.
+int oracle_poisson_solve(int prec_bits, const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
+                         const double* f, double* p, int nthreads) {
+  int rc = check_args(n, bc, dzf);
+  if (rc) return rc;
+  nthreads = nthreads_or_default(nthreads);
+  if (prec_bits == 64) return solve_t<double>(n, len_xy, bc, dzf, f, p, nthreads);
+  if (prec_bits == 80) return solve_t<long double>(n, len_xy, bc, dzf, f, p, nthreads);
+  if (prec_bits == 128) return solve_t<quad>(n, len_xy, bc, dzf, f, p, nthreads);
+  return -1;
+}
+
+// out = L_h p (eq. poi, non-uniform z as in the Validation section).
+int oracle_apply_laplacian(int prec_bits, const int n[3], const double len_xy[2], const int bc[3],
+                           const double* dzf, const double* p, double* out, int nthreads) {
+  int rc = check_args(n, bc, dzf);
+  if (rc) return rc;
+  nthreads = nthreads_or_default(nthreads);
+  if (prec_bits == 64) return apply_t<double>(n, len_xy, bc, dzf, p, out, nthreads);
+  if (prec_bits == 80) return apply_t<long double>(n, len_xy, bc, dzf, p, out, nthreads);
+  if (prec_bits == 128) return apply_t<quad>(n, len_xy, bc, dzf, p, out, nthreads);
+  return -1;
+}
+
+// Dense orthonormal eigenbasis E (row-major n x n, columns = eigenvectors) and unit-spacing
+// eigenvalues lam of the 1-D operator with boundary condition bc.
+int oracle_eigenbasis(int bc, int n, double* E, double* lam) {
+  if (n < 1 || bc < 0 || bc > 2) return -1;
+  std::vector<double> e, l;
+  eigenbasis<double>(bc, n, e, l);
+  std::memcpy(E, e.data(), sizeof(double) * e.size());
+  std::memcpy(lam, l.data(), sizeof(double) * l.size());
+  return 0;
+}
+
+// Rows of the z operator for one mode: a_k p_{k-1} + b_k p_k + c_k p_{k+1}; a_0 = c_{nz-1} = 0 at walls.
+int oracle_z_rows(int bc_z, int nz, const double* dzf, double* a, double* b, double* c) {
+  if (nz < 1 || bc_z < 0 || bc_z > 2) return -1;
+  ZGrid<double> zg(nz, bc_z, dzf);
+  std::vector<double> va, vb, vc;
+  z_rows<double>(zg, va, vb, vc);
+  for (int k = 0; k < nz; ++k) {
+    a[k] = va[k];
+    b[k] = vb[k];
+    c[k] = vc[k];
+  }
+  return 0;
+}
+
+// Plain Thomas solve (no pivoting) of one tridiagonal system.
+int oracle_thomas(int n, const double* a, const double* b, const double* c, const double* d, double* x) {
+  if (n < 1) return -1;
+  thomas<double>(n, a, b, c, d, x);
+  return 0;
+}
+
+void oracle_set_fault(int mode) { g_fault = mode; }
+
+}  // extern "C"
