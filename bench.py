@@ -1,0 +1,377 @@
+"""Benchmark of the pressure-Poisson hot path on B300.
+
+Workload (one "step" = one solve of L_h p = f, i.e. one pass of the whole Poisson path): a
+1024 x 1024 x 512 staggered grid, x and y periodic, z Neumann on the tanh wall-clustered grid
+(faces z_k = (1 + tanh(1.8 (2k/N - 1)) / tanh(1.8)) / 2), right-hand side = 64 random separable Fourier
+modes + N(0, 1e-3) noise, compatible.  The headline is the mixed-precision solve (FP32 transforms,
+FP64 z-solves of the lowest-|mu| 1% of modes, double-float residual) with refinement sweeps that
+reach a 1e-12 relative residual, in Gpts/s (points / seconds per solve).  The plain FP64 solve of the
+same workload is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica: the solve does not
+shard without an exchange, so the multi-GPU run is replicas only, weak scaling, no collective on the
+data path.  --impl reference times the CPU oracle (dense-basis FP64 C++ with OpenMP) on a bounded
+slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Poisson solve Gpts/s (mixed precision refined to 1e-12 relative residual) on 1 B300"
+WORKLOAD = "poisson_1024x1024x512_P-P-NN_tanh1.8_modes64"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+PASS_BYTES_MIXED = {  # algorithmic bytes per point that each pass must move (mixed precision)
+    0: 12,  # x forward: read f (8), write the float work field (4)
+    1: 8,   # y forward: read + write float
+    2: 8,   # z solve: read + write float
+    3: 8,   # y inverse
+    4: 12,  # x inverse of the first solve: read work (4), write Phi (4) and Plo (4)
+    5: 20,  # x forward + residual: read f (8), Phi (4), Plo (4), write work (4)
+    6: 20,  # x inverse + update: read work (4), Phi (4), Plo (4), write p (8)
+}
+PASS_BYTES_FP64 = {0: 16, 1: 16, 2: 16, 3: 16, 4: 16}
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2001_05234_b300 as cans
+    from paper_2001_05234_b300 import build_lib
+    from paper_2001_05234_b300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+
+    case = I.case_modes()
+    npts = case.points
+    f = I.rhs_device(case, "cuda")
+    p = torch.empty_like(f)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # pick the refinement depth that reaches the 1e-12 target (checked with the library's FP64 residual)
+    sweeps_used, info_used = None, None
+    for sw in (1, 2, 3):
+        s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sw)
+        _, info, st = s.solve(f, p, info=True)
+        s.close()
+        if info[-1] <= 1e-12:
+            sweeps_used, info_used = sw, info
+            break
+    if sweeps_used is None:
+        sweeps_used, info_used = 3, info
+    solver = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sweeps_used)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.solve(f, p)
+    barrier()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    cans.cans_plan_profile(solver.plan, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.solve(f, p)
+    e1.record(stream)
+    barrier()
+    cans.cans_plan_profile(solver.plan, False)
+    clk = clocks.stop() if rank == 0 else None
+    ms_total = e0.elapsed_time(e1)
+    ms = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # per-pass device times inside the timed region
+    passes = {}
+    for k in range(7):
+        tot, n = cans.cans_plan_profile_read(solver.plan, k)
+        if n:
+            passes[cans.CANS_PASS_NAMES[k]] = {"ms_avg": tot / n, "launches": n, "share": None,
+                                               "bytes_per_pt": PASS_BYTES_MIXED[k], "kind": k}
+    ptot = sum(v["ms_avg"] * v["launches"] for v in passes.values())
+    for v in passes.values():
+        v["share"] = v["ms_avg"] * v["launches"] / ptot
+    dominant = max(passes.items(), key=lambda kv: kv[1]["ms_avg"] * kv[1]["launches"])
+    hbm_peak, peak_src = _peaks()
+    dom_bytes = dominant[1]["bytes_per_pt"] * npts
+    achieved = dom_bytes / (dominant[1]["ms_avg"] * 1e-3) / 1e9
+    kernels_per_solve = (6 * (1 + sweeps_used))  # x, y, z(float), z(double), y, x per solve and sweep
+
+    # plain FP64 solve of the same workload
+    s64 = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64)
+    s64.solve(f, p)
+    barrier()
+    f64_steps = max(2, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(f64_steps):
+        s64.solve(f, p)
+    e1.record(stream)
+    barrier()
+    ms64 = e0.elapsed_time(e1) / f64_steps
+    _, info64, _ = s64.solve(f, p, info=True)
+    s64.close()
+
+    # end to end through the C ABI with host buffers: H2D of f, solve, D2H of p every step
+    fh = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+    fh.copy_(f)
+    ph = torch.empty_like(fh, pin_memory=True)
+    fd = torch.empty_like(f)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fd.copy_(fh, non_blocking=True)
+        solver.solve(fd, p)
+        ph.copy_(p, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    solver.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    cpu = cpu_baseline(seconds_budget=args.cpu_budget)
+    out = {
+        "metric": METRIC,
+        "value": world * npts / (ms * 1e-3) / 1e9,
+        "unit": "Gpts/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 transforms + f64 low-mode z-solves + double-float residual (mixed)",
+        "data": "synthetic (seeded SplitMix64; 64 random Fourier modes + N(0,1e-3) noise)",
+        "config": {
+            "workload": WORKLOAD,
+            "n": list(case.n),
+            "bc": ["P", "P", "NN"],
+            "z_grid": "tanh faces, alpha 1.8",
+            "sweeps": sweeps_used,
+            "residual_per_sweep": [float(v) for v in info_used],
+            "l2": "inputs larger than L2 (f and p 4.3 GB each, work fields 6.4 GB)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "fp64_solve": {"ms_per_step": ms64, "value": npts / (ms64 * 1e-3) / 1e9, "unit": "Gpts/s",
+                       "residual": float(info64[0]), "speedup_mixed_over_fp64": ms64 / ms},
+        "passes": passes,
+        "roofline": {
+            "kernel": dominant[0],
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": hbm_peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": achieved / hbm_peak,
+            "traffic": None,
+            "algorithmic_bytes_per_launch": dom_bytes,
+            "whole_solve_frac": (sum(PASS_BYTES_MIXED[v["kind"]] * v["launches"] for v in passes.values())
+                                 / args.steps * npts / (ms * 1e-3) / 1e9) / hbm_peak,
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": npts / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8},
+        "gpu_launches": kernels_per_solve * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle: the baseline leg and the reference arm
+# ------------------------------------------------------------------------------------------------
+def _oracle_sample(nz_sample: int):
+    from paper_2001_05234_b300 import inputs as I
+
+    case = I.case_modes(n=(1024, 1024, nz_sample))
+    return case, I.rhs_host(case)
+
+
+def cpu_baseline(seconds_budget: float = 20.0):
+    """The oracle as it stands, on the host cores, on a slab of the workload: full 1024 x 1024 x-y
+    planes (the oracle's cost per point depends on Nx + Ny, so a slab keeps the per-point cost) and
+    a few z-levels."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    nz = 2
+    case, f = _oracle_sample(nz)
+    t0 = time.perf_counter()
+    oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
+    dt = time.perf_counter() - t0
+    reps = 1
+    while dt * (reps + 1) < seconds_budget and reps < 3:
+        t0 = time.perf_counter()
+        oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
+        dt = min(dt, time.perf_counter() - t0)
+        reps += 1
+    return {"value": case.points / dt / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+            "sample": f"1024x1024x{nz} slab of the workload (same x-y extent, BCs and RHS recipe), "
+                      f"FP64 dense-basis oracle, best of {reps}", "seconds": dt}
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    nz = 2
+    case, f = _oracle_sample(nz)
+    for _ in range(args.warmup):
+        oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = case.points / dt / 1e9
+    sample = (f"each step solves a 1024x1024x{nz} slab of the workload (same x-y extent, BCs and RHS recipe) "
+              f"with the FP64 dense-basis CPU oracle")
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": v,
+        "unit": "Gpts/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64)",
+        "config": {"workload": WORKLOAD, "n": list(case.n), "sample_of": [1024, 1024, 512]},
+        "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * cans.h -- C ABI of the B300 (sm_103a) pressure-Poisson library.
+ *
+ * The library solves the second-order, 7-point, staggered finite-difference Poisson equation
+ *     L_h p = f                                                     (paper: Eq. poi)
+ * by eigenfunction expansion: a forward real-to-real transform along x and along y chosen by the
+ * boundary condition (periodic -> real DFT, Neumann-Neumann -> DCT-II, Dirichlet-Dirichlet ->
+ * DST-II, the latter two through Makhoul's reordering around an FFT), one tridiagonal solve per
+ * (x, y) mode along a possibly non-uniform z grid (Eq. poi_reduced, Gauss elimination), then the
+ * inverse transforms (DFT^-1, DCT-III, DST-III).  Around it sit the fused divergence and projection
+ * kernels of the fractional step (Eq. up / poi_ns and the correction that follows it).
+ *
+ * Conventions shared by every entry point
+ *   - Fields are 3-D arrays of n[0] x n[1] x n[2] = Nx x Ny x Nz cells, x fastest:
+ *     idx = i + Nx * (j + Ny * k).  No halos.  Values are IEEE double unless stated otherwise.
+ *   - Device pointers are owned by the caller (any allocator, e.g. PyTorch).  The library never
+ *     allocates device memory inside a solve; scratch comes from the caller's `workspace`, whose
+ *     size cans_poisson_workspace_size() reports.  Plans own only small device tables.
+ *   - Work is enqueued on the CUDA stream passed as `cuda_stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and is asynchronous unless stated otherwise.
+ *   - Every function returns a cans_status; nothing is thrown across the ABI.  Argument errors are
+ *     detected on the host before anything is enqueued.
+ *   - Boundary conditions: the same type at both ends of a direction (CANS_BC_*).  x and y are
+ *     uniform (spacing L/N); z is given by its cell widths dzf (Validation section: z may be
+ *     non-uniform, x and y must be regular).  A periodic z must be uniform.
+ *   - Singular problems (no Dirichlet direction) have solutions up to a constant: the library
+ *     returns the one with zero cell-volume-weighted mean.
+ */
+#ifndef CANS_H
+#define CANS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cans_plan_s* cans_plan_t;
+
+enum cans_bc { CANS_BC_P = 0, CANS_BC_NN = 1, CANS_BC_DD = 2 };
+
+/* CANS_FP64: every pass in IEEE double.
+ * CANS_MIXED: transforms and most z-solves in float; the z-solves of the smallest-|mu| modes in
+ * double; residual r = f - L_h p and the accumulated p in double-float (pairs of floats with
+ * error-free sums and products, ~48 significant bits); max_sweeps refinement sweeps. */
+enum cans_prec { CANS_FP64 = 0, CANS_MIXED = 1 };
+
+enum cans_status {
+  CANS_OK = 0,
+  CANS_ERR_ARG = -1,           /* bad pointer, size, boundary condition, grid */
+  CANS_ERR_UNSUPPORTED = -2,   /* valid problem this build does not handle (odd periodic N, ...) */
+  CANS_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  CANS_ERR_WORKSPACE = -4,     /* workspace NULL or misaligned while one is required */
+  CANS_ERR_INCOMPATIBLE = -5,  /* singular problem whose f has a non-zero weighted mean */
+  CANS_ERR_NOT_CONVERGED = -6, /* refinement ended above opts.tol (only reported when synchronising) */
+  CANS_ERR_TIMEOUT = -7        /* a bounded device-side wait gave up */
+};
+
+typedef struct {
+  int prec;                  /* cans_prec */
+  int max_sweeps;            /* CANS_MIXED: refinement sweeps after the first solve (0..8) */
+  double tol;                /* CANS_MIXED: relative residual target checked when synchronising */
+  double fp64_mode_fraction; /* CANS_MIXED: fraction of (x,y) modes solved in double along z */
+  int autotune;              /* reserved: 0 = built-in tile shapes */
+} cans_opts;
+
+/* Fill *opts with the defaults: FP64, 2 sweeps, tol 1e-12, fraction 0.01, autotune 0. */
+void cans_opts_default(cans_opts* opts);
+
+/*
+ * Plan a solver for one grid and boundary-condition set (Eq. poi_reduced; host work only).
+ *   n       : {Nx, Ny, Nz}, each >= 1; a periodic x or y needs an even N; N/2 (x, y) must factor
+ *             into 2s and 3s (up to 4096).  Nz <= 8192.
+ *   len_xy  : {Lx, Ly} > 0, domain lengths in x and y.
+ *   bc      : {bc_x, bc_y, bc_z}, each a cans_bc.
+ *   dzf     : host array of Nz positive cell widths along z, or NULL for Nz cells of width 1/Nz.
+ *             Copied; the caller keeps ownership.
+ *   opts    : NULL for the defaults.
+ *   out     : receives the plan.  The plan uploads its coefficient tables to the current device.
+ * Errors: CANS_ERR_ARG (bad n, bc, lengths, dzf non-positive or non-finite, periodic z not
+ * uniform), CANS_ERR_UNSUPPORTED (odd periodic N, unsupported factor), CANS_ERR_CUDA.
+ */
+int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
+                      const cans_opts* opts, cans_plan_t* out);
+
+/* Bytes of device workspace one solve needs (0 for CANS_FP64, which works in p itself). */
+int cans_poisson_workspace_size(cans_plan_t plan, size_t* bytes);
+
+/*
+ * Solve L_h p = f (Eq. poi) for one right-hand side.
+ *   f, p       : device arrays of Nx*Ny*Nz doubles.  CANS_FP64 allows f == p (in place);
+ *                CANS_MIXED needs f != p because f is re-read for the residual.
+ *   workspace  : device buffer of at least cans_poisson_workspace_size() bytes, 256-byte aligned
+ *                (may be NULL when that size is 0).  Contents on entry are ignored.
+ *   cuda_stream: cudaStream_t to enqueue on.
+ *   info       : NULL for a fully asynchronous call.  Otherwise a host array of max_sweeps+2
+ *                doubles that receives ||f - L_h p_s||_2 / ||f||_2 after the first solve (s = 0)
+ *                and after every sweep, and the call synchronises the stream; with info the call
+ *                returns CANS_ERR_NOT_CONVERGED when the last value exceeds opts.tol (mixed only),
+ *                and CANS_ERR_INCOMPATIBLE when a singular problem's f has a weighted mean above
+ *                1e-10 of mean|f|.
+ * Singular problems always return the zero-mean solution of the compatible part of f.
+ */
+int cans_poisson_solve(cans_plan_t plan, const double* f, double* p, void* workspace, void* cuda_stream,
+                       double* info);
+
+/* Release the plan and its device tables. */
+int cans_plan_destroy(cans_plan_t plan);
+
+/* Static English text for a status code. */
+const char* cans_status_string(int status);
+
+/*
+ * Single pass entry points (the steps of the solve, exposed for tests and for callers that want to
+ * fuse their own work between them).  All operate on plan-shaped fields.
+ *
+ * cans_transform_xy: forward (dir = +1) or inverse (dir = -1) transforms along x then y (forward)
+ * or y then x (inverse), in double, in place on `field`.  Forward output order per line: periodic
+ * -> slot 0 = X_0, slots 2k-1, 2k = Re X_k, Im X_k (1 <= k < N/2), slot N-1 = X_{N/2};
+ * Neumann -> slot m = DCT-II_m; Dirichlet -> slot m = DST-II_m, all unnormalised (X_k = sum x_n
+ * e^{-2 pi i k n/N}, DCT-II_m = 2 sum x_n cos(pi m (2n+1)/(2N)), DST-II_m = 2 sum x_n
+ * sin(pi (m+1)(2n+1)/(2N))).  The inverse is the exact inverse times Nx*Ny (so a forward-inverse
+ * round trip multiplies by Nx*Ny).
+ */
+int cans_transform_xy(cans_plan_t plan, double* field, int dir, void* cuda_stream);
+
+/* cans_zsolve: in place on the transformed field, solve (A_z + mu_ij I) x = rhs along z for every
+ * (i, j) slot, mu_ij = lam_x(i)/dx^2 + lam_y(j)/dy^2 (Eq. poi_reduced), in double. */
+int cans_zsolve(cans_plan_t plan, double* field, void* cuda_stream);
+
+/*
+ * Per-pass timing with CUDA events on the solve's stream (the profiling hook a benchmark uses to
+ * time one kernel inside the timed region).  enable = 1 clears earlier records and records a pair of
+ * events around every pass launch of later solves on this plan; enable = 0 stops recording.
+ * cans_plan_profile_read synchronises on the recorded events and returns, for pass kind `pass`
+ * (a cans_pass), the summed milliseconds and the number of launches.
+ */
+enum cans_pass {
+  CANS_PASS_XF = 0, /* forward x (FP64 -> working precision) */
+  CANS_PASS_YF = 1, /* forward y */
+  CANS_PASS_Z = 2,  /* tridiagonal z (float and double column kernels together) */
+  CANS_PASS_YI = 3, /* inverse y */
+  CANS_PASS_XI = 4, /* inverse x of a first solve */
+  CANS_PASS_XR = 5, /* forward x fused with the double-float residual (refinement sweep) */
+  CANS_PASS_XU = 6, /* inverse x fused with the update of the iterate (refinement sweep) */
+  CANS_PASS_COUNT = 7
+};
+int cans_plan_profile(cans_plan_t plan, int enable);
+int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);
+
+/* Host copies of the per-slot eigenvalue terms lam_x(i)/dx^2 (length Nx) and lam_y(j)/dy^2
+ * (length Ny) the plan uses; either pointer may be NULL. */
+int cans_plan_eigenvalues(cans_plan_t plan, double* mu_x, double* mu_y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CANS_H */

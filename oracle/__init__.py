@@ -130,3 +130,95 @@ def set_fault(mode: int) -> None:
 def relative_residual(p, f, bc, length_xy=(1.0, 1.0), dzf=None, nthreads=0):
     r = apply_laplacian(p, bc, length_xy, dzf, nthreads=nthreads) - f
     return float(np.linalg.norm(r) / np.linalg.norm(f))
+
+
+# ---- fractional-step pieces (channel: x, y periodic, walls in z) --------------------------------
+def _chan_args(shape, length_xy, dzf):
+    nz, ny, nx = shape
+    n = np.array([nx, ny, nz], dtype=np.int32)
+    L = np.array(length_xy, dtype=np.float64)
+    dz = _dz(n, dzf)
+    return n, L, dz
+
+
+def _bind_chan():
+    L = lib()
+    if getattr(L, "_chan_bound", False):
+        return L
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.oracle_divergence.argtypes = [ip, dp, dp, dp, dp, dp, dp]
+    L.oracle_gradient.argtypes = [ip, dp, dp, dp, dp, dp, dp]
+    L.oracle_momentum_rhs.argtypes = [ip, dp, dp, ctypes.c_double, dp, dp, dp, dp, dp, dp]
+    L.oracle_stable_dt.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+    L.oracle_stable_dt.restype = ctypes.c_double
+    L.oracle_project.argtypes = [ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
+    L.oracle_rk3_step.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  dp, dp, dp, dp, dp, ctypes.c_int]
+    L._chan_bound = True
+    return L
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def divergence(u, v, w, length_xy, dzf):
+    """Cell-centred divergence of a face field (w is zero on both walls; w[-1] is the top wall)."""
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    out = np.empty_like(u)
+    L.oracle_divergence(_i(n), _d(Lxy), _d(dz), _d(u), _d(v), _d(w), _d(out))
+    return out
+
+
+def gradient(q, length_xy, dzf):
+    L = _bind_chan()
+    q = _c(q)
+    n, Lxy, dz = _chan_args(q.shape, length_xy, dzf)
+    gx, gy, gz = np.empty_like(q), np.empty_like(q), np.empty_like(q)
+    L.oracle_gradient(_i(n), _d(Lxy), _d(dz), _d(q), _d(gx), _d(gy), _d(gz))
+    return gx, gy, gz
+
+
+def momentum_rhs(u, v, w, nu, length_xy, dzf):
+    """A(u) + nu L(u) of Eq. up (conservative advection, no-slip walls)."""
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    ru, rv, rw = np.empty_like(u), np.empty_like(u), np.empty_like(u)
+    L.oracle_momentum_rhs(_i(n), _d(Lxy), _d(dz), float(nu), _d(u), _d(v), _d(w), _d(ru), _d(rv), _d(rw))
+    return ru, rv, rw
+
+
+def stable_dt(u, v, w, nu, cfl, length_xy, dzf):
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    return float(L.oracle_stable_dt(_i(n), _d(Lxy), _d(dz), float(nu), float(cfl), _d(u), _d(v), _d(w)))
+
+
+def project(u, v, w, length_xy, dzf, nthreads=0):
+    """u - G L^-1 D u and the potential phi (pressure problem periodic x, y, Neumann z)."""
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    uo, vo, wo, phi = (np.empty_like(u) for _ in range(4))
+    rc = L.oracle_project(_i(n), _d(Lxy), _d(dz), _d(u), _d(v), _d(w), _d(uo), _d(vo), _d(wo), _d(phi), int(nthreads))
+    if rc:
+        raise ValueError(rc)
+    return uo, vo, wo, phi
+
+
+def rk3_step(u, v, w, p, nu, cfl, ubulk, length_xy, dzf, dt=0.0, nthreads=0):
+    """One explicit low-storage RK3 fractional step; returns (u, v, w, p, dt) (copies)."""
+    L = _bind_chan()
+    u, v, w, p = (_c(a).copy() for a in (u, v, w, p))
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    dt_out = ctypes.c_double()
+    rc = L.oracle_rk3_step(_i(n), _d(Lxy), _d(dz), float(nu), float(cfl), float(ubulk), float(dt), _d(u), _d(v),
+                           _d(w), _d(p), ctypes.byref(dt_out), int(nthreads))
+    if rc:
+        raise ValueError(rc)
+    return u, v, w, p, float(dt_out.value)

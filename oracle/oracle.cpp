@@ -444,3 +444,270 @@ int oracle_thomas(int n, const double* a, const double* b, const double* c, cons
 void oracle_set_fault(int mode) { g_fault = mode; }
 
 }  // extern "C"
+
+// =================================================================================================
+// Fractional-step pieces around the Poisson solve (Numerical method: Eq. up, Eq. poi_ns and the
+// correction and pressure update after it; Eq. dt and its chkdt listing), for a channel: x and y
+// periodic, no-slip / no-penetration walls at z = 0 and z = Lz, Neumann pressure at the walls.
+//
+// Staggered (marker-and-cell) arrays, all Nx x Ny x Nz, x fastest:
+//   u[k][j][i] on the x-face between cells i and i+1, v on the y-face between j and j+1,
+//   w on the z-face between k and k+1 (w[Nz-1] is the top wall and stays 0; the bottom wall w = 0
+//   sits below k = 0), p at cell centres.
+// Advection is the conservative divergence of u (x) u with arithmetic two-point averages; diffusion
+// is the same 3-point Laplacian as the pressure with no-slip ghosts (ghost = -interior at the wall).
+// All loops are plain double arithmetic.
+// =================================================================================================
+namespace {
+
+struct Chan {
+  int nx, ny, nz;
+  double dx, dy;
+  std::vector<double> dzf, dzc;  // dzc[k] = distance between centres k-1 and k (k = 0..nz), wall ghosts
+  Chan(const int n[3], const double len_xy[2], const double* dz) : nx(n[0]), ny(n[1]), nz(n[2]), dzf(n[2]), dzc(n[2] + 1) {
+    dx = len_xy[0] / nx;
+    dy = len_xy[1] / ny;
+    for (int k = 0; k < nz; ++k) dzf[k] = dz[k];
+    for (int k = 1; k < nz; ++k) dzc[k] = 0.5 * (dzf[k - 1] + dzf[k]);
+    dzc[0] = dzf[0];
+    dzc[nz] = dzf[nz - 1];
+  }
+  size_t id(int i, int j, int k) const {
+    i = (i % nx + nx) % nx;
+    j = (j % ny + ny) % ny;
+    return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+  }
+  size_t size() const { return (size_t)nx * ny * nz; }
+};
+
+// cell-centred value of a face field with the wall rules: u, v (tangential) have ghosts -u at the
+// walls; w is zero on both walls.
+inline double U(const Chan& g, const double* a, int i, int j, int k) {
+  if (k < 0) return -a[g.id(i, j, 0)];
+  if (k >= g.nz) return -a[g.id(i, j, g.nz - 1)];
+  return a[g.id(i, j, k)];
+}
+inline double W(const Chan& g, const double* w, int i, int j, int k) {
+  if (k < 0 || k >= g.nz - 1) return 0.0;
+  return w[g.id(i, j, k)];
+}
+
+void divergence(const Chan& g, const double* u, const double* v, const double* w, double* out) {
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i)
+        out[g.id(i, j, k)] = (u[g.id(i, j, k)] - u[g.id(i - 1, j, k)]) / g.dx +
+                             (v[g.id(i, j, k)] - v[g.id(i, j - 1, k)]) / g.dy +
+                             (W(g, w, i, j, k) - W(g, w, i, j, k - 1)) / g.dzf[k];
+}
+
+void gradient(const Chan& g, const double* q, double* gx, double* gy, double* gz) {
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const size_t c = g.id(i, j, k);
+        gx[c] = (q[g.id(i + 1, j, k)] - q[c]) / g.dx;
+        gy[c] = (q[g.id(i, j + 1, k)] - q[c]) / g.dy;
+        gz[c] = (k < g.nz - 1) ? (q[g.id(i, j, k + 1)] - q[c]) / g.dzc[k + 1] : 0.0;
+      }
+}
+
+// 3-point Laplacian of a tangential velocity (no-slip ghosts) at its own location
+double lap_t(const Chan& g, const double* a, int i, int j, int k) {
+  const double c = a[g.id(i, j, k)];
+  const double lx = (a[g.id(i - 1, j, k)] - 2 * c + a[g.id(i + 1, j, k)]) / (g.dx * g.dx);
+  const double ly = (a[g.id(i, j - 1, k)] - 2 * c + a[g.id(i, j + 1, k)]) / (g.dy * g.dy);
+  const double lz = ((U(g, a, i, j, k + 1) - c) / g.dzc[k + 1] - (c - U(g, a, i, j, k - 1)) / g.dzc[k]) / g.dzf[k];
+  return lx + ly + lz;
+}
+
+// momentum right-hand side A(u) + nu L(u) of Eq. up (advection as -div(u u))
+void momentum_rhs(const Chan& g, double nu, const double* u, const double* v, const double* w, double* ru,
+                  double* rv, double* rw) {
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const size_t c = g.id(i, j, k);
+        // u on the face (i+1/2, j, k)
+        {
+          const double ue = 0.5 * (u[c] + u[g.id(i + 1, j, k)]), uw = 0.5 * (u[g.id(i - 1, j, k)] + u[c]);
+          const double un = 0.5 * (u[c] + u[g.id(i, j + 1, k)]) * 0.5 * (v[c] + v[g.id(i + 1, j, k)]);
+          const double us = 0.5 * (u[g.id(i, j - 1, k)] + u[c]) * 0.5 * (v[g.id(i, j - 1, k)] + v[g.id(i + 1, j - 1, k)]);
+          const double ut = 0.5 * (u[c] + U(g, u, i, j, k + 1)) * 0.5 * (W(g, w, i, j, k) + W(g, w, i + 1, j, k));
+          const double ub = 0.5 * (U(g, u, i, j, k - 1) + u[c]) * 0.5 * (W(g, w, i, j, k - 1) + W(g, w, i + 1, j, k - 1));
+          const double adv = (ue * ue - uw * uw) / g.dx + (un - us) / g.dy + (ut - ub) / g.dzf[k];
+          ru[c] = -adv + nu * lap_t(g, u, i, j, k);
+        }
+        // v on the face (i, j+1/2, k)
+        {
+          const double ve = 0.5 * (v[c] + v[g.id(i + 1, j, k)]) * 0.5 * (u[c] + u[g.id(i, j + 1, k)]);
+          const double vw = 0.5 * (v[g.id(i - 1, j, k)] + v[c]) * 0.5 * (u[g.id(i - 1, j, k)] + u[g.id(i - 1, j + 1, k)]);
+          const double vn = 0.5 * (v[c] + v[g.id(i, j + 1, k)]), vs = 0.5 * (v[g.id(i, j - 1, k)] + v[c]);
+          const double vt = 0.5 * (v[c] + U(g, v, i, j, k + 1)) * 0.5 * (W(g, w, i, j, k) + W(g, w, i, j + 1, k));
+          const double vb = 0.5 * (U(g, v, i, j, k - 1) + v[c]) * 0.5 * (W(g, w, i, j, k - 1) + W(g, w, i, j + 1, k - 1));
+          const double adv = (ve - vw) / g.dx + (vn * vn - vs * vs) / g.dy + (vt - vb) / g.dzf[k];
+          rv[c] = -adv + nu * lap_t(g, v, i, j, k);
+        }
+        // w on the face (i, j, k+1/2); the top wall face stays at rest
+        if (k == g.nz - 1) {
+          rw[c] = 0.0;
+        } else {
+          const double wc = w[c];
+          const double we = 0.5 * (wc + W(g, w, i + 1, j, k)) * 0.5 * (u[c] + u[g.id(i, j, k + 1)]);
+          const double ww = 0.5 * (W(g, w, i - 1, j, k) + wc) * 0.5 * (u[g.id(i - 1, j, k)] + u[g.id(i - 1, j, k + 1)]);
+          const double wn = 0.5 * (wc + W(g, w, i, j + 1, k)) * 0.5 * (v[c] + v[g.id(i, j, k + 1)]);
+          const double ws = 0.5 * (W(g, w, i, j - 1, k) + wc) * 0.5 * (v[g.id(i, j - 1, k)] + v[g.id(i, j - 1, k + 1)]);
+          const double wt = 0.5 * (wc + W(g, w, i, j, k + 1)), wb = 0.5 * (W(g, w, i, j, k - 1) + wc);
+          const double adv = (we - ww) / g.dx + (wn - ws) / g.dy + (wt * wt - wb * wb) / g.dzc[k + 1];
+          const double lx = (W(g, w, i - 1, j, k) - 2 * wc + W(g, w, i + 1, j, k)) / (g.dx * g.dx);
+          const double ly = (W(g, w, i, j - 1, k) - 2 * wc + W(g, w, i, j + 1, k)) / (g.dy * g.dy);
+          const double lz = ((W(g, w, i, j, k + 1) - wc) / g.dzf[k + 1] - (wc - W(g, w, i, j, k - 1)) / g.dzf[k]) / g.dzc[k + 1];
+          rw[c] = -adv + nu * (lx + ly + lz);
+        }
+      }
+}
+
+// largest inverse advective time scale (chkdt listing; the y and z rows follow the x row by symmetry)
+double max_dti(const Chan& g, const double* u, const double* v, const double* w) {
+  double dti = 0;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const size_t c = g.id(i, j, k);
+        const double ux = std::fabs(u[c]);
+        const double vx = 0.25 * std::fabs(v[c] + v[g.id(i, j - 1, k)] + v[g.id(i + 1, j, k)] + v[g.id(i + 1, j - 1, k)]);
+        const double wx = 0.25 * std::fabs(W(g, w, i, j, k) + W(g, w, i, j, k - 1) + W(g, w, i + 1, j, k) + W(g, w, i + 1, j, k - 1));
+        const double dtix = ux / g.dx + vx / g.dy + wx / g.dzf[k];
+        const double uy = 0.25 * std::fabs(u[c] + u[g.id(i - 1, j, k)] + u[g.id(i, j + 1, k)] + u[g.id(i - 1, j + 1, k)]);
+        const double vy = std::fabs(v[c]);
+        const double wy = 0.25 * std::fabs(W(g, w, i, j, k) + W(g, w, i, j, k - 1) + W(g, w, i, j + 1, k) + W(g, w, i, j + 1, k - 1));
+        const double dtiy = uy / g.dx + vy / g.dy + wy / g.dzf[k];
+        const double uz = 0.25 * std::fabs(u[c] + u[g.id(i - 1, j, k)] + U(g, u, i, j, k + 1) + U(g, u, i - 1, j, k + 1));
+        const double vz = 0.25 * std::fabs(v[c] + v[g.id(i, j - 1, k)] + U(g, v, i, j, k + 1) + U(g, v, i, j - 1, k + 1));
+        const double wz = std::fabs(W(g, w, i, j, k));
+        const double dtiz = uz / g.dx + vz / g.dy + wz / g.dzc[k + 1];
+        dti = std::max(dti, std::max(dtix, std::max(dtiy, dtiz)));
+      }
+  return dti;
+}
+
+// dt = cfl * min(sqrt(3)/dti, 1.65 dl^2/nu), dl = min(dx, dy, min dzf) (Eq. dt)
+double stable_dt(const Chan& g, double nu, double cfl, const double* u, const double* v, const double* w) {
+  double dl = std::min(g.dx, g.dy);
+  for (int k = 0; k < g.nz; ++k) dl = std::min(dl, g.dzf[k]);
+  const double dti = max_dti(g, u, v, w);
+  double dt = 1.65 * dl * dl / nu;
+  if (dti > 0) dt = std::min(dt, std::sqrt(3.0) / dti);
+  return cfl * dt;
+}
+
+double bulk_u(const Chan& g, const double* u) {
+  double s = 0, wsum = 0;
+  for (int k = 0; k < g.nz; ++k) {
+    double pl = 0;
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) pl += u[g.id(i, j, k)];
+    s += g.dzf[k] * pl;
+    wsum += g.dzf[k];
+  }
+  return s / (wsum * g.nx * g.ny);
+}
+
+const double RK_A[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+const double RK_B[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+}  // namespace
+
+extern "C" {
+
+int oracle_divergence(const int n[3], const double len_xy[2], const double* dzf, const double* u, const double* v,
+                      const double* w, double* out) {
+  Chan g(n, len_xy, dzf);
+  divergence(g, u, v, w, out);
+  return 0;
+}
+
+int oracle_gradient(const int n[3], const double len_xy[2], const double* dzf, const double* q, double* gx, double* gy,
+                    double* gz) {
+  Chan g(n, len_xy, dzf);
+  gradient(g, q, gx, gy, gz);
+  return 0;
+}
+
+int oracle_momentum_rhs(const int n[3], const double len_xy[2], const double* dzf, double nu, const double* u,
+                        const double* v, const double* w, double* ru, double* rv, double* rw) {
+  Chan g(n, len_xy, dzf);
+  momentum_rhs(g, nu, u, v, w, ru, rv, rw);
+  return 0;
+}
+
+double oracle_stable_dt(const int n[3], const double len_xy[2], const double* dzf, double nu, double cfl,
+                        const double* u, const double* v, const double* w) {
+  Chan g(n, len_xy, dzf);
+  return stable_dt(g, nu, cfl, u, v, w);
+}
+
+// Projection of a face field on discretely divergence-free fields: u - G L^-1 D u (the correction of
+// the fractional step with the gamma dt factors cancelled).  Pressure problem: (P, P, NN).
+int oracle_project(const int n[3], const double len_xy[2], const double* dzf, const double* u, const double* v,
+                   const double* w, double* uo, double* vo, double* wo, double* phi_out, int nthreads) {
+  Chan g(n, len_xy, dzf);
+  const size_t N = g.size();
+  std::vector<double> d(N), phi(N), gx(N), gy(N), gz(N);
+  divergence(g, u, v, w, d.data());
+  const int bc[3] = {BC_P, BC_P, BC_NN};
+  int rc = solve_t<double>(n, len_xy, bc, dzf, d.data(), phi.data(), nthreads_or_default(nthreads));
+  if (rc) return rc;
+  gradient(g, phi.data(), gx.data(), gy.data(), gz.data());
+  for (size_t c = 0; c < N; ++c) {
+    uo[c] = u[c] - gx[c];
+    vo[c] = v[c] - gy[c];
+    wo[c] = w[c] - gz[c];
+  }
+  if (phi_out) std::memcpy(phi_out, phi.data(), N * sizeof(double));
+  return 0;
+}
+
+// One explicit low-storage RK3 step (Eq. up with alpha, beta, gamma = alpha + beta), in place on
+// u, v, w, p.  dt is computed from the state at the start of the step (Eq. dt with cfl) unless
+// dt_in > 0.  After each substage's correction u is shifted to bulk velocity ubulk (constant flow
+// rate).  Returns the dt used through *dt_out.
+int oracle_rk3_step(const int n[3], const double len_xy[2], const double* dzf, double nu, double cfl, double ubulk,
+                    double dt_in, double* u, double* v, double* w, double* p, double* dt_out, int nthreads) {
+  Chan g(n, len_xy, dzf);
+  const size_t N = g.size();
+  const double dt = (dt_in > 0) ? dt_in : stable_dt(g, nu, cfl, u, v, w);
+  std::vector<double> ru(N), rv(N), rw(N), pu(N, 0.0), pv(N, 0.0), pw(N, 0.0), gx(N), gy(N), gz(N), d(N), phi(N);
+  const int bc[3] = {BC_P, BC_P, BC_NN};
+  nthreads = nthreads_or_default(nthreads);
+  for (int s = 0; s < 3; ++s) {
+    const double a = RK_A[s], b = RK_B[s], gm = a + b;
+    momentum_rhs(g, nu, u, v, w, ru.data(), rv.data(), rw.data());
+    gradient(g, p, gx.data(), gy.data(), gz.data());
+    for (size_t c = 0; c < N; ++c) {
+      u[c] += dt * (a * ru[c] + b * pu[c] - gm * gx[c]);
+      v[c] += dt * (a * rv[c] + b * pv[c] - gm * gy[c]);
+      w[c] += dt * (a * rw[c] + b * pw[c] - gm * gz[c]);
+    }
+    divergence(g, u, v, w, d.data());
+    for (size_t c = 0; c < N; ++c) d[c] /= gm * dt;
+    int rc = solve_t<double>(n, len_xy, bc, dzf, d.data(), phi.data(), nthreads);
+    if (rc) return rc;
+    gradient(g, phi.data(), gx.data(), gy.data(), gz.data());
+    for (size_t c = 0; c < N; ++c) {
+      u[c] -= gm * dt * gx[c];
+      v[c] -= gm * dt * gy[c];
+      w[c] -= gm * dt * gz[c];
+      p[c] += phi[c];
+    }
+    const double shift = ubulk - bulk_u(g, u);
+    for (size_t c = 0; c < N; ++c) u[c] += shift;
+    pu.swap(ru);
+    pv.swap(rv);
+    pw.swap(rw);
+  }
+  if (dt_out) *dt_out = dt;
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""Python binding of the B300 pressure-Poisson library (libcans.so, C ABI in include/cans.h).
+
+The functions named ``cans_*`` mirror the C entry points one to one and only marshal arguments:
+device pointers (ints), sizes and the CUDA stream handle.  ``PoissonSolver`` is a small torch
+convenience wrapper that owns a plan and its workspace.  Every step of a solve runs in the CUDA
+library; there is no CPU fallback, and loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded synthetic inputs)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcans.so")
+
+CANS_BC_P, CANS_BC_NN, CANS_BC_DD = 0, 1, 2
+CANS_FP64, CANS_MIXED = 0, 1
+CANS_OK = 0
+STATUS_NAMES = {0: "CANS_OK", -1: "CANS_ERR_ARG", -2: "CANS_ERR_UNSUPPORTED", -3: "CANS_ERR_CUDA",
+                -4: "CANS_ERR_WORKSPACE", -5: "CANS_ERR_INCOMPATIBLE", -6: "CANS_ERR_NOT_CONVERGED",
+                -7: "CANS_ERR_TIMEOUT"}
+
+
+class CansError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({cans_status_string(status)})")
+
+
+class cans_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
+                ("fp64_mode_fraction", ctypes.c_double), ("autotune", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcans.so (built in-tree by build_lib.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2001_05234_b300.build_lib.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        L.cans_opts_default.argtypes = [ctypes.POINTER(cans_opts)]
+        L.cans_opts_default.restype = None
+        L.cans_status_string.argtypes = [ctypes.c_int]
+        L.cans_status_string.restype = ctypes.c_char_p
+        L.cans_poisson_plan.argtypes = [ip, dp, ip, dp, ctypes.POINTER(cans_opts), ctypes.POINTER(vp)]
+        L.cans_poisson_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
+        L.cans_plan_destroy.argtypes = [vp]
+        L.cans_transform_xy.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.cans_zsolve.argtypes = [vp, vp, vp]
+        L.cans_plan_eigenvalues.argtypes = [vp, dp, dp]
+        L.cans_plan_profile.argtypes = [vp, ctypes.c_int]
+        L.cans_plan_profile_read.argtypes = [vp, ctypes.c_int, dp, ip]
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> int:
+    if status != CANS_OK:
+        raise CansError(status, where)
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- one-to-one C entry points ----------------------------------------------------------------
+def cans_status_string(status: int) -> str:
+    return lib().cans_status_string(int(status)).decode()
+
+
+def cans_opts_default() -> cans_opts:
+    o = cans_opts()
+    lib().cans_opts_default(ctypes.byref(o))
+    return o
+
+
+def cans_poisson_plan(n, len_xy, bc, dzf=None, opts: cans_opts | None = None, check: bool = True):
+    """Returns (status, plan handle)."""
+    n_a = (ctypes.c_int * 3)(*[int(v) for v in n])
+    l_a = (ctypes.c_double * 2)(*[float(v) for v in len_xy])
+    b_a = (ctypes.c_int * 3)(*[int(v) for v in bc])
+    dz = None
+    if dzf is not None:
+        dz = np.ascontiguousarray(dzf, dtype=np.float64)
+        if dz.shape != (int(n[2]),):
+            raise ValueError("dzf must hold n[2] cell widths")
+    h = ctypes.c_void_p()
+    st = lib().cans_poisson_plan(n_a, l_a, b_a, _dptr(dz) if dz is not None else None,
+                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    if check:
+        _check(st, "cans_poisson_plan")
+    return st, h
+
+
+def cans_poisson_workspace_size(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_poisson_workspace_size(plan, ctypes.byref(b)), "cans_poisson_workspace_size")
+    return int(b.value)
+
+
+def cans_poisson_solve(plan, f_ptr: int, p_ptr: int, workspace_ptr: int, stream_ptr: int, info=None) -> int:
+    """Returns the status; info (numpy float64 array of max_sweeps+2) is filled when given."""
+    return lib().cans_poisson_solve(plan, f_ptr, p_ptr, workspace_ptr or None, stream_ptr or None,
+                                    _dptr(info) if info is not None else None)
+
+
+def cans_plan_destroy(plan) -> int:
+    return lib().cans_plan_destroy(plan)
+
+
+def cans_transform_xy(plan, field_ptr: int, direction: int, stream_ptr: int) -> int:
+    return lib().cans_transform_xy(plan, field_ptr, int(direction), stream_ptr or None)
+
+
+def cans_zsolve(plan, field_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_zsolve(plan, field_ptr, stream_ptr or None)
+
+
+def cans_plan_eigenvalues(plan, nx: int, ny: int):
+    mx, my = np.empty(nx), np.empty(ny)
+    _check(lib().cans_plan_eigenvalues(plan, _dptr(mx), _dptr(my)), "cans_plan_eigenvalues")
+    return mx, my
+
+
+CANS_PASS_NAMES = ("x_forward", "y_forward", "z_solve", "y_inverse", "x_inverse", "x_forward_residual",
+                   "x_inverse_update")
+
+
+def cans_plan_profile(plan, enable: bool) -> int:
+    return lib().cans_plan_profile(plan, 1 if enable else 0)
+
+
+def cans_plan_profile_read(plan, pass_kind: int):
+    """(total milliseconds, launches) of one pass kind since profiling was enabled."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib().cans_plan_profile_read(plan, int(pass_kind), ctypes.byref(ms), ctypes.byref(n)),
+           "cans_plan_profile_read")
+    return float(ms.value), int(n.value)
+
+
+# ---- torch convenience -------------------------------------------------------------------------
+def _stream_ptr(stream=None) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class PoissonSolver:
+    """Owns a plan and its device workspace.  f, p: torch float64 CUDA tensors of shape (Nz, Ny, Nx)."""
+
+    def __init__(self, n, bc, length_xy=(1.0, 1.0), dzf=None, prec=CANS_FP64, sweeps=2, tol=1e-12,
+                 fp64_fraction=0.01):
+        import torch
+
+        self.n = tuple(int(v) for v in n)
+        self.bc = tuple(int(v) for v in bc)
+        o = cans_opts_default()
+        o.prec = int(prec)
+        o.max_sweeps = int(sweeps)
+        o.tol = float(tol)
+        o.fp64_mode_fraction = float(fp64_fraction)
+        self.opts = o
+        _, self.plan = cans_poisson_plan(self.n, length_xy, self.bc, dzf, o)
+        nbytes = cans_poisson_workspace_size(self.plan)
+        self.workspace = torch.empty(max(nbytes, 1) + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = self.workspace.data_ptr() + off if nbytes else 0
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def solve(self, f, out=None, stream=None, info: bool = False):
+        import torch
+
+        assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous() and tuple(f.shape) == self.shape
+        if out is None:
+            out = torch.empty_like(f)
+        buf = np.zeros(self.opts.max_sweeps + 2) if info else None
+        st = cans_poisson_solve(self.plan, f.data_ptr(), out.data_ptr(), self._ws_ptr, _stream_ptr(stream), buf)
+        if st != CANS_OK and not (info and st in (-5, -6)):
+            raise CansError(st, "cans_poisson_solve")
+        return (out, buf, st) if info else out
+
+    def close(self):
+        if getattr(self, "plan", None):
+            cans_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

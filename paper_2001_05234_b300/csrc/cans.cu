@@ -1,0 +1,553 @@
+// B300 (sm_103a) pressure-Poisson solver by eigenfunction expansion (Eq. poi, Eq. poi_reduced):
+// plan construction and the C ABI.  A solve is an x-pass (forward transform along contiguous x
+// lines), a y-pass (forward transform along y on tiles of consecutive x-slots), a z-pass (one
+// tridiagonal solve per mode), then the inverse y- and x-passes.  Plain mode runs every pass in
+// FP64 in place in p; mixed mode runs the passes in FP32 with a double-float residual / iterate and
+// FP64 z-solves for the smallest-|mu| modes.  The pass kernels live in kern_*.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "plan.cuh"
+
+using namespace cans;
+
+static constexpr int MAXV = 8;  // must match the pass kernels
+
+namespace {
+
+int factor_radices(int M, int* radix, int* nst) {
+  *nst = 0;
+  if (M <= 1) return 0;
+  int r = M;
+  int n3 = 0, n2 = 0;
+  while (r % 3 == 0) { r /= 3; ++n3; }
+  while (r % 2 == 0) { r /= 2; ++n2; }
+  if (r != 1) return -1;
+  for (int i = 0; i < n3; ++i) radix[(*nst)++] = 3;
+  while (n2 >= 3) { radix[(*nst)++] = 8; n2 -= 3; }
+  if (n2 == 2) radix[(*nst)++] = 4;
+  if (n2 == 1) radix[(*nst)++] = 2;
+  return (*nst <= 16) ? 0 : -1;
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// eigenvalue of the 1-D second-difference operator (unit spacing) for transform slot s
+long double slot_lambda(int bc, int N, int s) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  long double th;
+  if (bc == BC_P)
+    th = pi * (long double)((s + 1) / 2) / N;
+  else if (bc == BC_NN)
+    th = pi * (long double)s / (2.0L * N);
+  else
+    th = pi * (long double)(s + 1) / (2.0L * N);
+  const long double sn = sinl(th);
+  return -4.0L * sn * sn;
+}
+
+Launch line_launch(int N, int nlines_or_cols, size_t elem2, int prefer_nl) {
+  Launch L;
+  const int M = std::max(N / 2, 1);
+  int nl = prefer_nl;
+  while (nl > 1 && (size_t)nl * M * elem2 > (size_t)96 * 1024) nl >>= 1;
+  while (nl > 1 && nl * M > MAXV * 512) nl >>= 1;
+  const int need = 1 << ilog2(std::max(nlines_or_cols, 1));
+  while (nl > 1 && nl / 2 >= need) nl >>= 1;
+  L.nl = nl;
+  L.lognl = ilog2(nl);
+  int th = (nl * M + MAXV - 1) / MAXV;
+  const int J = MAXV / 2 + 2;
+  th = std::max(th, (int)(((M / 2 + 1) * nl + J - 1) / J));
+  th = std::max(32, ((th + 31) / 32) * 32);
+  L.threads = std::min(th, 512);
+  L.smem = (size_t)nl * M * elem2;
+  return L;
+}
+
+template <typename T>
+void fill_line_tab(LineTab<T>& t, const DirHost& d, const void* tw, const void* post, const void* mak) {
+  t.tw = reinterpret_cast<const typename V2<T>::t*>(tw);
+  t.post = reinterpret_cast<const typename V2<T>::t*>(post);
+  t.mak = reinterpret_cast<const typename V2<T>::t*>(mak);
+  t.n = d.n;
+  t.m = d.m;
+  t.bc = d.bc;
+  t.nst = d.nst;
+  for (int i = 0; i < 16; ++i) t.radix[i] = d.radix[i];
+}
+
+// one device allocation holding every table; returns byte offsets via a simple bump allocator
+struct Bump {
+  std::vector<unsigned char> host;
+  size_t add(const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + bytes);
+    std::memcpy(host.data() + off, src, bytes);
+    return off;
+  }
+};
+
+void dir_tables(const DirHost& d, std::vector<double>& tw, std::vector<double>& post, std::vector<double>& mak) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const int M = std::max(d.m, 1), N = d.n;
+  tw.assign(2 * M, 0.0);
+  post.assign(2 * (M + 1), 0.0);
+  mak.assign(2 * (M + 1), 0.0);
+  for (int t = 0; t < M; ++t) {
+    const long double th = -2.0L * pi * t / M;
+    tw[2 * t] = (double)cosl(th);
+    tw[2 * t + 1] = (double)sinl(th);
+  }
+  for (int k = 0; k <= M; ++k) {
+    const long double th = -2.0L * pi * k / N;
+    post[2 * k] = (double)cosl(th);
+    post[2 * k + 1] = (double)sinl(th);
+    const long double tm = -pi * k / (2.0L * N);
+    mak[2 * k] = (double)cosl(tm);
+    mak[2 * k + 1] = (double)sinl(tm);
+  }
+}
+
+std::vector<float> to_float(const std::vector<double>& v) {
+  std::vector<float> r(v.size());
+  for (size_t i = 0; i < v.size(); ++i) r[i] = (float)v[i];
+  return r;
+}
+
+void split_df(const std::vector<double>& v, std::vector<float>& hi, std::vector<float>& lo) {
+  hi.resize(v.size());
+  lo.resize(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    hi[i] = (float)v[i];
+    lo[i] = (float)(v[i] - (double)hi[i]);
+  }
+}
+
+
+size_t field_points(const cans_plan_s* P) { return (size_t)P->n[0] * P->n[1] * P->n[2]; }
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+void cans_opts_default(cans_opts* o) {
+  if (!o) return;
+  o->prec = CANS_FP64;
+  o->max_sweeps = 2;
+  o->tol = 1e-12;
+  o->fp64_mode_fraction = 0.01;
+  o->autotune = 0;
+}
+
+const char* cans_status_string(int s) {
+  switch (s) {
+    case CANS_OK: return "ok";
+    case CANS_ERR_ARG: return "invalid argument";
+    case CANS_ERR_UNSUPPORTED: return "unsupported problem for this build";
+    case CANS_ERR_CUDA: return "CUDA runtime error";
+    case CANS_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case CANS_ERR_INCOMPATIBLE: return "right-hand side incompatible with a singular problem";
+    case CANS_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+    case CANS_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
+                      const cans_opts* opts, cans_plan_t* out) {
+  if (!n || !len_xy || !bc || !out) return CANS_ERR_ARG;
+  *out = nullptr;
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1) return CANS_ERR_ARG;
+    if (bc[d] < 0 || bc[d] > 2) return CANS_ERR_ARG;
+  }
+  for (int d = 0; d < 2; ++d)
+    if (!(len_xy[d] > 0) || !std::isfinite(len_xy[d])) return CANS_ERR_ARG;
+  cans_opts o;
+  cans_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.prec != CANS_FP64 && o.prec != CANS_MIXED) return CANS_ERR_ARG;
+  if (o.max_sweeps < 0 || o.max_sweeps > 8) return CANS_ERR_ARG;
+  if (!(o.fp64_mode_fraction >= 0 && o.fp64_mode_fraction <= 1)) return CANS_ERR_ARG;
+  const int nz = n[2];
+  std::vector<double> dz(nz);
+  for (int k = 0; k < nz; ++k) {
+    dz[k] = dzf ? dzf[k] : 1.0 / nz;
+    if (!(dz[k] > 0) || !std::isfinite(dz[k])) return CANS_ERR_ARG;
+  }
+  if (bc[2] == BC_P) {
+    for (int k = 1; k < nz; ++k)
+      if (dz[k] != dz[0]) return CANS_ERR_ARG;
+    return CANS_ERR_UNSUPPORTED;  // periodic z: not in this build
+  }
+  for (int d = 0; d < 2; ++d) {
+    if (n[d] > 1 && (n[d] % 2)) return CANS_ERR_UNSUPPORTED;
+    if (n[d] > 8192) return CANS_ERR_UNSUPPORTED;
+  }
+  if (nz > 512) return CANS_ERR_UNSUPPORTED;
+  if ((size_t)n[0] * n[1] * n[2] >= ((size_t)1 << 40)) return CANS_ERR_UNSUPPORTED;
+
+  cans_plan_s* P = new (std::nothrow) cans_plan_s();
+  if (!P) return CANS_ERR_ARG;
+  std::memcpy(P->n, n, sizeof(P->n));
+  std::memcpy(P->len, len_xy, sizeof(P->len));
+  std::memcpy(P->bc, bc, sizeof(P->bc));
+  P->opts = o;
+  cudaGetDevice(&P->device);
+  P->singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+
+  DirHost* dirs[2] = {&P->dx, &P->dy};
+  for (int d = 0; d < 2; ++d) {
+    DirHost& D = *dirs[d];
+    D.n = n[d];
+    D.bc = bc[d];
+    D.m = (n[d] >= 2) ? n[d] / 2 : 0;
+    if (factor_radices(D.m, D.radix, &D.nst) != 0) {
+      delete P;
+      return CANS_ERR_UNSUPPORTED;
+    }
+  }
+  // eigenvalue terms per slot
+  const double hx = len_xy[0] / n[0], hy = len_xy[1] / n[1];
+  P->mux_h.resize(n[0]);
+  P->muy_h.resize(n[1]);
+  for (int s = 0; s < n[0]; ++s) P->mux_h[s] = (double)(slot_lambda(bc[0], n[0], s) / ((long double)hx * hx));
+  for (int s = 0; s < n[1]; ++s) P->muy_h[s] = (double)(slot_lambda(bc[1], n[1], s) / ((long double)hy * hy));
+  if (n[0] == 1) P->mux_h[0] = (bc[0] == BC_DD) ? -4.0 / (hx * hx) : 0.0;
+  if (n[1] == 1) P->muy_h[0] = (bc[1] == BC_DD) ? -4.0 / (hy * hy) : 0.0;
+  P->idx2 = 1.0 / (hx * hx);
+  P->idy2 = 1.0 / (hy * hy);
+
+  // z grid: centre distances with mirrored wall ghosts; stencil and tridiagonal rows
+  std::vector<double> dzc(nz + 1);  // dzc[k] = distance between centres k-1 and k (k = 0..nz)
+  for (int k = 1; k < nz; ++k) dzc[k] = 0.5 * (dz[k - 1] + dz[k]);
+  dzc[0] = dz[0];
+  dzc[nz] = dz[nz - 1];
+  std::vector<double> sa(nz), sc(nz), za(nz), zb(nz), zc(nz);
+  for (int k = 0; k < nz; ++k) {
+    sa[k] = 1.0 / (dz[k] * dzc[k]);
+    sc[k] = 1.0 / (dz[k] * dzc[k + 1]);
+    za[k] = sa[k];
+    zc[k] = sc[k];
+    zb[k] = -(sa[k] + sc[k]);
+  }
+  if (bc[2] == BC_NN) {
+    zb[0] += sa[0];
+    zb[nz - 1] += sc[nz - 1];
+  } else {  // Dirichlet
+    zb[0] -= sa[0];
+    zb[nz - 1] -= sc[nz - 1];
+  }
+  za[0] = 0;
+  zc[nz - 1] = 0;
+
+  // tables -> one device block
+  Bump B;
+  std::vector<double> tw[2], post[2], mak[2];
+  size_t o_tw_d[2], o_post_d[2], o_mak_d[2], o_tw_f[2], o_post_f[2], o_mak_f[2];
+  for (int d = 0; d < 2; ++d) {
+    dir_tables(*dirs[d], tw[d], post[d], mak[d]);
+    o_tw_d[d] = B.add(tw[d].data(), tw[d].size() * 8);
+    o_post_d[d] = B.add(post[d].data(), post[d].size() * 8);
+    o_mak_d[d] = B.add(mak[d].data(), mak[d].size() * 8);
+    auto twf = to_float(tw[d]), postf = to_float(post[d]), makf = to_float(mak[d]);
+    o_tw_f[d] = B.add(twf.data(), twf.size() * 4);
+    o_post_f[d] = B.add(postf.data(), postf.size() * 4);
+    o_mak_f[d] = B.add(makf.data(), makf.size() * 4);
+  }
+  const size_t o_mux_d = B.add(P->mux_h.data(), n[0] * 8), o_muy_d = B.add(P->muy_h.data(), n[1] * 8);
+  auto muxf = to_float(P->mux_h), muyf = to_float(P->muy_h);
+  const size_t o_mux_f = B.add(muxf.data(), n[0] * 4), o_muy_f = B.add(muyf.data(), n[1] * 4);
+  const size_t o_dzf = B.add(dz.data(), nz * 8);
+  std::vector<float> dzff, dzflo;
+  split_df(dz, dzff, dzflo);
+  const size_t o_dzff = B.add(dzff.data(), nz * 4);
+  const size_t o_dzflo = B.add(dzflo.data(), nz * 4);
+  const size_t o_sa = B.add(sa.data(), nz * 8), o_sc = B.add(sc.data(), nz * 8);
+  std::vector<float> sahi, salo, schi, sclo;
+  split_df(sa, sahi, salo);
+  split_df(sc, schi, sclo);
+  const size_t o_sahi = B.add(sahi.data(), nz * 4), o_salo = B.add(salo.data(), nz * 4);
+  const size_t o_schi = B.add(schi.data(), nz * 4), o_sclo = B.add(sclo.data(), nz * 4);
+  const size_t o_za = B.add(za.data(), nz * 8), o_zb = B.add(zb.data(), nz * 8), o_zc = B.add(zc.data(), nz * 8);
+  auto zaf = to_float(za), zbf = to_float(zb), zcf = to_float(zc);
+  const size_t o_zaf = B.add(zaf.data(), nz * 4), o_zbf = B.add(zbf.data(), nz * 4), o_zcf = B.add(zcf.data(), nz * 4);
+  size_t o_mask = 0;
+  bool has_mask = false;
+  if (o.prec == CANS_MIXED) {
+    // the ceil(fraction * Nx * Ny) slots with the smallest |mu| (ties by linear index) solve in double
+    const size_t ncol = (size_t)n[0] * n[1];
+    size_t want = (size_t)std::ceil(o.fp64_mode_fraction * (double)ncol);
+    want = std::min(std::max(want, (size_t)1), ncol);
+    std::vector<std::pair<double, uint32_t>> keyed(ncol);
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        const size_t c = (size_t)j * n[0] + i;
+        keyed[c] = {std::fabs(P->mux_h[i] + P->muy_h[j]), (uint32_t)c};
+      }
+    std::nth_element(keyed.begin(), keyed.begin() + (want - 1), keyed.end());
+    std::vector<unsigned char> mask(ncol, 0);
+    for (size_t q = 0; q < want; ++q) {
+      const uint32_t c = keyed[q].second;
+      mask[c] = 1;
+      P->mask_i_end = std::max(P->mask_i_end, (int)(c % n[0]) + 1);
+      P->mask_j_end = std::max(P->mask_j_end, (int)(c / n[0]) + 1);
+    }
+    o_mask = B.add(mask.data(), ncol);
+    has_mask = true;
+  }
+  P->nacc = 2 * (o.max_sweeps + 4);  // [0] |f|^2, [1+s] |r_s|^2, [nacc-5] gauge sum, [nacc-4..] reports
+  std::vector<double> zeros(P->nacc, 0.0);
+  const size_t o_acc = B.add(zeros.data(), P->nacc * 8);
+
+  if (cudaMalloc(&P->dtab, B.host.size()) != cudaSuccess ||
+      cudaMemcpy(P->dtab, B.host.data(), B.host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (P->dtab) cudaFree(P->dtab);
+    delete P;
+    return CANS_ERR_CUDA;
+  }
+  unsigned char* base = static_cast<unsigned char*>(P->dtab);
+  fill_line_tab<double>(P->tx_d, P->dx, base + o_tw_d[0], base + o_post_d[0], base + o_mak_d[0]);
+  fill_line_tab<double>(P->ty_d, P->dy, base + o_tw_d[1], base + o_post_d[1], base + o_mak_d[1]);
+  fill_line_tab<float>(P->tx_f, P->dx, base + o_tw_f[0], base + o_post_f[0], base + o_mak_f[0]);
+  fill_line_tab<float>(P->ty_f, P->dy, base + o_tw_f[1], base + o_post_f[1], base + o_mak_f[1]);
+  P->mux_d = reinterpret_cast<const double*>(base + o_mux_d);
+  P->muy_d = reinterpret_cast<const double*>(base + o_muy_d);
+  P->mux_f = reinterpret_cast<const float*>(base + o_mux_f);
+  P->muy_f = reinterpret_cast<const float*>(base + o_muy_f);
+  P->dzf_d = reinterpret_cast<const double*>(base + o_dzf);
+  P->dzf_f = reinterpret_cast<const float*>(base + o_dzff);
+  P->dzf_flo = reinterpret_cast<const float*>(base + o_dzflo);
+  {
+    // column mean target: a (0,0) value v contributes v * cx * cy / (Nx Ny) to every cell, with
+    // cx = 1 for a periodic or single-cell direction and 1/2 for a Neumann one (DCT-II of a constant)
+    const double cx = (bc[0] == BC_NN && n[0] > 1) ? 0.5 : 1.0;
+    const double cy = (bc[1] == BC_NN && n[1] > 1) ? 0.5 : 1.0;
+    double wsum = 0;
+    for (int k = 0; k < nz; ++k) wsum += dz[k];
+    P->gauge_scale = -1.0 / (wsum * cx * cy);
+  }
+  P->sa_d = reinterpret_cast<const double*>(base + o_sa);
+  P->sc_d = reinterpret_cast<const double*>(base + o_sc);
+  P->sa_hi = reinterpret_cast<const float*>(base + o_sahi);
+  P->sa_lo = reinterpret_cast<const float*>(base + o_salo);
+  P->sc_hi = reinterpret_cast<const float*>(base + o_schi);
+  P->sc_lo = reinterpret_cast<const float*>(base + o_sclo);
+  P->zt_d = {reinterpret_cast<const double*>(base + o_za), reinterpret_cast<const double*>(base + o_zb),
+             reinterpret_cast<const double*>(base + o_zc)};
+  P->zt_f = {reinterpret_cast<const float*>(base + o_zaf), reinterpret_cast<const float*>(base + o_zbf),
+             reinterpret_cast<const float*>(base + o_zcf)};
+  P->mask_d = has_mask ? base + o_mask : nullptr;
+  P->acc_d = reinterpret_cast<double*>(base + o_acc);
+
+  // launch shapes
+  const int nlines = n[1] * n[2];
+  P->x_l[0] = line_launch(n[0], nlines, sizeof(double2), 16);
+  P->x_l[1] = line_launch(n[0], nlines, sizeof(float2), 32);
+  P->y_l[0] = line_launch(n[1], n[0], sizeof(double2), 8);
+  P->y_l[1] = line_launch(n[1], n[0], sizeof(float2), 16);
+  P->z_m = (nz + 31) / 32;
+  P->z_mmax = 1;
+  while (P->z_mmax < P->z_m) P->z_mmax <<= 1;
+  for (int s = 0; s < 2; ++s) {
+    int ti = (s == 0) ? 16 : 32;
+    const size_t es = (s == 0) ? 8 : 4;
+    while (ti > 1 && (size_t)ti * nz * es > (size_t)96 * 1024) ti >>= 1;
+    while (ti > 1 && ti / 2 >= n[0]) ti >>= 1;
+    P->z_ti[s] = ti;
+    P->z_smem[s] = (size_t)ti * nz * es;
+  }
+  *out = P;
+  return CANS_OK;
+}
+
+int cans_poisson_workspace_size(cans_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return CANS_ERR_ARG;
+  const size_t N = field_points(P);
+  *bytes = (P->opts.prec == CANS_MIXED) ? 3 * align256(N * sizeof(float)) : 0;
+  return CANS_OK;
+}
+
+int cans_plan_destroy(cans_plan_t P) {
+  if (!P) return CANS_ERR_ARG;
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  if (P->dtab) cudaFree(P->dtab);
+  delete P;
+  return CANS_OK;
+}
+
+int cans_plan_profile(cans_plan_t P, int enable) {
+  if (!P) return CANS_ERR_ARG;
+  P->profiling = enable != 0;
+  if (enable) {
+    P->ev_used = 0;
+    P->ev_kind.clear();
+  }
+  return CANS_OK;
+}
+
+int cans_plan_profile_read(cans_plan_t P, int pass, double* total_ms, int* launches) {
+  if (!P || pass < 0 || pass >= CANS_PASS_COUNT || !total_ms || !launches) return CANS_ERR_ARG;
+  double tot = 0;
+  int cnt = 0;
+  for (int r = 0; r < P->ev_used; ++r) {
+    if (P->ev_kind[r] != pass) continue;
+    if (cudaEventSynchronize(P->ev_pool[2 * r + 1]) != cudaSuccess) return CANS_ERR_CUDA;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, P->ev_pool[2 * r], P->ev_pool[2 * r + 1]) != cudaSuccess) return CANS_ERR_CUDA;
+    tot += ms;
+    ++cnt;
+  }
+  *total_ms = tot;
+  *launches = cnt;
+  return CANS_OK;
+}
+
+int cans_plan_eigenvalues(cans_plan_t P, double* mux, double* muy) {
+  if (!P) return CANS_ERR_ARG;
+  if (mux) std::memcpy(mux, P->mux_h.data(), sizeof(double) * P->n[0]);
+  if (muy) std::memcpy(muy, P->muy_h.data(), sizeof(double) * P->n[1]);
+  return CANS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Event pair around one pass launch when profiling is on.
+struct PassTimer {
+  cans_plan_s* P;
+  cudaStream_t st;
+  int rec = -1;
+  PassTimer(cans_plan_s* P_, int kind, cudaStream_t st_) : P(P_), st(st_) {
+    if (!P->profiling) return;
+    if ((size_t)(2 * P->ev_used + 2) > P->ev_pool.size()) {
+      for (int q = 0; q < 64; ++q) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        P->ev_pool.push_back(e);
+      }
+    }
+    rec = P->ev_used++;
+    P->ev_kind.push_back(kind);
+    cudaEventRecord(P->ev_pool[2 * rec], st);
+  }
+  ~PassTimer() {
+    if (rec >= 0) cudaEventRecord(P->ev_pool[2 * rec + 1], st);
+  }
+};
+
+#define CK(...)                                  \
+  do {                                           \
+    cudaError_t e_ = (__VA_ARGS__);              \
+    if (e_ != cudaSuccess) return CANS_ERR_CUDA; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspace, void* cuda_stream, double* info) {
+  if (!P || !f || !p) return CANS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t N = field_points(P);
+  const int sweeps = P->opts.max_sweeps;
+  const double inv_scale = 1.0 / ((double)P->n[0] * P->n[1]);
+#define TIMED(kind, ...)                    \
+  do {                                      \
+    PassTimer tm_(P, kind, st);             \
+    CK(__VA_ARGS__);                        \
+  } while (0)
+  if (P->opts.prec == CANS_FP64) {
+    TIMED(CANS_PASS_XF, launch_xfwd<double, 0>(P, f, nullptr, nullptr, p, nullptr, st));
+    TIMED(CANS_PASS_YF, launch_y<double, 1>(P, p, st));
+    TIMED(CANS_PASS_Z, launch_z<double>(P, p, nullptr, st));
+    TIMED(CANS_PASS_YI, launch_y<double, -1>(P, p, st));
+    TIMED(CANS_PASS_XI, launch_xinv<double, 0>(P, p, p, nullptr, nullptr, inv_scale, nullptr, st));
+  } else {
+    if (f == p) return CANS_ERR_ARG;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CANS_ERR_WORKSPACE;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    float* W = reinterpret_cast<float*>(ws);
+    float* Phi = reinterpret_cast<float*>(ws + align256(N * 4));
+    float* Plo = reinterpret_cast<float*>(ws + 2 * align256(N * 4));
+    CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
+    TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
+    TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
+    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st));
+    TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
+    if (sweeps == 0) {
+      TIMED(CANS_PASS_XI, launch_xinv<float, 0>(P, W, p, nullptr, nullptr, inv_scale, nullptr, st));
+    } else {
+      double* gauge = P->singular ? P->acc_d + P->nacc - 5 : nullptr;
+      TIMED(CANS_PASS_XI, launch_xinv<float, 1>(P, W, nullptr, Phi, Plo, inv_scale, gauge, st));
+      for (int s = 0; s < sweeps; ++s) {
+        TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
+        TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
+        TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st));
+        TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
+        if (s + 1 < sweeps)
+          TIMED(CANS_PASS_XU, launch_xinv<float, 2>(P, W, nullptr, Phi, Plo, inv_scale, nullptr, st));
+        else
+          TIMED(CANS_PASS_XU, launch_xinv<float, 3>(P, W, p, Phi, Plo, inv_scale, nullptr, st));
+      }
+    }
+  }
+  if (info) {
+    double* acc2 = P->acc_d + P->nacc - 4;
+    CK(launch_residual_norms(P, f, p, acc2, st));
+    if (P->singular) CK(launch_weighted_sum(P, f, acc2 + 2, st));
+    std::vector<double> h(P->nacc);
+    CK(cudaMemcpyAsync(h.data(), P->acc_d, P->nacc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double rr = h[P->nacc - 4], ff = h[P->nacc - 3];
+    const double fn = std::sqrt(ff);
+    if (P->opts.prec == CANS_MIXED) {
+      for (int s = 0; s < sweeps; ++s) info[s] = std::sqrt(h[1 + s]) / fn;
+      info[sweeps] = std::sqrt(rr) / fn;
+      info[sweeps + 1] = std::sqrt(rr) / fn;
+    } else {
+      info[0] = std::sqrt(rr) / fn;
+      for (int s = 1; s < sweeps + 2; ++s) info[s] = info[0];
+    }
+    if (P->singular && std::fabs(h[P->nacc - 2]) > 1e-10 * h[P->nacc - 1]) return CANS_ERR_INCOMPATIBLE;
+    if (P->opts.prec == CANS_MIXED && info[sweeps] > P->opts.tol) return CANS_ERR_NOT_CONVERGED;
+  }
+  return CANS_OK;
+}
+
+int cans_transform_xy(cans_plan_t P, double* field, int dir, void* cuda_stream) {
+  if (!P || !field || (dir != 1 && dir != -1)) return CANS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (dir > 0) {
+    CK(launch_xfwd<double, 0>(P, field, nullptr, nullptr, field, nullptr, st));
+    CK((launch_y<double, 1>(P, field, st)));
+  } else {
+    CK((launch_y<double, -1>(P, field, st)));
+    // inverse x without the 1/(Nx Ny) normalisation
+    CK((launch_xinv<double, 0>(P, field, field, nullptr, nullptr, 1.0, nullptr, st)));
+  }
+  return CANS_OK;
+}
+
+int cans_zsolve(cans_plan_t P, double* field, void* cuda_stream) {
+  if (!P || !field) return CANS_ERR_ARG;
+  CK(launch_z<double>(P, field, nullptr, static_cast<cudaStream_t>(cuda_stream)));
+  return CANS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Reporting kernels (only run when the caller asks for residual norms): ||f - L_h p||^2 in FP64
+// (Eq. poi with a non-uniform z) and the dzf-weighted sum of f for the compatibility check of a
+// singular problem.
+#include "plan.cuh"
+
+namespace cans {
+
+__global__ void residual_norm_kernel(const double* __restrict__ f, const double* __restrict__ p, int nx, int ny, int nz,
+                                     int bx, int by, int bz, double idx2, double idy2, const double* __restrict__ sa,
+                                     const double* __restrict__ sc, double* out) {
+  const size_t N = (size_t)nx * ny * nz;
+  double rr = 0, ff = 0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
+    const double pc = p[c];
+    auto nb = [&](int bc, bool edge, size_t idx_in, size_t idx_wrap) -> double {
+      if (!edge) return p[idx_in];
+      if (bc == BC_P) return p[idx_wrap];
+      if (bc == BC_NN) return pc;
+      return -pc;
+    };
+    const size_t sy = nx, sz = (size_t)nx * ny;
+    const double xm = nb(bx, i == 0, c - 1, c + (nx - 1)), xp = nb(bx, i == nx - 1, c + 1, c - (nx - 1));
+    const double ym = nb(by, j == 0, c - sy, c + (ny - 1) * sy), yp = nb(by, j == ny - 1, c + sy, c - (ny - 1) * sy);
+    const double zm = nb(bz, k == 0, c - sz, c + (nz - 1) * sz), zp = nb(bz, k == nz - 1, c + sz, c - (nz - 1) * sz);
+    const double Lp = (xm - 2 * pc + xp) * idx2 + (ym - 2 * pc + yp) * idy2 + sc[k] * (zp - pc) + sa[k] * (zm - pc);
+    const double r = f[c] - Lp;
+    rr += r * r;
+    ff += f[c] * f[c];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], rr);
+    atomicAdd(&out[1], ff);
+  }
+}
+
+__global__ void weighted_sum_kernel(const double* __restrict__ f, int nx, int ny, int nz, const double* __restrict__ dzf,
+                                    double* out) {
+  const size_t N = (size_t)nx * ny * nz;
+  double s = 0, sa = 0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c / ((size_t)nx * ny));
+    s += dzf[k] * f[c];
+    sa += dzf[k] * fabs(f[c]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], s);
+    atomicAdd(&out[1], sa);
+  }
+}
+
+cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  residual_norm_kernel<<<148 * 8, 256, 0, st>>>(f, p, P->n[0], P->n[1], P->n[2], P->bc[0], P->bc[1], P->bc[2], P->idx2,
+                                                 P->idy2, P->sa_d, P->sc_d, acc2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  weighted_sum_kernel<<<148 * 4, 256, 0, st>>>(f, P->n[0], P->n[1], P->n[2], P->dzf_d, acc2);
+  return cudaGetLastError();
+}
+
+}  // namespace cans

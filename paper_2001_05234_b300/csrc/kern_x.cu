@@ -1,0 +1,270 @@
+// x-passes of the solver: forward transform along contiguous x lines (fused with the FP64->FP32
+// conversion, or with the double-float residual of a refinement sweep) and the inverse transform
+// (fused with the normalisation and the update of the iterate).  Transform along x = the operator
+// F^x of Eq. poi_reduced.
+#include "plan.cuh"
+
+namespace cans {
+
+constexpr int MAXV = 8;  // complex values per thread per FFT stage
+
+__device__ __forceinline__ float ghost_or(int bc, int at_edge, float inner_c, float wrap, float nb) {
+  if (!at_edge) return nb;
+  if (bc == BC_P) return wrap;
+  if (bc == BC_NN) return inner_c;
+  return -inner_c;
+}
+
+// r(i,j,k) = f - L_h(Phi + Plo) (Eq. poi): the Phi part in double-float arithmetic, the small Plo
+// part in float.  Ghost rules: periodic wrap, Neumann mirror, Dirichlet antisymmetric mirror.
+__device__ __forceinline__ float residual_point(const double* __restrict__ f, const float* __restrict__ Phi,
+                                                const float* __restrict__ Plo, const StencilDF& S, int i, int j,
+                                                int k) {
+  const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+  const size_t sy = nx, sz = (size_t)nx * ny;
+  const size_t c = (size_t)i + sy * j + sz * k;
+  const float pc = Phi[c], qc = Plo[c];
+  const bool xm_e = (i == 0), xp_e = (i == nx - 1), ym_e = (j == 0), yp_e = (j == ny - 1), zm_e = (k == 0),
+             zp_e = (k == nz - 1);
+  const size_t cxm = xm_e ? c + (nx - 1) : c - 1, cxp = xp_e ? c - (nx - 1) : c + 1;
+  const size_t cym = ym_e ? c + (ny - 1) * sy : c - sy, cyp = yp_e ? c - (ny - 1) * sy : c + sy;
+  const size_t czm = zm_e ? c + (nz - 1) * sz : c - sz, czp = zp_e ? c - (nz - 1) * sz : c + sz;
+  const float Pxm = Phi[cxm], Pxp = Phi[cxp], Pym = Phi[cym], Pyp = Phi[cyp], Pzm = Phi[czm], Pzp = Phi[czp];
+  const float xm = ghost_or(S.bc[0], xm_e, pc, Pxm, Pxm), xp = ghost_or(S.bc[0], xp_e, pc, Pxp, Pxp);
+  const float ym = ghost_or(S.bc[1], ym_e, pc, Pym, Pym), yp = ghost_or(S.bc[1], yp_e, pc, Pyp, Pyp);
+  const float zm = ghost_or(S.bc[2], zm_e, pc, Pzm, Pzm), zp = ghost_or(S.bc[2], zp_e, pc, Pzp, Pzp);
+  // x and y second differences, exact as double-floats
+  df sx = df_add(two_sum(xm, xp), df_make(-2.f * pc, 0.f));
+  df sy2 = df_add(two_sum(ym, yp), df_make(-2.f * pc, 0.f));
+  df L = df_add(df_mul(S.idx2, sx), df_mul(S.idy2, sy2));
+  const df za = df_make(S.sa_hi[k], S.sa_lo[k]), zc = df_make(S.sc_hi[k], S.sc_lo[k]);
+  L = df_add(L, df_mul(zc, two_sum(zp, -pc)));
+  L = df_add(L, df_mul(za, two_sum(zm, -pc)));
+  const df r = df_add(df_from_double(f[c]), df_neg(L));
+  const float Qxm = Plo[cxm], Qxp = Plo[cxp], Qym = Plo[cym], Qyp = Plo[cyp], Qzm = Plo[czm], Qzp = Plo[czp];
+  const float qxm = ghost_or(S.bc[0], xm_e, qc, Qxm, Qxm), qxp = ghost_or(S.bc[0], xp_e, qc, Qxp, Qxp);
+  const float qym = ghost_or(S.bc[1], ym_e, qc, Qym, Qym), qyp = ghost_or(S.bc[1], yp_e, qc, Qyp, Qyp);
+  const float qzm = ghost_or(S.bc[2], zm_e, qc, Qzm, Qzm), qzp = ghost_or(S.bc[2], zp_e, qc, Qzp, Qzp);
+  const float Lq = S.idx2.hi * (qxm + qxp - 2.f * qc) + S.idy2.hi * (qym + qyp - 2.f * qc) + S.sc_hi[k] * (qzp - qc) +
+                   S.sa_hi[k] * (qzm - qc);
+  return (r.hi + r.lo) - Lq;
+}
+
+__device__ __forceinline__ void block_accumulate(float v, double* dst) {
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(dst, (double)v);
+  }
+}
+
+__device__ __forceinline__ void block_accumulate_d(double v, double* dst) {
+  __shared__ double redd[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) redd[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? redd[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(dst, v);
+  }
+}
+
+// Forward x-pass.  MODE 0: read f (double) -> T.  MODE 1 (T = float): the residual
+// f - L_h(Phi + Plo) computed on the fly.  Output lines go to dst (T) in transform slot order.
+// norm_acc (optional) receives sum f^2 (MODE 0) or sum r^2 (MODE 1).
+template <typename T, int MODE, int MC>
+__global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
+                                                      const float* __restrict__ Plo, T* __restrict__ dst, XArgs a,
+                                                      LineTab<T> tb, StencilDF S, double* norm_acc) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int nl = 1 << a.lognl;
+  const Lay L{nl};
+  const int N = MC > 0 ? 2 * MC : a.nx;
+  const int line0 = blockIdx.x * nl;
+  float acc = 0.f;
+  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+    const int l = e / N, n = e - l * N;
+    const int line = line0 + l;
+    T v = 0;
+    if (line < a.nlines) {
+      if (MODE == 0) {
+        const double fv = f[(size_t)line * N + n];
+        const float ff = (float)fv;
+        acc += ff * ff;
+        v = (T)fv;
+      } else {
+        const int j = line % S.n[1], k = line / S.n[1];
+        const float r = residual_point(f, Phi, Plo, S, n, j, k);
+        acc += r * r;
+        v = (T)r;
+      }
+    }
+    forward_store<T, MC>(buf, L, tb, n, l, v);
+  }
+  __syncthreads();
+  line_forward<MAXV, T, MC>(buf, L, a.lognl, tb);
+  const T* bufT = reinterpret_cast<const T*>(buf);
+  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+    const int l = e / N, s = e - l * N;
+    const int line = line0 + l;
+    if (line < a.nlines) dst[(size_t)line * N + s] = bufT[L.r(s, l)];
+  }
+  if (norm_acc != nullptr) block_accumulate(acc, norm_acc);
+}
+
+// Inverse x-pass.  MODE 0: p (double) = scale * x.  MODE 1: Phi = scale * x, Plo = 0, and (when
+// gauge != nullptr) sum_c dzf_k Phi_c into *gauge.  MODE 2: (Phi, Plo) += scale * x (double-float).
+// MODE 3: p = Phi + Plo + scale * x (double).
+template <typename T, int MODE, int MC>
+__global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src, double* __restrict__ p,
+                                                      float* __restrict__ Phi, float* __restrict__ Plo, XArgs a,
+                                                      LineTab<T> tb, const float* __restrict__ wz,
+                                                      const float* __restrict__ wz_lo, int ny, double* gauge) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int nl = 1 << a.lognl;
+  const Lay L{nl};
+  const int N = MC > 0 ? 2 * MC : a.nx;
+  const int line0 = blockIdx.x * nl;
+  T* bufT = reinterpret_cast<T*>(buf);
+  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+    const int l = e / N, s = e - l * N;
+    const int line = line0 + l;
+    bufT[L.r(s, l)] = (line < a.nlines) ? src[(size_t)line * N + s] : (T)0;
+  }
+  __syncthreads();
+  line_inverse<MAXV, T, MC>(buf, L, a.lognl, tb);
+  df gacc = df_make(0.f, 0.f);
+  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
+    const int l = e / N, n = e - l * N;
+    const int line = line0 + l;
+    if (line >= a.nlines) continue;
+    const size_t o = (size_t)line * N + n;
+    const T v = inverse_sample<T, MC>(buf, L, tb, n, l);
+    if (MODE == 0) {
+      p[o] = (double)v * a.scale;
+    } else if (MODE == 1) {
+      const float ph = (float)v * (float)a.scale;
+      Phi[o] = ph;
+      Plo[o] = 0.f;
+      if (gauge != nullptr) {
+        const int k = line / ny;
+        df t = two_prod(ph, wz[k]);  // ph * dzf_k with dzf_k = wz + wz_lo (double-float weight)
+        t.lo = __fmaf_rn(ph, wz_lo[k], t.lo);
+        gacc = df_add(gacc, t);
+      }
+    } else {
+      const float d = (float)v * (float)a.scale;
+      df s = two_sum(Phi[o], d);
+      s = fast_two_sum(s.hi, s.lo + Plo[o]);
+      if (MODE == 2) {
+        Phi[o] = s.hi;
+        Plo[o] = s.lo;
+      } else {
+        p[o] = df_to_double(s);
+      }
+    }
+  }
+  if (MODE == 1 && gauge != nullptr) block_accumulate_d((double)gacc.hi + (double)gacc.lo, gauge);
+}
+
+StencilDF stencil_df(const cans_plan_s* P) {
+  StencilDF S;
+  S.idx2.hi = (float)P->idx2;
+  S.idx2.lo = (float)(P->idx2 - (double)S.idx2.hi);
+  S.idy2.hi = (float)P->idy2;
+  S.idy2.lo = (float)(P->idy2 - (double)S.idy2.hi);
+  S.sa_hi = P->sa_hi;
+  S.sa_lo = P->sa_lo;
+  S.sc_hi = P->sc_hi;
+  S.sc_lo = P->sc_lo;
+  for (int d = 0; d < 3; ++d) {
+    S.bc[d] = P->bc[d];
+    S.n[d] = P->n[d];
+  }
+  return S;
+}
+
+template <typename T, int MODE, int MC>
+static cudaError_t xfwd_m(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
+                          double* acc, cudaStream_t st) {
+  const Launch& L = P->x_l[sizeof(T) == 8 ? 0 : 1];
+  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, 1.0};
+  cudaError_t e = set_smem((const void*)xfwd_kernel<T, MODE, MC>, L.smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.nlines + L.nl - 1) / L.nl;
+  xfwd_kernel<T, MODE, MC><<<grid, L.threads, L.smem, st>>>(f, Phi, Plo, dst, a, tab_x<T>(P), stencil_df(P), acc);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
+                        double* acc, cudaStream_t st) {
+  switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xfwd_m<T, MODE, MM>(P, f, Phi, Plo, dst, acc, st);
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return xfwd_m<T, MODE, 0>(P, f, Phi, Plo, dst, acc, st);
+  }
+}
+
+template <typename T, int MODE, int MC>
+static cudaError_t xinv_m(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
+                          double* gauge, cudaStream_t st) {
+  const Launch& L = P->x_l[sizeof(T) == 8 ? 0 : 1];
+  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, scale};
+  cudaError_t e = set_smem((const void*)xinv_kernel<T, MODE, MC>, L.smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.nlines + L.nl - 1) / L.nl;
+  xinv_kernel<T, MODE, MC><<<grid, L.threads, L.smem, st>>>(src, p, Phi, Plo, a, tab_x<T>(P), P->dzf_f,
+                                                            P->dzf_flo, P->n[1], gauge);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
+                        double* gauge, cudaStream_t st) {
+  switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xinv_m<T, MODE, MM>(P, src, p, Phi, Plo, scale, gauge, st);
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return xinv_m<T, MODE, 0>(P, src, p, Phi, Plo, scale, gauge, st);
+  }
+}
+
+template cudaError_t launch_xfwd<double, 0>(const cans_plan_s*, const double*, const float*, const float*, double*,
+                                            double*, cudaStream_t);
+template cudaError_t launch_xfwd<float, 0>(const cans_plan_s*, const double*, const float*, const float*, float*,
+                                           double*, cudaStream_t);
+template cudaError_t launch_xfwd<float, 1>(const cans_plan_s*, const double*, const float*, const float*, float*,
+                                           double*, cudaStream_t);
+template cudaError_t launch_xinv<double, 0>(const cans_plan_s*, const double*, double*, float*, float*, double, double*,
+                                            cudaStream_t);
+template cudaError_t launch_xinv<float, 0>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_xinv<float, 1>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_xinv<float, 2>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_xinv<float, 3>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+
+}  // namespace cans

@@ -1,0 +1,201 @@
+// z-pass of the solver: one tridiagonal solve along z per (x, y) mode (Eq. poi_reduced).
+//   zpass_f32_kernel : float columns of the mixed path (skips the columns the plan marks as double).
+//   zpass_f64_kernel : double columns -- every column of the FP64 path, or the marked low-|mu|
+//                      columns of the mixed path (including the singular (0,0) mode), over the
+//                      bounding box of the marked columns only.
+#include "plan.cuh"
+
+namespace cans {
+
+// Coalesced copy of a TI x Nz tile (TI consecutive x-slots of one y-slot, all z) into the swizzled
+// shared layout and back.  Rows are TI elements long; 16-byte vectors when the grid allows it.
+template <typename T>
+__device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, int TI, int nz, int m, int ncols,
+                                          bool vec) {
+  constexpr int V = 16 / sizeof(T);
+  if (vec && ncols == TI) {
+    const int per_row = TI / V;
+    for (int e = threadIdx.x; e < per_row * nz; e += blockDim.x) {
+      const int k = e / per_row, q = (e - k * per_row) * V;
+      const T* src = col0 + (size_t)k * plane + q;
+      if (V == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tile[ztile_idx(k, q + u, TI, m)] = (T)vv[u];
+      } else {
+        const double2 v = *reinterpret_cast<const double2*>(src);
+        tile[ztile_idx(k, q, TI, m)] = (T)v.x;
+        tile[ztile_idx(k, q + 1, TI, m)] = (T)v.y;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < TI * nz; e += blockDim.x) {
+      const int k = e / TI, ii = e - k * TI;
+      if (ii < ncols) tile[ztile_idx(k, ii, TI, m)] = col0[(size_t)k * plane + ii];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane, int TI, int nz, int m, int ncols,
+                                           bool vec) {
+  constexpr int V = 16 / sizeof(T);
+  if (vec && ncols == TI) {
+    const int per_row = TI / V;
+    for (int e = threadIdx.x; e < per_row * nz; e += blockDim.x) {
+      const int k = e / per_row, q = (e - k * per_row) * V;
+      T* dst = col0 + (size_t)k * plane + q;
+      if (V == 4) {
+        float4 v;
+        v.x = (float)tile[ztile_idx(k, q, TI, m)];
+        v.y = (float)tile[ztile_idx(k, q + 1, TI, m)];
+        v.z = (float)tile[ztile_idx(k, q + 2, TI, m)];
+        v.w = (float)tile[ztile_idx(k, q + 3, TI, m)];
+        *reinterpret_cast<float4*>(dst) = v;
+      } else {
+        double2 v;
+        v.x = (double)tile[ztile_idx(k, q, TI, m)];
+        v.y = (double)tile[ztile_idx(k, q + 1, TI, m)];
+        *reinterpret_cast<double2*>(dst) = v;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < TI * nz; e += blockDim.x) {
+      const int k = e / TI, ii = e - k * TI;
+      if (ii < ncols) col0[(size_t)k * plane + ii] = tile[ztile_idx(k, ii, TI, m)];
+    }
+  }
+}
+
+template <int MMAX>
+__global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, int vec) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TI = a.ti, m = a.m;
+  float* sa = reinterpret_cast<float*>(smem_raw);
+  float* sb = sa + 32 * m;
+  float* sc = sb + 32 * m;
+  float* tile = sc + 32 * m;
+  const int i0 = blockIdx.x * TI, j = blockIdx.y;
+  const size_t plane = (size_t)a.nx * a.ny;
+  float* col0 = w + (size_t)j * a.nx + i0;
+  const int ncols = min(TI, a.nx - i0);
+  stage_zrows<float, float>(sa, sb, sc, zf, a.nz, m);
+  tile_load<float>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float muy = a.muy_f[j];
+  for (int cidx = warp; cidx < ncols; cidx += nwarps) {
+    const int i = i0 + cidx;
+    if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
+    zsolve_column<MMAX, float, float, false>(tile, cidx, TI, a.nz, m, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
+  }
+  __syncthreads();
+  tile_store<float>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+}
+
+template <typename T, int MMAX>
+__global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TI = a.ti, m = a.m;
+  double* sa = reinterpret_cast<double*>(smem_raw);
+  double* sb = sa + 32 * m;
+  double* sc = sb + 32 * m;
+  T* tile = reinterpret_cast<T*>(sc + 32 * m);
+  const int i0 = blockIdx.x * TI, j = blockIdx.y;
+  const size_t plane = (size_t)a.nx * a.ny;
+  T* col0 = w + (size_t)j * a.nx + i0;
+  const int ncols = min(TI, a.nx - i0);
+  if (a.mask != nullptr) {  // skip tiles without a marked column
+    bool any = false;
+    for (int c = 0; c < ncols; ++c) any |= a.mask[(size_t)j * a.nx + i0 + c] != 0;
+    if (!any) return;
+  }
+  stage_zrows<double, double>(sa, sb, sc, zd, a.nz, m);
+  tile_load<T>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const double muy = a.muy_d[j];
+  for (int cidx = warp; cidx < ncols; cidx += nwarps) {
+    const int i = i0 + cidx;
+    if (a.mask != nullptr && !a.mask[(size_t)j * a.nx + i]) continue;
+    const double mu = a.mux_d[i] + muy;
+    if (a.singular && i == 0 && j == 0) {
+      const double target = (a.gauge != nullptr) ? a.gauge_scale * (*a.gauge) : 0.0;
+      zsolve_column<MMAX, double, T, true>(tile, cidx, TI, a.nz, m, mu, sa, sb, sc, a.dzf, target);
+    } else {
+      zsolve_column<MMAX, double, T, false>(tile, cidx, TI, a.nz, m, mu, sa, sb, sc, nullptr, 0.0);
+    }
+  }
+  __syncthreads();
+  tile_store<T>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+}
+
+static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
+  ZArgs a;
+  a.nx = P->n[0];
+  a.ny = P->n[1];
+  a.nz = P->n[2];
+  a.ti = ti;
+  a.m = P->z_m;
+  a.singular = P->singular ? 1 : 0;
+  a.mask = nullptr;
+  a.mux_d = P->mux_d;
+  a.muy_d = P->muy_d;
+  a.mux_f = P->mux_f;
+  a.muy_f = P->muy_f;
+  a.dzf = P->dzf_d;
+  a.gauge = gauge;
+  a.gauge_scale = P->gauge_scale;
+  a.i_end = P->n[0];
+  a.j_end = P->n[1];
+  return a;
+}
+
+template <typename T, int MMAX>
+static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  const int vec = (P->n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
+  if (sizeof(T) == 4) {
+    // float columns first, then the double columns of the marked bounding box
+    ZArgs a = zargs(P, P->z_ti[1], gauge);
+    a.mask = P->mask_d;
+    const size_t smem = 3 * 32 * a.m * sizeof(float) + P->z_smem[1];
+    cudaError_t e = set_smem((const void*)zpass_f32_kernel<MMAX>, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
+    zpass_f32_kernel<MMAX><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ZArgs b = zargs(P, P->z_ti[1], gauge);
+    b.mask = P->mask_d;
+    const size_t smem64 = 3 * 32 * b.m * sizeof(double) + P->z_smem[1];
+    e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem64);
+    if (e != cudaSuccess) return e;
+    dim3 grid64((P->mask_i_end + b.ti - 1) / b.ti, P->mask_j_end);
+    if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec);
+    return cudaGetLastError();
+  }
+  ZArgs a = zargs(P, P->z_ti[0], gauge);
+  const size_t smem = 3 * 32 * a.m * sizeof(double) + P->z_smem[0];
+  cudaError_t e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
+  zpass_f64_kernel<T, MMAX><<<grid, 256, smem, st>>>(w, a, P->zt_d, vec);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  switch (P->z_mmax) {
+    case 1: return z_m<T, 1>(P, w, gauge, st);
+    case 2: return z_m<T, 2>(P, w, gauge, st);
+    case 4: return z_m<T, 4>(P, w, gauge, st);
+    case 8: return z_m<T, 8>(P, w, gauge, st);
+    default: return z_m<T, 16>(P, w, gauge, st);
+  }
+}
+
+template cudaError_t launch_z<double>(const cans_plan_s*, double*, const double*, cudaStream_t);
+template cudaError_t launch_z<float>(const cans_plan_s*, float*, const double*, cudaStream_t);
+
+}  // namespace cans

@@ -1,0 +1,465 @@
+// Shared-memory line transforms for the x and y passes of the eigenfunction-expansion solver
+// (the operator F^{x_i} of Eq. poi_reduced: real DFT for periodic, DCT-II/DST-II for Neumann /
+// Dirichlet walls, with the inverses DFT^-1, DCT-III, DST-III).
+//
+// A CTA holds `nl` lines (nl a power of two) of N = 2M reals in shared memory.  Each real line is
+// packed into M complex numbers (even -> real part, odd -> imaginary part), transformed by a
+// mixed-radix (2, 3, 4, 8) Stockham FFT of length M, and post-processed into the N real
+// coefficients (the standard half-length real-FFT split, plus Makhoul's 1980 reordering and
+// quarter-wave twiddle for the cosine/sine transforms).  Complex element m of line l lives at
+// phys(m, l) = m*nl + (l ^ (m & (nl-1))): lines are interleaved so that lanes of a warp that work
+// on different lines at the same m hit different banks, and the xor keeps the strided copy phases
+// from piling onto one bank.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cans {
+
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2 };
+
+template <typename T> struct V2;
+template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<double> { typedef double2 t; };
+
+template <typename T> __device__ __forceinline__ typename V2<T>::t mk2(T x, T y) {
+  typename V2<T>::t r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = fma(a.x, b.x, -a.y * b.y);
+  r.y = fma(a.x, b.y, a.y * b.x);
+  return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// multiply by -i
+template <typename C> __device__ __forceinline__ C cmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+
+// Per-direction line-transform tables (device pointers) and the FFT factorisation of M = N/2.
+template <typename T>
+struct LineTab {
+  const typename V2<T>::t* tw;    // M entries: exp(-2 pi i t / M)
+  const typename V2<T>::t* post;  // M+1 entries: exp(-2 pi i k / N)
+  const typename V2<T>::t* mak;   // M+1 entries: exp(-i pi k / (2N))
+  int n, m, bc, nst;
+  int radix[16];
+};
+
+struct Lay {
+  int nl;
+  __device__ __forceinline__ int c(int m, int l) const { return m * nl + (l ^ (m & (nl - 1))); }
+  // real slot s of line l inside the same storage (two reals per complex cell)
+  __device__ __forceinline__ int r(int s, int l) const { return 2 * c(s >> 1, l) + (s & 1); }
+};
+
+// position of input sample n inside the sequence fed to the half-length FFT
+//   periodic: identity.  Neumann / Dirichlet (Makhoul): even samples first in order, odd samples
+//   after them in reverse order.
+__device__ __forceinline__ int perm_in(int bc, int N, int n) {
+  if (bc == BC_P) return n;
+  return (n & 1) ? (N - 1 - (n >> 1)) : (n >> 1);
+}
+
+// ---- small DFTs (forward sign) --------------------------------------------------------------
+template <int R, typename C> struct Dft;
+template <typename C> struct Dft<2, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+template <typename C> struct Dft<3, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(v[0].x) T;
+    const T c1 = (T)-0.5, s1 = (T)-0.86602540378443864676372317075294;  // exp(-2 pi i/3)
+    C t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
+    C y0 = cadd(v[0], t);
+    C m;
+    m.x = fma(c1, t.x, v[0].x);
+    m.y = fma(c1, t.y, v[0].y);
+    C su;  // i * s1 * u
+    su.x = -s1 * u.y;
+    su.y = s1 * u.x;
+    v[0] = y0;
+    v[1] = cadd(m, su);
+    v[2] = csub(m, su);
+  }
+};
+template <typename C> struct Dft<4, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    C a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    C c = cadd(v[1], v[3]), d = cmi(csub(v[1], v[3]));
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, d);
+    v[3] = csub(b, d);
+  }
+};
+template <typename C> struct Dft<8, C> {
+  static __device__ __forceinline__ void run(C* v) {
+    typedef decltype(v[0].x) T;
+    const T r = (T)0.70710678118654752440084436210485;
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<4, C>::run(e);
+    Dft<4, C>::run(o);
+    // twiddles exp(-i pi k/4), k = 1, 2, 3
+    C o1;
+    o1.x = r * (o[1].x + o[1].y);
+    o1.y = r * (o[1].y - o[1].x);
+    C o2 = cmi(o[2]);
+    C o3;
+    o3.x = r * (o[3].y - o[3].x);
+    o3.y = -r * (o[3].x + o[3].y);
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+  }
+};
+
+// One Stockham radix-R stage over all nl lines, in place in shared memory.  Every thread first
+// loads and transforms its butterflies into registers, the CTA synchronises, then every thread
+// stores.  Requires nl*M <= MAXV*blockDim.x.
+template <int R, int MAXV, typename T>
+__device__ __forceinline__ void fft_stage(typename V2<T>::t* buf, const Lay& L, int lognl, int M, int Ns,
+                                          const typename V2<T>::t* __restrict__ tw) {
+  typedef typename V2<T>::t C;
+  constexpr int Q = (MAXV + R - 1) / R;
+  const int nb = M / R;
+  const int total = nb << lognl;
+  const int tstride = M / (Ns * R);
+  C v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = buf[L.c(j + r * nb, l)];
+      if (Ns > 1) {
+        const int k = j % Ns;
+        const int st = tstride * k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], __ldg(&tw[r * st]));
+      }
+      Dft<R, C>::run(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[L.c(base + r * Ns, l)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// ---- compile-time radix schedule for M = 2^a 3^b: threes first, then eights, then a 4 or a 2 ----
+__host__ __device__ constexpr int m_threes(int M) {
+  int n = 0;
+  while (M > 1 && M % 3 == 0) { M /= 3; ++n; }
+  return n;
+}
+__host__ __device__ constexpr int m_twos(int M) {
+  while (M > 1 && M % 3 == 0) M /= 3;
+  int n = 0;
+  while (M > 1 && M % 2 == 0) { M /= 2; ++n; }
+  return n;
+}
+__host__ __device__ constexpr int m_nst(int M) { return m_threes(M) + m_twos(M) / 3 + ((m_twos(M) % 3) ? 1 : 0); }
+__host__ __device__ constexpr int m_radix(int M, int s) {
+  return (s < m_threes(M)) ? 3 : (s < m_threes(M) + m_twos(M) / 3) ? 8 : ((m_twos(M) % 3 == 2) ? 4 : 2);
+}
+__host__ __device__ constexpr int m_ns(int M, int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= m_radix(M, i);
+  return p;
+}
+
+// Stage with compile-time length and stride (all index arithmetic folds to shifts and multiplies).
+template <int R, int MAXV, typename T, int M, int Ns>
+__device__ __forceinline__ void fft_stage_ct(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                             const typename V2<T>::t* __restrict__ tw) {
+  typedef typename V2<T>::t C;
+  constexpr int Q = (MAXV + R - 1) / R;
+  constexpr int nb = M / R;
+  constexpr int tstride = M / (Ns * R);
+  const int total = nb << lognl;
+  C v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = buf[L.c(j + r * nb, l)];
+      if (Ns > 1) {
+        const int k = j % Ns;
+        const int st = tstride * k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], __ldg(&tw[r * st]));
+      }
+      Dft<R, C>::run(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+      const int k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[L.c(base + r * Ns, l)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int MAXV, typename T, int M, int S, int NST>
+struct FftStages {
+  static __device__ __forceinline__ void run(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                             const typename V2<T>::t* tw) {
+    fft_stage_ct<m_radix(M, S), MAXV, T, M, m_ns(M, S)>(buf, L, lognl, tw);
+    FftStages<MAXV, T, M, S + 1, NST>::run(buf, L, lognl, tw);
+  }
+};
+template <int MAXV, typename T, int M, int NST>
+struct FftStages<MAXV, T, M, NST, NST> {
+  static __device__ __forceinline__ void run(typename V2<T>::t*, const Lay&, int, const typename V2<T>::t*) {}
+};
+
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void fft_lines(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  if (MC > 0) {
+    FftStages<MAXV, T, MC, 0, m_nst(MC)>::run(buf, L, lognl, tb.tw);
+    return;
+  }
+  int Ns = 1;
+  for (int s = 0; s < tb.nst; ++s) {
+    const int R = tb.radix[s];
+    if (R == 8)
+      fft_stage<8, MAXV, T>(buf, L, lognl, tb.m, Ns, tb.tw);
+    else if (R == 4)
+      fft_stage<4, MAXV, T>(buf, L, lognl, tb.m, Ns, tb.tw);
+    else if (R == 3)
+      fft_stage<3, MAXV, T>(buf, L, lognl, tb.m, Ns, tb.tw);
+    else
+      fft_stage<2, MAXV, T>(buf, L, lognl, tb.m, Ns, tb.tw);
+    Ns *= R;
+  }
+}
+
+// Output slots of the pair (k, M-k) of the forward post-processing (-1 = none).
+__device__ __forceinline__ void fwd_slots(int bc, int N, int M, int k, int s[4]) {
+  s[0] = s[1] = s[2] = s[3] = -1;
+  if (bc == BC_P) {
+    if (k == 0) { s[0] = 0; s[1] = N - 1; }
+    else {
+      s[0] = 2 * k - 1; s[1] = 2 * k;
+      if (k != M - k) { s[2] = 2 * (M - k) - 1; s[3] = 2 * (M - k); }
+    }
+  } else {
+    if (k == 0) { s[0] = 0; s[1] = M; }
+    else {
+      s[0] = k; s[1] = N - k;
+      if (k != M - k) { s[2] = M - k; s[3] = M + k; }
+    }
+    if (bc == BC_DD) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (s[e] >= 0) s[e] = N - 1 - s[e];
+    }
+  }
+}
+
+// Forward post-processing: buf holds FFT_M of the packed line; afterwards the storage holds the N
+// real output slots (read with Lay::r).  Pairs (k, M-k) are handled together:
+//   V_k = E_k + exp(-2 pi i k/N) O_k with E, O the even/odd half spectra (real-FFT split);
+//   periodic: slots carry Re/Im V_k;  cosine: Y_k = 2 Re(W^k V_k), Y_{N-k} = -2 Im(W^k V_k),
+//   W = exp(-i pi/(2N)) (Makhoul);  sine: the cosine result of the sign-alternated input, reversed.
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void post_forward(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  typedef typename V2<T>::t C;
+  constexpr int J = MAXV / 2 + 2;
+  const int M = MC > 0 ? MC : tb.m, N = 2 * M, half = M >> 1;
+  const int total = (half + 1) << lognl;
+  T val[J][4];
+  T* bufT = reinterpret_cast<T*>(buf);
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      if (k == 0) {
+        const C z = buf[L.c(0, l)];
+        const T v0 = z.x + z.y, vm = z.x - z.y;
+        if (tb.bc == BC_P) {
+          val[q][0] = v0;
+          val[q][1] = vm;
+        } else {
+          val[q][0] = (T)2 * v0;
+          val[q][1] = (T)1.41421356237309504880168872420970 * vm;
+        }
+        val[q][2] = val[q][3] = (T)0;
+      } else {
+        const C zk = buf[L.c(k, l)], zm = buf[L.c(M - k, l)];
+        C E, O;
+        E.x = (T)0.5 * (zk.x + zm.x);
+        E.y = (T)0.5 * (zk.y - zm.y);
+        O.x = (T)0.5 * (zk.y + zm.y);
+        O.y = (T)-0.5 * (zk.x - zm.x);
+        const C wO = cmul(__ldg(&tb.post[k]), O);
+        const C vk = cadd(E, wO);
+        const C vmk = cconj(csub(E, wO));
+        if (tb.bc == BC_P) {
+          val[q][0] = vk.x;
+          val[q][1] = vk.y;
+          val[q][2] = vmk.x;
+          val[q][3] = vmk.y;
+        } else {
+          const C a = cmul(__ldg(&tb.mak[k]), vk);
+          const C b = cmul(__ldg(&tb.mak[M - k]), vmk);
+          val[q][0] = (T)2 * a.x;
+          val[q][1] = (T)-2 * a.y;
+          val[q][2] = (T)2 * b.x;
+          val[q][3] = (T)-2 * b.y;
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      int s[4];
+      fwd_slots(tb.bc, N, M, k, s);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (s[e] >= 0) bufT[L.r(s[e], l)] = val[q][e];
+    }
+  }
+  __syncthreads();
+}
+
+// Inverse pre-processing: storage holds the N real slots; afterwards buf holds conj(Z) where
+// IFFT_M(Z) is the packed line times N (the caller runs the forward FFT and conjugates back).
+//   periodic: Z_k = (X_k + conj X_{M-k}) + i exp(2 pi i k/N) (X_k - conj X_{M-k});
+//   cosine / sine: first V_k = W^{-k} (Y_k - i Y_{N-k}) / 2, then the same with X = V.
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void pre_inverse(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  typedef typename V2<T>::t C;
+  constexpr int J = MAXV / 2 + 2;
+  const int M = MC > 0 ? MC : tb.m, N = 2 * M, half = M >> 1;
+  const int total = (half + 1) << lognl;
+  C zk_out[J], zm_out[J];
+  const T* bufT = reinterpret_cast<const T*>(buf);
+  const bool dd = (tb.bc == BC_DD);
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      C xk, xm;
+      if (tb.bc == BC_P) {
+        if (k == 0) {
+          xk = mk2<T>(bufT[L.r(0, l)], (T)0);
+          xm = mk2<T>(bufT[L.r(N - 1, l)], (T)0);  // X_M
+        } else {
+          xk = mk2<T>(bufT[L.r(2 * k - 1, l)], bufT[L.r(2 * k, l)]);
+          xm = mk2<T>(bufT[L.r(2 * (M - k) - 1, l)], bufT[L.r(2 * (M - k), l)]);
+        }
+      } else {
+#define SLOT(q_) (dd ? (N - 1 - (q_)) : (q_))
+        if (k == 0) {
+          xk = mk2<T>((T)0.5 * bufT[L.r(SLOT(0), l)], (T)0);
+          xm = mk2<T>((T)0.70710678118654752440084436210485 * bufT[L.r(SLOT(M), l)], (T)0);  // V_M
+        } else {
+          const C yk = mk2<T>((T)0.5 * bufT[L.r(SLOT(k), l)], (T)-0.5 * bufT[L.r(SLOT(N - k), l)]);
+          const C ym = mk2<T>((T)0.5 * bufT[L.r(SLOT(M - k), l)], (T)-0.5 * bufT[L.r(SLOT(M + k), l)]);
+          xk = cmul(cconj(__ldg(&tb.mak[k])), yk);
+          xm = cmul(cconj(__ldg(&tb.mak[M - k])), ym);
+        }
+#undef SLOT
+      }
+      if (k == 0) {
+        zk_out[q] = mk2<T>(xk.x + xm.x, xk.x - xm.x);
+      } else {
+        const C A = cadd(xk, cconj(xm));
+        const C B = csub(xk, cconj(xm));
+        const C wB = cmul(cconj(__ldg(&tb.post[k])), B);  // exp(+2 pi i k/N) B
+        const C iwB = mk2<T>(-wB.y, wB.x);                 // times i
+        zk_out[q] = cadd(A, iwB);
+        zm_out[q] = cconj(csub(A, iwB));
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      buf[L.c(k, l)] = cconj(zk_out[q]);
+      if (k != 0 && k != M - k) buf[L.c(M - k, l)] = cconj(zm_out[q]);
+    }
+  }
+  __syncthreads();
+}
+
+// Value of output sample n of the inverse transform (times N), after pre_inverse + fft_lines.
+template <typename T, int MC = 0>
+__device__ __forceinline__ T inverse_sample(const typename V2<T>::t* buf, const Lay& L, const LineTab<T>& tb, int n,
+                                            int l) {
+  const int s = perm_in(tb.bc, MC > 0 ? 2 * MC : tb.n, n);
+  const T* bufT = reinterpret_cast<const T*>(buf);
+  T v = bufT[L.r(s, l)];
+  if (s & 1) v = -v;  // conjugate back
+  if (tb.bc == BC_DD && (n & 1)) v = -v;
+  return v;
+}
+
+// Store input sample n of line l (forward transform) into the packed position.
+template <typename T, int MC = 0>
+__device__ __forceinline__ void forward_store(typename V2<T>::t* buf, const Lay& L, const LineTab<T>& tb, int n, int l,
+                                              T v) {
+  const int s = perm_in(tb.bc, MC > 0 ? 2 * MC : tb.n, n);
+  if (tb.bc == BC_DD && (n & 1)) v = -v;
+  reinterpret_cast<T*>(buf)[L.r(s, l)] = v;
+}
+
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void line_forward(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  if (MC == 0 && tb.n < 2) return;
+  fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
+  post_forward<MAXV, T, MC>(buf, L, lognl, tb);
+}
+
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void line_inverse(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  if (MC == 0 && tb.n < 2) return;
+  pre_inverse<MAXV, T, MC>(buf, L, lognl, tb);
+  fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
+}
+
+}  // namespace cans

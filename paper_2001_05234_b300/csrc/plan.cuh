@@ -1,0 +1,120 @@
+// Plan object shared by the host code and the pass launchers (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "cans.h"
+#include "dfloat.cuh"
+#include "lines.cuh"
+#include "zsolve.cuh"
+
+namespace cans {
+
+struct DirHost {
+  int n = 1, m = 0, bc = 0, nst = 0;
+  int radix[16] = {0};
+};
+
+struct Launch {
+  int nl = 1, lognl = 0, threads = 32;
+  size_t smem = 0;
+};
+
+// Stencil coefficients for the residual r = f - L_h p (Eq. poi with a non-uniform z).
+struct StencilDF {
+  df idx2, idy2;
+  const float *sa_hi, *sa_lo, *sc_hi, *sc_lo;  // z: a_k (to k-1), c_k (to k+1), wall ghosts included
+  int bc[3];
+  int n[3];
+};
+
+struct XArgs {
+  int nx, nlines, lognl;
+  double scale;  // inverse only
+};
+
+struct ZArgs {
+  int nx, ny, nz, ti, m;
+  int singular;               // the (0,0) mode is singular (Neumann z, no Dirichlet direction)
+  const unsigned char* mask;  // mixed: 1 = solve this column in double
+  const double* mux_d;
+  const double* muy_d;
+  const float* mux_f;
+  const float* muy_f;
+  const double* dzf;
+  const double* gauge;  // optional: target weighted column mean = gauge_scale * (*gauge)
+  double gauge_scale;
+  int j_end, i_end;     // FP64-column kernel: bounding box of the columns it owns
+};
+
+}  // namespace cans
+
+struct cans_plan_s {
+  int n[3];
+  double len[2];
+  int bc[3];
+  cans_opts opts;
+  int device = 0;
+  bool singular = false;
+  cans::DirHost dx, dy;
+  std::vector<double> mux_h, muy_h;
+  void* dtab = nullptr;
+  cans::LineTab<double> tx_d, ty_d;
+  cans::LineTab<float> tx_f, ty_f;
+  cans::ZTab<double> zt_d;
+  cans::ZTab<float> zt_f;
+  const double *mux_d, *muy_d, *dzf_d, *sa_d, *sc_d;
+  const float* dzf_f;
+  const float* dzf_flo;  // dzf - (float)dzf
+  double gauge_scale = 0;
+  const float *mux_f, *muy_f, *sa_hi, *sa_lo, *sc_hi, *sc_lo;
+  const unsigned char* mask_d = nullptr;
+  int mask_i_end = 0, mask_j_end = 0;  // bounding box of the double-precision columns (mixed)
+  double* acc_d = nullptr;             // [0] |f|^2, [1+s] |r_s|^2, [nacc-5] gauge sum, [nacc-4..] reports
+  int nacc = 0;
+  double idx2, idy2;
+  cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
+  int z_ti[2], z_m, z_mmax;
+  size_t z_smem[2];
+  // per-pass event records (cans_plan_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // pass kind of record r (events 2r, 2r+1)
+  int ev_used = 0;
+};
+
+namespace cans {
+
+// pass launchers (each in its own translation unit)
+template <typename T, int MODE>
+cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
+                        double* acc, cudaStream_t st);
+template <typename T, int MODE>
+cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
+                        double* gauge, cudaStream_t st);
+template <typename T, int DIR>
+cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st);
+template <typename T>
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
+cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st);
+cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st);
+
+StencilDF stencil_df(const cans_plan_s* P);
+
+inline cudaError_t set_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T> const LineTab<T>& tab_x(const cans_plan_s* P);
+template <> inline const LineTab<double>& tab_x<double>(const cans_plan_s* P) { return P->tx_d; }
+template <> inline const LineTab<float>& tab_x<float>(const cans_plan_s* P) { return P->tx_f; }
+template <typename T> const LineTab<T>& tab_y(const cans_plan_s* P);
+template <> inline const LineTab<double>& tab_y<double>(const cans_plan_s* P) { return P->ty_d; }
+template <> inline const LineTab<float>& tab_y<float>(const cans_plan_s* P) { return P->ty_f; }
+
+// Compile-time FFT lengths (M = N/2) that get specialised kernels; others use the runtime path.
+#define CANS_FOR_EACH_M(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(256) X(512)
+
+}  // namespace cans

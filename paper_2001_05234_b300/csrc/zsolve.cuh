@@ -1,0 +1,213 @@
+// Tridiagonal solves along z, one per (x, y) mode (Eq. poi_reduced; Gauss elimination along a
+// non-uniform z grid).
+//
+// A CTA stages a tile of TI consecutive x-slots x Nz rows (one y-slot) in shared memory with
+// coalesced loads, then one warp solves one column at a time: lane p owns the contiguous rows
+// [p*m, p*m + m) (m = ceil(Nz/32)).  Each lane eliminates its own rows, expressing them through the
+// last unknown of the previous lane's segment and of its own segment (a partitioned Thomas
+// solve); the 32 interface unknowns form a tridiagonal system that the warp solves by parallel
+// cyclic reduction over shuffles; each lane then back-substitutes its rows.  Rows past Nz are
+// identity rows.  The column's precision C (float or double) is independent of the storage type.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace cans {
+
+template <typename T>
+struct ZTab {
+  const T* a;  // sub-diagonal a_k (a_0 = 0 at a wall)
+  const T* b;  // diagonal b_k (without mu)
+  const T* c;  // super-diagonal c_k (c_{Nz-1} = 0 at a wall)
+};
+
+// Reciprocal: approximate (one MUFU op, ~1 ulp) for float columns -- the mixed path corrects the
+// float solve by refinement anyway -- and IEEE division for double columns.
+__device__ __forceinline__ float rcp_(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+
+// Swizzled position of (row k, column i) inside the [Nz][TI] tile: lane p = k / m reads column w of
+// its rows at bank w ^ p.
+__device__ __forceinline__ int ztile_idx(int k, int i, int TI, int m) { return k * TI + (i ^ ((k / m) & (TI - 1))); }
+
+// Per-CTA copy of the z rows in lane-major order: row k = lane*m + r sits at [r*32 + lane], so the 32
+// lanes of a warp read 32 consecutive words.  Rows past Nz become identity rows (a = c = 0, b = 1).
+template <typename C, typename S>
+__device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& zt, int Nz, int m) {
+  for (int q = threadIdx.x; q < 32 * m; q += blockDim.x) {
+    const int lane = q & 31, r = q >> 5;
+    const int k = lane * m + r;
+    const bool in = k < Nz;
+    sa[q] = in ? (C)zt.a[k] : (C)0;
+    sb[q] = in ? (C)zt.b[k] : (C)1;
+    sc[q] = in ? (C)zt.c[k] : (C)0;
+  }
+}
+
+// Solve one column (tile column `col`) in precision C with rows staged by stage_zrows.
+// mu is the x-y eigenvalue term of the mode.  SING: the singular Neumann mode -- the right-hand side
+// is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
+// x = 0, and the result is shifted to the dzf-weighted mean `target`.
+template <int MMAX, typename C, typename T, bool SING>
+__device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, int m, C mu, const C* sa,
+                                              const C* sb, const C* sc, const double* weights, C target) {
+  const int lane = threadIdx.x & 31;
+  const int k0 = lane * m;
+  const unsigned full = 0xffffffffu;
+  C proj = 0;
+  if (SING) {
+    C sw = 0, swd = 0;
+    for (int r = 0; r < m; ++r) {
+      const int k = k0 + r;
+      if (k < Nz) {
+        const C w = (C)weights[k];
+        sw += w;
+        swd += w * (C)tile[ztile_idx(k, col, TI, m)];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sw += __shfl_xor_sync(full, sw, o);
+      swd += __shfl_xor_sync(full, swd, o);
+    }
+    proj = swd / sw;
+  }
+  C cp[MMAX], dp[MMAX], lp[MMAX];
+  C rr = 0;
+  // local forward elimination over rows r = 0..m-2 of the segment
+  C cprev = 0, dprev = 0, lprev = 0;
+#pragma unroll
+  for (int r = 0; r < MMAX; ++r) {
+    if (r < m - 1) {
+      const int k = k0 + r;
+      C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + mu, c = sc[r * 32 + lane], d = 0;
+      if (k < Nz) d = (C)tile[ztile_idx(k, col, TI, m)] - proj;
+      if (SING && k == Nz - 1) {
+        a = 0;
+        b = 1;
+        c = 0;
+        d = 0;
+      }
+      const C inv = rcp_(b - a * cprev);
+      const bool last_inner = (r == m - 2);
+      cp[r] = last_inner ? (C)0 : c * inv;
+      if (last_inner) rr = -c * inv;
+      dp[r] = (d - a * dprev) * inv;
+      lp[r] = ((r == 0) ? -a : -a * lprev) * inv;
+      cprev = c * inv;
+      dprev = dp[r];
+      lprev = lp[r];
+    }
+  }
+  // backward sweep for the expressions x_r = D + V E_prev + W E_own at r = m-2 and r = 0
+  C Dl = 0, Vl = 1, Wl = 0, Df = 0, Vf = 0, Wf = 1;
+  if (m >= 2) {
+    C D = 0, V = 0, W = 0;
+#pragma unroll
+    for (int r = MMAX - 1; r >= 0; --r) {
+      if (r <= m - 2) {
+        if (r == m - 2) {
+          D = dp[r];
+          V = lp[r];
+          W = rr;
+          Dl = D;
+          Vl = V;
+          Wl = W;
+        } else {
+          D = dp[r] - cp[r] * D;
+          V = lp[r] - cp[r] * V;
+          W = -cp[r] * W;
+        }
+      }
+    }
+    Df = D;
+    Vf = V;
+    Wf = W;
+  }
+  // this segment's last row ties the interface unknowns together
+  const int kl = k0 + m - 1;
+  const int rl = m - 1;
+  C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + mu, cl = sc[rl * 32 + lane], dl = 0;
+  if (kl < Nz) dl = (C)tile[ztile_idx(kl, col, TI, m)] - proj;
+  if (SING && kl == Nz - 1) {
+    al = 0;
+    bl = 1;
+    cl = 0;
+    dl = 0;
+  }
+  const C Dfn = __shfl_down_sync(full, Df, 1);
+  const C Vfn = __shfl_down_sync(full, Vf, 1);
+  const C Wfn = __shfl_down_sync(full, Wf, 1);
+  C alpha = (lane == 0) ? (C)0 : al * Vl;
+  C beta = bl + al * Wl + ((lane < 31) ? cl * Vfn : (C)0);
+  C gamma = (lane < 31) ? cl * Wfn : (C)0;
+  C delta = dl - al * Dl - ((lane < 31) ? cl * Dfn : (C)0);
+  // parallel cyclic reduction of the 32 interface equations
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    C am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
+    C gm = __shfl_up_sync(full, gamma, s), dm = __shfl_up_sync(full, delta, s);
+    C ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
+    C gp = __shfl_down_sync(full, gamma, s), dpv = __shfl_down_sync(full, delta, s);
+    if (lane < s) { am = 0; bm = 1; gm = 0; dm = 0; }
+    if (lane + s > 31) { ap = 0; bp = 1; gp = 0; dpv = 0; }
+    const C k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
+    const C na = -am * k1, ng = -gp * k2;
+    const C nb = beta - gm * k1 - ap * k2;
+    const C nd = delta - dm * k1 - dpv * k2;
+    alpha = na;
+    beta = nb;
+    gamma = ng;
+    delta = nd;
+  }
+  const C E = delta * rcp_(beta);
+  C Ep = __shfl_up_sync(full, E, 1);
+  if (lane == 0) Ep = 0;
+  // back-substitution
+  C x[MMAX];
+  C xn = E;
+#pragma unroll
+  for (int r = MMAX - 1; r >= 0; --r) {
+    if (r <= m - 2) {
+      if (r == m - 2)
+        xn = dp[r] + lp[r] * Ep + rr * E;
+      else
+        xn = dp[r] + lp[r] * Ep - cp[r] * xn;
+      x[r] = xn;
+    }
+  }
+  C shift = 0;
+  if (SING) {
+    C sw = 0, swx = 0;
+#pragma unroll
+    for (int r = 0; r < MMAX; ++r) {
+      if (r < m) {
+        const int k = k0 + r;
+        if (k < Nz) {
+          const C xv = (r == m - 1) ? E : x[r];
+          const C w = (C)weights[k];
+          sw += w;
+          swx += w * xv;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sw += __shfl_xor_sync(full, sw, o);
+      swx += __shfl_xor_sync(full, swx, o);
+    }
+    shift = swx / sw - target;
+  }
+#pragma unroll
+  for (int r = 0; r < MMAX; ++r) {
+    if (r < m) {
+      const int k = k0 + r;
+      if (k < Nz) tile[ztile_idx(k, col, TI, m)] = (T)(((r == m - 1) ? E : x[r]) - shift);
+    }
+  }
+}
+
+}  // namespace cans

@@ -1,0 +1,269 @@
+"""GPU parity of the Poisson path (through the C ABI) against the CPU oracle and library transforms."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle
+from paper_2001_05234_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+P, NN, DD = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def cans():
+    from paper_2001_05234_b300 import build_lib
+
+    build_lib.build()
+    import paper_2001_05234_b300 as C
+
+    return C
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    import torch
+
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def stream():
+    import torch
+
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def ref_forward(x, bc, axis):
+    """Unnormalised forward transform in the library's slot order (scipy / numpy definitions)."""
+    if bc == NN:
+        return scipy.fft.dct(x, type=2, axis=axis)
+    if bc == DD:
+        return scipy.fft.dst(x, type=2, axis=axis)
+    n = x.shape[axis]
+    X = np.fft.rfft(x, axis=axis)
+    X = np.moveaxis(X, axis, -1)
+    out = np.empty(X.shape[:-1] + (n,))
+    out[..., 0] = X[..., 0].real
+    for k in range(1, n // 2):
+        out[..., 2 * k - 1] = X[..., k].real
+        out[..., 2 * k] = X[..., k].imag
+    if n > 1:
+        out[..., n - 1] = X[..., n // 2].real
+    return np.moveaxis(out, -1, axis)
+
+
+def make_plan(cans, n, bc, L=(1.0, 1.0), dzf=None, prec=0, sweeps=2, frac=0.01):
+    o = cans.cans_opts_default()
+    o.prec, o.max_sweeps, o.fp64_mode_fraction = prec, sweeps, frac
+    _, h = cans.cans_poisson_plan(n, L, bc, dzf, o)
+    return h
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------------------------
+# transforms (x then y) against numpy / scipy
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bcx,bcy", list(itertools.product((P, NN, DD), (P, NN, DD))))
+@pytest.mark.parametrize("n", [(16, 8, 3), (48, 96, 2), (1024, 64, 1), (2, 6, 2)])
+def test_transform_xy_matches_library_transforms(cans, bcx, bcy, n):
+    h = make_plan(cans, n, (bcx, bcy, NN))
+    x = np.random.default_rng(1).standard_normal((n[2], n[1], n[0]))
+    t = dev(x)
+    assert cans.cans_transform_xy(h, t.data_ptr(), 1, stream()) == 0
+    want = ref_forward(ref_forward(x, bcx, 2), bcy, 1)
+    got = host(t)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    assert cans.cans_transform_xy(h, t.data_ptr(), -1, stream()) == 0
+    back = host(t)
+    assert np.abs(back - n[0] * n[1] * x).max() <= 1e-13 * n[0] * n[1] * np.abs(x).max()
+    cans.cans_plan_destroy(h)
+
+
+# ---------------------------------------------------------------------------------------------
+# z tridiagonal pass against the oracle's rows and Thomas
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nz", [1, 2, 5, 33, 64, 200, 512])
+@pytest.mark.parametrize("bcz", [NN, DD])
+def test_zsolve_matches_thomas(cans, nz, bcz):
+    n = (48, 6, nz)
+    bc = (P, DD, bcz)
+    dzf = I.tanh_dzf(nz, 1.6) if nz > 1 else np.ones(1)
+    h = make_plan(cans, n, bc, (1.3, 0.9), dzf)
+    g = np.random.default_rng(nz).standard_normal((nz, n[1], n[0]))
+    t = dev(g)
+    assert cans.cans_zsolve(h, t.data_ptr(), stream()) == 0
+    got = host(t)
+    _, lx = oracle.eigenbasis(bc[0], n[0])
+    _, ly = oracle.eigenbasis(bc[1], n[1])
+    mux = lx / (1.3 / n[0]) ** 2
+    muy = ly / (0.9 / n[1]) ** 2
+    a, b, c = oracle.z_rows(bcz, dzf)
+    want = np.empty_like(g)
+    for j in range(n[1]):
+        for i in range(n[0]):
+            want[:, j, i] = oracle.thomas(a, b + mux[i] + muy[j], c, g[:, j, i])
+    assert rel(got, want) < 1e-12
+    cans.cans_plan_destroy(h)
+
+
+def test_plan_eigenvalues_match_oracle(cans):
+    n = (24, 12, 4)
+    h = make_plan(cans, n, (P, DD, NN), (2.0, 3.0))
+    mx, my = cans.cans_plan_eigenvalues(h, 24, 12)
+    _, lx = oracle.eigenbasis(P, 24)
+    _, ly = oracle.eigenbasis(DD, 12)
+    assert np.abs(mx - lx / (2.0 / 24) ** 2).max() < 1e-12 * np.abs(mx).max()
+    assert np.abs(my - ly / (3.0 / 12) ** 2).max() < 1e-12 * np.abs(my).max()
+    cans.cans_plan_destroy(h)
+
+
+# ---------------------------------------------------------------------------------------------
+# full FP64 solve against the oracle
+# ---------------------------------------------------------------------------------------------
+def solve_gpu(cans, f, n, bc, L, dzf, prec=0, sweeps=2, frac=0.01, info=False):
+    import torch
+
+    h = make_plan(cans, n, bc, L, dzf, prec, sweeps, frac)
+    nbytes = cans.cans_poisson_workspace_size(h)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    wp = (ws.data_ptr() + 255) // 256 * 256 if nbytes else 0
+    ft = dev(f)
+    pt = torch.full_like(ft, float("nan"))
+    buf = np.zeros(sweeps + 2) if info else None
+    st = cans.cans_poisson_solve(h, ft.data_ptr(), pt.data_ptr(), wp, stream(), buf)
+    p = host(pt)
+    cans.cans_plan_destroy(h)
+    return p, st, buf
+
+
+def test_uniform32_fp64_matches_oracle(cans):
+    case = I.case_uniform32()
+    f = I.rhs_host(case)
+    p, st, info = solve_gpu(cans, f, case.n, case.bc, case.length_xy, case.dzf, info=True)
+    assert st == 0
+    ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf)
+    assert rel(p, ref) <= 1e-12
+    assert oracle.relative_residual(p, f, case.bc, case.length_xy, case.dzf) <= 1e-13
+    assert info[0] <= 1e-13  # the library's own residual report agrees
+
+
+def test_dense_lu_8cubed_copy(cans):
+    from tests.test_oracle_pins import dense_operator, dense_solve, volumes
+
+    case = I.case_uniform32(n=(8, 8, 8))
+    f = I.rhs_host(case)
+    A = dense_operator(case.n, case.bc, case.length_xy, case.dzf)
+    ref = dense_solve(A, f.ravel(), volumes(case.n, case.length_xy, case.dzf)).reshape(f.shape)
+    p, st, _ = solve_gpu(cans, f, case.n, case.bc, case.length_xy, case.dzf)
+    assert st == 0 and rel(p, ref) <= 1e-12
+
+
+BC_CASES = [(bx, by, bz) for bx in (P, NN, DD) for by in (P, NN, DD) for bz in (NN, DD)]
+
+
+@pytest.mark.parametrize("bc", BC_CASES)
+def test_fp64_solve_all_boundary_conditions(cans, bc):
+    n = (48, 24, 20)  # radix-3 lengths, a ragged z segment, x tiles with a tail
+    dzf = I.tanh_dzf(20, 1.8)
+    L = (1.5, 0.75)
+    f = np.random.default_rng(sum(bc)).uniform(-1, 1, (20, 24, 48))
+    if DD not in bc:
+        f = I.weighted_mean_removed(f, dzf)
+    p, st, _ = solve_gpu(cans, f, n, bc, L, dzf)
+    assert st == 0
+    ref = oracle.poisson_solve(f, bc, L, dzf)
+    assert rel(p, ref) <= 1e-12
+
+
+@pytest.mark.parametrize(
+    "n,bc",
+    [
+        ((1, 1, 17), (P, P, DD)),  # pure z problem
+        ((1, 8, 8), (NN, P, NN)),  # one x cell
+        ((8, 1, 8), (DD, NN, NN)),  # one y cell
+        ((8, 8, 1), (P, DD, NN)),  # one z cell
+        ((2, 2, 2), (P, P, NN)),  # smallest even lengths, singular
+        ((64, 96, 31), (P, NN, DD)),  # radix 3 in y, odd Nz
+        ((16, 16, 512), (P, P, NN)),  # 16 rows per lane
+    ],
+)
+def test_fp64_solve_edge_shapes(cans, n, bc):
+    nx, ny, nz = n
+    dzf = I.tanh_dzf(nz, 1.4) if nz > 2 else I.uniform_dzf(nz)
+    f = np.random.default_rng(nx + 7 * ny + 13 * nz).uniform(-1, 1, (nz, ny, nx))
+    if DD not in bc:
+        f = I.weighted_mean_removed(f, dzf)
+    p, st, _ = solve_gpu(cans, f, n, bc, (1.0, 1.0), dzf)
+    assert st == 0
+    ref = oracle.poisson_solve(f, bc, (1.0, 1.0), dzf)
+    assert rel(p, ref) <= 1e-12
+
+
+def test_in_place_fp64(cans):
+    import torch
+
+    case = I.case_channel(n=(64, 32, 16))
+    f = I.rhs_host(case)
+    h = make_plan(cans, case.n, case.bc, case.length_xy, case.dzf)
+    t = dev(f)
+    assert cans.cans_poisson_solve(h, t.data_ptr(), t.data_ptr(), 0, stream(), None) == 0
+    ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf)
+    assert rel(host(t), ref) <= 1e-12
+    cans.cans_plan_destroy(h)
+
+
+def test_incompatible_rhs_is_reported(cans):
+    case = I.case_uniform32(n=(16, 16, 8))
+    f = I.rhs_host(case) + 0.3  # non-zero mean on a singular problem
+    p, st, info = solve_gpu(cans, f, case.n, case.bc, case.length_xy, case.dzf, info=True)
+    assert st == -5
+    # the returned p still solves the compatible part and has zero weighted mean
+    fc = I.weighted_mean_removed(f, case.dzf)
+    assert rel(p, oracle.poisson_solve(fc, case.bc, case.length_xy, case.dzf)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# mixed precision + refinement
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [(P, P, NN), (P, DD, NN), (NN, DD, DD), (DD, NN, NN)])
+def test_mixed_refined_reaches_fp64_accuracy(cans, bc):
+    n = (64, 48, 40)
+    dzf = I.tanh_dzf(40, 1.8)
+    case = I.case_modes(n=n)
+    case.bc = bc
+    case.dzf = dzf
+    f = I.rhs_host(case)
+    p, st, info = solve_gpu(cans, f, n, bc, (1.0, 1.0), dzf, prec=1, sweeps=2, info=True)
+    ref = oracle.poisson_solve(f, bc, (1.0, 1.0), dzf)
+    res = oracle.relative_residual(p, f, bc, (1.0, 1.0), dzf)
+    floor = oracle.relative_residual(ref, f, bc, (1.0, 1.0), dzf)
+    d = p - ref
+    w = dzf[:, None, None] * np.ones_like(d)
+    offset = float((d * w).sum() / w.sum())
+    diag = dict(res=res, floor=floor, info=info, rel=rel(p, ref), offset_rel=offset / np.abs(ref).max(),
+                rel_without_offset=rel(p - offset, ref))
+    assert res <= max(1e-12, 2 * floor), diag
+    assert rel(p, ref) <= 1e-11, diag
+    assert info[0] > info[1], info
+    assert st == 0
+
+
+def test_mixed_first_solve_only(cans):
+    case = I.case_modes(n=(32, 32, 16))
+    f = I.rhs_host(case)
+    p, st, info = solve_gpu(cans, f, case.n, case.bc, case.length_xy, case.dzf, prec=1, sweeps=0, info=True)
+    ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf)
+    assert rel(p, ref) < 1e-4  # FP32 transforms alone
+    assert st == -6  # tolerance 1e-12 not reached without refinement
