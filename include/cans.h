@@ -148,6 +148,28 @@ enum cans_pass {
 int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);
 
+/*
+ * cans_poisson_solve_noalloc -- the solve for callers that cannot allocate device memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * Some callers cannot call cudaMalloc: a plugin inside a framework that owns the whole device
+ * memory pool, code under a device-memory budget fixed at start-up, or a time-critical loop where
+ * an allocation (which can wait for the device to go idle) is not acceptable.  Such a caller passes
+ * f and p as for cans_poisson_solve but no workspace: the library uses a fixed scratch array of
+ * cans_noalloc_scratch_bytes() bytes (48 MiB: mixed-precision problems up to 4,194,304 points) that
+ * every GPU loading the library holds until the process exits.
+ *   - Arguments and results are those of cans_poisson_solve (info as there).
+ *   - A plan whose workspace exceeds the scratch size is rejected with CANS_ERR_WORKSPACE before any
+ *     work is enqueued.  FP64 plans need no scratch and always fit.
+ *   - The first call on each device looks up the scratch array's device address (with that device
+ *     current); make that first call before any stream capture begins.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (several streams or threads
+ *     at once) race on it and must be serialised by the caller.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ */
+int cans_poisson_solve_noalloc(cans_plan_t plan, const double* f, double* p, void* cuda_stream, double* info);
+size_t cans_noalloc_scratch_bytes(void);
+
 /* Host copies of the per-slot eigenvalue terms lam_x(i)/dx^2 (length Nx) and lam_y(j)/dy^2
  * (length Ny) the plan uses; either pointer may be NULL. */
 int cans_plan_eigenvalues(cans_plan_t plan, double* mu_x, double* mu_y);

@@ -59,6 +59,9 @@ def lib() -> ctypes.CDLL:
         L.cans_zsolve.argtypes = [vp, vp, vp]
         L.cans_plan_eigenvalues.argtypes = [vp, dp, dp]
         L.cans_plan_profile.argtypes = [vp, ctypes.c_int]
+        L.cans_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp, dp]
+        L.cans_noalloc_scratch_bytes.argtypes = []
+        L.cans_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.cans_plan_profile_read.argtypes = [vp, ctypes.c_int, dp, ip]
         _lib = L
     return _lib
@@ -113,6 +116,17 @@ def cans_poisson_solve(plan, f_ptr: int, p_ptr: int, workspace_ptr: int, stream_
     """Returns the status; info (numpy float64 array of max_sweeps+2) is filled when given."""
     return lib().cans_poisson_solve(plan, f_ptr, p_ptr, workspace_ptr or None, stream_ptr or None,
                                     _dptr(info) if info is not None else None)
+
+
+def cans_poisson_solve_noalloc(plan, f_ptr: int, p_ptr: int, stream_ptr: int, info=None) -> int:
+    """cans_poisson_solve without a caller workspace: the library's fixed scratch array is used
+    (for callers that cannot allocate device memory).  Calls that overlap on the GPU race."""
+    return lib().cans_poisson_solve_noalloc(plan, f_ptr, p_ptr, stream_ptr or None,
+                                            _dptr(info) if info is not None else None)
+
+
+def cans_noalloc_scratch_bytes() -> int:
+    return int(lib().cans_noalloc_scratch_bytes())
 
 
 def cans_plan_destroy(plan) -> int:
