@@ -149,6 +149,44 @@ int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);
 
 /*
+ * Fractional-step pieces for a channel plan (bc = {CANS_BC_P, CANS_BC_P, CANS_BC_NN}: x and y
+ * periodic, no-slip walls at z = 0 and z = Lz).  Velocities live on the faces of the staggered grid
+ * (u on the x-face between cells i and i+1, v on the y-face between j and j+1, w on the z-face between
+ * k and k+1, w[Nz-1] being the top wall, kept at 0), p at cell centres; all Nx*Ny*Nz doubles, x fastest.
+ *
+ * cans_rk3_step: one explicit low-storage RK3 step (Eq. up with alpha = {8/15, 5/12, 3/4},
+ * beta = {0, -17/60, -5/12}, gamma = alpha + beta; Eq. poi_ns solved with the plan; correction
+ * u = u* - gamma dt G Phi and p += Phi), in place on u, v, w, p.  Advection is the conservative
+ * divergence of u (x) u with two-point averages, diffusion the 3-point Laplacian with no-slip ghosts.
+ * dt = cfl * min(sqrt(3)/dti, 1.65 dl^2/nu) from the state at the start of the step (Eq. dt and the
+ * chkdt listing, reduced on the device), or params->dt when > 0.  With params->forcing != 0, u is
+ * shifted to bulk velocity params->ubulk after every substage (constant flow rate).  dt_dev: device
+ * double that receives dt (NULL: kept in the workspace).  workspace: cans_rk3_workspace_size()
+ * bytes, 256-byte aligned.  Asynchronous; no host synchronisation inside.
+ */
+typedef struct {
+  double nu;    /* kinematic viscosity > 0 */
+  double cfl;   /* Courant factor > 0 applied to the stability bound */
+  double ubulk; /* bulk velocity kept by the forcing */
+  double dt;    /* > 0: fixed time step; <= 0: computed */
+  int forcing;  /* 1: constant-flow-rate forcing */
+} cans_rk3_params;
+int cans_rk3_workspace_size(cans_plan_t plan, size_t* bytes);
+int cans_rk3_step(cans_plan_t plan, double* u, double* v, double* w, double* p, const cans_rk3_params* params,
+                  double* dt_dev, void* workspace, void* cuda_stream);
+
+/*
+ * cans_project: in place, u <- P u = u - G L^-1 D u, the discretely divergence-free part of a face field
+ * (the correction of Eq. poi_ns with gamma dt cancelled).  cans_project_adjoint: u <- P^T u =
+ * W_f P W_f^-1 u with W_f the face volumes (dzf for u and v faces, the centre distance for w faces),
+ * which is the transpose because P is self-adjoint in the W_f inner product (D^T W_c = -W_f G).
+ * Channel plans only.  workspace: cans_project_workspace_size() bytes, 256-byte aligned.
+ */
+int cans_project_workspace_size(cans_plan_t plan, size_t* bytes);
+int cans_project(cans_plan_t plan, double* u, double* v, double* w, void* workspace, void* cuda_stream);
+int cans_project_adjoint(cans_plan_t plan, double* u, double* v, double* w, void* workspace, void* cuda_stream);
+
+/*
  * cans_poisson_solve_noalloc -- the solve for callers that cannot allocate device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

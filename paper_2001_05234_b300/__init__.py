@@ -36,6 +36,11 @@ class cans_opts(ctypes.Structure):
                 ("fp64_mode_fraction", ctypes.c_double), ("autotune", ctypes.c_int)]
 
 
+class cans_rk3_params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("cfl", ctypes.c_double), ("ubulk", ctypes.c_double),
+                ("dt", ctypes.c_double), ("forcing", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -60,6 +65,11 @@ def lib() -> ctypes.CDLL:
         L.cans_plan_eigenvalues.argtypes = [vp, dp, dp]
         L.cans_plan_profile.argtypes = [vp, ctypes.c_int]
         L.cans_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp, dp]
+        L.cans_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
+        L.cans_project_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_project.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.cans_project_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
         L.cans_noalloc_scratch_bytes.argtypes = []
         L.cans_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.cans_plan_profile_read.argtypes = [vp, ctypes.c_int, dp, ip]
@@ -123,6 +133,32 @@ def cans_poisson_solve_noalloc(plan, f_ptr: int, p_ptr: int, stream_ptr: int, in
     (for callers that cannot allocate device memory).  Calls that overlap on the GPU race."""
     return lib().cans_poisson_solve_noalloc(plan, f_ptr, p_ptr, stream_ptr or None,
                                             _dptr(info) if info is not None else None)
+
+
+def cans_rk3_workspace_size(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_rk3_workspace_size(plan, ctypes.byref(b)), "cans_rk3_workspace_size")
+    return int(b.value)
+
+
+def cans_rk3_step(plan, u_ptr: int, v_ptr: int, w_ptr: int, p_ptr: int, params: cans_rk3_params, dt_dev_ptr: int,
+                  workspace_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_rk3_step(plan, u_ptr, v_ptr, w_ptr, p_ptr, ctypes.byref(params), dt_dev_ptr or None,
+                               workspace_ptr, stream_ptr or None)
+
+
+def cans_project_workspace_size(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_project_workspace_size(plan, ctypes.byref(b)), "cans_project_workspace_size")
+    return int(b.value)
+
+
+def cans_project(plan, u_ptr: int, v_ptr: int, w_ptr: int, workspace_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_project(plan, u_ptr, v_ptr, w_ptr, workspace_ptr, stream_ptr or None)
+
+
+def cans_project_adjoint(plan, u_ptr: int, v_ptr: int, w_ptr: int, workspace_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_project_adjoint(plan, u_ptr, v_ptr, w_ptr, workspace_ptr, stream_ptr or None)
 
 
 def cans_noalloc_scratch_bytes() -> int:
@@ -219,3 +255,80 @@ class PoissonSolver:
             self.close()
         except Exception:
             pass
+
+
+def _aligned_workspace(nbytes: int):
+    import torch
+
+    buf = torch.empty(max(nbytes, 1) + 256, dtype=torch.uint8, device="cuda")
+    return buf, (buf.data_ptr() + 255) // 256 * 256
+
+
+class Channel:
+    """Channel flow (x, y periodic, no-slip walls in z) on one GPU: plan + workspaces for the RK3 step
+    and the projection.  Velocities u, v, w and pressure p are float64 CUDA tensors (Nz, Ny, Nx)."""
+
+    def __init__(self, n, length_xy, dzf, prec=CANS_FP64, sweeps=2):
+        self.n = tuple(int(v) for v in n)
+        o = cans_opts_default()
+        o.prec = int(prec)
+        o.max_sweeps = int(sweeps)
+        _, self.plan = cans_poisson_plan(self.n, length_xy, (CANS_BC_P, CANS_BC_P, CANS_BC_NN), dzf, o)
+        self._rk_buf, self._rk_ws = _aligned_workspace(cans_rk3_workspace_size(self.plan))
+        self._pj_buf, self._pj_ws = _aligned_workspace(cans_project_workspace_size(self.plan))
+
+    def rk3_step(self, u, v, w, p, nu, cfl=0.9, ubulk=1.0, dt=0.0, forcing=True, dt_out=None, stream=None):
+        prm = cans_rk3_params(float(nu), float(cfl), float(ubulk), float(dt), 1 if forcing else 0)
+        st = cans_rk3_step(self.plan, u.data_ptr(), v.data_ptr(), w.data_ptr(), p.data_ptr(), prm,
+                           dt_out.data_ptr() if dt_out is not None else 0, self._rk_ws, _stream_ptr(stream))
+        _check(st, "cans_rk3_step")
+
+    def project_(self, u, v, w, adjoint=False, stream=None):
+        fn = cans_project_adjoint if adjoint else cans_project
+        _check(fn(self.plan, u.data_ptr(), v.data_ptr(), w.data_ptr(), self._pj_ws, _stream_ptr(stream)),
+               "cans_project")
+        return u, v, w
+
+    def close(self):
+        if getattr(self, "plan", None):
+            cans_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _projection_function():
+    import torch
+
+    class Projection(torch.autograd.Function):
+        """u* -> P u* (divergence-free part); backward applies P^T through cans_project_adjoint."""
+
+        @staticmethod
+        def forward(ctx, chan, u, v, w):
+            ctx.chan = chan
+            uo, vo, wo = u.detach().clone(), v.detach().clone(), w.detach().clone()
+            chan.project_(uo, vo, wo)
+            return uo, vo, wo
+
+        @staticmethod
+        def backward(ctx, gu, gv, gw):
+            gu, gv, gw = gu.contiguous().clone(), gv.contiguous().clone(), gw.contiguous().clone()
+            ctx.chan.project_(gu, gv, gw, adjoint=True)
+            return None, gu, gv, gw
+
+    return Projection
+
+
+_Projection = None
+
+
+def projection(chan, u, v, w):
+    """Differentiable projection: returns P(u, v, w); gradients flow through the adjoint kernel."""
+    global _Projection
+    if _Projection is None:
+        _Projection = _projection_function()
+    return _Projection.apply(chan, u, v, w)

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -61,7 +62,7 @@ Launch line_launch(int N, int nlines_or_cols, size_t elem2, int prefer_nl) {
   Launch L;
   const int M = std::max(N / 2, 1);
   int nl = prefer_nl;
-  while (nl > 1 && (size_t)nl * M * elem2 > (size_t)96 * 1024) nl >>= 1;
+  while (nl > 1 && (size_t)(nl + 1) * M * elem2 > (size_t)96 * 1024) nl >>= 1;
   while (nl > 1 && nl * M > MAXV * 512) nl >>= 1;
   const int need = 1 << ilog2(std::max(nlines_or_cols, 1));
   while (nl > 1 && nl / 2 >= need) nl >>= 1;
@@ -72,7 +73,7 @@ Launch line_launch(int N, int nlines_or_cols, size_t elem2, int prefer_nl) {
   th = std::max(th, (int)(((M / 2 + 1) * nl + J - 1) / J));
   th = std::max(32, ((th + 31) / 32) * 32);
   L.threads = std::min(th, 512);
-  L.smem = (size_t)nl * M * elem2;
+  L.smem = (size_t)(nl + 1) * M * elem2;
   return L;
 }
 
@@ -275,6 +276,13 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   const size_t o_dzf = B.add(dz.data(), nz * 8);
   std::vector<float> dzff, dzflo;
   split_df(dz, dzff, dzflo);
+  std::vector<double> dzfi(nz), dzci(nz);
+  for (int k = 0; k < nz; ++k) {
+    dzfi[k] = 1.0 / dz[k];
+    dzci[k] = 1.0 / dzc[k + 1];
+  }
+  const size_t o_dzfi = B.add(dzfi.data(), nz * 8), o_dzci = B.add(dzci.data(), nz * 8);
+  P->dzf_h = dz;
   const size_t o_dzff = B.add(dzff.data(), nz * 4);
   const size_t o_dzflo = B.add(dzflo.data(), nz * 4);
   const size_t o_sa = B.add(sa.data(), nz * 8), o_sc = B.add(sc.data(), nz * 8);
@@ -332,6 +340,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->dzf_d = reinterpret_cast<const double*>(base + o_dzf);
   P->dzf_f = reinterpret_cast<const float*>(base + o_dzff);
   P->dzf_flo = reinterpret_cast<const float*>(base + o_dzflo);
+  P->dzfi_d = reinterpret_cast<const double*>(base + o_dzfi);
+  P->dzci_d = reinterpret_cast<const double*>(base + o_dzci);
   {
     // column mean target: a (0,0) value v contributes v * cx * cy / (Nx Ny) to every cell, with
     // cx = 1 for a periodic or single-cell direction and 1/2 for a Neumann one (DCT-II of a constant)
@@ -360,9 +370,10 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->x_l[1] = line_launch(n[0], nlines, sizeof(float2), 32);
   P->y_l[0] = line_launch(n[1], n[0], sizeof(double2), 8);
   P->y_l[1] = line_launch(n[1], n[0], sizeof(float2), 16);
-  P->z_m = (nz + 31) / 32;
+  // rows per lane: the power of two >= Nz/32 (rows past Nz are identity rows)
   P->z_mmax = 1;
-  while (P->z_mmax < P->z_m) P->z_mmax <<= 1;
+  while (32 * P->z_mmax < nz) P->z_mmax <<= 1;
+  P->z_m = P->z_mmax;
   for (int s = 0; s < 2; ++s) {
     int ti = (s == 0) ? 16 : 32;
     const size_t es = (s == 0) ? 8 : 4;
@@ -425,6 +436,30 @@ int cans_plan_eigenvalues(cans_plan_t P, double* mux, double* muy) {
 }
 
 }  // extern "C"
+
+namespace {
+
+}  // namespace
+
+cudaError_t cans::set_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex lock;
+  static std::vector<std::pair<std::pair<const void*, int>, size_t>> done;  // (kernel, device) -> bytes
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> guard(lock);
+  for (auto& d : done)
+    if (d.first.first == fn && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  for (auto& d : done)
+    if (d.first.first == fn && d.first.second == dev) {
+      d.second = bytes;
+      return cudaSuccess;
+    }
+  done.push_back({{fn, dev}, bytes});
+  return cudaSuccess;
+}
 
 namespace {
 
@@ -496,11 +531,19 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
       double* gauge = P->singular ? P->acc_d + P->nacc - 5 : nullptr;
       TIMED(CANS_PASS_XI, launch_xinv<float, 1>(P, W, nullptr, Phi, Plo, inv_scale, gauge, st));
       for (int s = 0; s < sweeps; ++s) {
-        TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
+        if (s == 0)
+          TIMED(CANS_PASS_XR, launch_xfwd<float, 2>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
+        else
+          TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
         TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
         TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st));
         TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
-        if (s + 1 < sweeps)
+        const bool last = (s + 1 == sweeps);
+        if (s == 0 && !last)
+          TIMED(CANS_PASS_XU, launch_xinv<float, 4>(P, W, nullptr, Phi, Plo, inv_scale, nullptr, st));
+        else if (s == 0)
+          TIMED(CANS_PASS_XU, launch_xinv<float, 5>(P, W, p, Phi, Plo, inv_scale, nullptr, st));
+        else if (!last)
           TIMED(CANS_PASS_XU, launch_xinv<float, 2>(P, W, nullptr, Phi, Plo, inv_scale, nullptr, st));
         else
           TIMED(CANS_PASS_XU, launch_xinv<float, 3>(P, W, p, Phi, Plo, inv_scale, nullptr, st));

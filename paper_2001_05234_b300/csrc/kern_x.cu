@@ -15,39 +15,77 @@ __device__ __forceinline__ float ghost_or(int bc, int at_edge, float inner_c, fl
   return -inner_c;
 }
 
-// r(i,j,k) = f - L_h(Phi + Plo) (Eq. poi): the Phi part in double-float arithmetic, the small Plo
-// part in float.  Ghost rules: periodic wrap, Neumann mirror, Dirichlet antisymmetric mirror.
+// acc - coef * x for double-float acc, coef and x: the product's error-free head and a float tail.
+__device__ __forceinline__ df df_sub_prod(df acc, df coef, df x) {
+  df p = two_prod(coef.hi, x.hi);
+  p.lo = __fmaf_rn(coef.hi, x.lo, __fmaf_rn(coef.lo, x.hi, p.lo));
+  const df s = two_sum(acc.hi, -p.hi);
+  return df_make(s.hi, __fadd_rn(s.lo, __fsub_rn(acc.lo, p.lo)));
+}
+
+// xm + xp - 2 c as an (almost exact) double-float: two error-free sums
+__device__ __forceinline__ df second_difference(float xm, float xp, float c) {
+  const df a = two_sum(xm, xp);
+  const df b = two_sum(a.hi, -2.f * c);
+  return df_make(b.hi, __fadd_rn(b.lo, a.lo));
+}
+
+// Wall ghost of a cell-centred value: Neumann mirrors it, Dirichlet mirrors it with the sign flipped.
+__device__ __forceinline__ float wall_ghost(int bc, float c) { return (bc == BC_NN) ? c : -c; }
+
+// r = f - L_h(Phi + Plo) at cell (i, j, k) (Eq. poi): the Phi part in double-float arithmetic, the
+// small Plo part in float (skipped when PLO is false, i.e. Plo is known to be zero).
+template <bool PLO>
 __device__ __forceinline__ float residual_point(const double* __restrict__ f, const float* __restrict__ Phi,
-                                                const float* __restrict__ Plo, const StencilDF& S, int i, int j,
-                                                int k) {
+                                                const float* __restrict__ Plo, const StencilDF& S, size_t c, int i,
+                                                int j, int k) {
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
-  const size_t sy = nx, sz = (size_t)nx * ny;
-  const size_t c = (size_t)i + sy * j + sz * k;
-  const float pc = Phi[c], qc = Plo[c];
-  const bool xm_e = (i == 0), xp_e = (i == nx - 1), ym_e = (j == 0), yp_e = (j == ny - 1), zm_e = (k == 0),
-             zp_e = (k == nz - 1);
-  const size_t cxm = xm_e ? c + (nx - 1) : c - 1, cxp = xp_e ? c - (nx - 1) : c + 1;
-  const size_t cym = ym_e ? c + (ny - 1) * sy : c - sy, cyp = yp_e ? c - (ny - 1) * sy : c + sy;
-  const size_t czm = zm_e ? c + (nz - 1) * sz : c - sz, czp = zp_e ? c - (nz - 1) * sz : c + sz;
-  const float Pxm = Phi[cxm], Pxp = Phi[cxp], Pym = Phi[cym], Pyp = Phi[cyp], Pzm = Phi[czm], Pzp = Phi[czp];
-  const float xm = ghost_or(S.bc[0], xm_e, pc, Pxm, Pxm), xp = ghost_or(S.bc[0], xp_e, pc, Pxp, Pxp);
-  const float ym = ghost_or(S.bc[1], ym_e, pc, Pym, Pym), yp = ghost_or(S.bc[1], yp_e, pc, Pyp, Pyp);
-  const float zm = ghost_or(S.bc[2], zm_e, pc, Pzm, Pzm), zp = ghost_or(S.bc[2], zp_e, pc, Pzp, Pzp);
-  // x and y second differences, exact as double-floats
-  df sx = df_add(two_sum(xm, xp), df_make(-2.f * pc, 0.f));
-  df sy2 = df_add(two_sum(ym, yp), df_make(-2.f * pc, 0.f));
-  df L = df_add(df_mul(S.idx2, sx), df_mul(S.idy2, sy2));
-  const df za = df_make(S.sa_hi[k], S.sa_lo[k]), zc = df_make(S.sc_hi[k], S.sc_lo[k]);
-  L = df_add(L, df_mul(zc, two_sum(zp, -pc)));
-  L = df_add(L, df_mul(za, two_sum(zm, -pc)));
-  const df r = df_add(df_from_double(f[c]), df_neg(L));
-  const float Qxm = Plo[cxm], Qxp = Plo[cxp], Qym = Plo[cym], Qyp = Plo[cyp], Qzm = Plo[czm], Qzp = Plo[czp];
-  const float qxm = ghost_or(S.bc[0], xm_e, qc, Qxm, Qxm), qxp = ghost_or(S.bc[0], xp_e, qc, Qxp, Qxp);
-  const float qym = ghost_or(S.bc[1], ym_e, qc, Qym, Qym), qyp = ghost_or(S.bc[1], yp_e, qc, Qyp, Qyp);
-  const float qzm = ghost_or(S.bc[2], zm_e, qc, Qzm, Qzm), qzp = ghost_or(S.bc[2], zp_e, qc, Qzp, Qzp);
-  const float Lq = S.idx2.hi * (qxm + qxp - 2.f * qc) + S.idy2.hi * (qym + qyp - 2.f * qc) + S.sc_hi[k] * (qzp - qc) +
-                   S.sa_hi[k] * (qzm - qc);
-  return (r.hi + r.lo) - Lq;
+  const long long sz = (long long)nx * ny;
+  // neighbour offsets with periodic wrap; at a wall the loaded value is replaced by the ghost
+  const int oxm = (i == 0) ? nx - 1 : -1, oxp = (i == nx - 1) ? 1 - nx : 1;
+  const int oym = (j == 0) ? (ny - 1) * nx : -nx, oyp = (j == ny - 1) ? (1 - ny) * nx : nx;
+  const long long ozm = (k == 0) ? (nz - 1) * sz : -sz, ozp = (k == nz - 1) ? (1 - nz) * sz : sz;
+  const float* q = Phi + c;
+  const float pc = q[0];
+  float xm = q[oxm], xp = q[oxp], ym = q[oym], yp = q[oyp], zm = q[ozm], zp = q[ozp];
+  if (S.bc[0] != BC_P) {
+    if (i == 0) xm = wall_ghost(S.bc[0], pc);
+    if (i == nx - 1) xp = wall_ghost(S.bc[0], pc);
+  }
+  if (S.bc[1] != BC_P) {
+    if (j == 0) ym = wall_ghost(S.bc[1], pc);
+    if (j == ny - 1) yp = wall_ghost(S.bc[1], pc);
+  }
+  if (S.bc[2] != BC_P) {
+    if (k == 0) zm = wall_ghost(S.bc[2], pc);
+    if (k == nz - 1) zp = wall_ghost(S.bc[2], pc);
+  }
+  df acc = df_from_double(f[c]);
+  acc = df_sub_prod(acc, S.idx2, second_difference(xm, xp, pc));
+  acc = df_sub_prod(acc, S.idy2, second_difference(ym, yp, pc));
+  acc = df_sub_prod(acc, df_make(S.sc_hi[k], S.sc_lo[k]), two_sum(zp, -pc));
+  acc = df_sub_prod(acc, df_make(S.sa_hi[k], S.sa_lo[k]), two_sum(zm, -pc));
+  float r = acc.hi + acc.lo;
+  if (PLO) {
+    const float* o = Plo + c;
+    const float qc = o[0];
+    float qxm = o[oxm], qxp = o[oxp], qym = o[oym], qyp = o[oyp], qzm = o[ozm], qzp = o[ozp];
+    if (S.bc[0] != BC_P) {
+      if (i == 0) qxm = wall_ghost(S.bc[0], qc);
+      if (i == nx - 1) qxp = wall_ghost(S.bc[0], qc);
+    }
+    if (S.bc[1] != BC_P) {
+      if (j == 0) qym = wall_ghost(S.bc[1], qc);
+      if (j == ny - 1) qyp = wall_ghost(S.bc[1], qc);
+    }
+    if (S.bc[2] != BC_P) {
+      if (k == 0) qzm = wall_ghost(S.bc[2], qc);
+      if (k == nz - 1) qzp = wall_ghost(S.bc[2], qc);
+    }
+    r -= S.idx2.hi * (qxm + qxp - 2.f * qc) + S.idy2.hi * (qym + qyp - 2.f * qc) + S.sc_hi[k] * (qzp - qc) +
+         S.sa_hi[k] * (qzm - qc);
+  }
+  return r;
 }
 
 __device__ __forceinline__ void block_accumulate(float v, double* dst) {
@@ -83,8 +121,9 @@ __device__ __forceinline__ void block_accumulate_d(double v, double* dst) {
 }
 
 // Forward x-pass.  MODE 0: read f (double) -> T.  MODE 1 (T = float): the residual
-// f - L_h(Phi + Plo) computed on the fly.  Output lines go to dst (T) in transform slot order.
-// norm_acc (optional) receives sum f^2 (MODE 0) or sum r^2 (MODE 1).
+// f - L_h(Phi + Plo) computed on the fly; MODE 2: the same with Plo known to be zero (first sweep).
+// Output lines go to dst (T) in transform slot order.  norm_acc (optional) receives sum f^2 (MODE 0)
+// or sum r^2.
 template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
                                                       const float* __restrict__ Plo, T* __restrict__ dst, XArgs a,
@@ -96,20 +135,24 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
   const Lay L{nl};
   const int N = MC > 0 ? 2 * MC : a.nx;
   const int line0 = blockIdx.x * nl;
+  const float inv_ny = 1.0f / (float)S.n[1];
   float acc = 0.f;
   for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
     const int l = e / N, n = e - l * N;
     const int line = line0 + l;
     T v = 0;
     if (line < a.nlines) {
+      const size_t c = (size_t)line * N + n;
       if (MODE == 0) {
-        const double fv = f[(size_t)line * N + n];
+        const double fv = f[c];
         const float ff = (float)fv;
         acc += ff * ff;
         v = (T)fv;
       } else {
-        const int j = line % S.n[1], k = line / S.n[1];
-        const float r = residual_point(f, Phi, Plo, S, n, j, k);
+        // k = line / Ny, exact: (line + 1/2)/Ny stays >= 1/(2 Ny) away from an integer
+        const int k = (int)(((float)line + 0.5f) * inv_ny);
+        const int j = line - k * S.n[1];
+        const float r = residual_point<MODE == 1>(f, Phi, Plo, S, c, n, j, k);
         acc += r * r;
         v = (T)r;
       }
@@ -127,9 +170,10 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
   if (norm_acc != nullptr) block_accumulate(acc, norm_acc);
 }
 
-// Inverse x-pass.  MODE 0: p (double) = scale * x.  MODE 1: Phi = scale * x, Plo = 0, and (when
-// gauge != nullptr) sum_c dzf_k Phi_c into *gauge.  MODE 2: (Phi, Plo) += scale * x (double-float).
-// MODE 3: p = Phi + Plo + scale * x (double).
+// Inverse x-pass.  MODE 0: p (double) = scale * x.  MODE 1: Phi = scale * x (the iterate's tail Plo
+// is implicitly zero), and (when gauge != nullptr) sum_c dzf_k Phi_c into *gauge.
+// MODE 2: (Phi, Plo) += scale * x (double-float).  MODE 3: p = Phi + Plo + scale * x (double).
+// MODE 4, 5: as 2, 3 with the old Plo known to be zero (first sweep).
 template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src, double* __restrict__ p,
                                                       float* __restrict__ Phi, float* __restrict__ Plo, XArgs a,
@@ -162,7 +206,6 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
     } else if (MODE == 1) {
       const float ph = (float)v * (float)a.scale;
       Phi[o] = ph;
-      Plo[o] = 0.f;
       if (gauge != nullptr) {
         const int k = line / ny;
         df t = two_prod(ph, wz[k]);  // ph * dzf_k with dzf_k = wz + wz_lo (double-float weight)
@@ -172,8 +215,8 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
     } else {
       const float d = (float)v * (float)a.scale;
       df s = two_sum(Phi[o], d);
-      s = fast_two_sum(s.hi, s.lo + Plo[o]);
-      if (MODE == 2) {
+      s = fast_two_sum(s.hi, (MODE <= 3) ? s.lo + Plo[o] : s.lo);
+      if (MODE == 2 || MODE == 4) {
         Phi[o] = s.hi;
         Plo[o] = s.lo;
       } else {
@@ -256,6 +299,8 @@ template cudaError_t launch_xfwd<float, 0>(const cans_plan_s*, const double*, co
                                            double*, cudaStream_t);
 template cudaError_t launch_xfwd<float, 1>(const cans_plan_s*, const double*, const float*, const float*, float*,
                                            double*, cudaStream_t);
+template cudaError_t launch_xfwd<float, 2>(const cans_plan_s*, const double*, const float*, const float*, float*,
+                                           double*, cudaStream_t);
 template cudaError_t launch_xinv<double, 0>(const cans_plan_s*, const double*, double*, float*, float*, double, double*,
                                             cudaStream_t);
 template cudaError_t launch_xinv<float, 0>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
@@ -265,6 +310,10 @@ template cudaError_t launch_xinv<float, 1>(const cans_plan_s*, const float*, dou
 template cudaError_t launch_xinv<float, 2>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
                                            cudaStream_t);
 template cudaError_t launch_xinv<float, 3>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_xinv<float, 4>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_xinv<float, 5>(const cans_plan_s*, const float*, double*, float*, float*, double, double*,
                                            cudaStream_t);
 
 }  // namespace cans

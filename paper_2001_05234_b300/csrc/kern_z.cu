@@ -10,8 +10,9 @@ namespace cans {
 // Coalesced copy of a TI x Nz tile (TI consecutive x-slots of one y-slot, all z) into the swizzled
 // shared layout and back.  Rows are TI elements long; 16-byte vectors when the grid allows it.
 template <typename T>
-__device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, int TI, int nz, int m, int ncols,
+__device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, const ZSwz& Z, int nz, int ncols,
                                           bool vec) {
+  const int TI = Z.TI;
   constexpr int V = 16 / sizeof(T);
   if (vec && ncols == TI) {
     const int per_row = TI / V;
@@ -22,24 +23,25 @@ __device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, 
         const float4 v = *reinterpret_cast<const float4*>(src);
         const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) tile[ztile_idx(k, q + u, TI, m)] = (T)vv[u];
+        for (int u = 0; u < 4; ++u) tile[Z.at(k, q + u)] = (T)vv[u];
       } else {
         const double2 v = *reinterpret_cast<const double2*>(src);
-        tile[ztile_idx(k, q, TI, m)] = (T)v.x;
-        tile[ztile_idx(k, q + 1, TI, m)] = (T)v.y;
+        tile[Z.at(k, q)] = (T)v.x;
+        tile[Z.at(k, q + 1)] = (T)v.y;
       }
     }
   } else {
     for (int e = threadIdx.x; e < TI * nz; e += blockDim.x) {
       const int k = e / TI, ii = e - k * TI;
-      if (ii < ncols) tile[ztile_idx(k, ii, TI, m)] = col0[(size_t)k * plane + ii];
+      if (ii < ncols) tile[Z.at(k, ii)] = col0[(size_t)k * plane + ii];
     }
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane, int TI, int nz, int m, int ncols,
+__device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane, const ZSwz& Z, int nz, int ncols,
                                            bool vec) {
+  const int TI = Z.TI;
   constexpr int V = 16 / sizeof(T);
   if (vec && ncols == TI) {
     const int per_row = TI / V;
@@ -48,22 +50,22 @@ __device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane,
       T* dst = col0 + (size_t)k * plane + q;
       if (V == 4) {
         float4 v;
-        v.x = (float)tile[ztile_idx(k, q, TI, m)];
-        v.y = (float)tile[ztile_idx(k, q + 1, TI, m)];
-        v.z = (float)tile[ztile_idx(k, q + 2, TI, m)];
-        v.w = (float)tile[ztile_idx(k, q + 3, TI, m)];
+        v.x = (float)tile[Z.at(k, q)];
+        v.y = (float)tile[Z.at(k, q + 1)];
+        v.z = (float)tile[Z.at(k, q + 2)];
+        v.w = (float)tile[Z.at(k, q + 3)];
         *reinterpret_cast<float4*>(dst) = v;
       } else {
         double2 v;
-        v.x = (double)tile[ztile_idx(k, q, TI, m)];
-        v.y = (double)tile[ztile_idx(k, q + 1, TI, m)];
+        v.x = (double)tile[Z.at(k, q)];
+        v.y = (double)tile[Z.at(k, q + 1)];
         *reinterpret_cast<double2*>(dst) = v;
       }
     }
   } else {
     for (int e = threadIdx.x; e < TI * nz; e += blockDim.x) {
       const int k = e / TI, ii = e - k * TI;
-      if (ii < ncols) col0[(size_t)k * plane + ii] = tile[ztile_idx(k, ii, TI, m)];
+      if (ii < ncols) col0[(size_t)k * plane + ii] = tile[Z.at(k, ii)];
     }
   }
 }
@@ -80,18 +82,19 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   const size_t plane = (size_t)a.nx * a.ny;
   float* col0 = w + (size_t)j * a.nx + i0;
   const int ncols = min(TI, a.nx - i0);
+  const ZSwz Z = make_zswz(TI, m);
   stage_zrows<float, float>(sa, sb, sc, zf, a.nz, m);
-  tile_load<float>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float muy = a.muy_f[j];
   for (int cidx = warp; cidx < ncols; cidx += nwarps) {
     const int i = i0 + cidx;
     if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
-    zsolve_column<MMAX, float, float, false>(tile, cidx, TI, a.nz, m, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
+    zsolve_column<MMAX, float, float, false>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
   }
   __syncthreads();
-  tile_store<float>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
 
 template <typename T, int MMAX>
@@ -111,8 +114,9 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     for (int c = 0; c < ncols; ++c) any |= a.mask[(size_t)j * a.nx + i0 + c] != 0;
     if (!any) return;
   }
+  const ZSwz Z = make_zswz(TI, m);
   stage_zrows<double, double>(sa, sb, sc, zd, a.nz, m);
-  tile_load<T>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  tile_load<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const double muy = a.muy_d[j];
@@ -122,13 +126,13 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     const double mu = a.mux_d[i] + muy;
     if (a.singular && i == 0 && j == 0) {
       const double target = (a.gauge != nullptr) ? a.gauge_scale * (*a.gauge) : 0.0;
-      zsolve_column<MMAX, double, T, true>(tile, cidx, TI, a.nz, m, mu, sa, sb, sc, a.dzf, target);
+      zsolve_column<MMAX, double, T, true>(tile, cidx, Z, a.nz, mu, sa, sb, sc, a.dzf, target);
     } else {
-      zsolve_column<MMAX, double, T, false>(tile, cidx, TI, a.nz, m, mu, sa, sb, sc, nullptr, 0.0);
+      zsolve_column<MMAX, double, T, false>(tile, cidx, Z, a.nz, mu, sa, sb, sc, nullptr, 0.0);
     }
   }
   __syncthreads();
-  tile_store<T>(tile, col0, plane, TI, a.nz, m, ncols, vec != 0);
+  tile_store<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
 
 static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {

@@ -7,9 +7,9 @@
 // mixed-radix (2, 3, 4, 8) Stockham FFT of length M, and post-processed into the N real
 // coefficients (the standard half-length real-FFT split, plus Makhoul's 1980 reordering and
 // quarter-wave twiddle for the cosine/sine transforms).  Complex element m of line l lives at
-// phys(m, l) = m*nl + (l ^ (m & (nl-1))): lines are interleaved so that lanes of a warp that work
-// on different lines at the same m hit different banks, and the xor keeps the strided copy phases
-// from piling onto one bank.
+// m*(nl+1) + l: lines are interleaved so that lanes of a warp that work on different lines at the
+// same m hit consecutive banks, and the one-cell row padding spreads the copy phases (consecutive
+// samples of one line) over all banks.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -51,8 +51,8 @@ struct LineTab {
 };
 
 struct Lay {
-  int nl;
-  __device__ __forceinline__ int c(int m, int l) const { return m * nl + (l ^ (m & (nl - 1))); }
+  int nl;  // lines in the tile (power of two); rows are padded to nl + 1 complex cells
+  __device__ __forceinline__ int c(int m, int l) const { return m * (nl + 1) + l; }
   // real slot s of line l inside the same storage (two reals per complex cell)
   __device__ __forceinline__ int r(int s, int l) const { return 2 * c(s >> 1, l) + (s & 1); }
 };

@@ -67,6 +67,9 @@ struct cans_plan_s {
   const double *mux_d, *muy_d, *dzf_d, *sa_d, *sc_d;
   const float* dzf_f;
   const float* dzf_flo;  // dzf - (float)dzf
+  const double* dzfi_d;  // 1/dzf
+  const double* dzci_d;  // 1/dzc_{k+1/2} (top: 1/dzf of the wall cell)
+  std::vector<double> dzf_h;
   double gauge_scale = 0;
   const float *mux_f, *muy_f, *sa_hi, *sa_lo, *sc_hi, *sc_lo;
   const unsigned char* mask_d = nullptr;
@@ -99,13 +102,25 @@ template <typename T>
 cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
 cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st);
 cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st);
+cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double* v, const double* w, const double* p,
+                            double* ru, double* rv, double* rw, double* us, double* vs, double* ws, double nu,
+                            double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st);
+cudaError_t launch_divergence(const cans_plan_s* P, const double* u, const double* v, const double* w, double* f,
+                              double scale_num, const double* dt_dev, double gamma, int weighted, cudaStream_t st);
+cudaError_t launch_correct(const cans_plan_s* P, const double* us, const double* vs, const double* ws,
+                           const double* phi, double* u, double* v, double* w, double* p, double gamma,
+                           const double* dt_dev, int weighted, double* bulk, cudaStream_t st);
+cudaError_t launch_forcing(const cans_plan_s* P, double* u, const double* bulk, double ubulk, cudaStream_t st);
+cudaError_t launch_chkdt(const cans_plan_s* P, const double* u, const double* v, const double* w,
+                         unsigned long long* dti_bits, double* dt_dev, double cfl, double nu, double dt_fixed,
+                         cudaStream_t st);
 
 StencilDF stencil_df(const cans_plan_s* P);
 
-inline cudaError_t set_smem(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+// Opt a kernel into more than 48 KB of dynamic shared memory.  The attribute is set once per kernel
+// and size (remembered per device), so later launches -- including those inside a stream capture --
+// make no attribute call.
+cudaError_t set_smem(const void* fn, size_t bytes);
 
 template <typename T> const LineTab<T>& tab_x(const cans_plan_s* P);
 template <> inline const LineTab<double>& tab_x<double>(const cans_plan_s* P) { return P->tx_d; }

@@ -29,9 +29,24 @@ __device__ __forceinline__ float rcp_(float x) {
 }
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 
-// Swizzled position of (row k, column i) inside the [Nz][TI] tile: lane p = k / m reads column w of
-// its rows at bank w ^ p.
-__device__ __forceinline__ int ztile_idx(int k, int i, int TI, int m) { return k * TI + (i ^ ((k / m) & (TI - 1))); }
+// Swizzled position of (row k, column i) inside the [Nz][TI] tile.  Every lane owns m = 2^sh rows
+// (rows past Nz are identity rows), so row k belongs to lane seg = k >> sh; the column index is
+// xor-ed with seg (the 32 lanes reading one column hit 32 banks) and, when m >= 4, with k & 3 (the
+// row-major copy phases, four rows at a time, spread over all banks as well).
+struct ZSwz {
+  int TI, sh, low;
+  __device__ __forceinline__ int seg(int k) const { return k >> sh; }
+  __device__ __forceinline__ int at(int k, int i, int sg) const { return k * TI + (i ^ ((sg ^ (k & low)) & (TI - 1))); }
+  __device__ __forceinline__ int at(int k, int i) const { return at(k, i, seg(k)); }
+};
+__device__ __forceinline__ ZSwz make_zswz(int TI, int m) {
+  ZSwz s;
+  s.TI = TI;
+  s.sh = 0;
+  while ((1 << s.sh) < m) ++s.sh;
+  s.low = (m >= 4) ? 3 : 0;
+  return s;
+}
 
 // Per-CTA copy of the z rows in lane-major order: row k = lane*m + r sits at [r*32 + lane], so the 32
 // lanes of a warp read 32 consecutive words.  Rows past Nz become identity rows (a = c = 0, b = 1).
@@ -52,9 +67,10 @@ __device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& 
 // is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
 // x = 0, and the result is shifted to the dzf-weighted mean `target`.
 template <int MMAX, typename C, typename T, bool SING>
-__device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, int m, C mu, const C* sa,
+__device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, int Nz, C mu, const C* sa,
                                               const C* sb, const C* sc, const double* weights, C target) {
   const int lane = threadIdx.x & 31;
+  constexpr int m = MMAX;  // rows per lane (compile time: keeps the row arrays in registers)
   const int k0 = lane * m;
   const unsigned full = 0xffffffffu;
   C proj = 0;
@@ -65,7 +81,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
       if (k < Nz) {
         const C w = (C)weights[k];
         sw += w;
-        swd += w * (C)tile[ztile_idx(k, col, TI, m)];
+        swd += w * (C)tile[Z.at(k, col, lane)];
       }
     }
 #pragma unroll
@@ -84,7 +100,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
     if (r < m - 1) {
       const int k = k0 + r;
       C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + mu, c = sc[r * 32 + lane], d = 0;
-      if (k < Nz) d = (C)tile[ztile_idx(k, col, TI, m)] - proj;
+      if (k < Nz) d = (C)tile[Z.at(k, col, lane)] - proj;
       if (SING && k == Nz - 1) {
         a = 0;
         b = 1;
@@ -131,7 +147,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
   const int kl = k0 + m - 1;
   const int rl = m - 1;
   C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + mu, cl = sc[rl * 32 + lane], dl = 0;
-  if (kl < Nz) dl = (C)tile[ztile_idx(kl, col, TI, m)] - proj;
+  if (kl < Nz) dl = (C)tile[Z.at(kl, col, lane)] - proj;
   if (SING && kl == Nz - 1) {
     al = 0;
     bl = 1;
@@ -166,8 +182,8 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
   const C E = delta * rcp_(beta);
   C Ep = __shfl_up_sync(full, E, 1);
   if (lane == 0) Ep = 0;
-  // back-substitution
-  C x[MMAX];
+  // back-substitution, written straight into the tile
+  if (lane * m + m - 1 < Nz) tile[Z.at(k0 + m - 1, col, lane)] = (T)E;
   C xn = E;
 #pragma unroll
   for (int r = MMAX - 1; r >= 0; --r) {
@@ -176,22 +192,18 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
         xn = dp[r] + lp[r] * Ep + rr * E;
       else
         xn = dp[r] + lp[r] * Ep - cp[r] * xn;
-      x[r] = xn;
+      if (k0 + r < Nz) tile[Z.at(k0 + r, col, lane)] = (T)xn;
     }
   }
-  C shift = 0;
   if (SING) {
+    // shift the column to the weighted mean `target`
     C sw = 0, swx = 0;
-#pragma unroll
-    for (int r = 0; r < MMAX; ++r) {
-      if (r < m) {
-        const int k = k0 + r;
-        if (k < Nz) {
-          const C xv = (r == m - 1) ? E : x[r];
-          const C w = (C)weights[k];
-          sw += w;
-          swx += w * xv;
-        }
+    for (int r = 0; r < m; ++r) {
+      const int k = k0 + r;
+      if (k < Nz) {
+        const C w = (C)weights[k];
+        sw += w;
+        swx += w * (C)tile[Z.at(k, col, lane)];
       }
     }
 #pragma unroll
@@ -199,13 +211,10 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, int TI, int Nz, 
       sw += __shfl_xor_sync(full, sw, o);
       swx += __shfl_xor_sync(full, swx, o);
     }
-    shift = swx / sw - target;
-  }
-#pragma unroll
-  for (int r = 0; r < MMAX; ++r) {
-    if (r < m) {
+    const C shift = swx / sw - target;
+    for (int r = 0; r < m; ++r) {
       const int k = k0 + r;
-      if (k < Nz) tile[ztile_idx(k, col, TI, m)] = (T)(((r == m - 1) ? E : x[r]) - shift);
+      if (k < Nz) tile[Z.at(k, col, lane)] = (T)((C)tile[Z.at(k, col, lane)] - shift);
     }
   }
 }
