@@ -61,7 +61,10 @@ typedef struct {
   int max_sweeps;            /* CANS_MIXED: refinement sweeps after the first solve (0..8) */
   double tol;                /* CANS_MIXED: relative residual target checked when synchronising */
   double fp64_mode_fraction; /* CANS_MIXED: fraction of (x,y) modes solved in double along z */
-  int autotune;              /* reserved: 0 = built-in tile shapes */
+  int autotune;              /* 1: time candidate tile shapes at plan time and keep the fastest (needs
+                                temporary device scratch of about 12-16 bytes per point during planning;
+                                results cached per device / shape / boundary conditions / precision,
+                                and in the file named by CANS_AUTOTUNE_CACHE when set); 0: built-in */
 } cans_opts;
 
 /* Fill *opts with the defaults: FP64, 2 sweeps, tol 1e-12, fraction 0.01, autotune 0. */
@@ -69,8 +72,9 @@ void cans_opts_default(cans_opts* opts);
 
 /*
  * Plan a solver for one grid and boundary-condition set (Eq. poi_reduced; host work only).
- *   n       : {Nx, Ny, Nz}, each >= 1; a periodic x or y needs an even N; N/2 (x, y) must factor
- *             into 2s and 3s (up to 4096).  Nz <= 8192.
+ *   n       : {Nx, Ny, Nz}, each >= 1.  x and y: N = 1, or N even with N/2 = 2^a 3^b, N <= 8192.
+ *             z: Nz <= 512 for Neumann / Dirichlet z; a periodic z is uniform with Nz = 1 or
+ *             Nz even, Nz/2 = 2^a 3^b, Nz <= 1024 (it is diagonalised by a real DFT as well).
  *   len_xy  : {Lx, Ly} > 0, domain lengths in x and y.
  *   bc      : {bc_x, bc_y, bc_z}, each a cans_bc.
  *   dzf     : host array of Nz positive cell widths along z, or NULL for Nz cells of width 1/Nz.
@@ -78,7 +82,7 @@ void cans_opts_default(cans_opts* opts);
  *   opts    : NULL for the defaults.
  *   out     : receives the plan.  The plan uploads its coefficient tables to the current device.
  * Errors: CANS_ERR_ARG (bad n, bc, lengths, dzf non-positive or non-finite, periodic z not
- * uniform), CANS_ERR_UNSUPPORTED (odd periodic N, unsupported factor), CANS_ERR_CUDA.
+ * uniform), CANS_ERR_UNSUPPORTED (sizes outside the list above), CANS_ERR_CUDA.
  */
 int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
                       const cans_opts* opts, cans_plan_t* out);
@@ -147,6 +151,24 @@ enum cans_pass {
 };
 int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);
+
+/*
+ * Batched solves: many independent problems (each with its own plan: shapes, boundary conditions and
+ * precisions may all differ) in one asynchronous call.  The batch fans the problems out over
+ * `nstreams` internal streams (largest problems first, greedy balancing by point count; problems that
+ * share a plan share a stream) that fork from and join back into the caller's stream with events, so
+ * the call can be captured into one CUDA graph whose branches run concurrently.
+ *   cans_batch_create : plans[count] stay owned by the caller and must outlive the batch.
+ *   cans_batch_workspace_size : total workspace (sum of the problems' workspaces, 256-byte aligned).
+ *   cans_batch_solve : f[i], p[i] device arrays of problem i (as in cans_poisson_solve); workspace of
+ *                      the size above, 256-byte aligned; enqueued on cuda_stream.
+ */
+typedef struct cans_batch_s* cans_batch_t;
+int cans_batch_create(int count, const cans_plan_t* plans, int nstreams, cans_batch_t* out);
+int cans_batch_workspace_size(cans_batch_t batch, size_t* bytes);
+int cans_batch_solve(cans_batch_t batch, const double* const* f, double* const* p, void* workspace,
+                     void* cuda_stream);
+int cans_batch_destroy(cans_batch_t batch);
 
 /*
  * Fractional-step pieces for a channel plan (bc = {CANS_BC_P, CANS_BC_P, CANS_BC_NN}: x and y

@@ -65,6 +65,10 @@ def lib() -> ctypes.CDLL:
         L.cans_plan_eigenvalues.argtypes = [vp, dp, dp]
         L.cans_plan_profile.argtypes = [vp, ctypes.c_int]
         L.cans_poisson_solve_noalloc.argtypes = [vp, vp, vp, vp, dp]
+        L.cans_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+        L.cans_batch_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+        L.cans_batch_destroy.argtypes = [vp]
         L.cans_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
         L.cans_project_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -159,6 +163,29 @@ def cans_project(plan, u_ptr: int, v_ptr: int, w_ptr: int, workspace_ptr: int, s
 
 def cans_project_adjoint(plan, u_ptr: int, v_ptr: int, w_ptr: int, workspace_ptr: int, stream_ptr: int) -> int:
     return lib().cans_project_adjoint(plan, u_ptr, v_ptr, w_ptr, workspace_ptr, stream_ptr or None)
+
+
+def cans_batch_create(plans, nstreams: int = 8):
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if hasattr(p, "value") else p for p in plans])
+    h = ctypes.c_void_p()
+    _check(lib().cans_batch_create(len(plans), arr, int(nstreams), ctypes.byref(h)), "cans_batch_create")
+    return h
+
+
+def cans_batch_workspace_size(batch) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_batch_workspace_size(batch, ctypes.byref(b)), "cans_batch_workspace_size")
+    return int(b.value)
+
+
+def cans_batch_solve(batch, f_ptrs, p_ptrs, workspace_ptr: int, stream_ptr: int) -> int:
+    fa = (ctypes.c_void_p * len(f_ptrs))(*f_ptrs)
+    pa = (ctypes.c_void_p * len(p_ptrs))(*p_ptrs)
+    return lib().cans_batch_solve(batch, fa, pa, workspace_ptr or None, stream_ptr or None)
+
+
+def cans_batch_destroy(batch) -> int:
+    return lib().cans_batch_destroy(batch)
 
 
 def cans_noalloc_scratch_bytes() -> int:
@@ -332,3 +359,37 @@ def projection(chan, u, v, w):
     if _Projection is None:
         _Projection = _projection_function()
     return _Projection.apply(chan, u, v, w)
+
+
+class Batch:
+    """Many independent Poisson problems solved in one asynchronous call (cans_batch_*).
+    cases: objects with .n, .bc, .length_xy, .dzf (e.g. inputs.PoissonCase)."""
+
+    def __init__(self, cases, prec=CANS_MIXED, sweeps=2, nstreams=8):
+        self.cases = list(cases)
+        self.plans = []
+        for c in self.cases:
+            o = cans_opts_default()
+            o.prec, o.max_sweeps = int(prec), int(sweeps)
+            self.plans.append(cans_poisson_plan(c.n, c.length_xy, c.bc, c.dzf, o)[1])
+        self.batch = cans_batch_create(self.plans, nstreams)
+        self._ws_buf, self._ws = _aligned_workspace(cans_batch_workspace_size(self.batch))
+
+    def solve(self, fs, ps, stream=None):
+        _check(cans_batch_solve(self.batch, [t.data_ptr() for t in fs], [t.data_ptr() for t in ps], self._ws,
+                                _stream_ptr(stream)), "cans_batch_solve")
+        return ps
+
+    def close(self):
+        if getattr(self, "batch", None):
+            cans_batch_destroy(self.batch)
+            self.batch = None
+        for p in getattr(self, "plans", []):
+            cans_plan_destroy(p)
+        self.plans = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

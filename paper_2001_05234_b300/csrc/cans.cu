@@ -9,7 +9,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -20,6 +23,10 @@
 using namespace cans;
 
 static constexpr int MAXV = 8;  // must match the pass kernels
+
+namespace {
+int autotune_plan(cans_plan_s* P);
+}
 
 namespace {
 
@@ -193,13 +200,14 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   if (bc[2] == BC_P) {
     for (int k = 1; k < nz; ++k)
       if (dz[k] != dz[0]) return CANS_ERR_ARG;
-    return CANS_ERR_UNSUPPORTED;  // periodic z: not in this build
+    if (nz > 1 && (nz % 2)) return CANS_ERR_UNSUPPORTED;
+    if (nz > 1024) return CANS_ERR_UNSUPPORTED;
   }
   for (int d = 0; d < 2; ++d) {
     if (n[d] > 1 && (n[d] % 2)) return CANS_ERR_UNSUPPORTED;
     if (n[d] > 8192) return CANS_ERR_UNSUPPORTED;
   }
-  if (nz > 512) return CANS_ERR_UNSUPPORTED;
+  if (bc[2] != BC_P && nz > 512) return CANS_ERR_UNSUPPORTED;
   if ((size_t)n[0] * n[1] * n[2] >= ((size_t)1 << 40)) return CANS_ERR_UNSUPPORTED;
 
   cans_plan_s* P = new (std::nothrow) cans_plan_s();
@@ -218,6 +226,15 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     D.bc = bc[d];
     D.m = (n[d] >= 2) ? n[d] / 2 : 0;
     if (factor_radices(D.m, D.radix, &D.nst) != 0) {
+      delete P;
+      return CANS_ERR_UNSUPPORTED;
+    }
+  }
+  if (bc[2] == BC_P) {  // uniform periodic z is diagonalised as well
+    P->dz.n = nz;
+    P->dz.bc = BC_P;
+    P->dz.m = (nz >= 2) ? nz / 2 : 0;
+    if (factor_radices(P->dz.m, P->dz.radix, &P->dz.nst) != 0) {
       delete P;
       return CANS_ERR_UNSUPPORTED;
     }
@@ -294,6 +311,24 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   const size_t o_za = B.add(za.data(), nz * 8), o_zb = B.add(zb.data(), nz * 8), o_zc = B.add(zc.data(), nz * 8);
   auto zaf = to_float(za), zbf = to_float(zb), zcf = to_float(zc);
   const size_t o_zaf = B.add(zaf.data(), nz * 4), o_zbf = B.add(zbf.data(), nz * 4), o_zcf = B.add(zcf.data(), nz * 4);
+  size_t o_tz_d = 0, o_post_zd = 0, o_mak_zd = 0, o_tz_f = 0, o_post_zf = 0, o_mak_zf = 0, o_muz_d = 0, o_muz_f = 0;
+  if (bc[2] == BC_P) {
+    std::vector<double> twz, postz, makz;
+    dir_tables(P->dz, twz, postz, makz);
+    o_tz_d = B.add(twz.data(), twz.size() * 8);
+    o_post_zd = B.add(postz.data(), postz.size() * 8);
+    o_mak_zd = B.add(makz.data(), makz.size() * 8);
+    auto twzf = to_float(twz), postzf = to_float(postz), makzf = to_float(makz);
+    o_tz_f = B.add(twzf.data(), twzf.size() * 4);
+    o_post_zf = B.add(postzf.data(), postzf.size() * 4);
+    o_mak_zf = B.add(makzf.data(), makzf.size() * 4);
+    std::vector<double> muz(nz);
+    const double hz = dz[0];
+    for (int s = 0; s < nz; ++s) muz[s] = (nz == 1) ? 0.0 : (double)(slot_lambda(BC_P, nz, s) / ((long double)hz * hz));
+    auto muzf = to_float(muz);
+    o_muz_d = B.add(muz.data(), nz * 8);
+    o_muz_f = B.add(muzf.data(), nz * 4);
+  }
   size_t o_mask = 0;
   bool has_mask = false;
   if (o.prec == CANS_MIXED) {
@@ -362,6 +397,14 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->zt_f = {reinterpret_cast<const float*>(base + o_zaf), reinterpret_cast<const float*>(base + o_zbf),
              reinterpret_cast<const float*>(base + o_zcf)};
   P->mask_d = has_mask ? base + o_mask : nullptr;
+  if (bc[2] == BC_P) {
+    fill_line_tab<double>(P->tz_d, P->dz, base + o_tz_d, base + o_post_zd, base + o_mak_zd);
+    fill_line_tab<float>(P->tz_f, P->dz, base + o_tz_f, base + o_post_zf, base + o_mak_zf);
+    P->muz_d = reinterpret_cast<const double*>(base + o_muz_d);
+    P->muz_f = reinterpret_cast<const float*>(base + o_muz_f);
+    P->zs_l[0] = line_launch(nz, n[0], sizeof(double2), 8);
+    P->zs_l[1] = line_launch(nz, n[0], sizeof(float2), 16);
+  }
   P->acc_d = reinterpret_cast<double*>(base + o_acc);
 
   // launch shapes
@@ -381,6 +424,14 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     while (ti > 1 && ti / 2 >= n[0]) ti >>= 1;
     P->z_ti[s] = ti;
     P->z_smem[s] = (size_t)ti * nz * es;
+  }
+  if (o.autotune) {
+    const int rc = autotune_plan(P);
+    if (rc != CANS_OK) {
+      cudaFree(P->dtab);
+      delete P;
+      return rc;
+    }
   }
   *out = P;
   return CANS_OK;
@@ -491,6 +542,159 @@ struct PassTimer {
     cudaError_t e_ = (__VA_ARGS__);              \
     if (e_ != cudaSuccess) return CANS_ERR_CUDA; \
   } while (0)
+
+}  // namespace
+
+// ---- autotuner ---------------------------------------------------------------------------------
+// With opts.autotune = 1 the plan times candidate tile shapes for each pass on scratch fields (CUDA
+// events, best of 3 launches after a warm-up) and keeps the fastest: lines per CTA of the x and y
+// passes (and of the spectral z pass), x-slots per CTA of the tridiagonal z pass.  Results are cached
+// per (device, shape, boundary conditions, precision) for the life of the process and, when the
+// environment variable CANS_AUTOTUNE_CACHE names a file, read from and appended to that file.
+namespace {
+
+std::mutex g_tune_lock;
+std::vector<std::pair<std::string, std::vector<int>>> g_tune_cache;
+
+std::string tune_key(const cans_plan_s* P) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s|%d,%d,%d|%d,%d,%d|%d", prop.name, P->n[0], P->n[1], P->n[2], P->bc[0], P->bc[1],
+                P->bc[2], P->opts.prec);
+  std::string k(buf);
+  for (char& ch : k)
+    if (ch == ' ') ch = '_';
+  return k;
+}
+
+bool tune_lookup(const std::string& key, std::vector<int>& v) {
+  std::lock_guard<std::mutex> g(g_tune_lock);
+  for (auto& e : g_tune_cache)
+    if (e.first == key) {
+      v = e.second;
+      return true;
+    }
+  const char* path = std::getenv("CANS_AUTOTUNE_CACHE");
+  if (!path) return false;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), fh)) {
+    char k[400];
+    int a, b, cc, d;
+    if (std::sscanf(line, "%399s %d %d %d %d", k, &a, &b, &cc, &d) == 5 && key == k) {
+      v = {a, b, cc, d};
+      found = true;
+    }
+  }
+  std::fclose(fh);
+  if (found) g_tune_cache.push_back({key, v});
+  return found;
+}
+
+void tune_store(const std::string& key, const std::vector<int>& v) {
+  std::lock_guard<std::mutex> g(g_tune_lock);
+  g_tune_cache.push_back({key, v});
+  const char* path = std::getenv("CANS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%s %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+  std::fclose(fh);
+}
+
+template <typename F>
+float time_best(F&& launch) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  launch();
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    cudaEventRecord(a, 0);
+    cudaError_t e = launch();
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 1e30f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+int autotune_plan(cans_plan_s* P) {
+  const int s = (P->opts.prec == CANS_FP64) ? 0 : 1;
+  const size_t es = s ? sizeof(float2) : sizeof(double2);
+  const std::string key = tune_key(P);
+  std::vector<int> v;
+  auto apply = [&](const std::vector<int>& c) {
+    const int nlines = P->n[1] * P->n[2];
+    P->x_l[s] = line_launch(P->n[0], nlines, es, c[0]);
+    P->y_l[s] = line_launch(P->n[1], P->n[0], es, c[1]);
+    if (P->bc[2] == BC_P) {
+      P->zs_l[s] = line_launch(P->n[2], P->n[0], es, c[2]);
+    } else {
+      P->z_ti[s] = c[3];
+      P->z_smem[s] = (size_t)c[3] * P->n[2] * (s ? 4 : 8);
+    }
+  };
+  if (tune_lookup(key, v)) {
+    apply(v);
+    return CANS_OK;
+  }
+  const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+  double* f = nullptr;
+  void* w = nullptr;
+  if (cudaMalloc(&f, N * sizeof(double)) != cudaSuccess) return CANS_ERR_CUDA;
+  if (cudaMalloc(&w, N * (s ? 4 : 8)) != cudaSuccess) {
+    cudaFree(f);
+    return CANS_ERR_CUDA;
+  }
+  cudaMemset(f, 0, N * sizeof(double));
+  cudaMemset(w, 0, N * (s ? 4 : 8));
+  std::vector<int> best = {P->x_l[s].nl, P->y_l[s].nl, P->zs_l[s].nl, P->z_ti[s]};
+  const int cand_nl[4] = {4, 8, 16, 32};
+  const int cand_ti[3] = {s ? 8 : 4, s ? 16 : 8, s ? 32 : 16};
+  const int nlines = P->n[1] * P->n[2];
+  float bx = 1e30f, by = 1e30f, bz = 1e30f;
+  for (int c : cand_nl) {
+    P->x_l[s] = line_launch(P->n[0], nlines, es, c);
+    const float t = s ? time_best([&] { return launch_xfwd<float, 0>(P, f, nullptr, nullptr, (float*)w, nullptr, 0); })
+                      : time_best([&] { return launch_xfwd<double, 0>(P, f, nullptr, nullptr, (double*)w, nullptr, 0); });
+    if (t < bx) { bx = t; best[0] = c; }
+    P->y_l[s] = line_launch(P->n[1], P->n[0], es, c);
+    const float ty = s ? time_best([&] { return launch_y<float, 1>(P, (float*)w, 0); })
+                       : time_best([&] { return launch_y<double, 1>(P, (double*)w, 0); });
+    if (ty < by) { by = ty; best[1] = c; }
+    if (P->bc[2] == BC_P) {
+      P->zs_l[s] = line_launch(P->n[2], P->n[0], es, c);
+      const float tz = s ? time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); })
+                         : time_best([&] { return launch_z<double>(P, (double*)w, nullptr, 0); });
+      if (tz < bz) { bz = tz; best[2] = c; }
+    }
+  }
+  if (P->bc[2] != BC_P) {
+    for (int ti : cand_ti) {
+      if ((size_t)ti * P->n[2] * (s ? 4 : 8) > (size_t)96 * 1024) continue;
+      P->z_ti[s] = ti;
+      P->z_smem[s] = (size_t)ti * P->n[2] * (s ? 4 : 8);
+      const float tz = s ? time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); })
+                         : time_best([&] { return launch_z<double>(P, (double*)w, nullptr, 0); });
+      if (tz < bz) { bz = tz; best[3] = ti; }
+    }
+  }
+  cudaFree(f);
+  cudaFree(w);
+  apply(best);
+  tune_store(key, best);
+  return (cudaGetLastError() == cudaSuccess) ? CANS_OK : CANS_ERR_CUDA;
+}
 
 }  // namespace
 

@@ -60,6 +60,85 @@ cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st) {
   }
 }
 
+// Periodic (uniform) z: the z operator is diagonalised too.  A CTA takes nl consecutive x-slots of one
+// y-slot, transforms each column along z (real DFT), divides slot s by mu_x(i) + mu_y(j) + mu_z(s),
+// and transforms back (scaled by 1/Nz).  The singular (0,0,0) mode gets Nz * target, which makes the
+// column mean `target` (0, or the gauge correction of the mixed path's first sweep).
+template <typename T, int MC>
+__global__ void __launch_bounds__(512, 2) zspec_kernel(T* __restrict__ w, int nx, int ny, int nz, int lognl,
+                                                       LineTab<T> tb, const T* __restrict__ mux,
+                                                       const T* __restrict__ muy, const T* __restrict__ muz,
+                                                       int singular, const double* gauge, double gauge_scale) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int nl = 1 << lognl;
+  const Lay L{nl};
+  const int NZ = MC > 0 ? 2 * MC : nz;
+  const int i0 = blockIdx.x * nl, j = blockIdx.y;
+  const size_t plane = (size_t)nx * ny;
+  T* col0 = w + (size_t)j * nx + i0;
+  T* bufT = reinterpret_cast<T*>(buf);
+  for (int e = threadIdx.x; e < nl * NZ; e += blockDim.x) {
+    const int l = e & (nl - 1), n = e >> lognl;
+    const T v = (i0 + l < nx) ? col0[(size_t)n * plane + l] : (T)0;
+    forward_store<T, MC>(buf, L, tb, n, l, v);
+  }
+  __syncthreads();
+  line_forward<MAXV, T, MC>(buf, L, lognl, tb);
+  const T my = muy[j];
+  for (int e = threadIdx.x; e < nl * NZ; e += blockDim.x) {
+    const int l = e & (nl - 1), s = e >> lognl;
+    const int i = i0 + l;
+    if (i >= nx) continue;
+    T v = bufT[L.r(s, l)];
+    if (singular && i == 0 && j == 0 && s == 0)
+      v = (gauge != nullptr) ? (T)(gauge_scale * (*gauge) * NZ) : (T)0;
+    else
+      v = v / (mux[i] + my + muz[s]);
+    bufT[L.r(s, l)] = v;
+  }
+  __syncthreads();
+  line_inverse<MAXV, T, MC>(buf, L, lognl, tb);
+  const T inv = (T)1 / (T)NZ;
+  for (int e = threadIdx.x; e < nl * NZ; e += blockDim.x) {
+    const int l = e & (nl - 1), n = e >> lognl;
+    if (i0 + l < nx) col0[(size_t)n * plane + l] = inverse_sample<T, MC>(buf, L, tb, n, l) * inv;
+  }
+}
+
+template <typename T> const LineTab<T>& tab_z(const cans_plan_s* P);
+template <> const LineTab<double>& tab_z<double>(const cans_plan_s* P) { return P->tz_d; }
+template <> const LineTab<float>& tab_z<float>(const cans_plan_s* P) { return P->tz_f; }
+
+template <typename T, int MC>
+static cudaError_t zspec_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  const Launch& L = P->zs_l[sizeof(T) == 8 ? 0 : 1];
+  cudaError_t e = set_smem((const void*)zspec_kernel<T, MC>, L.smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((P->n[0] + L.nl - 1) / L.nl, P->n[1]);
+  const T* mux = sizeof(T) == 8 ? (const T*)P->mux_d : (const T*)P->mux_f;
+  const T* muy = sizeof(T) == 8 ? (const T*)P->muy_d : (const T*)P->muy_f;
+  const T* muz = sizeof(T) == 8 ? (const T*)P->muz_d : (const T*)P->muz_f;
+  zspec_kernel<T, MC><<<grid, L.threads, L.smem, st>>>(w, P->n[0], P->n[1], P->n[2], L.lognl, tab_z<T>(P), mux, muy,
+                                                       muz, P->singular ? 1 : 0, gauge, P->gauge_scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  switch (P->dz.m) {
+#define CASE_M(MM) \
+  case MM: return zspec_m<T, MM>(P, w, gauge, st);
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return zspec_m<T, 0>(P, w, gauge, st);
+  }
+}
+
+template cudaError_t launch_zspec<double>(const cans_plan_s*, double*, const double*, cudaStream_t);
+template cudaError_t launch_zspec<float>(const cans_plan_s*, float*, const double*, cudaStream_t);
+
 template cudaError_t launch_y<double, 1>(const cans_plan_s*, double*, cudaStream_t);
 template cudaError_t launch_y<double, -1>(const cans_plan_s*, double*, cudaStream_t);
 template cudaError_t launch_y<float, 1>(const cans_plan_s*, float*, cudaStream_t);

@@ -190,6 +190,7 @@ static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStre
 
 template <typename T>
 cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  if (P->bc[2] == BC_P) return launch_zspec<T>(P, w, gauge, st);
   switch (P->z_mmax) {
     case 1: return z_m<T, 1>(P, w, gauge, st);
     case 2: return z_m<T, 2>(P, w, gauge, st);

@@ -57,11 +57,16 @@ struct cans_plan_s {
   cans_opts opts;
   int device = 0;
   bool singular = false;
-  cans::DirHost dx, dy;
+  cans::DirHost dx, dy, dz;  // dz only for a periodic z
   std::vector<double> mux_h, muy_h;
   void* dtab = nullptr;
   cans::LineTab<double> tx_d, ty_d;
   cans::LineTab<float> tx_f, ty_f;
+  cans::LineTab<double> tz_d;  // periodic z only
+  cans::LineTab<float> tz_f;
+  const double* muz_d = nullptr;
+  const float* muz_f = nullptr;
+  cans::Launch zs_l[2];
   cans::ZTab<double> zt_d;
   cans::ZTab<float> zt_f;
   const double *mux_d, *muy_d, *dzf_d, *sa_d, *sc_d;
@@ -100,6 +105,8 @@ template <typename T, int DIR>
 cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st);
 template <typename T>
 cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
+template <typename T>
+cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
 cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st);
 cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st);
 cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double* v, const double* w, const double* p,

@@ -266,3 +266,23 @@ def rhs_device(case: PoissonCase, device):
     m = (f.mean(dim=(1, 2)) * w).sum()
     f -= m
     return f.contiguous()
+
+
+def ensemble_cases(count=64, seed=SEED_BASE + 5, sizes=(32, 48, 64, 96, 128, 192)):
+    """Uneven ensemble: every dimension from `sizes`, the boundary condition of every direction from
+    {periodic, Neumann, Dirichlet}; a non-periodic z is uniform (probability 1/2) or tanh-stretched
+    with alpha ~ U[1.0, 2.2]; unit box; f ~ U[-1, 1] (made compatible by rhs_host)."""
+    cases = []
+    dims = randint(seed, 3 * count, 0, len(sizes) - 1, stream=21).reshape(count, 3)
+    bcs = randint(seed, 3 * count, 0, 2, stream=22).reshape(count, 3)
+    coin = uniform(seed, (count,), stream=23)
+    alphas = uniform(seed, (count,), 1.0, 2.2, stream=24)
+    for q in range(count):
+        n = tuple(int(sizes[d]) for d in dims[q])
+        bc = tuple(int(b) for b in bcs[q])
+        if bc[2] == BC_P or coin[q] < 0.5:
+            dzf = uniform_dzf(n[2])
+        else:
+            dzf = tanh_dzf(n[2], float(alphas[q]))
+        cases.append(PoissonCase(f"ensemble{q}", n, bc, (1.0, 1.0), dzf, seed * 1000 + q, "uniform"))
+    return cases

@@ -62,7 +62,7 @@ def test_opts_defaults(cans):
         ((8, 8, 4), (1, 1), (0, 0, 1), [0.25, 0.25, -0.1, 0.6], -1),  # negative cell width
         ((8, 8, 4), (1, 1), (0, 0, 1), [0.25, 0.25, float("nan"), 0.5], -1),  # non-finite cell width
         ((8, 8, 4), (1, 1), (0, 0, 0), [0.2, 0.3, 0.25, 0.25], -1),  # periodic z must be uniform
-        ((8, 8, 4), (1, 1), (0, 0, 0), None, -2),  # periodic z not built
+        ((8, 8, 5), (1, 1), (0, 0, 0), None, -2),  # odd periodic Nz
         ((7, 8, 4), (1, 1), (0, 0, 1), None, -2),  # odd periodic N
         ((8, 10, 4), (1, 1), (0, 1, 1), None, -2),  # N/2 = 5 does not factor into 2s and 3s
         ((8, 8, 600), (1, 1), (0, 0, 1), None, -2),  # Nz above 512

@@ -170,15 +170,16 @@ def test_dense_lu_8cubed_copy(cans):
     assert st == 0 and rel(p, ref) <= 1e-12
 
 
-BC_CASES = [(bx, by, bz) for bx in (P, NN, DD) for by in (P, NN, DD) for bz in (NN, DD)]
+BC_CASES = [(bx, by, bz) for bx in (P, NN, DD) for by in (P, NN, DD) for bz in (P, NN, DD)]
 
 
 @pytest.mark.parametrize("bc", BC_CASES)
 def test_fp64_solve_all_boundary_conditions(cans, bc):
-    n = (48, 24, 20)  # radix-3 lengths, a ragged z segment, x tiles with a tail
-    dzf = I.tanh_dzf(20, 1.8)
+    nz = 20 if bc[2] != P else 24  # a ragged z segment; a periodic z needs N/2 = 2^a 3^b
+    n = (48, 24, nz)  # radix-3 lengths, x tiles with a tail
+    dzf = I.tanh_dzf(nz, 1.8) if bc[2] != P else I.uniform_dzf(nz)
     L = (1.5, 0.75)
-    f = np.random.default_rng(sum(bc)).uniform(-1, 1, (20, 24, 48))
+    f = np.random.default_rng(sum(bc)).uniform(-1, 1, (nz, 24, 48))
     if DD not in bc:
         f = I.weighted_mean_removed(f, dzf)
     p, st, _ = solve_gpu(cans, f, n, bc, L, dzf)
@@ -197,11 +198,13 @@ def test_fp64_solve_all_boundary_conditions(cans, bc):
         ((2, 2, 2), (P, P, NN)),  # smallest even lengths, singular
         ((64, 96, 31), (P, NN, DD)),  # radix 3 in y, odd Nz
         ((16, 16, 512), (P, P, NN)),  # 16 rows per lane
+        ((8, 6, 1), (P, P, P)),  # one periodic z cell
+        ((16, 12, 96), (DD, P, P)),  # periodic z, radix 3
     ],
 )
 def test_fp64_solve_edge_shapes(cans, n, bc):
     nx, ny, nz = n
-    dzf = I.tanh_dzf(nz, 1.4) if nz > 2 else I.uniform_dzf(nz)
+    dzf = I.tanh_dzf(nz, 1.4) if (nz > 2 and bc[2] != P) else I.uniform_dzf(nz)
     f = np.random.default_rng(nx + 7 * ny + 13 * nz).uniform(-1, 1, (nz, ny, nx))
     if DD not in bc:
         f = I.weighted_mean_removed(f, dzf)
@@ -237,10 +240,10 @@ def test_incompatible_rhs_is_reported(cans):
 # ---------------------------------------------------------------------------------------------
 # mixed precision + refinement
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("bc", [(P, P, NN), (P, DD, NN), (NN, DD, DD), (DD, NN, NN)])
+@pytest.mark.parametrize("bc", [(P, P, NN), (P, DD, NN), (NN, DD, DD), (DD, NN, NN), (P, P, P), (NN, DD, P)])
 def test_mixed_refined_reaches_fp64_accuracy(cans, bc):
-    n = (64, 48, 40)
-    dzf = I.tanh_dzf(40, 1.8)
+    n = (64, 48, 40) if bc[2] != P else (64, 48, 48)
+    dzf = I.tanh_dzf(40, 1.8) if bc[2] != P else I.uniform_dzf(48)
     case = I.case_modes(n=n)
     case.bc = bc
     case.dzf = dzf
@@ -267,3 +270,28 @@ def test_mixed_first_solve_only(cans):
     ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf)
     assert rel(p, ref) < 1e-4  # FP32 transforms alone
     assert st == -6  # tolerance 1e-12 not reached without refinement
+
+
+def test_autotuned_plan_matches_oracle(cans, tmp_path, monkeypatch):
+    """opts.autotune = 1 picks tile shapes by timing; results stay exact and the cache file is written."""
+    import torch
+
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("CANS_AUTOTUNE_CACHE", str(cache))
+    case = I.case_channel(n=(128, 64, 48))
+    f = I.rhs_host(case)
+    ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf)
+    for prec in (0, 1):
+        o = cans.cans_opts_default()
+        o.prec, o.max_sweeps, o.autotune = prec, 2, 1
+        _, h = cans.cans_poisson_plan(case.n, case.length_xy, case.bc, case.dzf, o)
+        nbytes = cans.cans_poisson_workspace_size(h)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        wp = (ws.data_ptr() + 255) // 256 * 256 if nbytes else 0
+        ft = dev(f)
+        pt = torch.empty_like(ft)
+        assert cans.cans_poisson_solve(h, ft.data_ptr(), pt.data_ptr(), wp, stream(), None) == 0
+        assert rel(host(pt), ref) <= (1e-12 if prec == 0 else 1e-11)
+        cans.cans_plan_destroy(h)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 2 and all(len(l.split()) == 5 for l in lines)
