@@ -102,15 +102,22 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
-PASS_BYTES_MIXED = {  # algorithmic bytes per point that each pass must move (mixed precision)
-    0: 12,  # x forward: read f (8), write the float work field (4)
-    1: 8,   # y forward: read + write float
-    2: 8,   # z solve: read + write float
-    3: 8,   # y inverse
-    4: 12,  # x inverse of the first solve: read work (4), write Phi (4) and Plo (4)
-    5: 20,  # x forward + residual: read f (8), Phi (4), Plo (4), write work (4)
-    6: 20,  # x inverse + update: read work (4), Phi (4), Plo (4), write p (8)
-}
+def pass_bytes_mixed(sweeps: int):
+    """Algorithmic bytes per point each pass kind must move in the mixed solve with `sweeps` sweeps
+    (the first sweep knows the iterate's tail Plo is zero, later sweeps read and write it)."""
+    first, later = 16, 20
+    avg = (first + later * (sweeps - 1)) / max(sweeps, 1)
+    return {
+        0: 12,   # x forward: read f (8), write the float work field (4)
+        1: 8,    # y forward: read + write float
+        2: 8,    # z solve: read + write float
+        3: 8,    # y inverse
+        4: 8,    # x inverse of the first solve: read work (4), write Phi (4)
+        5: avg,  # x forward + residual: read f (8), Phi (4) [, Plo (4)], write work (4)
+        6: avg,  # x inverse + update: read work (4), Phi (4) [, Plo (4)], write p (8) or Phi, Plo (8)
+    }
+
+
 PASS_BYTES_FP64 = {0: 16, 1: 16, 2: 16, 3: 16, 4: 16}
 
 
@@ -121,6 +128,7 @@ def gpu_arm(args):
     import paper_2001_05234_b300 as cans
     from paper_2001_05234_b300 import build_lib
     from paper_2001_05234_b300 import inputs as I
+    from paper_2001_05234_b300 import replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -154,7 +162,8 @@ def gpu_arm(args):
             break
     if sweeps_used is None:
         sweeps_used, info_used = 3, info
-    solver = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sweeps_used)
+    solver = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sweeps_used,
+                                autotune=True)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -175,12 +184,9 @@ def gpu_arm(args):
     cans.cans_plan_profile(solver.plan, False)
     clk = clocks.stop() if rank == 0 else None
     ms_total = e0.elapsed_time(e1)
-    ms = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms_total / args.steps, device="cuda")
     # per-pass device times inside the timed region
+    PASS_BYTES_MIXED = pass_bytes_mixed(sweeps_used)
     passes = {}
     for k in range(7):
         tot, n = cans.cans_plan_profile_read(solver.plan, k)
@@ -197,7 +203,7 @@ def gpu_arm(args):
     kernels_per_solve = (6 * (1 + sweeps_used))  # x, y, z(float), z(double), y, x per solve and sweep
 
     # plain FP64 solve of the same workload
-    s64 = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64)
+    s64 = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64, autotune=True)
     s64.solve(f, p)
     barrier()
     f64_steps = max(2, min(args.steps, 5))
@@ -225,6 +231,11 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     solver.close()
+    del fh, ph, fd, f, p
+    torch.cuda.empty_cache()
+
+    rk3 = rk3_measure(cans, I, args)
+    ens = ensemble_measure(cans, I, args)
 
     if rank != 0:
         if world > 1:
@@ -235,7 +246,7 @@ def gpu_arm(args):
     cpu = cpu_baseline(seconds_budget=args.cpu_budget)
     out = {
         "metric": METRIC,
-        "value": world * npts / (ms * 1e-3) / 1e9,
+        "value": replicas.aggregate_gpts(npts, ms, world),
         "unit": "Gpts/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -277,11 +288,86 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8},
         "gpu_launches": kernels_per_solve * args.steps,
         "clocks": clk,
+        "rk3_step": rk3,
+        "ensemble": ens,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def rk3_measure(cans, I, args):
+    """ms per RK3 step of the 512x256x192 channel (Lx = 4 pi, Ly = 2 pi, Lz = 2, tanh 1.8, Re_b = 5600,
+    CFL 0.9), FP64 momentum / divergence / correction, Poisson solves mixed+refined and FP64."""
+    import torch
+
+    n, L = (512, 256, 192), (4 * np.pi, 2 * np.pi)
+    dzf = I.tanh_dzf(192, 1.8, 2.0)
+    shape = (n[2], n[1], n[0])
+    zc = torch.tensor(I.z_centres(dzf), device="cuda")
+    npts = n[0] * n[1] * n[2]
+    seed = I.SEED_BASE + 4
+    out = {"workload": "channel_512x256x192_Re5600_tanh1.8", "unit": "ms/step"}
+    for name, prec in (("mixed", cans.CANS_MIXED), ("fp64", cans.CANS_FP64)):
+        u = (1.5 * (1 - (zc - 1) ** 2))[:, None, None] + 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=11).view(shape) - 1)
+        v = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=12).view(shape) - 1)
+        w = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=13).view(shape) - 1)
+        w[-1] = 0
+        p = torch.zeros_like(u)
+        ch = cans.Channel(n, L, dzf, prec=prec, sweeps=1)
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0, dt_out=dt)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0, dt_out=dt)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 5
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / steps
+        out[name + "_dt"] = float(dt.item())
+        ch.close()
+        del u, v, w, p, g
+    torch.cuda.empty_cache()
+    out["note"] = "one CUDA graph per step; mixed = Poisson solves mixed precision with 1 refinement sweep"
+    return out
+
+
+def ensemble_measure(cans, I, args):
+    """Aggregate Gpts/s of the 64-problem uneven ensemble (dims from {32..192}, BC per direction from
+    P/NN/DD, uniform or tanh z), mixed + 2 sweeps, one CUDA graph per batch."""
+    import torch
+
+    cases = I.ensemble_cases()
+    fs = [I.rhs_device(c, "cuda") for c in cases]
+    ps = [torch.empty_like(f) for f in fs]
+    b = cans.Batch(cases, prec=cans.CANS_MIXED, sweeps=2, nstreams=16)
+    b.solve(fs, ps)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.solve(fs, ps)
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pts = sum(c.points for c in cases)
+    b.close()
+    return {"workload": "ensemble64_dims32-192_mixed_2sweeps", "problems": len(cases), "points": pts,
+            "ms_per_batch": ms, "value": pts / (ms * 1e-3) / 1e9, "unit": "Gpts/s"}
 
 
 # ------------------------------------------------------------------------------------------------

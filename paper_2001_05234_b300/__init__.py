@@ -239,7 +239,7 @@ class PoissonSolver:
     """Owns a plan and its device workspace.  f, p: torch float64 CUDA tensors of shape (Nz, Ny, Nx)."""
 
     def __init__(self, n, bc, length_xy=(1.0, 1.0), dzf=None, prec=CANS_FP64, sweeps=2, tol=1e-12,
-                 fp64_fraction=0.01):
+                 fp64_fraction=0.01, autotune=False):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -249,6 +249,7 @@ class PoissonSolver:
         o.max_sweeps = int(sweeps)
         o.tol = float(tol)
         o.fp64_mode_fraction = float(fp64_fraction)
+        o.autotune = 1 if autotune else 0
         self.opts = o
         _, self.plan = cans_poisson_plan(self.n, length_xy, self.bc, dzf, o)
         nbytes = cans_poisson_workspace_size(self.plan)
