@@ -1,0 +1,23 @@
+// Asynchronous global -> shared copies (cp.async, sm_80+ instruction family, available on sm_103a):
+// a tile for the next iteration is fetched into one half of a double buffer while the current tile
+// is transformed in the other.  wait_group is a hardware wait on this thread's own copies.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace cans {
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND));
+}
+
+}  // namespace cans

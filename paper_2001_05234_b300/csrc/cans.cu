@@ -216,6 +216,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   std::memcpy(P->len, len_xy, sizeof(P->len));
   std::memcpy(P->bc, bc, sizeof(P->bc));
   P->opts = o;
+  P->wblk = 0;  // the blocked work-field layout measured no faster on B300; kept selectable
   cudaGetDevice(&P->device);
   P->singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
 
@@ -437,10 +438,17 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   return CANS_OK;
 }
 
+// Mixed-path workspace: the float work field W (blocked layout, x padded to a multiple of 32 slots),
+// then the double-float iterate Phi, Plo (natural layout).
+static size_t work_field_bytes(const cans_plan_s* P) {
+  const size_t nxp = P->wblk ? (size_t)((P->n[0] + 31) / 32) * 32 : (size_t)P->n[0];
+  return align256(nxp * P->n[1] * P->n[2] * sizeof(float));
+}
+
 int cans_poisson_workspace_size(cans_plan_t P, size_t* bytes) {
   if (!P || !bytes) return CANS_ERR_ARG;
   const size_t N = field_points(P);
-  *bytes = (P->opts.prec == CANS_MIXED) ? 3 * align256(N * sizeof(float)) : 0;
+  *bytes = (P->opts.prec == CANS_MIXED) ? work_field_bytes(P) + 2 * align256(N * sizeof(float)) : 0;
   return CANS_OK;
 }
 
@@ -491,6 +499,10 @@ int cans_plan_eigenvalues(cans_plan_t P, double* mux, double* muy) {
 namespace {
 
 }  // namespace
+
+Launch cans::line_launch_shape(int N, int count, size_t elem2, int prefer_nl) {
+  return line_launch(N, count, elem2, prefer_nl);
+}
 
 cudaError_t cans::set_smem(const void* fn, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -652,12 +664,13 @@ int autotune_plan(cans_plan_s* P) {
   double* f = nullptr;
   void* w = nullptr;
   if (cudaMalloc(&f, N * sizeof(double)) != cudaSuccess) return CANS_ERR_CUDA;
-  if (cudaMalloc(&w, N * (s ? 4 : 8)) != cudaSuccess) {
+  const size_t wbytes = s ? work_field_bytes(P) : N * 8;
+  if (cudaMalloc(&w, wbytes) != cudaSuccess) {
     cudaFree(f);
     return CANS_ERR_CUDA;
   }
   cudaMemset(f, 0, N * sizeof(double));
-  cudaMemset(w, 0, N * (s ? 4 : 8));
+  cudaMemset(w, 0, wbytes);
   std::vector<int> best = {P->x_l[s].nl, P->y_l[s].nl, P->zs_l[s].nl, P->z_ti[s]};
   const int cand_nl[4] = {4, 8, 16, 32};
   const int cand_ti[3] = {s ? 8 : 4, s ? 16 : 8, s ? 32 : 16};
@@ -722,8 +735,8 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CANS_ERR_WORKSPACE;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     float* W = reinterpret_cast<float*>(ws);
-    float* Phi = reinterpret_cast<float*>(ws + align256(N * 4));
-    float* Plo = reinterpret_cast<float*>(ws + 2 * align256(N * 4));
+    float* Phi = reinterpret_cast<float*>(ws + work_field_bytes(P));
+    float* Plo = reinterpret_cast<float*>(ws + work_field_bytes(P) + align256(N * 4));
     CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
     TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));

@@ -2,6 +2,9 @@
 // conversion, or with the double-float residual of a refinement sweep) and the inverse transform
 // (fused with the normalisation and the update of the iterate).  Transform along x = the operator
 // F^x of Eq. poi_reduced.
+#include <algorithm>
+
+#include "async.cuh"
 #include "plan.cuh"
 
 namespace cans {
@@ -137,27 +140,39 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
   const int line0 = blockIdx.x * nl;
   const float inv_ny = 1.0f / (float)S.n[1];
   float acc = 0.f;
-  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-    const int l = e / N, n = e - l * N;
-    const int line = line0 + l;
-    T v = 0;
-    if (line < a.nlines) {
-      const size_t c = (size_t)line * N + n;
-      if (MODE == 0) {
-        const double fv = f[c];
-        const float ff = (float)fv;
-        acc += ff * ff;
-        v = (T)fv;
-      } else {
-        // k = line / Ny, exact: (line + 1/2)/Ny stays >= 1/(2 Ny) away from an integer
-        const int k = (int)(((float)line + 0.5f) * inv_ny);
-        const int j = line - k * S.n[1];
-        const float r = residual_point<MODE == 1>(f, Phi, Plo, S, c, n, j, k);
-        acc += r * r;
-        v = (T)r;
+  // copy-in with U independent loads (or residual evaluations) in flight per thread
+  constexpr int U = (MODE == 0) ? 8 : 2;
+  const int total = nl * N;
+  for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      const int l = e / N, n = e - l * N;
+      const int line = line0 + l;
+      v[u] = (T)0;
+      if (e < total && line < a.nlines) {
+        const size_t c = (size_t)line * N + n;
+        if (MODE == 0) {
+          v[u] = (T)f[c];
+        } else {
+          // k = line / Ny, exact: (line + 1/2)/Ny stays >= 1/(2 Ny) away from an integer
+          const int k = (int)(((float)line + 0.5f) * inv_ny);
+          const int j = line - k * S.n[1];
+          v[u] = (T)residual_point<MODE == 1>(f, Phi, Plo, S, c, n, j, k);
+        }
       }
     }
-    forward_store<T, MC>(buf, L, tb, n, l, v);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * blockDim.x;
+      if (e < total) {
+        const float vf = (float)v[u];
+        acc += vf * vf;
+        const int l = e / N;
+        forward_store<T, MC>(buf, L, tb, e - l * N, l, v[u]);
+      }
+    }
   }
   __syncthreads();
   line_forward<MAXV, T, MC>(buf, L, a.lognl, tb);
@@ -165,7 +180,14 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
   for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
     const int l = e / N, s = e - l * N;
     const int line = line0 + l;
-    if (line < a.nlines) dst[(size_t)line * N + s] = bufT[L.r(s, l)];
+    if (line < a.nlines) {
+      if (a.w.blk) {
+        const int k = (int)(((float)line + 0.5f) * inv_ny);
+        dst[a.w.at(s, line - k * a.w.ny, k)] = bufT[L.r(s, l)];
+      } else {
+        dst[(size_t)line * N + s] = bufT[L.r(s, l)];
+      }
+    }
   }
   if (norm_acc != nullptr) block_accumulate(acc, norm_acc);
 }
@@ -187,10 +209,35 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
   const int N = MC > 0 ? 2 * MC : a.nx;
   const int line0 = blockIdx.x * nl;
   T* bufT = reinterpret_cast<T*>(buf);
-  for (int e = threadIdx.x; e < nl * N; e += blockDim.x) {
-    const int l = e / N, s = e - l * N;
-    const int line = line0 + l;
-    bufT[L.r(s, l)] = (line < a.nlines) ? src[(size_t)line * N + s] : (T)0;
+  const float inv_ny = 1.0f / (float)ny;
+  {
+    constexpr int U = 8;
+    const int total = nl * N;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * blockDim.x;
+        const int line = line0 + e / N;
+        v[u] = (T)0;
+        if (e < total && line < a.nlines) {
+          if (a.w.blk) {
+            const int k = (int)(((float)line + 0.5f) * inv_ny);
+            v[u] = src[a.w.at(e - (e / N) * N, line - k * a.w.ny, k)];
+          } else {
+            v[u] = src[(size_t)line0 * N + e];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * blockDim.x;
+        if (e < total) {
+          const int l = e / N;
+          bufT[L.r(e - l * N, l)] = v[u];
+        }
+      }
+    }
   }
   __syncthreads();
   line_inverse<MAXV, T, MC>(buf, L, a.lognl, tb);
@@ -227,6 +274,145 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
   if (MODE == 1 && gauge != nullptr) block_accumulate_d((double)gacc.hi + (double)gacc.lo, gauge);
 }
 
+// ---- pipelined x-passes -------------------------------------------------------------------------
+// A tile is nl consecutive lines, contiguous in memory: it is staged with 16-byte cp.async copies
+// into padded shared rows (row stride N + PADE elements spreads the lanes of one sample index over
+// the banks) while the previous tile is transformed.  The first FFT stage reads the staged rows
+// directly; the post-processing (forward) or last stage (inverse) writes to global memory with
+// consecutive threads on consecutive slots of one line.
+template <typename S>
+__device__ __forceinline__ void stage_lines(S* dst, const S* src, int nl, int N, int pad, int lines_valid) {
+  constexpr int V = 16 / sizeof(S);
+  const int per_line = N / V;
+  for (int e = threadIdx.x; e < nl * per_line; e += blockDim.x) {
+    const int l = e / per_line, c = (e - l * per_line) * V;
+    S* d = dst + (size_t)l * (N + pad) + c;
+    if (l < lines_valid) {
+      cp_async16(d, src + (size_t)l * N + c);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[v] = (S)0;
+    }
+  }
+  cp_async_commit();
+}
+
+template <int MC>
+__global__ void __launch_bounds__(512, 2) xfwd_pipe_kernel(const double* __restrict__ f, float* __restrict__ dst,
+                                                           int nlines, int lognl, LineTab<float> tb, double* norm_acc) {
+  typedef float2 C;
+  constexpr int N = 2 * MC, PAD = 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = 1 << lognl;
+  double* raw = reinterpret_cast<double*>(smem_raw);  // [2][nl][N + PAD]
+  C* buf = reinterpret_cast<C*>(smem_raw + 2 * (size_t)nl * (N + PAD) * sizeof(double));
+  const Lay L{nl};
+  const int ntiles = (nlines + nl - 1) / nl;
+  float acc = 0.f;
+  int t = blockIdx.x;
+  if (t < ntiles) stage_lines<double>(raw, f + (size_t)t * nl * N, nl, N, PAD, min(nl, nlines - t * nl));
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int slot = it & 1;
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      stage_lines<double>(raw + (size_t)(slot ^ 1) * nl * (N + PAD), f + (size_t)tn * nl * N, nl, N, PAD,
+                          min(nl, nlines - tn * nl));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const double* src = raw + (size_t)slot * nl * (N + PAD);
+    const int line0 = t * nl;
+    auto load = [&](int l, int n) -> float {
+      const float v = (float)src[l * (N + PAD) + n];
+      acc += v * v;
+      return v;
+    };
+    auto store = [&](int l, int s, float v) {
+      if (line0 + l < nlines) dst[(size_t)(line0 + l) * N + s] = v;
+    };
+    line_forward_fused<MAXV, float, MC, true>(buf, L, lognl, tb, load, store);
+    __syncthreads();
+  }
+  if (norm_acc != nullptr) block_accumulate(acc, norm_acc);
+}
+
+// Inverse x-pass, pipelined; MODE as xinv_kernel.
+template <typename T, int MODE, int MC>
+__global__ void __launch_bounds__(512, 2) xinv_pipe_kernel(const T* __restrict__ src, double* __restrict__ p,
+                                                           float* __restrict__ Phi, float* __restrict__ Plo,
+                                                           int nlines, int lognl, double scale, LineTab<T> tb,
+                                                           const float* __restrict__ wz,
+                                                           const float* __restrict__ wz_lo, int ny, double* gauge) {
+  typedef typename V2<T>::t C;
+  constexpr int N = 2 * MC, PAD = 16 / sizeof(T);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nl = 1 << lognl;
+  T* raw = reinterpret_cast<T*>(smem_raw);  // [2][nl][N + PAD]
+  C* buf = reinterpret_cast<C*>(smem_raw + 2 * (size_t)nl * (N + PAD) * sizeof(T));
+  const Lay L{nl};
+  const int ntiles = (nlines + nl - 1) / nl;
+  const float fscale = (float)scale;
+  df gacc = df_make(0.f, 0.f);
+  int t = blockIdx.x;
+  if (t < ntiles) stage_lines<T>(raw, src + (size_t)t * nl * N, nl, N, PAD, min(nl, nlines - t * nl));
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int slot = it & 1;
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      stage_lines<T>(raw + (size_t)(slot ^ 1) * nl * (N + PAD), src + (size_t)tn * nl * N, nl, N, PAD,
+                     min(nl, nlines - tn * nl));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const T* rs = raw + (size_t)slot * nl * (N + PAD);
+    const int line0 = t * nl;
+    auto loadslot = [&](int l, int s) -> T { return rs[l * (N + PAD) + s]; };
+    auto store = [&](int l, int n, T v) {
+      const int line = line0 + l;
+      if (line >= nlines) return;
+      const size_t o = (size_t)line * N + n;
+      if (MODE == 0) {
+        p[o] = (double)v * scale;
+      } else if (MODE == 1) {
+        const float ph = (float)v * fscale;
+        Phi[o] = ph;
+        if (gauge != nullptr) {
+          const int k = line / ny;
+          df tt = two_prod(ph, wz[k]);
+          tt.lo = __fmaf_rn(ph, wz_lo[k], tt.lo);
+          gacc = df_add(gacc, tt);
+        }
+      } else {
+        const float d = (float)v * fscale;
+        df s2 = two_sum(Phi[o], d);
+        s2 = fast_two_sum(s2.hi, (MODE <= 3) ? s2.lo + Plo[o] : s2.lo);
+        if (MODE == 2 || MODE == 4) {
+          Phi[o] = s2.hi;
+          Plo[o] = s2.lo;
+        } else {
+          p[o] = df_to_double(s2);
+        }
+      }
+    };
+    line_inverse_fused<MAXV, T, MC, true>(buf, L, lognl, tb, loadslot, store);
+    __syncthreads();
+  }
+  if (MODE == 1 && gauge != nullptr) block_accumulate_d((double)gacc.hi + (double)gacc.lo, gauge);
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int ntiles) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(ntiles, std::max(per_sm, 1) * sms));
+}
+
 StencilDF stencil_df(const cans_plan_s* P) {
   StencilDF S;
   S.idx2.hi = (float)P->idx2;
@@ -248,7 +434,7 @@ template <typename T, int MODE, int MC>
 static cudaError_t xfwd_m(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
                           double* acc, cudaStream_t st) {
   const Launch& L = P->x_l[sizeof(T) == 8 ? 0 : 1];
-  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, 1.0};
+  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, 1.0, wlay(P, sizeof(T) == 4)};
   cudaError_t e = set_smem((const void*)xfwd_kernel<T, MODE, MC>, L.smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.nlines + L.nl - 1) / L.nl;
@@ -256,9 +442,34 @@ static cudaError_t xfwd_m(const cans_plan_s* P, const double* f, const float* Ph
   return cudaGetLastError();
 }
 
+template <int MC>
+static cudaError_t xfwd_pipe_m(const cans_plan_s* P, const double* f, float* dst, double* acc, cudaStream_t st) {
+  Launch L = P->x_l[1];
+  size_t smem = L.smem + 2 * (size_t)L.nl * (2 * MC + 2) * sizeof(double);
+  while (smem > (size_t)110 * 1024 && L.nl > 1) {  // keep two CTAs per SM
+    L = line_launch_shape(2 * MC, P->n[1] * P->n[2], sizeof(float2), L.nl / 2);
+    smem = L.smem + 2 * (size_t)L.nl * (2 * MC + 2) * sizeof(double);
+  }
+  cudaError_t e = set_smem((const void*)xfwd_pipe_kernel<MC>, smem);
+  if (e != cudaSuccess) return e;
+  const int nlines = P->n[1] * P->n[2];
+  const int grid = persistent_grid(xfwd_pipe_kernel<MC>, L.threads, smem, (nlines + L.nl - 1) / L.nl);
+  xfwd_pipe_kernel<MC><<<grid, L.threads, smem, st>>>(f, dst, nlines, L.lognl, P->tx_f, acc);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODE>
 cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
                         double* acc, cudaStream_t st) {
+  if (MODE == 0 && sizeof(T) == 4 && !P->wblk) {
+    switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xfwd_pipe_m<MM>(P, f, reinterpret_cast<float*>(dst), acc, st);
+      CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+      default: break;
+    }
+  }
   switch (P->dx.m) {
 #define CASE_M(MM) \
   case MM: return xfwd_m<T, MODE, MM>(P, f, Phi, Plo, dst, acc, st);
@@ -272,7 +483,7 @@ template <typename T, int MODE, int MC>
 static cudaError_t xinv_m(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
                           double* gauge, cudaStream_t st) {
   const Launch& L = P->x_l[sizeof(T) == 8 ? 0 : 1];
-  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, scale};
+  XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, scale, wlay(P, sizeof(T) == 4)};
   cudaError_t e = set_smem((const void*)xinv_kernel<T, MODE, MC>, L.smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.nlines + L.nl - 1) / L.nl;
@@ -281,9 +492,37 @@ static cudaError_t xinv_m(const cans_plan_s* P, const T* src, double* p, float* 
   return cudaGetLastError();
 }
 
+template <typename T, int MODE, int MC>
+static cudaError_t xinv_pipe_m(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
+                               double* gauge, cudaStream_t st) {
+  Launch L = P->x_l[sizeof(T) == 8 ? 0 : 1];
+  constexpr int PAD = 16 / sizeof(T);
+  size_t smem = L.smem + 2 * (size_t)L.nl * (2 * MC + PAD) * sizeof(T);
+  while (smem > (size_t)110 * 1024 && L.nl > 1) {
+    L = line_launch_shape(2 * MC, P->n[1] * P->n[2], sizeof(typename V2<T>::t), L.nl / 2);
+    smem = L.smem + 2 * (size_t)L.nl * (2 * MC + PAD) * sizeof(T);
+  }
+  cudaError_t e = set_smem((const void*)xinv_pipe_kernel<T, MODE, MC>, smem);
+  if (e != cudaSuccess) return e;
+  const int nlines = P->n[1] * P->n[2];
+  const int grid = persistent_grid(xinv_pipe_kernel<T, MODE, MC>, L.threads, smem, (nlines + L.nl - 1) / L.nl);
+  xinv_pipe_kernel<T, MODE, MC><<<grid, L.threads, smem, st>>>(src, p, Phi, Plo, nlines, L.lognl, scale, tab_x<T>(P),
+                                                               P->dzf_f, P->dzf_flo, P->n[1], gauge);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODE>
 cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
                         double* gauge, cudaStream_t st) {
+  if (!(sizeof(T) == 4 && P->wblk)) {
+    switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xinv_pipe_m<T, MODE, MM>(P, src, p, Phi, Plo, scale, gauge, st);
+      CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+      default: break;
+    }
+  }
   switch (P->dx.m) {
 #define CASE_M(MM) \
   case MM: return xinv_m<T, MODE, MM>(P, src, p, Phi, Plo, scale, gauge, st);

@@ -15,19 +15,35 @@ __device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, 
   const int TI = Z.TI;
   constexpr int V = 16 / sizeof(T);
   if (vec && ncols == TI) {
+    // 16-byte vectors, four in flight per thread before the shared-memory stores
     const int per_row = TI / V;
-    for (int e = threadIdx.x; e < per_row * nz; e += blockDim.x) {
-      const int k = e / per_row, q = (e - k * per_row) * V;
-      const T* src = col0 + (size_t)k * plane + q;
-      if (V == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(src);
-        const float vv[4] = {v.x, v.y, v.z, v.w};
+    const int total = per_row * nz;
+    constexpr int U = 4;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+      float4 raw[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) tile[Z.at(k, q + u)] = (T)vv[u];
-      } else {
-        const double2 v = *reinterpret_cast<const double2*>(src);
-        tile[Z.at(k, q)] = (T)v.x;
-        tile[Z.at(k, q + 1)] = (T)v.y;
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * blockDim.x;
+        if (e < total) {
+          const int k = e / per_row, q = (e - k * per_row) * V;
+          raw[u] = *reinterpret_cast<const float4*>(col0 + (size_t)k * plane + q);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = base + u * blockDim.x;
+        if (e < total) {
+          const int k = e / per_row, q = (e - k * per_row) * V;
+          if (V == 4) {
+            const float vv[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) tile[Z.at(k, q + w)] = (T)vv[w];
+          } else {
+            const double2 v = *reinterpret_cast<const double2*>(&raw[u]);
+            tile[Z.at(k, q)] = (T)v.x;
+            tile[Z.at(k, q + 1)] = (T)v.y;
+          }
+        }
       }
     }
   } else {
@@ -71,7 +87,8 @@ __device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane,
 }
 
 template <int MMAX>
-__global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, int vec) {
+__global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, int vec,
+                                                           WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = a.ti, m = a.m;
   float* sa = reinterpret_cast<float*>(smem_raw);
@@ -79,8 +96,8 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   float* sc = sb + 32 * m;
   float* tile = sc + 32 * m;
   const int i0 = blockIdx.x * TI, j = blockIdx.y;
-  const size_t plane = (size_t)a.nx * a.ny;
-  float* col0 = w + (size_t)j * a.nx + i0;
+  const size_t plane = wl.zstride();
+  float* col0 = w + wl.zbase(i0, j);
   const int ncols = min(TI, a.nx - i0);
   const ZSwz Z = make_zswz(TI, m);
   stage_zrows<float, float>(sa, sb, sc, zf, a.nz, m);
@@ -98,7 +115,8 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
 }
 
 template <typename T, int MMAX>
-__global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec) {
+__global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec,
+                                                           WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = a.ti, m = a.m;
   double* sa = reinterpret_cast<double*>(smem_raw);
@@ -106,8 +124,8 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
   double* sc = sb + 32 * m;
   T* tile = reinterpret_cast<T*>(sc + 32 * m);
   const int i0 = blockIdx.x * TI, j = blockIdx.y;
-  const size_t plane = (size_t)a.nx * a.ny;
-  T* col0 = w + (size_t)j * a.nx + i0;
+  const size_t plane = wl.zstride();
+  T* col0 = w + wl.zbase(i0, j);
   const int ncols = min(TI, a.nx - i0);
   if (a.mask != nullptr) {  // skip tiles without a marked column
     bool any = false;
@@ -158,7 +176,8 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
 
 template <typename T, int MMAX>
 static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
-  const int vec = (P->n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
+  const WLay wl = wlay(P, sizeof(T) == 4);
+  const int vec = ((wl.blk || P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
   if (sizeof(T) == 4) {
     // float columns first, then the double columns of the marked bounding box
     ZArgs a = zargs(P, P->z_ti[1], gauge);
@@ -167,7 +186,7 @@ static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStre
     cudaError_t e = set_smem((const void*)zpass_f32_kernel<MMAX>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-    zpass_f32_kernel<MMAX><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec);
+    zpass_f32_kernel<MMAX><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ZArgs b = zargs(P, P->z_ti[1], gauge);
@@ -176,7 +195,7 @@ static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStre
     e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem64);
     if (e != cudaSuccess) return e;
     dim3 grid64((P->mask_i_end + b.ti - 1) / b.ti, P->mask_j_end);
-    if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec);
+    if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec, wl);
     return cudaGetLastError();
   }
   ZArgs a = zargs(P, P->z_ti[0], gauge);
@@ -184,7 +203,7 @@ static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStre
   cudaError_t e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-  zpass_f64_kernel<T, MMAX><<<grid, 256, smem, st>>>(w, a, P->zt_d, vec);
+  zpass_f64_kernel<T, MMAX><<<grid, 256, smem, st>>>(w, a, P->zt_d, vec, wl);
   return cudaGetLastError();
 }
 

@@ -448,6 +448,238 @@ __device__ __forceinline__ void forward_store(typename V2<T>::t* buf, const Lay&
   reinterpret_cast<T*>(buf)[L.r(s, l)] = v;
 }
 
+// ---- fused variants: first stage reads the staged input directly, last step writes to global -------
+// sample index n of a line whose value sits at position s of the half-length FFT's real input
+__device__ __forceinline__ int perm_out(int bc, int N, int s) {
+  if (bc == BC_P) return s;
+  return (s < (N >> 1)) ? 2 * s : 2 * (N - 1 - s) + 1;
+}
+
+// Stockham stage 1 (stride 1) with its inputs fetched through load(l, n) (real sample n of line l):
+// the packed complex z_m = (v_2m, v_2m+1) of the permuted sequence v is assembled on the fly.
+template <int R, int MAXV, typename T, int M, typename LoadF>
+__device__ __forceinline__ void fft_stage1_loaded(typename V2<T>::t* buf, const Lay& L, int lognl, int bc,
+                                                  LoadF load) {
+  typedef typename V2<T>::t C;
+  constexpr int Q = (MAXV + R - 1) / R;
+  constexpr int nb = M / R;
+  constexpr int N = 2 * M;
+  const int total = nb << lognl;
+  C v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int m = j + r * nb;
+        const int n0 = perm_out(bc, N, 2 * m), n1 = perm_out(bc, N, 2 * m + 1);
+        T x0 = load(l, n0), x1 = load(l, n1);
+        if (bc == BC_DD) {
+          if (n0 & 1) x0 = -x0;
+          if (n1 & 1) x1 = -x1;
+        }
+        v[q][r] = mk2<T>(x0, x1);
+      }
+      Dft<R, C>::run(v[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), j = t >> lognl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[L.c(j * R + r, l)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Forward post-processing whose N output slots go straight to store(l, slot, value).
+// JFAST: consecutive threads take consecutive k of one line (coalesced stores along contiguous
+// lines); otherwise consecutive threads take consecutive lines at one k (strided lines).
+template <int MAXV, typename T, int M, bool JFAST = false, typename StoreF>
+__device__ __forceinline__ void post_forward_store(const typename V2<T>::t* buf, const Lay& L, int lognl,
+                                                   const LineTab<T>& tb, StoreF store) {
+  typedef typename V2<T>::t C;
+  constexpr int N = 2 * M, half = M >> 1;
+  const int total = (half + 1) << lognl;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = JFAST ? t / (half + 1) : (t & (L.nl - 1));
+    const int k = JFAST ? t - l * (half + 1) : (t >> lognl);
+    T val[4];
+    if (k == 0) {
+      const C z = buf[L.c(0, l)];
+      const T v0 = z.x + z.y, vm = z.x - z.y;
+      if (tb.bc == BC_P) {
+        val[0] = v0;
+        val[1] = vm;
+      } else {
+        val[0] = (T)2 * v0;
+        val[1] = (T)1.41421356237309504880168872420970 * vm;
+      }
+      val[2] = val[3] = (T)0;
+    } else {
+      const C zk = buf[L.c(k, l)], zm = buf[L.c(M - k, l)];
+      C E, O;
+      E.x = (T)0.5 * (zk.x + zm.x);
+      E.y = (T)0.5 * (zk.y - zm.y);
+      O.x = (T)0.5 * (zk.y + zm.y);
+      O.y = (T)-0.5 * (zk.x - zm.x);
+      const C wO = cmul(__ldg(&tb.post[k]), O);
+      const C vk = cadd(E, wO);
+      const C vmk = cconj(csub(E, wO));
+      if (tb.bc == BC_P) {
+        val[0] = vk.x;
+        val[1] = vk.y;
+        val[2] = vmk.x;
+        val[3] = vmk.y;
+      } else {
+        const C a = cmul(__ldg(&tb.mak[k]), vk);
+        const C b = cmul(__ldg(&tb.mak[M - k]), vmk);
+        val[0] = (T)2 * a.x;
+        val[1] = (T)-2 * a.y;
+        val[2] = (T)2 * b.x;
+        val[3] = (T)-2 * b.y;
+      }
+    }
+    int sl[4];
+    fwd_slots(tb.bc, N, M, k, sl);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (sl[e] >= 0) store(l, sl[e], val[e]);
+  }
+}
+
+// Inverse pre-processing whose input slots come from loadslot(l, slot) (no read of buf), writing
+// conj(Z) into buf; the caller then runs the FFT stages.
+template <int MAXV, typename T, int M, typename LoadF>
+__device__ __forceinline__ void pre_inverse_loaded(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                                   const LineTab<T>& tb, LoadF loadslot) {
+  typedef typename V2<T>::t C;
+  constexpr int N = 2 * M, half = M >> 1;
+  const int total = (half + 1) << lognl;
+  const bool dd = (tb.bc == BC_DD);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = t & (L.nl - 1), k = t >> lognl;
+    C xk, xm;
+    if (tb.bc == BC_P) {
+      if (k == 0) {
+        xk = mk2<T>(loadslot(l, 0), (T)0);
+        xm = mk2<T>(loadslot(l, N - 1), (T)0);
+      } else {
+        xk = mk2<T>(loadslot(l, 2 * k - 1), loadslot(l, 2 * k));
+        xm = mk2<T>(loadslot(l, 2 * (M - k) - 1), loadslot(l, 2 * (M - k)));
+      }
+    } else {
+#define SLOT(q_) (dd ? (N - 1 - (q_)) : (q_))
+      if (k == 0) {
+        xk = mk2<T>((T)0.5 * loadslot(l, SLOT(0)), (T)0);
+        xm = mk2<T>((T)0.70710678118654752440084436210485 * loadslot(l, SLOT(M)), (T)0);
+      } else {
+        const C yk = mk2<T>((T)0.5 * loadslot(l, SLOT(k)), (T)-0.5 * loadslot(l, SLOT(N - k)));
+        const C ym = mk2<T>((T)0.5 * loadslot(l, SLOT(M - k)), (T)-0.5 * loadslot(l, SLOT(M + k)));
+        xk = cmul(cconj(__ldg(&tb.mak[k])), yk);
+        xm = cmul(cconj(__ldg(&tb.mak[M - k])), ym);
+      }
+#undef SLOT
+    }
+    if (k == 0) {
+      buf[L.c(0, l)] = cconj(mk2<T>(xk.x + xm.x, xk.x - xm.x));
+    } else {
+      const C A = cadd(xk, cconj(xm));
+      const C B = csub(xk, cconj(xm));
+      const C wB = cmul(cconj(__ldg(&tb.post[k])), B);
+      const C iwB = mk2<T>(-wB.y, wB.x);
+      buf[L.c(k, l)] = cconj(cadd(A, iwB));
+      if (k != M - k) buf[L.c(M - k, l)] = csub(A, iwB);  // conj(conj(A - i w B))
+    }
+  }
+  __syncthreads();
+}
+
+// Last Stockham stage of the inverse transform with its outputs sent to store(l, n, value): the
+// conjugate-back and the unpacking of z_m into samples 2m, 2m+1 of v (and v -> x) are fused.
+template <int R, int MAXV, typename T, int M, int Ns, bool JFAST = false, typename StoreF>
+__device__ __forceinline__ void fft_last_stage_store(const typename V2<T>::t* buf, const Lay& L, int lognl, int bc,
+                                                     const typename V2<T>::t* __restrict__ tw, StoreF store) {
+  typedef typename V2<T>::t C;
+  constexpr int Q = (MAXV + R - 1) / R;
+  constexpr int nb = M / R;
+  constexpr int tstride = M / (Ns * R);
+  constexpr int N = 2 * M;
+  const int total = nb << lognl;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = JFAST ? t / nb : (t & (L.nl - 1));
+      const int j = JFAST ? t - l * nb : (t >> lognl);
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = buf[L.c(j + r * nb, l)];
+      const int k = j % Ns;
+      if (Ns > 1) {
+        const int st = tstride * k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw[r * st]));
+      }
+      Dft<R, C>::run(v);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int m = base + r * Ns;
+        const int n0 = perm_out(bc, N, 2 * m), n1 = perm_out(bc, N, 2 * m + 1);
+        T x0 = v[r].x, x1 = -v[r].y;  // conjugate back
+        if (bc == BC_DD) {
+          if (n0 & 1) x0 = -x0;
+          if (n1 & 1) x1 = -x1;
+        }
+        store(l, n0, x0);
+        store(l, n1, x1);
+      }
+    }
+  }
+}
+
+template <int MAXV, typename T, int M, int S, int NST>
+struct FftStagesButLast {
+  static __device__ __forceinline__ void run(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                             const typename V2<T>::t* tw) {
+    if (S < NST - 1) {
+      fft_stage_ct<m_radix(M, S), MAXV, T, M, m_ns(M, S)>(buf, L, lognl, tw);
+      FftStagesButLast<MAXV, T, M, (S + 1 < NST ? S + 1 : NST), NST>::run(buf, L, lognl, tw);
+    }
+  }
+};
+template <int MAXV, typename T, int M, int NST>
+struct FftStagesButLast<MAXV, T, M, NST, NST> {
+  static __device__ __forceinline__ void run(typename V2<T>::t*, const Lay&, int, const typename V2<T>::t*) {}
+};
+
+// Whole forward line transform from a loader to a slot store (M compile time, M >= 2).
+template <int MAXV, typename T, int M, bool JFAST = false, typename LoadF, typename StoreF>
+__device__ __forceinline__ void line_forward_fused(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                                   const LineTab<T>& tb, LoadF load, StoreF store) {
+  constexpr int NST = m_nst(M);
+  fft_stage1_loaded<m_radix(M, 0), MAXV, T, M>(buf, L, lognl, tb.bc, load);
+  FftStages<MAXV, T, M, 1, NST>::run(buf, L, lognl, tb.tw);
+  post_forward_store<MAXV, T, M, JFAST>(buf, L, lognl, tb, store);
+}
+
+// Whole inverse line transform from a slot loader to a sample store (M compile time, M >= 2).
+template <int MAXV, typename T, int M, bool JFAST = false, typename LoadF, typename StoreF>
+__device__ __forceinline__ void line_inverse_fused(typename V2<T>::t* buf, const Lay& L, int lognl,
+                                                   const LineTab<T>& tb, LoadF loadslot, StoreF store) {
+  constexpr int NST = m_nst(M);
+  pre_inverse_loaded<MAXV, T, M>(buf, L, lognl, tb, loadslot);
+  FftStagesButLast<MAXV, T, M, 0, NST>::run(buf, L, lognl, tb.tw);
+  fft_last_stage_store<m_radix(M, NST - 1), MAXV, T, M, m_ns(M, NST - 1), JFAST>(buf, L, lognl, tb.bc, tb.tw,
+                                                                                 store);
+}
+
 template <int MAXV, typename T, int MC = 0>
 __device__ __forceinline__ void line_forward(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
   if (MC == 0 && tb.n < 2) return;

@@ -29,9 +29,27 @@ struct StencilDF {
   int n[3];
 };
 
+// Layout of a transformed work field.  natural: [k][j][i] (x fastest, as the user's fields);
+// blocked: [k][i / 32][j][i % 32] -- 32 consecutive x-slots of every (j, k) stay together, so a y-pass
+// tile of up to 32 x-slots reads consecutive 128-byte rows and a z-pass tile reads 128-byte rows.
+struct WLay {
+  int blk, nx, ny, nbx;  // nbx = number of 32-slot blocks per line (blocked layout)
+  __device__ __forceinline__ size_t at(int i, int j, int k) const {
+    if (!blk) return (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+    return ((size_t)k * nbx + (i >> 5)) * ((size_t)ny * 32) + (size_t)j * 32 + (i & 31);
+  }
+  // y-pass tile of x-slots i0 .. (i0 + nl - 1 within one block) at plane k: element (l, j) = base + j*rs + l
+  __device__ __forceinline__ size_t ybase(int i0, int k) const { return at(i0, 0, k); }
+  __device__ __forceinline__ int yrow() const { return blk ? 32 : nx; }
+  // z-pass tile of x-slots i0.. at y-slot j: element (ii, k) = base + k*zs + ii
+  __device__ __forceinline__ size_t zbase(int i0, int j) const { return at(i0, j, 0); }
+  __device__ __forceinline__ size_t zstride() const { return blk ? (size_t)nbx * ny * 32 : (size_t)nx * ny; }
+};
+
 struct XArgs {
   int nx, nlines, lognl;
   double scale;  // inverse only
+  WLay w;        // layout of the transformed field (xfwd output, xinv input)
 };
 
 struct ZArgs {
@@ -85,6 +103,7 @@ struct cans_plan_s {
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
   size_t z_smem[2];
+  int wblk = 0;  // mixed path: work field in the blocked layout
   // per-pass event records (cans_plan_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -93,6 +112,16 @@ struct cans_plan_s {
 };
 
 namespace cans {
+
+// layout of the working field of this plan and precision (the FP64 path works in p: natural)
+inline WLay wlay(const cans_plan_s* P, bool working_float) {
+  WLay w;
+  w.blk = (working_float && P->wblk) ? 1 : 0;
+  w.nx = P->n[0];
+  w.ny = P->n[1];
+  w.nbx = (P->n[0] + 31) / 32;
+  return w;
+}
 
 // pass launchers (each in its own translation unit)
 template <typename T, int MODE>
@@ -123,6 +152,10 @@ cudaError_t launch_chkdt(const cans_plan_s* P, const double* u, const double* v,
                          cudaStream_t st);
 
 StencilDF stencil_df(const cans_plan_s* P);
+
+// launch shape of a line-transform kernel (lines of N reals, `count` lines or columns, complex
+// element size elem2, preferred lines per CTA)
+Launch line_launch_shape(int N, int count, size_t elem2, int prefer_nl);
 
 // Opt a kernel into more than 48 KB of dynamic shared memory.  The attribute is set once per kernel
 // and size (remembered per device), so later launches -- including those inside a stream capture --
