@@ -234,6 +234,21 @@ size_t cans_noalloc_scratch_bytes(void);
  * (length Ny) the plan uses; either pointer may be NULL. */
 int cans_plan_eigenvalues(cans_plan_t plan, double* mu_x, double* mu_y);
 
+/*
+ * cans_split_f64 -- the element-wise double/float conversions of the mixed-precision path, exposed
+ * so that they can be checked on their own.  The mixed path represents extended-precision values as
+ * pairs of floats (Section on the mixed-precision solve: FP32 transforms, residual and iterate in
+ * higher precision); on this GPU the hardware double<->float conversions run at the FP64 rate, so
+ * the library converts on the bit patterns instead.
+ *   x     : device, n doubles (read only).
+ *   rn    : device, n floats or NULL -- the nearest float to x[i], ties to even (bit-identical to
+ *           a round-to-nearest hardware conversion, including zeros, subnormals, inf and NaN).
+ *   hi,lo : device, n floats each or NULL -- x[i] = hi + lo with hi = rn and |x - hi - lo| <= 2^-46 |x|.
+ *   back  : device, n doubles or NULL -- hi + lo evaluated in double (exact widening, one add).
+ * Asynchronous on cuda_stream; CANS_ERR_ARG if x is NULL while n > 0.
+ */
+int cans_split_f64(const double* x, size_t n, float* rn, float* hi, float* lo, double* back, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         L.cans_noalloc_scratch_bytes.argtypes = []
         L.cans_noalloc_scratch_bytes.restype = ctypes.c_size_t
         L.cans_plan_profile_read.argtypes = [vp, ctypes.c_int, dp, ip]
+        L.cans_split_f64.argtypes = [vp, ctypes.c_size_t, vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -208,6 +209,13 @@ def cans_plan_eigenvalues(plan, nx: int, ny: int):
     mx, my = np.empty(nx), np.empty(ny)
     _check(lib().cans_plan_eigenvalues(plan, _dptr(mx), _dptr(my)), "cans_plan_eigenvalues")
     return mx, my
+
+
+def cans_split_f64(x_ptr: int, n: int, rn_ptr: int = 0, hi_ptr: int = 0, lo_ptr: int = 0, back_ptr: int = 0,
+                   stream_ptr: int = 0) -> int:
+    """Element-wise double -> float conversions of the mixed path (device pointers; 0 = not wanted)."""
+    return lib().cans_split_f64(x_ptr or None, int(n), rn_ptr or None, hi_ptr or None, lo_ptr or None,
+                                back_ptr or None, stream_ptr or None)
 
 
 CANS_PASS_NAMES = ("x_forward", "y_forward", "z_solve", "y_inverse", "x_inverse", "x_forward_residual",

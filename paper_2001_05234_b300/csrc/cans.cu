@@ -573,10 +573,9 @@ std::string tune_key(const cans_plan_s* P) {
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, dev);
-  char buf[256];
-  std::snprintf(buf, sizeof(buf), "%s|%d,%d,%d|%d,%d,%d|%d", prop.name, P->n[0], P->n[1], P->n[2], P->bc[0], P->bc[1],
-                P->bc[2], P->opts.prec);
-  std::string k(buf);
+  auto I = [](int v) { return std::to_string(v); };
+  std::string k = std::string(prop.name) + "|" + I(P->n[0]) + "," + I(P->n[1]) + "," + I(P->n[2]) + "|" + I(P->bc[0]) +
+                  "," + I(P->bc[1]) + "," + I(P->bc[2]) + "|" + I(P->opts.prec);
   for (char& ch : k)
     if (ch == ' ') ch = '_';
   return k;

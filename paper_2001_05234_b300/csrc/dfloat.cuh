@@ -58,13 +58,70 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return fast_two_sum(p.hi, lo);
 }
 
-// split a double into hi + lo floats (hi = nearest float, lo = nearest float of the remainder)
-__device__ __forceinline__ df df_from_double(double x) {
-  const float hi = __double2float_rn(x);
-  const float lo = __double2float_rn(x - (double)hi);
-  return df_make(hi, lo);
+// ---- conversions between binary64 and binary32 in integer arithmetic --------------------------
+// On B300 the double<->float conversion instructions share the slow FP64-class pipe (measured at
+// about 0.6-0.7 T conversions/s per GPU, the rate of an FP64 add), so the per-point conversions of
+// the mixed path are done on the bit patterns instead.  binary64: sign | 11-bit biased exponent e
+// (bias 1023) | 52-bit fraction; binary32: sign | 8-bit biased exponent (bias 127) | 23-bit fraction.
+// A binary64 with 897 <= e <= 1150 rounds to a normal binary32 (or overflows to infinity) whose
+// exponent field is e - 896; other inputs (zeros, subnormals, tiny or huge values, inf, NaN) take
+// the hardware conversion, whose results these match bit for bit.
+
+// nearest float, ties to even (= __double2float_rn)
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {
+    const unsigned t = __funnelshift_l(lo, hi, 3);  // exponent and top 23 fraction bits, shifted into place
+    unsigned bits = (t - (896u << 23)) | (hi & 0x80000000u);
+    // round half to even on the 29 dropped fraction bits; a carry propagates into the exponent
+    bits += ((lo & 0x1fffffffu) + (t & 1u) + 0x0fffffffu) >> 29;
+    return __uint_as_float(bits);
+  }
+  return __double2float_rn(x);
 }
 
-__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+// x = hi + lo with hi = d2f_rn(x) and lo the remainder to within 2^-46 |x| (exact for |x| >= 2^-80
+// up to the 6 lowest of its 29 remainder bits).  Outside 2^-80 <= |x| < 2^127 the FP64 route is used.
+__device__ __forceinline__ df df_split(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 943u < 207u) {
+    const unsigned t = __funnelshift_l(lo, hi, 3);
+    const unsigned sgn = hi & 0x80000000u;
+    const unsigned up = ((lo & 0x1fffffffu) + (t & 1u) + 0x0fffffffu) >> 29;
+    const float h = __uint_as_float(((t - (896u << 23)) | sgn) + up);
+    // remainder in units of 2^(e-1075): the dropped bits, minus 2^29 when hi was rounded up;
+    // |r| <= 2^28, so r / 64 fits the exact float-from-integer trick 1.5*2^23 + r/64 - 1.5*2^23
+    const int r = (int)(lo & 0x1fffffffu) - (int)(up << 29);
+    const float rf = __int_as_float(0x4b400000 + (r >> 6)) - 12582912.0f;
+    const float scale = __uint_as_float(sgn | ((e - 942u) << 23));  // +-2^(e-1069)
+    return df_make(h, rf * scale);
+  }
+  if (((hi << 1) | lo) == 0u) return df_make(__uint_as_float(hi & 0x80000000u), 0.f);
+  const float h = __double2float_rn(x);
+  return df_make(h, __double2float_rn(x - (double)h));
+}
+
+// exact float -> double
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  if (((b >> 23) & 0xffu) - 1u < 254u)  // normal: rebias the exponent (+896), widen the fraction
+    return __hiloint2double((int)((b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20))), (int)(b << 29));
+  if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)x;
+}
+
+// value conversion between the storage and compute precisions of a kernel
+template <typename To, typename From> struct Cvt { static __device__ __forceinline__ To run(From x) { return (To)x; } };
+template <> struct Cvt<float, double> { static __device__ __forceinline__ float run(double x) { return d2f_rn(x); } };
+template <> struct Cvt<double, float> { static __device__ __forceinline__ double run(float x) { return f2d(x); } };
+template <typename To, typename From> __device__ __forceinline__ To cvt(From x) { return Cvt<To, From>::run(x); }
+
+// split a double into hi + lo floats (hi = nearest float, lo = the remainder, see df_split)
+__device__ __forceinline__ df df_from_double(double x) { return df_split(x); }
+
+// hi + lo as a double: exact widening of both parts and one FP64 add
+__device__ __forceinline__ double df_to_double(df a) { return f2d(a.hi) + f2d(a.lo); }
 
 }  // namespace cans

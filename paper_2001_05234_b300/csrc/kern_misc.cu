@@ -1,6 +1,8 @@
 // Reporting kernels (only run when the caller asks for residual norms): ||f - L_h p||^2 in FP64
 // (Eq. poi with a non-uniform z) and the dzf-weighted sum of f for the compatibility check of a
 // singular problem.
+#include <algorithm>
+
 #include "plan.cuh"
 
 namespace cans {
@@ -72,4 +74,26 @@ cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* a
   return cudaGetLastError();
 }
 
+// Element-wise double <-> float conversions of the mixed path (integer-arithmetic versions).
+__global__ void split_f64_kernel(const double* __restrict__ x, size_t n, float* rn, float* hi, float* lo,
+                                 double* back) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (rn) rn[i] = d2f_rn(v);
+    const df s = df_split(v);
+    if (hi) hi[i] = s.hi;
+    if (lo) lo[i] = s.lo;
+    if (back) back[i] = df_to_double(s);
+  }
+}
+
 }  // namespace cans
+
+extern "C" int cans_split_f64(const double* x, size_t n, float* rn, float* hi, float* lo, double* back,
+                              void* cuda_stream) {
+  if (n == 0) return CANS_OK;
+  if (!x) return CANS_ERR_ARG;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  cans::split_f64_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(x, n, rn, hi, lo, back);
+  return cudaGetLastError() == cudaSuccess ? CANS_OK : CANS_ERR_CUDA;
+}

@@ -11,6 +11,10 @@ namespace cans {
 
 constexpr int MAXV = 8;  // complex values per thread per FFT stage
 
+template <typename T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
+
 __device__ __forceinline__ float ghost_or(int bc, int at_edge, float inner_c, float wrap, float nb) {
   if (!at_edge) return nb;
   if (bc == BC_P) return wrap;
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
       if (e < total && line < a.nlines) {
         const size_t c = (size_t)line * N + n;
         if (MODE == 0) {
-          v[u] = (T)f[c];
+          v[u] = from_double<T>(f[c]);
         } else {
           // k = line / Ny, exact: (line + 1/2)/Ny stays >= 1/(2 Ny) away from an integer
           const int k = (int)(((float)line + 0.5f) * inv_ny);
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(512, 2) xfwd_pipe_kernel(const double* __restr
     const double* src = raw + (size_t)slot * nl * (N + PAD);
     const int line0 = t * nl;
     auto load = [&](int l, int n) -> float {
-      const float v = (float)src[l * (N + PAD) + n];
+      const float v = d2f_rn(src[l * (N + PAD) + n]);
       acc += v * v;
       return v;
     };

@@ -11,6 +11,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace cans {
 
 template <typename T>
@@ -81,7 +83,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
       if (k < Nz) {
         const C w = (C)weights[k];
         sw += w;
-        swd += w * (C)tile[Z.at(k, col, lane)];
+        swd += w * cvt<C>(tile[Z.at(k, col, lane)]);
       }
     }
 #pragma unroll
@@ -100,7 +102,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
     if (r < m - 1) {
       const int k = k0 + r;
       C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + mu, c = sc[r * 32 + lane], d = 0;
-      if (k < Nz) d = (C)tile[Z.at(k, col, lane)] - proj;
+      if (k < Nz) d = cvt<C>(tile[Z.at(k, col, lane)]) - proj;
       if (SING && k == Nz - 1) {
         a = 0;
         b = 1;
@@ -147,7 +149,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
   const int kl = k0 + m - 1;
   const int rl = m - 1;
   C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + mu, cl = sc[rl * 32 + lane], dl = 0;
-  if (kl < Nz) dl = (C)tile[Z.at(kl, col, lane)] - proj;
+  if (kl < Nz) dl = cvt<C>(tile[Z.at(kl, col, lane)]) - proj;
   if (SING && kl == Nz - 1) {
     al = 0;
     bl = 1;
@@ -183,7 +185,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
   C Ep = __shfl_up_sync(full, E, 1);
   if (lane == 0) Ep = 0;
   // back-substitution, written straight into the tile
-  if (lane * m + m - 1 < Nz) tile[Z.at(k0 + m - 1, col, lane)] = (T)E;
+  if (lane * m + m - 1 < Nz) tile[Z.at(k0 + m - 1, col, lane)] = cvt<T>(E);
   C xn = E;
 #pragma unroll
   for (int r = MMAX - 1; r >= 0; --r) {
@@ -192,7 +194,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
         xn = dp[r] + lp[r] * Ep + rr * E;
       else
         xn = dp[r] + lp[r] * Ep - cp[r] * xn;
-      if (k0 + r < Nz) tile[Z.at(k0 + r, col, lane)] = (T)xn;
+      if (k0 + r < Nz) tile[Z.at(k0 + r, col, lane)] = cvt<T>(xn);
     }
   }
   if (SING) {
@@ -203,7 +205,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
       if (k < Nz) {
         const C w = (C)weights[k];
         sw += w;
-        swx += w * (C)tile[Z.at(k, col, lane)];
+        swx += w * cvt<C>(tile[Z.at(k, col, lane)]);
       }
     }
 #pragma unroll
@@ -214,7 +216,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, i
     const C shift = swx / sw - target;
     for (int r = 0; r < m; ++r) {
       const int k = k0 + r;
-      if (k < Nz) tile[Z.at(k, col, lane)] = (T)((C)tile[Z.at(k, col, lane)] - shift);
+      if (k < Nz) tile[Z.at(k, col, lane)] = cvt<T>(cvt<C>(tile[Z.at(k, col, lane)]) - shift);
     }
   }
 }
