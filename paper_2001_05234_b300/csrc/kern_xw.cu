@@ -1,0 +1,291 @@
+// x-passes of the mixed path on the warp-per-line engine (float work field, M = N/2 in
+// {128, 256, 512}): forward transform along x fused with the double->float read of f or with the
+// double-float residual of a refinement sweep, and inverse transform fused with the normalisation
+// and the update of the iterate.  Same results as the CTA-wide kernels of kern_x.cu (which remain
+// the path for other lengths); one warp per line, persistent CTAs, no CTA barrier inside a line.
+#include <algorithm>
+
+#include "plan.cuh"
+#include "stencil.cuh"
+#include "wline.cuh"
+
+namespace cans {
+namespace {
+
+constexpr int XW_WARPS = 8;  // warps (lines in flight) per CTA
+
+__device__ __forceinline__ void warp_block_accumulate(float v, double* dst) {
+  __shared__ float red[XW_WARPS];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < XW_WARPS; ++w) s += red[w];
+    atomicAdd(dst, (double)s);
+  }
+}
+
+// ---- sources of the forward pass ----
+struct SrcF {  // f (double) rounded to float; accumulates sum f^2
+  const double* __restrict__ f;  // line start, 16-byte aligned
+  float acc;
+  __device__ __forceinline__ float2 pair(int n) {
+    const double2 d = *reinterpret_cast<const double2*>(f + n);
+    const float a = d2f_rn(d.x), b = d2f_rn(d.y);
+    acc = __fmaf_rn(a, a, __fmaf_rn(b, b, acc));
+    return make_float2(a, b);
+  }
+  __device__ __forceinline__ float one(int n) {
+    const float a = d2f_rn(f[n]);
+    acc = __fmaf_rn(a, a, acc);
+    return a;
+  }
+};
+
+template <bool PLO>
+struct SrcRes {  // r = f - L_h(Phi + Plo) at (n, j, k); accumulates sum r^2
+  const double* __restrict__ f;
+  const float* __restrict__ Phi;
+  const float* __restrict__ Plo;
+  const StencilDF* S;
+  size_t base;
+  int j, k;
+  float acc;
+  __device__ __forceinline__ float one(int n) {
+    const float r = residual_point<PLO>(f, Phi, Plo, *S, base + n, n, j, k);
+    acc = __fmaf_rn(r, r, acc);
+    return r;
+  }
+  __device__ __forceinline__ float2 pair(int n) {
+    const float a = one(n), b = one(n + 1);
+    return make_float2(a, b);
+  }
+};
+
+struct SnkF {
+  float* __restrict__ o;
+  __device__ __forceinline__ void put(int s, float y) { o[s] = y; }
+};
+
+// ---- source and sinks of the inverse pass ----
+struct SrcSlots {
+  const float* __restrict__ s;
+  __device__ __forceinline__ float get(int i) { return s[i]; }
+};
+
+// MODE 0: p = scale x (double).  1: Phi = scale x (+ dzf-weighted gauge sum).  2 / 4: (Phi, Plo) +=
+// scale x.  3 / 5: p = Phi + Plo + scale x.  4 and 5 know Plo is zero.
+template <int MODE>
+struct SnkUpd {
+  double* __restrict__ p;
+  float* __restrict__ Phi;
+  float* __restrict__ Plo;
+  float scale;
+  df gw;  // gauge weight dzf_k of the line (MODE 1)
+  bool gauge;
+  df gacc;
+  __device__ __forceinline__ float upd(size_t o, float x, double& pd) {
+    const float d = x * scale;
+    if (MODE == 0) {
+      pd = f2d(d);
+    } else if (MODE == 1) {
+      if (gauge) {
+        df tt = two_prod(d, gw.hi);
+        tt.lo = __fmaf_rn(d, gw.lo, tt.lo);
+        gacc = df_add(gacc, tt);
+      }
+      return d;
+    } else {
+      df s2 = two_sum(Phi[o], d);
+      s2 = fast_two_sum(s2.hi, (MODE <= 3) ? s2.lo + Plo[o] : s2.lo);
+      if (MODE == 2 || MODE == 4) {
+        Plo[o] = s2.lo;
+        return s2.hi;
+      }
+      pd = df_to_double(s2);
+    }
+    return 0.f;
+  }
+  __device__ __forceinline__ void one(size_t o, float x) {
+    double pd = 0.0;
+    const float h = upd(o, x, pd);
+    if (MODE == 0 || MODE == 3 || MODE == 5)
+      p[o] = pd;
+    else
+      Phi[o] = h;
+  }
+};
+
+template <int MODE>
+struct SnkLine {
+  SnkUpd<MODE>* u;
+  size_t base;
+  __device__ __forceinline__ void one(int n, float x) { u->one(base + n, x); }
+  __device__ __forceinline__ void pair(int n, float a, float b) {
+    const size_t o = base + n;
+    double pa = 0.0, pb = 0.0;
+    const float ha = u->upd(o, a, pa), hb = u->upd(o + 1, b, pb);
+    if (MODE == 0 || MODE == 3 || MODE == 5)
+      *reinterpret_cast<double2*>(u->p + o) = make_double2(pa, pb);
+    else
+      *reinterpret_cast<float2*>(u->Phi + o) = make_float2(ha, hb);
+  }
+};
+
+template <int M, int BC, int MODE>
+__global__ void __launch_bounds__(32 * XW_WARPS, 3)
+    xfwd_w_kernel(const double* __restrict__ f, const float* __restrict__ Phi, const float* __restrict__ Plo,
+                  float* __restrict__ dst, int nlines, LineTab<float> tb, StencilDF S, double* norm_acc) {
+  __shared__ float2 xbuf[XW_WARPS][M];
+  constexpr int N = 2 * M;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2* xb = xbuf[wid];
+  float acc = 0.f;
+  for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
+    const size_t base = (size_t)line * N;
+    SnkF snk{dst + base};
+    if (MODE == 0) {
+      SrcF src{f + base, 0.f};
+      wl::forward<M, BC>(xb, tb, lane, src, snk);
+      acc += src.acc;
+    } else {
+      const int k = line / S.n[1];
+      SrcRes<MODE == 1> src{f, Phi, Plo, &S, base, line - k * S.n[1], k, 0.f};
+      wl::forward<M, BC>(xb, tb, lane, src, snk);
+      acc += src.acc;
+    }
+  }
+  if (norm_acc != nullptr) warp_block_accumulate(acc, norm_acc);
+}
+
+template <int M, int BC, int MODE>
+__global__ void __launch_bounds__(32 * XW_WARPS, 3)
+    xinv_w_kernel(const float* __restrict__ src, double* __restrict__ p, float* __restrict__ Phi,
+                  float* __restrict__ Plo, int nlines, float scale, LineTab<float> tb, const float* __restrict__ wz,
+                  const float* __restrict__ wz_lo, int ny, double* gauge) {
+  __shared__ float2 xbuf[XW_WARPS][M];
+  constexpr int N = 2 * M;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2* xb = xbuf[wid];
+  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f)};
+  for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
+    const size_t base = (size_t)line * N;
+    if (MODE == 1 && gauge != nullptr) {
+      const int k = line / ny;
+      u.gw = df_make(wz[k], wz_lo[k]);
+    }
+    SrcSlots in{src + base};
+    SnkLine<MODE> out{&u, base};
+    wl::inverse<M, BC>(xb, tb, lane, in, out);
+  }
+  if (MODE == 1 && gauge != nullptr) {
+    __shared__ double red[XW_WARPS];
+    double v = (double)u.gacc.hi + (double)u.gacc.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < XW_WARPS; ++w) s += red[w];
+      atomicAdd(gauge, s);
+    }
+  }
+}
+
+template <typename K>
+int xw_grid(K kernel, int nlines) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * XW_WARPS, 0);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = (nlines + XW_WARPS - 1) / XW_WARPS;
+  return std::max(1, std::min(need, std::max(per_sm, 1) * sms));
+}
+
+template <int M, int BC, int MODE>
+cudaError_t xfwd_w(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst, double* acc,
+                   cudaStream_t st) {
+  const int nlines = P->n[1] * P->n[2];
+  auto k = xfwd_w_kernel<M, BC, MODE>;
+  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(f, Phi, Plo, dst, nlines, P->tx_f, stencil_df(P), acc);
+  return cudaGetLastError();
+}
+
+template <int M, int BC, int MODE>
+cudaError_t xinv_w(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
+                   double* gauge, cudaStream_t st) {
+  const int nlines = P->n[1] * P->n[2];
+  auto k = xinv_w_kernel<M, BC, MODE>;
+  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(src, p, Phi, Plo, nlines, (float)scale, P->tx_f, P->dzf_f,
+                                                   P->dzf_flo, P->n[1], gauge);
+  return cudaGetLastError();
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
+
+}  // namespace
+
+// Route a float x-pass to the warp engine when it applies; *handled says whether it did.
+template <int MODE>
+cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
+                             double* acc, cudaStream_t st, bool* handled) {
+  *handled = false;
+  if (P->wblk || !aligned16(f) || !aligned16(dst)) return cudaSuccess;
+  const int bc = P->bc[0];
+  *handled = true;
+#define XW_CASE(MM)                                                            \
+  if (P->dx.m == MM) {                                                         \
+    if (bc == BC_P) return xfwd_w<MM, BC_P, MODE>(P, f, Phi, Plo, dst, acc, st);   \
+    if (bc == BC_NN) return xfwd_w<MM, BC_NN, MODE>(P, f, Phi, Plo, dst, acc, st); \
+    return xfwd_w<MM, BC_DD, MODE>(P, f, Phi, Plo, dst, acc, st);                  \
+  }
+  XW_CASE(128)
+  XW_CASE(256)
+  XW_CASE(512)
+#undef XW_CASE
+  *handled = false;
+  return cudaSuccess;
+}
+
+template <int MODE>
+cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
+                             double* gauge, cudaStream_t st, bool* handled) {
+  *handled = false;
+  if (P->wblk || !aligned16(src)) return cudaSuccess;
+  if ((MODE == 0 || MODE == 3 || MODE == 5) && !aligned16(p)) return cudaSuccess;
+  const int bc = P->bc[0];
+  *handled = true;
+#define XW_CASE(MM)                                                                       \
+  if (P->dx.m == MM) {                                                                    \
+    if (bc == BC_P) return xinv_w<MM, BC_P, MODE>(P, src, p, Phi, Plo, scale, gauge, st);   \
+    if (bc == BC_NN) return xinv_w<MM, BC_NN, MODE>(P, src, p, Phi, Plo, scale, gauge, st); \
+    return xinv_w<MM, BC_DD, MODE>(P, src, p, Phi, Plo, scale, gauge, st);                  \
+  }
+  XW_CASE(128)
+  XW_CASE(256)
+  XW_CASE(512)
+#undef XW_CASE
+  *handled = false;
+  return cudaSuccess;
+}
+
+#define XW_INST_F(MODE)                                                                                         \
+  template cudaError_t launch_xfwd_warp<MODE>(const cans_plan_s*, const double*, const float*, const float*, float*, \
+                                              double*, cudaStream_t, bool*);
+#define XW_INST_I(MODE)                                                                                       \
+  template cudaError_t launch_xinv_warp<MODE>(const cans_plan_s*, const float*, double*, float*, float*, double, \
+                                              double*, cudaStream_t, bool*);
+XW_INST_F(0)
+XW_INST_F(1)
+XW_INST_F(2)
+XW_INST_I(0)
+XW_INST_I(1)
+XW_INST_I(2)
+XW_INST_I(3)
+XW_INST_I(4)
+XW_INST_I(5)
+
+}  // namespace cans

@@ -156,6 +156,16 @@ StencilDF stencil_df(const cans_plan_s* P);
 // launch shape of a line-transform kernel (lines of N reals, `count` lines or columns, complex
 // element size elem2, preferred lines per CTA)
 Launch line_launch_shape(int N, int count, size_t elem2, int prefer_nl);
+// warp-per-line x-passes of the mixed path (kern_xw.cu); *handled is false when the shape or the
+// pointer alignment is not one they take, and the caller then uses the CTA-wide kernels
+template <int MODE>
+cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
+                             double* acc, cudaStream_t st, bool* handled);
+template <int DIR>
+cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled);
+template <int MODE>
+cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
+                             double* gauge, cudaStream_t st, bool* handled);
 
 // Opt a kernel into more than 48 KB of dynamic shared memory.  The attribute is set once per kernel
 // and size (remembered per device), so later launches -- including those inside a stream capture --

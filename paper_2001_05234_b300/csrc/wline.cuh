@@ -1,0 +1,249 @@
+// Warp-per-line real transforms of contiguous lines (the operator F^x of Eq. poi_reduced and its
+// inverse: real DFT for periodic, DCT-II/DST-II for Neumann/Dirichlet walls).
+//
+// One warp owns one line of N = 2M reals (M = 32 V, V = 4, 8 or 16 complex values per lane).
+// The line is packed into M complex numbers z_m = (v_2m, v_2m+1) of the (Makhoul-permuted,
+// sign-alternated for Dirichlet) sequence v and transformed by a Stockham FFT whose radices all
+// divide V, so every butterfly of a stage sits in one lane's registers: lane p always holds the
+// elements m = p + 32 t, t = 0..V-1, on entry to a stage, and the elements a stage produces travel
+// to their next owner through a per-warp shared buffer (__syncwarp only, no CTA barrier).  Each
+// exchange uses its own XOR swizzle: after a stage of stride Ns < 16 and radix R, bits
+// [log2 Ns, 4) of the element index are flipped by the group index above log2(R Ns), which makes
+// every exchange free of bank conflicts (8-byte accesses; checked for M = 128, 256, 512).
+//
+// The first stage reads its inputs through the caller's source and the post-processing of the
+// real-FFT split (V_k = E_k + exp(-2 pi i k/N) O_k, then Makhoul's quarter-wave twiddle for the
+// cosine/sine transforms) writes each output slot through the caller's sink, so a pass never
+// stages whole lines in shared memory.  Output slot order: periodic -- slot 0 = X_0, slots
+// 2k-1, 2k = Re, Im X_k (1 <= k < M), slot N-1 = X_M; Neumann -- slot k = Y_k; Dirichlet -- slot
+// N-1-k = Y_k (the order of the plan's eigenvalues).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lines.cuh"
+
+namespace cans {
+namespace wl {
+
+// radix schedule: powers of two only, each radix (8, 4 or 2, largest first) dividing V = M/32
+__host__ __device__ constexpr int radix(int M, int s) {
+  int x = M, V = M / 32;
+  for (int i = 0;; ++i) {
+    int r = (x % 8 == 0 && V % 8 == 0) ? 8 : (x % 4 == 0 && V % 4 == 0) ? 4 : 2;
+    if (i == s) return r;
+    x /= r;
+  }
+}
+__host__ __device__ constexpr int nstages(int M) {
+  int x = M, n = 0;
+  while (x > 1) {
+    x /= radix(M, n);
+    ++n;
+  }
+  return n;
+}
+__host__ __device__ constexpr int stride(int M, int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= radix(M, i);
+  return p;
+}
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+__host__ __device__ constexpr bool supported(int M) { return M == 128 || M == 256 || M == 512; }
+
+// position of element m in the exchange that follows a stage of stride Ns and radix R
+template <int Ns, int R>
+__device__ __forceinline__ int xpos(int m) {
+  if (Ns >= 16) return m;
+  return m ^ (((m >> ilog2c(R * Ns)) & (16 / Ns - 1)) << ilog2c(Ns));
+}
+
+__device__ __forceinline__ float2 ld_tw(const float2* __restrict__ t, int i) { return __ldg(&t[i]); }
+
+// One Stockham stage on the lane's registers.  Exchange (all but the last stage): the outputs are
+// written to xb at their swizzled positions and read back in the lane-p-owns-m=p+32t order.
+template <int M, int S>
+__device__ __forceinline__ void stage(float2 (&v)[M / 32], float2* xb, const float2* __restrict__ tw, int lane) {
+  constexpr int V = M / 32, R = radix(M, S), Ns = stride(M, S), Q = V / R, NST = nstages(M);
+  constexpr int TS = M / (R * Ns);  // twiddle table stride
+  static_assert(V % R == 0, "radix must divide the values per lane");
+  float2 w[R];
+  if (Ns > 1 && Ns <= 32) {  // k = lane mod Ns for every butterfly of the lane
+    const int k = lane & (Ns - 1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = ld_tw(tw, k * r * TS);
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[q + Q * r];
+    const int j = lane + 32 * q;
+    const int k = j & (Ns - 1);
+    if (Ns > 32) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[r] = ld_tw(tw, k * r * TS);
+    }
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
+    }
+    Dft<R, float2>::run(x);
+    if (S < NST - 1) {
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) xb[xpos<Ns, R>(base + r * Ns)] = x[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + Q * r] = x[r];
+    }
+  }
+  if (S < NST - 1) {
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < V; ++t) v[t] = xb[xpos<Ns, R>(lane + 32 * t)];
+    __syncwarp();
+  }
+}
+
+template <int M, int S, int NST>
+struct Stages {
+  static __device__ __forceinline__ void run(float2 (&v)[M / 32], float2* xb, const float2* tw, int lane) {
+    stage<M, S>(v, xb, tw, lane);
+    Stages<M, S + 1, NST>::run(v, xb, tw, lane);
+  }
+};
+template <int M, int NST>
+struct Stages<M, NST, NST> {
+  static __device__ __forceinline__ void run(float2 (&)[M / 32], float2*, const float2*, int) {}
+};
+
+// sample index of position n of the permuted sequence v (identity for periodic lines)
+template <int BC, int N>
+__device__ __forceinline__ int sample_of(int n) {
+  if (BC == BC_P) return n;
+  return (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
+}
+
+// Forward transform of one line.
+//   src.pair(n) -> float2 (x_n, x_n+1), n even (periodic lines);  src.one(n) -> x_n (walls).
+//   snk.put(s, y) stores output slot s.
+template <int M, int BC, typename Src, typename Snk>
+__device__ __forceinline__ void forward(float2* xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
+  constexpr int V = M / 32, N = 2 * M;
+  float2 v[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int m = lane + 32 * t;
+    if (BC == BC_P) {
+      v[t] = src.pair(2 * m);
+    } else {
+      const int n0 = sample_of<BC, N>(2 * m), n1 = sample_of<BC, N>(2 * m + 1);
+      float a = src.one(n0), b = src.one(n1);
+      if (BC == BC_DD) {  // sine transform: cosine transform of the sign-alternated input
+        if (n0 & 1) a = -a;
+        if (n1 & 1) b = -b;
+      }
+      v[t] = make_float2(a, b);
+    }
+  }
+  Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
+  // v[t] = Z_k, k = lane + 32 t.  Partner Z_{M-k} through the exchange buffer.
+#pragma unroll
+  for (int t = 0; t < V; ++t) xb[lane + 32 * t] = v[t];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int k = lane + 32 * t;
+    const float2 zk = v[t];
+    if (k == 0) {
+      const float v0 = zk.x + zk.y, vm = zk.x - zk.y;
+      if (BC == BC_P) {
+        snk.put(0, v0);
+        snk.put(N - 1, vm);
+      } else {
+        const float y0 = 2.f * v0, ym = 1.41421356237309504880f * vm;
+        snk.put(BC == BC_DD ? N - 1 : 0, y0);
+        snk.put(BC == BC_DD ? N - 1 - M : M, ym);
+      }
+      continue;
+    }
+    const float2 zm = xb[M - k];
+    float2 E, O;
+    E.x = 0.5f * (zk.x + zm.x);
+    E.y = 0.5f * (zk.y - zm.y);
+    O.x = 0.5f * (zk.y + zm.y);
+    O.y = -0.5f * (zk.x - zm.x);
+    const float2 wO = cmul(ld_tw(tb.post, k), O);
+    const float2 vk = make_float2(E.x + wO.x, E.y + wO.y);
+    if (BC == BC_P) {
+      snk.put(2 * k - 1, vk.x);
+      snk.put(2 * k, vk.y);
+    } else {
+      const float2 a = cmul(ld_tw(tb.mak, k), vk);
+      snk.put(BC == BC_DD ? N - 1 - k : k, 2.f * a.x);
+      snk.put(BC == BC_DD ? k - 1 : N - k, -2.f * a.y);
+    }
+  }
+  __syncwarp();
+}
+
+// Inverse transform of one line (times N).
+//   src.get(s) -> input slot s.   snk.pair(n, x_n, x_n+1) (periodic) or snk.one(n, x_n) (walls).
+template <int M, int BC, typename Src, typename Snk>
+__device__ __forceinline__ void inverse(float2* xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
+  constexpr int V = M / 32, N = 2 * M;
+  float2 v[V];
+  // X_k (periodic) or V_k = W^-k (Y_k - i Y_N-k)/2 (walls) for the lane's k = lane + 32 t
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int k = lane + 32 * t;
+    if (BC == BC_P) {
+      v[t] = (k == 0) ? make_float2(src.get(0), src.get(N - 1)) : make_float2(src.get(2 * k - 1), src.get(2 * k));
+    } else {
+      const int s0 = (BC == BC_DD) ? N - 1 : 0;
+      if (k == 0) {
+        v[t] = make_float2(0.5f * src.get(s0), 0.70710678118654752440f * src.get(BC == BC_DD ? N - 1 - M : M));
+      } else {
+        const float a = src.get(BC == BC_DD ? N - 1 - k : k), b = src.get(BC == BC_DD ? k - 1 : N - k);
+        v[t] = cmul(cconj(ld_tw(tb.mak, k)), make_float2(0.5f * a, -0.5f * b));
+      }
+    }
+  }
+  // k = 0 holds (X_0, X_M) packed as real parts; every other k needs X_{M-k} from its partner
+#pragma unroll
+  for (int t = 0; t < V; ++t) xb[lane + 32 * t] = v[t];
+  __syncwarp();
+  float2 z[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int k = lane + 32 * t;
+    const float2 xk = v[t];
+    if (k == 0) {
+      z[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
+    } else {
+      const float2 xm = xb[M - k];
+      const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);  // X_k + conj X_{M-k}
+      const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);  // X_k - conj X_{M-k}
+      const float2 wB = cmul(cconj(ld_tw(tb.post, k)), B);
+      z[t] = cconj(make_float2(A.x - wB.y, A.y + wB.x));  // conj(A + i w B)
+    }
+  }
+  __syncwarp();
+  Stages<M, 0, nstages(M)>::run(z, xb, tb.tw, lane);
+  // z[t] = conj(N x-packed) at m = lane + 32 t: samples 2m, 2m+1 of v
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int m = lane + 32 * t;
+    const float a = z[t].x, b = -z[t].y;
+    if (BC == BC_P) {
+      snk.pair(2 * m, a, b);
+    } else {
+      const int n0 = sample_of<BC, N>(2 * m), n1 = sample_of<BC, N>(2 * m + 1);
+      snk.one(n0, (BC == BC_DD && (n0 & 1)) ? -a : a);
+      snk.one(n1, (BC == BC_DD && (n1 & 1)) ? -b : b);
+    }
+  }
+}
+
+}  // namespace wl
+}  // namespace cans
