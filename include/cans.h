@@ -128,6 +128,13 @@ const char* cans_status_string(int status);
  */
 int cans_transform_xy(cans_plan_t plan, double* field, int dir, void* cuda_stream);
 
+/* cans_transform_xy_f32: the same transforms with the mixed-precision path's FP32 passes (mixed
+ * plans only; CANS_ERR_ARG otherwise).  dir = +1: field (double, read only) -> work (float,
+ * plan-shaped, same slot order as above).  dir = -1: work (float, overwritten) -> field (double),
+ * unnormalised as above.  The FP32 rounding of every stage bounds the agreement with the double
+ * transforms to a few float ulps times log2(Nx Ny). */
+int cans_transform_xy_f32(cans_plan_t plan, double* field, float* work, int dir, void* cuda_stream);
+
 /* cans_zsolve: in place on the transformed field, solve (A_z + mu_ij I) x = rhs along z for every
  * (i, j) slot, mu_ij = lam_x(i)/dx^2 + lam_y(j)/dy^2 (Eq. poi_reduced), in double. */
 int cans_zsolve(cans_plan_t plan, double* field, void* cuda_stream);

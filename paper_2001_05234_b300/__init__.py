@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_transform_xy.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.cans_transform_xy_f32.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.cans_zsolve.argtypes = [vp, vp, vp]
         L.cans_plan_eigenvalues.argtypes = [vp, dp, dp]
         L.cans_plan_profile.argtypes = [vp, ctypes.c_int]
@@ -199,6 +200,10 @@ def cans_plan_destroy(plan) -> int:
 
 def cans_transform_xy(plan, field_ptr: int, direction: int, stream_ptr: int) -> int:
     return lib().cans_transform_xy(plan, field_ptr, int(direction), stream_ptr or None)
+
+
+def cans_transform_xy_f32(plan, field_ptr: int, work_ptr: int, direction: int, stream_ptr: int) -> int:
+    return lib().cans_transform_xy_f32(plan, field_ptr, work_ptr, int(direction), stream_ptr or None)
 
 
 def cans_zsolve(plan, field_ptr: int, stream_ptr: int) -> int:

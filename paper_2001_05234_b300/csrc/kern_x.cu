@@ -359,6 +359,7 @@ StencilDF stencil_df(const cans_plan_s* P) {
     S.bc[d] = P->bc[d];
     S.n[d] = P->n[d];
   }
+  S.iso = (P->idx2 == P->idy2) ? 1 : 0;
   return S;
 }
 

@@ -59,9 +59,16 @@ struct SrcRes {  // r = f - L_h(Phi + Plo) at (n, j, k); accumulates sum r^2
     return r;
   }
   __device__ __forceinline__ float2 pair(int n) {
-    const float a = one(n), b = one(n + 1);
-    return make_float2(a, b);
+    const float2 r = residual_pair<PLO>(f, Phi, Plo, *S, base + n, n, j, k);
+    acc = __fmaf_rn(r.x, r.x, __fmaf_rn(r.y, r.y, acc));
+    return r;
   }
+};
+
+struct SrcF32 {  // float input (may be the output line itself: every value is read before any write)
+  const float* s;
+  __device__ __forceinline__ float2 pair(int n) { return *reinterpret_cast<const float2*>(s + n); }
+  __device__ __forceinline__ float one(int n) { return s[n]; }
 };
 
 struct SnkF {
@@ -135,7 +142,7 @@ struct SnkLine {
 };
 
 template <int M, int BC, int MODE>
-__global__ void __launch_bounds__(32 * XW_WARPS, 3)
+__global__ void __launch_bounds__(32 * XW_WARPS, MODE == 0 ? 3 : 2)
     xfwd_w_kernel(const double* __restrict__ f, const float* __restrict__ Phi, const float* __restrict__ Plo,
                   float* __restrict__ dst, int nlines, LineTab<float> tb, StencilDF S, double* norm_acc) {
   __shared__ float2 xbuf[XW_WARPS][M];
@@ -148,16 +155,32 @@ __global__ void __launch_bounds__(32 * XW_WARPS, 3)
     SnkF snk{dst + base};
     if (MODE == 0) {
       SrcF src{f + base, 0.f};
-      wl::forward<M, BC>(xb, tb, lane, src, snk);
+      wl::forward<M, BC>(wl::Plain{xb}, tb, lane, src, snk);
       acc += src.acc;
     } else {
       const int k = line / S.n[1];
       SrcRes<MODE == 1> src{f, Phi, Plo, &S, base, line - k * S.n[1], k, 0.f};
-      wl::forward<M, BC>(xb, tb, lane, src, snk);
+      wl::forward<M, BC>(wl::Plain{xb}, tb, lane, src, snk);
       acc += src.acc;
     }
   }
   if (norm_acc != nullptr) warp_block_accumulate(acc, norm_acc);
+}
+
+// Forward transform of float lines, in place allowed (no restrict: in may equal out).
+template <int M, int BC>
+__global__ void __launch_bounds__(32 * XW_WARPS, 3) xfwd32_w_kernel(const float* in, float* out, int nlines,
+                                                                    LineTab<float> tb) {
+  __shared__ float2 xbuf[XW_WARPS][M];
+  constexpr int N = 2 * M;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2* xb = xbuf[wid];
+  for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
+    const size_t base = (size_t)line * N;
+    SrcF32 src{in + base};
+    SnkF snk{out + base};
+    wl::forward<M, BC>(wl::Plain{xb}, tb, lane, src, snk);
+  }
 }
 
 template <int M, int BC, int MODE>
@@ -178,7 +201,7 @@ __global__ void __launch_bounds__(32 * XW_WARPS, 3)
     }
     SrcSlots in{src + base};
     SnkLine<MODE> out{&u, base};
-    wl::inverse<M, BC>(xb, tb, lane, in, out);
+    wl::inverse<M, BC>(wl::Plain{xb}, tb, lane, in, out);
   }
   if (MODE == 1 && gauge != nullptr) {
     __shared__ double red[XW_WARPS];
@@ -221,6 +244,14 @@ cudaError_t xinv_w(const cans_plan_s* P, const float* src, double* p, float* Phi
   auto k = xinv_w_kernel<M, BC, MODE>;
   k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(src, p, Phi, Plo, nlines, (float)scale, P->tx_f, P->dzf_f,
                                                    P->dzf_flo, P->n[1], gauge);
+  return cudaGetLastError();
+}
+
+template <int M, int BC>
+cudaError_t xfwd32_w(const cans_plan_s* P, const float* in, float* out, cudaStream_t st) {
+  const int nlines = P->n[1] * P->n[2];
+  auto k = xfwd32_w_kernel<M, BC>;
+  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(in, out, nlines, P->tx_f);
   return cudaGetLastError();
 }
 
@@ -270,6 +301,29 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
 #undef XW_CASE
   *handled = false;
   return cudaSuccess;
+}
+
+// Residual sweep, split form: the streaming residual stencil writes r into W, then the x-forward
+// transforms W in place.  Taken whenever the x lines fit the warp engine; otherwise *handled is false.
+cudaError_t launch_xres_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
+                             float* W, double* acc, cudaStream_t st, bool* handled) {
+  *handled = false;
+  if (P->wblk || !aligned16(W) || !wl::supported(P->dx.m)) return cudaSuccess;
+  *handled = true;
+  cudaError_t e = launch_residual(P, f, Phi, Plo, plo, W, acc, st);
+  if (e != cudaSuccess) return e;
+  const int bc = P->bc[0];
+#define XW_CASE(MM)                                                \
+  if (P->dx.m == MM) {                                             \
+    if (bc == BC_P) return xfwd32_w<MM, BC_P>(P, W, W, st);        \
+    if (bc == BC_NN) return xfwd32_w<MM, BC_NN>(P, W, W, st);      \
+    return xfwd32_w<MM, BC_DD>(P, W, W, st);                       \
+  }
+  XW_CASE(128)
+  XW_CASE(256)
+  XW_CASE(512)
+#undef XW_CASE
+  return cudaErrorInvalidValue;
 }
 
 #define XW_INST_F(MODE)                                                                                         \

@@ -156,6 +156,11 @@ static cudaError_t y_m(const cans_plan_s* P, T* w, cudaStream_t st) {
 template <typename T, int DIR>
 cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st) {
   if (P->n[1] < 2) return cudaSuccess;
+  if (sizeof(T) == 4) {
+    bool handled = false;
+    const cudaError_t e = launch_y_warp<DIR>(P, reinterpret_cast<float*>(w), st, &handled);
+    if (handled) return e;
+  }
   switch (P->dy.m) {
 #define CASE_M(MM) \
   case MM: return ypipe_m<T, DIR, MM>(P, w, st);

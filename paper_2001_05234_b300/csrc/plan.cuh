@@ -27,6 +27,7 @@ struct StencilDF {
   const float *sa_hi, *sa_lo, *sc_hi, *sc_lo;  // z: a_k (to k-1), c_k (to k+1), wall ghosts included
   int bc[3];
   int n[3];
+  int iso;  // 1/dx^2 == 1/dy^2 exactly
 };
 
 // Layout of a transformed work field.  natural: [k][j][i] (x fastest, as the user's fields);
@@ -161,6 +162,10 @@ Launch line_launch_shape(int N, int count, size_t elem2, int prefer_nl);
 template <int MODE>
 cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
                              double* acc, cudaStream_t st, bool* handled);
+cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
+                            float* r, double* norm_acc, cudaStream_t st);
+cudaError_t launch_xres_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
+                             float* W, double* acc, cudaStream_t st, bool* handled);
 template <int DIR>
 cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled);
 template <int MODE>

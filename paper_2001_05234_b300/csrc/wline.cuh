@@ -59,10 +59,22 @@ __device__ __forceinline__ int xpos(int m) {
 
 __device__ __forceinline__ float2 ld_tw(const float2* __restrict__ t, int i) { return __ldg(&t[i]); }
 
+// Exchange buffer of M float2 cells: contiguous (Plain) or one column of a row-padded tile whose
+// rows are RS cells apart (Strided; conflict-free whenever Plain is, for odd RS).
+struct Plain {
+  float2* p;
+  __device__ __forceinline__ float2& operator[](int i) const { return p[i]; }
+};
+template <int RS>
+struct Strided {
+  float2* p;
+  __device__ __forceinline__ float2& operator[](int i) const { return p[i * RS]; }
+};
+
 // One Stockham stage on the lane's registers.  Exchange (all but the last stage): the outputs are
 // written to xb at their swizzled positions and read back in the lane-p-owns-m=p+32t order.
-template <int M, int S>
-__device__ __forceinline__ void stage(float2 (&v)[M / 32], float2* xb, const float2* __restrict__ tw, int lane) {
+template <int M, int S, typename XB>
+__device__ __forceinline__ void stage(float2 (&v)[M / 32], const XB& xb, const float2* __restrict__ tw, int lane) {
   constexpr int V = M / 32, R = radix(M, S), Ns = stride(M, S), Q = V / R, NST = nstages(M);
   constexpr int TS = M / (R * Ns);  // twiddle table stride
   static_assert(V % R == 0, "radix must divide the values per lane");
@@ -107,14 +119,16 @@ __device__ __forceinline__ void stage(float2 (&v)[M / 32], float2* xb, const flo
 
 template <int M, int S, int NST>
 struct Stages {
-  static __device__ __forceinline__ void run(float2 (&v)[M / 32], float2* xb, const float2* tw, int lane) {
+  template <typename XB>
+  static __device__ __forceinline__ void run(float2 (&v)[M / 32], const XB& xb, const float2* tw, int lane) {
     stage<M, S>(v, xb, tw, lane);
     Stages<M, S + 1, NST>::run(v, xb, tw, lane);
   }
 };
 template <int M, int NST>
 struct Stages<M, NST, NST> {
-  static __device__ __forceinline__ void run(float2 (&)[M / 32], float2*, const float2*, int) {}
+  template <typename XB>
+  static __device__ __forceinline__ void run(float2 (&)[M / 32], const XB&, const float2*, int) {}
 };
 
 // sample index of position n of the permuted sequence v (identity for periodic lines)
@@ -124,11 +138,26 @@ __device__ __forceinline__ int sample_of(int n) {
   return (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
 }
 
+// output slots of k: periodic (0, N-1) for k = 0 else (2k-1, 2k); Neumann (0, M) / (k, N-k);
+// Dirichlet the Neumann slots s mirrored to N-1-s
+template <int BC, int M, typename Snk>
+__device__ __forceinline__ void put_pair(Snk& snk, int k, float o0, float o1) {
+  constexpr int N = 2 * M;
+  if (BC == BC_P) {
+    snk.put(k == 0 ? 0 : 2 * k - 1, o0);
+    snk.put(k == 0 ? N - 1 : 2 * k, o1);
+  } else {
+    const int s0 = k, s1 = (k == 0) ? M : N - k;
+    snk.put(BC == BC_DD ? N - 1 - s0 : s0, o0);
+    snk.put(BC == BC_DD ? N - 1 - s1 : s1, o1);
+  }
+}
+
 // Forward transform of one line.
 //   src.pair(n) -> float2 (x_n, x_n+1), n even (periodic lines);  src.one(n) -> x_n (walls).
 //   snk.put(s, y) stores output slot s.
-template <int M, int BC, typename Src, typename Snk>
-__device__ __forceinline__ void forward(float2* xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
+template <int M, int BC, bool ALIAS = false, typename XB, typename Src, typename Snk>
+__device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
   constexpr int V = M / 32, N = 2 * M;
   float2 v[V];
 #pragma unroll
@@ -146,6 +175,7 @@ __device__ __forceinline__ void forward(float2* xb, const LineTab<float>& tb, in
       v[t] = make_float2(a, b);
     }
   }
+  if (ALIAS) __syncwarp();  // every lane has read its inputs before the buffer is overwritten
   Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
   // v[t] = Z_k, k = lane + 32 t.  Partner Z_{M-k} through the exchange buffer.
 #pragma unroll
@@ -155,42 +185,47 @@ __device__ __forceinline__ void forward(float2* xb, const LineTab<float>& tb, in
   for (int t = 0; t < V; ++t) {
     const int k = lane + 32 * t;
     const float2 zk = v[t];
+    float o0, o1;  // the two output values of k (slots below)
     if (k == 0) {
       const float v0 = zk.x + zk.y, vm = zk.x - zk.y;
-      if (BC == BC_P) {
-        snk.put(0, v0);
-        snk.put(N - 1, vm);
-      } else {
-        const float y0 = 2.f * v0, ym = 1.41421356237309504880f * vm;
-        snk.put(BC == BC_DD ? N - 1 : 0, y0);
-        snk.put(BC == BC_DD ? N - 1 - M : M, ym);
-      }
-      continue;
-    }
-    const float2 zm = xb[M - k];
-    float2 E, O;
-    E.x = 0.5f * (zk.x + zm.x);
-    E.y = 0.5f * (zk.y - zm.y);
-    O.x = 0.5f * (zk.y + zm.y);
-    O.y = -0.5f * (zk.x - zm.x);
-    const float2 wO = cmul(ld_tw(tb.post, k), O);
-    const float2 vk = make_float2(E.x + wO.x, E.y + wO.y);
-    if (BC == BC_P) {
-      snk.put(2 * k - 1, vk.x);
-      snk.put(2 * k, vk.y);
+      o0 = (BC == BC_P) ? v0 : 2.f * v0;
+      o1 = (BC == BC_P) ? vm : 1.41421356237309504880f * vm;
     } else {
-      const float2 a = cmul(ld_tw(tb.mak, k), vk);
-      snk.put(BC == BC_DD ? N - 1 - k : k, 2.f * a.x);
-      snk.put(BC == BC_DD ? k - 1 : N - k, -2.f * a.y);
+      const float2 zm = xb[M - k];
+      float2 E, O;
+      E.x = 0.5f * (zk.x + zm.x);
+      E.y = 0.5f * (zk.y - zm.y);
+      O.x = 0.5f * (zk.y + zm.y);
+      O.y = -0.5f * (zk.x - zm.x);
+      const float2 wO = cmul(ld_tw(tb.post, k), O);
+      const float2 vk = make_float2(E.x + wO.x, E.y + wO.y);
+      if (BC == BC_P) {
+        o0 = vk.x;
+        o1 = vk.y;
+      } else {
+        const float2 a = cmul(ld_tw(tb.mak, k), vk);
+        o0 = 2.f * a.x;
+        o1 = -2.f * a.y;
+      }
+    }
+    if (ALIAS) {
+      v[t] = make_float2(o0, o1);  // written after every lane has read its partners
+    } else {
+      put_pair<BC, M>(snk, k, o0, o1);
     }
   }
   __syncwarp();
+  if (ALIAS) {
+#pragma unroll
+    for (int t = 0; t < V; ++t) put_pair<BC, M>(snk, lane + 32 * t, v[t].x, v[t].y);
+    __syncwarp();
+  }
 }
 
 // Inverse transform of one line (times N).
 //   src.get(s) -> input slot s.   snk.pair(n, x_n, x_n+1) (periodic) or snk.one(n, x_n) (walls).
-template <int M, int BC, typename Src, typename Snk>
-__device__ __forceinline__ void inverse(float2* xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
+template <int M, int BC, typename XB, typename Src, typename Snk>
+__device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
   constexpr int V = M / 32, N = 2 * M;
   float2 v[V];
   // X_k (periodic) or V_k = W^-k (Y_k - i Y_N-k)/2 (walls) for the lane's k = lane + 32 t
@@ -210,31 +245,31 @@ __device__ __forceinline__ void inverse(float2* xb, const LineTab<float>& tb, in
     }
   }
   // k = 0 holds (X_0, X_M) packed as real parts; every other k needs X_{M-k} from its partner
+  __syncwarp();  // (the source may be the exchange buffer itself)
 #pragma unroll
   for (int t = 0; t < V; ++t) xb[lane + 32 * t] = v[t];
   __syncwarp();
-  float2 z[V];
 #pragma unroll
   for (int t = 0; t < V; ++t) {
     const int k = lane + 32 * t;
     const float2 xk = v[t];
     if (k == 0) {
-      z[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
+      v[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
     } else {
       const float2 xm = xb[M - k];
       const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);  // X_k + conj X_{M-k}
       const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);  // X_k - conj X_{M-k}
       const float2 wB = cmul(cconj(ld_tw(tb.post, k)), B);
-      z[t] = cconj(make_float2(A.x - wB.y, A.y + wB.x));  // conj(A + i w B)
+      v[t] = cconj(make_float2(A.x - wB.y, A.y + wB.x));  // conj(A + i w B)
     }
   }
   __syncwarp();
-  Stages<M, 0, nstages(M)>::run(z, xb, tb.tw, lane);
-  // z[t] = conj(N x-packed) at m = lane + 32 t: samples 2m, 2m+1 of v
+  Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
+  // v[t] = conj(N x-packed) at m = lane + 32 t: samples 2m, 2m+1 of the permuted sequence
 #pragma unroll
   for (int t = 0; t < V; ++t) {
     const int m = lane + 32 * t;
-    const float a = z[t].x, b = -z[t].y;
+    const float a = v[t].x, b = -v[t].y;
     if (BC == BC_P) {
       snk.pair(2 * m, a, b);
     } else {

@@ -91,6 +91,55 @@ def test_transform_xy_matches_library_transforms(cans, bcx, bcy, n):
     cans.cans_plan_destroy(h)
 
 
+@pytest.mark.parametrize("bcx,bcy", list(itertools.product((P, NN, DD), (P, NN, DD))))
+@pytest.mark.parametrize("n", [(256, 512, 2), (1024, 128, 1), (512, 1024, 1), (64, 48, 2), (24, 256, 2)])
+def test_transform_xy_f32_matches_library_transforms(cans, bcx, bcy, n):
+    """The mixed path's FP32 x/y passes: warp-per-line kernels for N in {256, 512, 1024} (Nx a
+    multiple of 16 for y), CTA-wide kernels otherwise; agreement to FP32 rounding."""
+    import torch
+
+    h = make_plan(cans, n, (bcx, bcy, NN), prec=1)
+    x = np.random.default_rng(2).standard_normal((n[2], n[1], n[0]))
+    t = dev(x)
+    w = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+    assert cans.cans_transform_xy_f32(h, t.data_ptr(), w.data_ptr(), 1, stream()) == 0
+    want = ref_forward(ref_forward(x, bcx, 2), bcy, 1)
+    got = host(w).astype(np.float64)
+    assert np.abs(got - want).max() <= 4e-6 * np.abs(want).max()
+    assert cans.cans_transform_xy_f32(h, t.data_ptr(), w.data_ptr(), -1, stream()) == 0
+    back = host(t)
+    assert np.abs(back - n[0] * n[1] * x).max() <= 4e-6 * n[0] * n[1] * np.abs(x).max()
+    cans.cans_plan_destroy(h)
+
+
+def test_transform_xy_f32_rejects_fp64_plans(cans):
+    import torch
+
+    h = make_plan(cans, (32, 32, 2), (P, P, NN), prec=0)
+    t = torch.zeros((2, 32, 32), dtype=torch.float64, device="cuda")
+    w = torch.zeros((2, 32, 32), dtype=torch.float32, device="cuda")
+    assert cans.cans_transform_xy_f32(h, t.data_ptr(), w.data_ptr(), 1, stream()) != 0
+    cans.cans_plan_destroy(h)
+
+
+@pytest.mark.parametrize("bc", [(P, P, NN), (NN, DD, NN), (DD, P, DD)])
+def test_mixed_refined_warp_engine_sizes(cans, bc):
+    """Refined mixed solve on a shape every fused pass of which runs on the warp-per-line kernels."""
+    n = (256, 128, 12)
+    dzf = I.tanh_dzf(12, 1.6)
+    case = I.case_modes(n=n)
+    case.bc = bc
+    case.dzf = dzf
+    f = I.rhs_host(case)
+    p, st, info = solve_gpu(cans, f, n, bc, (1.0, 1.0), dzf, prec=1, sweeps=2, info=True)
+    ref = oracle.poisson_solve(f, bc, (1.0, 1.0), dzf)
+    res = oracle.relative_residual(p, f, bc, (1.0, 1.0), dzf)
+    floor = oracle.relative_residual(ref, f, bc, (1.0, 1.0), dzf)
+    assert res <= max(1e-12, 2 * floor), (res, floor, info)
+    assert rel(p, ref) <= 1e-11
+    assert st == 0
+
+
 # ---------------------------------------------------------------------------------------------
 # z tridiagonal pass against the oracle's rows and Thomas
 # ---------------------------------------------------------------------------------------------
