@@ -102,9 +102,11 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
-def pass_bytes_mixed(sweeps: int):
+def pass_bytes_mixed(sweeps: int, split_residual: bool):
     """Algorithmic bytes per point each pass kind must move in the mixed solve with `sweeps` sweeps
-    (the first sweep knows the iterate's tail Plo is zero, later sweeps read and write it)."""
+    (the first sweep knows the iterate's tail Plo is zero, later sweeps read and write it).  With the
+    residual as its own stencil kernel, that kernel reads f (8), Phi (4) [, Plo (4)] and writes r (4),
+    and the x forward of the sweep reads and writes the float work field (8)."""
     first, later = 16, 20
     avg = (first + later * (sweeps - 1)) / max(sweeps, 1)
     return {
@@ -113,8 +115,9 @@ def pass_bytes_mixed(sweeps: int):
         2: 8,    # z solve: read + write float
         3: 8,    # y inverse
         4: 8,    # x inverse of the first solve: read work (4), write Phi (4)
-        5: avg,  # x forward + residual: read f (8), Phi (4) [, Plo (4)], write work (4)
+        5: 8 if split_residual else avg,  # x forward of the residual (fused: + f, Phi [, Plo] reads)
         6: avg,  # x inverse + update: read work (4), Phi (4) [, Plo (4)], write p (8) or Phi, Plo (8)
+        7: avg,  # residual stencil: read f (8), Phi (4) [, Plo (4)], write r (4)
     }
 
 
@@ -186,9 +189,10 @@ def gpu_arm(args):
     ms_total = e0.elapsed_time(e1)
     ms = replicas.max_over_ranks(ms_total / args.steps, device="cuda")
     # per-pass device times inside the timed region
-    PASS_BYTES_MIXED = pass_bytes_mixed(sweeps_used)
+    split = cans.cans_plan_profile_read(solver.plan, 7)[1] > 0
+    PASS_BYTES_MIXED = pass_bytes_mixed(sweeps_used, split)
     passes = {}
-    for k in range(7):
+    for k in range(8):
         tot, n = cans.cans_plan_profile_read(solver.plan, k)
         if n:
             passes[cans.CANS_PASS_NAMES[k]] = {"ms_avg": tot / n, "launches": n, "share": None,
@@ -200,7 +204,8 @@ def gpu_arm(args):
     hbm_peak, peak_src = _peaks()
     dom_bytes = dominant[1]["bytes_per_pt"] * npts
     achieved = dom_bytes / (dominant[1]["ms_avg"] * 1e-3) / 1e9
-    kernels_per_solve = (6 * (1 + sweeps_used))  # x, y, z(float), z(double), y, x per solve and sweep
+    # x, y, z(float), z(double), y, x per solve and sweep, plus the residual stencil of each sweep
+    kernels_per_solve = 6 * (1 + sweeps_used) + (sweeps_used if split else 0)
 
     # plain FP64 solve of the same workload
     s64 = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64, autotune=True)

@@ -154,7 +154,9 @@ enum cans_pass {
   CANS_PASS_XI = 4, /* inverse x of a first solve */
   CANS_PASS_XR = 5, /* forward x fused with the double-float residual (refinement sweep) */
   CANS_PASS_XU = 6, /* inverse x fused with the update of the iterate (refinement sweep) */
-  CANS_PASS_COUNT = 7
+  CANS_PASS_RS = 7, /* residual stencil of a refinement sweep, when it runs as its own kernel (then
+                       CANS_PASS_XR is the forward x transform of the residual alone) */
+  CANS_PASS_COUNT = 8
 };
 int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);

@@ -526,17 +526,6 @@ cudaError_t cans::set_smem(const void* fn, size_t bytes) {
 
 namespace {
 
-// Forward x-pass of a refinement sweep (the residual r = f - L_h(Phi + Plo) transformed along x):
-// the streaming stencil + in-place warp-engine transform where the lines fit it, otherwise the
-// CTA-wide transform with the residual fused into its loads.
-cudaError_t launch_xres(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo, float* W,
-                        double* acc, cudaStream_t st) {
-  bool handled = false;
-  const cudaError_t e = launch_xres_warp(P, f, Phi, Plo, plo, W, acc, st, &handled);
-  if (handled) return e;
-  return plo ? launch_xfwd<float, 1>(P, f, Phi, Plo, W, acc, st) : launch_xfwd<float, 2>(P, f, Phi, Plo, W, acc, st);
-}
-
 // Event pair around one pass launch when profiling is on.
 struct PassTimer {
   cans_plan_s* P;
@@ -758,7 +747,16 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
       double* gauge = P->singular ? P->acc_d + P->nacc - 5 : nullptr;
       TIMED(CANS_PASS_XI, launch_xinv<float, 1>(P, W, nullptr, Phi, Plo, inv_scale, gauge, st));
       for (int s = 0; s < sweeps; ++s) {
-        TIMED(CANS_PASS_XR, launch_xres(P, f, Phi, Plo, s > 0, W, P->acc_d + 1 + s, st));
+        // residual r = f - L_h(Phi + Plo) transformed along x: a streaming stencil + in-place transform
+        // where the x lines fit the warp-per-line kernels, else one CTA-wide kernel with both fused
+        if (xres_warp_ok(P, W)) {
+          TIMED(CANS_PASS_RS, launch_residual(P, f, Phi, Plo, s > 0, W, P->acc_d + 1 + s, st));
+          TIMED(CANS_PASS_XR, launch_xfwd32_warp(P, W, st));
+        } else if (s == 0) {
+          TIMED(CANS_PASS_XR, launch_xfwd<float, 2>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
+        } else {
+          TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
+        }
         TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
         TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st));
         TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));

@@ -103,6 +103,22 @@ __device__ __forceinline__ df df_split(double x) {
   return df_make(h, __double2float_rn(x - (double)h));
 }
 
+// x = hi + lo with hi = x truncated to a float (towards zero) and lo the remainder to within
+// 2^-46 |x|: the cheaper split for operands that only enter a sum (|lo| < ulp(hi) instead of
+// ulp(hi)/2).  Same range and fallback as df_split.
+__device__ __forceinline__ df df_split_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 943u < 207u) {
+    const unsigned sgn = hi & 0x80000000u;
+    const float h = __uint_as_float((__funnelshift_l(lo, hi, 3) - (896u << 23)) | sgn);
+    // the 29 dropped fraction bits, top 23 of them as an exact float, scaled by +-2^(e-1069)
+    const float rf = __uint_as_float(0x4b000000u | ((lo & 0x1fffffffu) >> 6)) - 8388608.0f;
+    return df_make(h, rf * __uint_as_float(sgn | ((e - 942u) << 23)));
+  }
+  return df_split(x);
+}
+
 // exact float -> double
 __device__ __forceinline__ double f2d(float x) {
   const unsigned b = __float_as_uint(x);

@@ -16,73 +16,135 @@ namespace {
 
 constexpr int RX = 32, RY = 8;  // CTA tile of columns
 
-template <bool PLO>
-__global__ void __launch_bounds__(RX * RY) res_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
+// compile-time boundary kinds: ghost of a wall neighbour (Neumann mirrors, Dirichlet flips sign)
+template <int BC>
+__device__ __forceinline__ float ghost(float c) {
+  return (BC == BC_NN) ? c : -c;
+}
+
+// coef * x as a double-float (coef and x double-float): the product's exact head and a float tail
+__device__ __forceinline__ df df_prod(df coef, df x) {
+  df p = two_prod(coef.hi, x.hi);
+  p.lo = __fmaf_rn(coef.hi, x.lo, __fmaf_rn(coef.lo, x.hi, p.lo));
+  return p;
+}
+// acc + coef * x
+__device__ __forceinline__ df df_add_prod(df acc, df coef, df x) {
+  const df p = df_prod(coef, x);
+  const df s = two_sum(acc.hi, p.hi);
+  return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, p.lo)));
+}
+
+template <bool PLO, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
                                                       const float* __restrict__ Plo, float* __restrict__ r,
                                                       StencilDF S, int kchunk, double* norm_acc) {
+  __shared__ float4 zc[64];  // (c_k hi, c_k lo, a_k hi, a_k lo) of the chunk's planes
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+  const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
+  for (int q = threadIdx.y * RX + threadIdx.x; q < k1 - k0; q += RX * RY)
+    zc[q] = make_float4(S.sc_hi[k0 + q], S.sc_lo[k0 + q], S.sa_hi[k0 + q], S.sa_lo[k0 + q]);
+  __syncthreads();
   const int i = blockIdx.x * RX + threadIdx.x, j = blockIdx.y * RY + threadIdx.y;
   const bool active = i < nx && j < ny;
   float acc = 0.f;
   if (active) {
-    const size_t sz = (size_t)nx * ny;
-    const bool wx = S.bc[0] != BC_P, wy = S.bc[1] != BC_P, wz = S.bc[2] != BC_P;
+    const int sz = nx * ny;  // in-plane offsets stay 32-bit (a plane has < 2^31 points)
     const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
     const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
-    const bool gxm = wx && i == 0, gxp = wx && i == nx - 1, gym = wy && j == 0, gyp = wy && j == ny - 1;
-    const size_t c0 = (size_t)j * nx + i;
-    const size_t cxm = (size_t)j * nx + im, cxp = (size_t)j * nx + ip;
-    const size_t cym = (size_t)jm * nx + i, cyp = (size_t)jp * nx + i;
-    const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-    // Phi (and Plo) at k0 - 1 (periodic wrap; a wall ghost is formed at k = 0 below)
-    const size_t kprev = (k0 == 0) ? (size_t)(nz - 1) : (size_t)(k0 - 1);
-    float p_prev = Phi[kprev * sz + c0], p_cur = Phi[(size_t)k0 * sz + c0];
+    const bool gxm = BX != BC_P && i == 0, gxp = BX != BC_P && i == nx - 1;
+    const bool gym = BY != BC_P && j == 0, gyp = BY != BC_P && j == ny - 1;
+    const int c0 = j * nx + i;
+    const int dxm = j * nx + im - c0, dxp = j * nx + ip - c0, dym = jm * nx + i - c0, dyp = jp * nx + i - c0;
+    const int kprev = (k0 == 0) ? nz - 1 : k0 - 1;
+    const float* pp = Phi + (size_t)k0 * sz + c0;  // Phi at (i, j, k)
+    const double* fp = f + (size_t)k0 * sz + c0;
+    float* rp = r + (size_t)k0 * sz + c0;
+    const float p_first_prev = Phi[(size_t)kprev * sz + c0];
+    float p_cur = pp[0];
+    // Phi_{k-1} - Phi_k exactly (k = k0; a wall ghost at k = 0)
+    df dm = two_sum((BZ != BC_P && k0 == 0) ? ghost<BZ>(p_cur) : p_first_prev, -p_cur);
+    const float* qp = PLO ? Plo + (size_t)k0 * sz + c0 : nullptr;
     float q_prev = 0.f, q_cur = 0.f;
     if (PLO) {
-      q_prev = Plo[kprev * sz + c0];
-      q_cur = Plo[(size_t)k0 * sz + c0];
+      q_prev = Plo[(size_t)kprev * sz + c0];
+      q_cur = qp[0];
     }
-    for (int k = k0; k < k1; ++k) {
-      const size_t o = (size_t)k * sz;
-      const size_t on = (k == nz - 1) ? 0 : o + sz;  // plane k+1 (periodic wrap)
-      const float p_next = Phi[on + c0];
-      const float xm = gxm ? wall_ghost(S.bc[0], p_cur) : Phi[o + cxm];
-      const float xp = gxp ? wall_ghost(S.bc[0], p_cur) : Phi[o + cxp];
-      const float ym = gym ? wall_ghost(S.bc[1], p_cur) : Phi[o + cym];
-      const float yp = gyp ? wall_ghost(S.bc[1], p_cur) : Phi[o + cyp];
-      const float zm = (wz && k == 0) ? wall_ghost(S.bc[2], p_cur) : p_prev;
-      const float zp = (wz && k == nz - 1) ? wall_ghost(S.bc[2], p_cur) : p_next;
-      df a = df_split(f[o + c0]);
-      if (S.iso) {
-        const df sx = two_sum(xm, xp);
-        const df sy = two_sum(ym, yp);
-        const df s2 = two_sum(sx.hi, sy.hi);
-        const df d = two_sum(s2.hi, -4.f * p_cur);
-        a = df_sub_prod(a, S.idx2, df_make(d.hi, __fadd_rn(d.lo, __fadd_rn(s2.lo, __fadd_rn(sx.lo, sy.lo)))));
-      } else {
-        a = df_sub_prod(a, S.idx2, second_difference(xm, xp, p_cur));
-        a = df_sub_prod(a, S.idy2, second_difference(ym, yp, p_cur));
+    // register ring of the next PF planes' f and Phi_{k+1}: the loads of plane k + PF are issued
+    // while plane k is computed, so each thread keeps PF plane loads in flight
+    constexpr int PF = 4;
+    double fr[PF];
+    float pr[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < k1) {
+        fr[u] = fp[(size_t)u * sz];
+        pr[u] = (k == nz - 1) ? Phi[c0] : pp[(size_t)(u + 1) * sz];  // Phi_{k+1}, periodic wrap
       }
-      a = df_sub_prod(a, df_make(S.sc_hi[k], S.sc_lo[k]), two_sum(zp, -p_cur));
-      a = df_sub_prod(a, df_make(S.sa_hi[k], S.sa_lo[k]), two_sum(zm, -p_cur));
-      float rr = a.hi + a.lo;
-      if (PLO) {
-        const float q_next = Plo[on + c0];
-        const float qxm = gxm ? wall_ghost(S.bc[0], q_cur) : Plo[o + cxm];
-        const float qxp = gxp ? wall_ghost(S.bc[0], q_cur) : Plo[o + cxp];
-        const float qym = gym ? wall_ghost(S.bc[1], q_cur) : Plo[o + cym];
-        const float qyp = gyp ? wall_ghost(S.bc[1], q_cur) : Plo[o + cyp];
-        const float qzm = (wz && k == 0) ? wall_ghost(S.bc[2], q_cur) : q_prev;
-        const float qzp = (wz && k == nz - 1) ? wall_ghost(S.bc[2], q_cur) : q_next;
-        rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
-              S.sc_hi[k] * (qzp - q_cur) + S.sa_hi[k] * (qzm - q_cur);
-        q_prev = q_cur;
-        q_cur = q_next;
+    }
+    for (int kb = k0; kb < k1; kb += PF) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int k = kb + u;
+        if (k < k1) {
+          const bool top = (k == nz - 1);
+          const float p_next = pr[u];
+          const double fk = fr[u];
+          if (k + PF < k1) {  // refill this ring slot with plane k + PF
+            fr[u] = fp[(size_t)PF * sz];
+            pr[u] = (k + PF == nz - 1) ? Phi[c0] : pp[(size_t)(PF + 1) * sz];
+          }
+          const float xm = gxm ? ghost<BX>(p_cur) : pp[dxm];
+          const float xp = gxp ? ghost<BX>(p_cur) : pp[dxp];
+          const float ym = gym ? ghost<BY>(p_cur) : pp[dym];
+          const float yp = gyp ? ghost<BY>(p_cur) : pp[dyp];
+          const float zp = (BZ != BC_P && top) ? ghost<BZ>(p_cur) : p_next;
+          const df dp = two_sum(zp, -p_cur);  // Phi_{k+1} - Phi_k exactly
+          const float4 co = zc[k - k0];
+          // L_h Phi as a double-float
+          df L;
+          if (S.iso) {
+            const df sx = two_sum(xm, xp);
+            const df sy = two_sum(ym, yp);
+            const df s2 = two_sum(sx.hi, sy.hi);
+            const df d = two_sum(s2.hi, -4.f * p_cur);
+            L = df_prod(S.idx2, df_make(d.hi, __fadd_rn(d.lo, __fadd_rn(s2.lo, __fadd_rn(sx.lo, sy.lo)))));
+          } else {
+            L = df_prod(S.idx2, second_difference(xm, xp, p_cur));
+            L = df_add_prod(L, S.idy2, second_difference(ym, yp, p_cur));
+          }
+          L = df_add_prod(L, df_make(co.x, co.y), dp);
+          L = df_add_prod(L, df_make(co.z, co.w), dm);
+          // r = (f_hi - L_hi) + (f_lo - L_lo): the first difference is exact when r is small against
+          // f (Sterbenz), and otherwise rounds relative to r itself
+          const df fs = df_split_rz(fk);
+          float rr = __fadd_rn(__fsub_rn(fs.hi, L.hi), __fsub_rn(fs.lo, L.lo));
+          if (PLO) {
+            const long long dzp = top ? -(long long)(nz - 1) * sz : (long long)sz;
+            const float q_next = qp[dzp];
+            const float qxm = gxm ? ghost<BX>(q_cur) : qp[dxm];
+            const float qxp = gxp ? ghost<BX>(q_cur) : qp[dxp];
+            const float qym = gym ? ghost<BY>(q_cur) : qp[dym];
+            const float qyp = gyp ? ghost<BY>(q_cur) : qp[dyp];
+            const float qzm = (BZ != BC_P && k == 0) ? ghost<BZ>(q_cur) : q_prev;
+            const float qzp = (BZ != BC_P && top) ? ghost<BZ>(q_cur) : q_next;
+            rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
+                  co.x * (qzp - q_cur) + co.z * (qzm - q_cur);
+            q_prev = q_cur;
+            q_cur = q_next;
+            qp += sz;
+          }
+          *rp = rr;
+          acc = __fmaf_rn(rr, rr, acc);
+          // next plane: Phi_k - Phi_{k+1} = -(Phi_{k+1} - Phi_k) exactly (TwoSum is odd and symmetric)
+          dm = df_make(-dp.hi, -dp.lo);
+          p_cur = p_next;
+          pp += sz;
+          fp += sz;
+          rp += sz;
+        }
       }
-      r[o + c0] = rr;
-      acc = __fmaf_rn(rr, rr, acc);
-      p_prev = p_cur;
-      p_cur = p_next;
     }
   }
   if (norm_acc != nullptr) {
@@ -100,20 +162,46 @@ __global__ void __launch_bounds__(RX * RY) res_kernel(const double* __restrict__
   }
 }
 
+template <bool PLO, int BX, int BY, int BZ>
+cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi, const float* Plo, float* r,
+                       const StencilDF& S, int kchunk, double* acc, cudaStream_t st) {
+  res_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
+  return cudaGetLastError();
+}
+
+template <bool PLO, int BX, int BY>
+cudaError_t res_bz(int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st) {
+  if (bz == BC_P) return res_launch<PLO, BX, BY, BC_P>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (bz == BC_NN) return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_launch<PLO, BX, BY, BC_DD>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+}
+template <bool PLO, int BX>
+cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st) {
+  if (by == BC_P) return res_bz<PLO, BX, BC_P>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (by == BC_NN) return res_bz<PLO, BX, BC_NN>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_bz<PLO, BX, BC_DD>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
+}
+template <bool PLO>
+cudaError_t res_bx(const int* bc, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st) {
+  if (bc[0] == BC_P) return res_by<PLO, BC_P>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (bc[0] == BC_NN) return res_by<PLO, BC_NN>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_by<PLO, BC_DD>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
+}
+
 }  // namespace
 
 cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
                             float* r, double* norm_acc, cudaStream_t st) {
   const int nx = P->n[0], ny = P->n[1], nz = P->n[2];
-  const int kchunk = std::min(nz, 64);
+  const int kchunk = std::min(nz, 64);  // at most the 64 planes whose z coefficients a CTA stages
   dim3 grid((nx + RX - 1) / RX, (ny + RY - 1) / RY, (nz + kchunk - 1) / kchunk);
   dim3 block(RX, RY);
   const StencilDF S = stencil_df(P);
-  if (plo)
-    res_kernel<true><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, norm_acc);
-  else
-    res_kernel<false><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, norm_acc);
-  return cudaGetLastError();
+  if (plo) return res_bx<true>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+  return res_bx<false>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
 }
 
 }  // namespace cans

@@ -303,15 +303,13 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
   return cudaSuccess;
 }
 
-// Residual sweep, split form: the streaming residual stencil writes r into W, then the x-forward
-// transforms W in place.  Taken whenever the x lines fit the warp engine; otherwise *handled is false.
-cudaError_t launch_xres_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
-                             float* W, double* acc, cudaStream_t st, bool* handled) {
-  *handled = false;
-  if (P->wblk || !aligned16(W) || !wl::supported(P->dx.m)) return cudaSuccess;
-  *handled = true;
-  cudaError_t e = launch_residual(P, f, Phi, Plo, plo, W, acc, st);
-  if (e != cudaSuccess) return e;
+// Residual sweep, split form: the streaming residual stencil (kern_res.cu) writes r into W, then
+// this x-forward transforms W in place.  Taken whenever the x lines fit the warp engine.
+bool xres_warp_ok(const cans_plan_s* P, const float* W) {
+  return !P->wblk && aligned16(W) && wl::supported(P->dx.m);
+}
+
+cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st) {
   const int bc = P->bc[0];
 #define XW_CASE(MM)                                                \
   if (P->dx.m == MM) {                                             \

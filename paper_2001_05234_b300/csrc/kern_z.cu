@@ -9,10 +9,10 @@ namespace cans {
 
 // Coalesced copy of a TI x Nz tile (TI consecutive x-slots of one y-slot, all z) into the swizzled
 // shared layout and back.  Rows are TI elements long; 16-byte vectors when the grid allows it.
-template <typename T>
-__device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, const ZSwz& Z, int nz, int ncols,
+template <typename T, typename ZS>
+__device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, const ZS& Z, int nz, int ncols,
                                           bool vec) {
-  const int TI = Z.TI;
+  const int TI = Z.ti();
   constexpr int V = 16 / sizeof(T);
   if (vec && ncols == TI) {
     // 16-byte vectors, four in flight per thread before the shared-memory stores
@@ -54,10 +54,10 @@ __device__ __forceinline__ void tile_load(T* tile, const T* col0, size_t plane, 
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane, const ZSwz& Z, int nz, int ncols,
+template <typename T, typename ZS>
+__device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane, const ZS& Z, int nz, int ncols,
                                            bool vec) {
-  const int TI = Z.TI;
+  const int TI = Z.ti();
   constexpr int V = 16 / sizeof(T);
   if (vec && ncols == TI) {
     const int per_row = TI / V;
@@ -86,11 +86,11 @@ __device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane,
   }
 }
 
-template <int MMAX>
+template <int MMAX, int TIC>
 __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, int vec,
                                                            WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TI = a.ti, m = a.m;
+  const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
   float* sa = reinterpret_cast<float*>(smem_raw);
   float* sb = sa + 32 * m;
   float* sc = sb + 32 * m;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   const size_t plane = wl.zstride();
   float* col0 = w + wl.zbase(i0, j);
   const int ncols = min(TI, a.nx - i0);
-  const ZSwz Z = make_zswz(TI, m);
+  const auto Z = make_zswz<TIC, MMAX>(TI, m);
   stage_zrows<float, float>(sa, sb, sc, zf, a.nz, m);
   tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
@@ -114,11 +114,11 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
 
-template <typename T, int MMAX>
+template <typename T, int MMAX, int TIC>
 __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec,
                                                            WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TI = a.ti, m = a.m;
+  const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
   double* sa = reinterpret_cast<double*>(smem_raw);
   double* sb = sa + 32 * m;
   double* sc = sb + 32 * m;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     for (int c = 0; c < ncols; ++c) any |= a.mask[(size_t)j * a.nx + i0 + c] != 0;
     if (!any) return;
   }
-  const ZSwz Z = make_zswz(TI, m);
+  const auto Z = make_zswz<TIC, MMAX>(TI, m);
   stage_zrows<double, double>(sa, sb, sc, zd, a.nz, m);
   tile_load<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
@@ -174,8 +174,8 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
   return a;
 }
 
-template <typename T, int MMAX>
-static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+template <typename T, int MMAX, int TIC>
+static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
   const WLay wl = wlay(P, sizeof(T) == 4);
   const int vec = ((wl.blk || P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
   if (sizeof(T) == 4) {
@@ -183,28 +183,39 @@ static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStre
     ZArgs a = zargs(P, P->z_ti[1], gauge);
     a.mask = P->mask_d;
     const size_t smem = 3 * 32 * a.m * sizeof(float) + P->z_smem[1];
-    cudaError_t e = set_smem((const void*)zpass_f32_kernel<MMAX>, smem);
+    cudaError_t e = set_smem((const void*)zpass_f32_kernel<MMAX, TIC>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-    zpass_f32_kernel<MMAX><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
+    zpass_f32_kernel<MMAX, TIC><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ZArgs b = zargs(P, P->z_ti[1], gauge);
     b.mask = P->mask_d;
     const size_t smem64 = 3 * 32 * b.m * sizeof(double) + P->z_smem[1];
-    e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem64);
+    e = set_smem((const void*)zpass_f64_kernel<T, MMAX, TIC>, smem64);
     if (e != cudaSuccess) return e;
     dim3 grid64((P->mask_i_end + b.ti - 1) / b.ti, P->mask_j_end);
-    if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec, wl);
+    if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX, TIC><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec, wl);
     return cudaGetLastError();
   }
   ZArgs a = zargs(P, P->z_ti[0], gauge);
   const size_t smem = 3 * 32 * a.m * sizeof(double) + P->z_smem[0];
-  cudaError_t e = set_smem((const void*)zpass_f64_kernel<T, MMAX>, smem);
+  cudaError_t e = set_smem((const void*)zpass_f64_kernel<T, MMAX, TIC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-  zpass_f64_kernel<T, MMAX><<<grid, 256, smem, st>>>(w, a, P->zt_d, vec, wl);
+  zpass_f64_kernel<T, MMAX, TIC><<<grid, 256, smem, st>>>(w, a, P->zt_d, vec, wl);
   return cudaGetLastError();
+}
+
+// compile-time tile widths for the common shapes (the z tile is TI x-slots wide, a power of two)
+template <typename T, int MMAX>
+static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+  switch (P->z_ti[sizeof(T) == 4 ? 1 : 0]) {
+    case 32: return z_mt<T, MMAX, 32>(P, w, gauge, st);
+    case 16: return z_mt<T, MMAX, 16>(P, w, gauge, st);
+    case 8: return z_mt<T, MMAX, 8>(P, w, gauge, st);
+    default: return z_mt<T, MMAX, 0>(P, w, gauge, st);
+  }
 }
 
 template <typename T>

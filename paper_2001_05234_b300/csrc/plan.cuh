@@ -164,8 +164,8 @@ cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float*
                              double* acc, cudaStream_t st, bool* handled);
 cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
                             float* r, double* norm_acc, cudaStream_t st);
-cudaError_t launch_xres_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
-                             float* W, double* acc, cudaStream_t st, bool* handled);
+bool xres_warp_ok(const cans_plan_s* P, const float* W);
+cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st);
 template <int DIR>
 cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled);
 template <int MODE>

@@ -35,14 +35,24 @@ __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
 // (rows past Nz are identity rows), so row k belongs to lane seg = k >> sh; the column index is
 // xor-ed with seg (the 32 lanes reading one column hit 32 banks) and, when m >= 4, with k & 3 (the
 // row-major copy phases, four rows at a time, spread over all banks as well).
+// TI_ > 0 fixes the tile width at compile time (with M_ the rows per lane), so that every index
+// folds into per-lane constants; TI_ = 0 keeps both at run time.
+template <int TI_ = 0, int M_ = 0>
 struct ZSwz {
   int TI, sh, low;
-  __device__ __forceinline__ int seg(int k) const { return k >> sh; }
-  __device__ __forceinline__ int at(int k, int i, int sg) const { return k * TI + (i ^ ((sg ^ (k & low)) & (TI - 1))); }
+  __device__ __forceinline__ int ti() const { return TI_ > 0 ? TI_ : TI; }
+  __device__ __forceinline__ int shift() const { return TI_ > 0 ? ilog2_c(M_) : sh; }
+  __device__ __forceinline__ int lowm() const { return TI_ > 0 ? (M_ >= 4 ? 3 : 0) : low; }
+  __device__ __forceinline__ int seg(int k) const { return k >> shift(); }
+  __device__ __forceinline__ int at(int k, int i, int sg) const {
+    return k * ti() + (i ^ ((sg ^ (k & lowm())) & (ti() - 1)));
+  }
   __device__ __forceinline__ int at(int k, int i) const { return at(k, i, seg(k)); }
+  static __host__ __device__ constexpr int ilog2_c(int x) { return x <= 1 ? 0 : 1 + ilog2_c(x / 2); }
 };
-__device__ __forceinline__ ZSwz make_zswz(int TI, int m) {
-  ZSwz s;
+template <int TI_ = 0, int M_ = 0>
+__device__ __forceinline__ ZSwz<TI_, M_> make_zswz(int TI, int m) {
+  ZSwz<TI_, M_> s;
   s.TI = TI;
   s.sh = 0;
   while ((1 << s.sh) < m) ++s.sh;
@@ -68,8 +78,8 @@ __device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& 
 // mu is the x-y eigenvalue term of the mode.  SING: the singular Neumann mode -- the right-hand side
 // is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
 // x = 0, and the result is shifted to the dzf-weighted mean `target`.
-template <int MMAX, typename C, typename T, bool SING>
-__device__ __forceinline__ void zsolve_column(T* tile, int col, const ZSwz& Z, int Nz, C mu, const C* sa,
+template <int MMAX, typename C, typename T, bool SING, typename ZS>
+__device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int Nz, C mu, const C* sa,
                                               const C* sb, const C* sc, const double* weights, C target) {
   const int lane = threadIdx.x & 31;
   constexpr int m = MMAX;  // rows per lane (compile time: keeps the row arrays in registers)
