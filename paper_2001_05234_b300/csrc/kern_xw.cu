@@ -5,6 +5,7 @@
 // the path for other lengths); one warp per line, persistent CTAs, no CTA barrier inside a line.
 #include <algorithm>
 
+#include "async.cuh"
 #include "plan.cuh"
 #include "stencil.cuh"
 #include "wline.cuh"
@@ -93,6 +94,9 @@ struct SnkUpd {
   df gw;  // gauge weight dzf_k of the line (MODE 1)
   bool gauge;
   df gacc;
+  const float* sphi;  // the line's Phi (and Plo) staged in shared memory (MODE >= 2)
+  const float* splo;
+  size_t base;
   __device__ __forceinline__ float upd(size_t o, float x, double& pd) {
     const float d = x * scale;
     if (MODE == 0) {
@@ -105,8 +109,9 @@ struct SnkUpd {
       }
       return d;
     } else {
-      df s2 = two_sum(Phi[o], d);
-      s2 = fast_two_sum(s2.hi, (MODE <= 3) ? s2.lo + Plo[o] : s2.lo);
+      const int n = (int)(o - base);
+      df s2 = two_sum(sphi[n], d);
+      s2 = fast_two_sum(s2.hi, (MODE <= 3) ? s2.lo + splo[n] : s2.lo);
       if (MODE == 2 || MODE == 4) {
         Plo[o] = s2.lo;
         return s2.hi;
@@ -183,25 +188,43 @@ __global__ void __launch_bounds__(32 * XW_WARPS, 3) xfwd32_w_kernel(const float*
   }
 }
 
+// number of iterate fields (Phi, Plo) an update mode reads
+template <int MODE>
+__host__ __device__ constexpr int upd_reads() {
+  return MODE <= 1 ? 0 : (MODE <= 3 ? 2 : 1);
+}
+
 template <int M, int BC, int MODE>
-__global__ void __launch_bounds__(32 * XW_WARPS, 3)
+__global__ void __launch_bounds__(32 * XW_WARPS, upd_reads<MODE>() == 2 ? 2 : 3)
     xinv_w_kernel(const float* __restrict__ src, double* __restrict__ p, float* __restrict__ Phi,
                   float* __restrict__ Plo, int nlines, float scale, LineTab<float> tb, const float* __restrict__ wz,
                   const float* __restrict__ wz_lo, int ny, double* gauge) {
-  __shared__ float2 xbuf[XW_WARPS][M];
-  constexpr int N = 2 * M;
+  constexpr int N = 2 * M, NR = upd_reads<MODE>();
+  extern __shared__ __align__(16) unsigned char xw_smem[];  // [XW_WARPS][M] float2, then [XW_WARPS][NR N] float
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float2* xb = xbuf[wid];
-  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f)};
+  float2* xb = reinterpret_cast<float2*>(xw_smem) + wid * M;
+  float* stg = reinterpret_cast<float*>(xw_smem + (size_t)XW_WARPS * M * sizeof(float2)) + (size_t)wid * NR * N;
+  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f),
+                 stg, stg + (NR == 2 ? N : 0), 0};
   for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
     const size_t base = (size_t)line * N;
     if (MODE == 1 && gauge != nullptr) {
       const int k = line / ny;
       u.gw = df_make(wz[k], wz_lo[k]);
     }
+    if (NR > 0) {  // stage the line's iterate; the copies complete while the line is transformed
+#pragma unroll
+      for (int q = lane; q < N / 4; q += 32) {
+        cp_async16(stg + 4 * q, Phi + base + 4 * q);
+        if (NR == 2) cp_async16(stg + N + 4 * q, Plo + base + 4 * q);
+      }
+      cp_async_commit();
+    }
+    u.base = base;
     SrcSlots in{src + base};
     SnkLine<MODE> out{&u, base};
-    wl::inverse<M, BC>(wl::Plain{xb}, tb, lane, in, out);
+    wl::inverse<M, BC, true>(wl::Plain{xb}, tb, lane, in, out);
+    if (NR > 0) __syncwarp();  // the staged iterate is read before the next line overwrites it
   }
   if (MODE == 1 && gauge != nullptr) {
     __shared__ double red[XW_WARPS];
@@ -242,8 +265,16 @@ cudaError_t xinv_w(const cans_plan_s* P, const float* src, double* p, float* Phi
                    double* gauge, cudaStream_t st) {
   const int nlines = P->n[1] * P->n[2];
   auto k = xinv_w_kernel<M, BC, MODE>;
-  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(src, p, Phi, Plo, nlines, (float)scale, P->tx_f, P->dzf_f,
-                                                   P->dzf_flo, P->n[1], gauge);
+  const size_t smem = (size_t)XW_WARPS * M * sizeof(float2) + (size_t)XW_WARPS * upd_reads<MODE>() * 2 * M * 4;
+  cudaError_t e = set_smem((const void*)k, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * XW_WARPS, smem);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min((nlines + XW_WARPS - 1) / XW_WARPS, std::max(per_sm, 1) * sms));
+  k<<<grid, 32 * XW_WARPS, smem, st>>>(src, p, Phi, Plo, nlines, (float)scale, P->tx_f, P->dzf_f, P->dzf_flo, P->n[1],
+                                        gauge);
   return cudaGetLastError();
 }
 
@@ -287,6 +318,8 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
   *handled = false;
   if (P->wblk || !aligned16(src)) return cudaSuccess;
   if ((MODE == 0 || MODE == 3 || MODE == 5) && !aligned16(p)) return cudaSuccess;
+  if (upd_reads<MODE>() > 0 && !aligned16(Phi)) return cudaSuccess;
+  if (upd_reads<MODE>() == 2 && !aligned16(Plo)) return cudaSuccess;
   const int bc = P->bc[0];
   *handled = true;
 #define XW_CASE(MM)                                                                       \

@@ -224,7 +224,7 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
 
 // Inverse transform of one line (times N).
 //   src.get(s) -> input slot s.   snk.pair(n, x_n, x_n+1) (periodic) or snk.one(n, x_n) (walls).
-template <int M, int BC, typename XB, typename Src, typename Snk>
+template <int M, int BC, bool WAIT_ASYNC = false, typename XB, typename Src, typename Snk>
 __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
   constexpr int V = M / 32, N = 2 * M;
   float2 v[V];
@@ -265,6 +265,10 @@ __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, 
   }
   __syncwarp();
   Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
+  if (WAIT_ASYNC) {  // the sink reads data the caller staged with cp.async before the line began
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+  }
   // v[t] = conj(N x-packed) at m = lane + 32 t: samples 2m, 2m+1 of the permuted sequence
 #pragma unroll
   for (int t = 0; t < V; ++t) {
