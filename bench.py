@@ -450,6 +450,28 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def solve_once(spec: str, sweeps: int):
+    """Two mixed-precision solves of the bench workload's recipe at size NX,NY,NZ (the second one is
+    the one a profiler captures with -s); no output but "ok".  Used for small ncu captures."""
+    import torch
+
+    import paper_2001_05234_b300 as cans
+    from paper_2001_05234_b300 import build_lib
+    from paper_2001_05234_b300 import inputs as I
+
+    build_lib.build()
+    n = tuple(int(v) for v in spec.split(","))
+    case = I.case_modes(n=n)
+    f = I.rhs_device(case, "cuda")
+    p = torch.empty_like(f)
+    s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sweeps)
+    s.solve(f, p)
+    s.solve(f, p)
+    torch.cuda.synchronize()
+    s.close()
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,8 +479,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--solve-once", default=None, metavar="NX,NY,NZ",
+                    help="profiling aid: two mixed solves of this size, no measurement")
+    ap.add_argument("--sweeps", type=int, default=1, help="refinement sweeps for --solve-once")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.solve_once:
+        solve_once(args.solve_once, args.sweeps)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

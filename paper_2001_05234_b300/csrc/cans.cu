@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "plan.cuh"
+#include "wline.cuh"
 
 using namespace cans;
 
@@ -288,6 +289,26 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     o_post_f[d] = B.add(postf.data(), postf.size() * 4);
     o_mak_f[d] = B.add(makf.data(), makf.size() * 4);
   }
+  // stage twiddles of the warp-per-line engine for the float x and y transforms it takes
+  size_t o_wst[2] = {0, 0};
+  bool has_wst[2] = {false, false};
+  for (int d = 0; d < 2; ++d) {
+    const int M = dirs[d]->m;
+    if (!wl::supported(M)) continue;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<float> wst;
+    for (int s = 1; s < wl::nstages(M); ++s) {
+      const int R = wl::radix(M, s), Ns = wl::stride(M, s);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const long double th = -2.0L * pi * k * r / ((long double)R * Ns);
+          wst.push_back((float)cosl(th));
+          wst.push_back((float)sinl(th));
+        }
+    }
+    o_wst[d] = B.add(wst.data(), wst.size() * 4);
+    has_wst[d] = true;
+  }
   const size_t o_mux_d = B.add(P->mux_h.data(), n[0] * 8), o_muy_d = B.add(P->muy_h.data(), n[1] * 8);
   auto muxf = to_float(P->mux_h), muyf = to_float(P->muy_h);
   const size_t o_mux_f = B.add(muxf.data(), n[0] * 4), o_muy_f = B.add(muyf.data(), n[1] * 4);
@@ -369,6 +390,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   fill_line_tab<double>(P->ty_d, P->dy, base + o_tw_d[1], base + o_post_d[1], base + o_mak_d[1]);
   fill_line_tab<float>(P->tx_f, P->dx, base + o_tw_f[0], base + o_post_f[0], base + o_mak_f[0]);
   fill_line_tab<float>(P->ty_f, P->dy, base + o_tw_f[1], base + o_post_f[1], base + o_mak_f[1]);
+  if (has_wst[0]) P->tx_f.wst = reinterpret_cast<const float2*>(base + o_wst[0]);
+  if (has_wst[1]) P->ty_f.wst = reinterpret_cast<const float2*>(base + o_wst[1]);
   P->mux_d = reinterpret_cast<const double*>(base + o_mux_d);
   P->muy_d = reinterpret_cast<const double*>(base + o_muy_d);
   P->mux_f = reinterpret_cast<const float*>(base + o_mux_f);

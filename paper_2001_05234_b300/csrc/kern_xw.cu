@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(32 * XW_WARPS, MODE == 0 ? 3 : 2)
 
 // Forward transform of float lines, in place allowed (no restrict: in may equal out).
 template <int M, int BC>
-__global__ void __launch_bounds__(32 * XW_WARPS, 3) xfwd32_w_kernel(const float* in, float* out, int nlines,
+__global__ void __launch_bounds__(32 * XW_WARPS, M >= 256 ? 2 : 3) xfwd32_w_kernel(const float* in, float* out, int nlines,
                                                                     LineTab<float> tb) {
   __shared__ float2 xbuf[XW_WARPS][M];
   constexpr int N = 2 * M;

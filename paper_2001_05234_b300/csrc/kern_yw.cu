@@ -1,12 +1,12 @@
 // y-pass of the mixed path on the warp-per-line engine (float work field, Ny = 2M with M in
 // {128, 256, 512}, Nx a multiple of 16): the transform F^y of Eq. poi_reduced, forward or inverse.
 //
-// A persistent CTA of 8 warps walks tiles of 16 consecutive x-slots x Ny rows of one z-plane.  The
-// tile is fetched with 4-byte cp.async copies into a row-pair layout T[m][l] = (x[2m][l],
-// x[2m+1][l]) of float2 with a row stride of 17 cells, so that a warp walking one column with its
-// lanes along m touches 16 different bank pairs.  Each warp transforms two columns in place, using
-// the column itself as its exchange buffer; the CTA then writes the tile back in 64-byte row
-// segments.  Three CTAs share an SM, so one CTA's copies overlap the others' transforms.
+// A persistent CTA of 16 warps walks tiles of 16 consecutive x-slots x Ny rows of one z-plane.  A
+// tile is fetched with 4-byte cp.async copies into a row-pair layout T[m][l] = (x[2m][l], x[2m+1][l])
+// of float2 with a row stride of 17 cells, so that a warp walking one column with its lanes along m
+// touches 16 different bank pairs.  Warp w transforms column w in place, using the column itself as
+// its exchange buffer; the CTA then writes the tile back in 64-byte row segments.  Two tile buffers:
+// the next tile's copies are in flight while the current one is transformed.
 #include <algorithm>
 
 #include "async.cuh"
@@ -16,8 +16,7 @@
 namespace cans {
 namespace {
 
-constexpr int YW_L = 16;   // x-slots (lines) per tile
-constexpr int YW_W = 8;    // warps per CTA
+constexpr int YW_L = 16;   // x-slots (lines) per tile = warps per CTA
 constexpr int YW_RS = 17;  // float2 cells per tile row
 
 struct ColSrc {  // column w of the tile: sample n = T[n/2][w].(n&1)
@@ -35,34 +34,47 @@ struct ColSnk {
   }
 };
 
+// One CTA of 16 warps per SM, one column per warp, two tile buffers: the copies of tile t + G run
+// while tile t is transformed.
 template <int M, int BC, int DIR>
-__global__ void __launch_bounds__(32 * YW_W, M >= 256 ? 2 : 3) yw_kernel(float* __restrict__ w, int nx, int nz, LineTab<float> tb) {
-  constexpr int NY = 2 * M;
+__global__ void __launch_bounds__(32 * YW_L, 1) yw_kernel(float* __restrict__ w, int nx, int nz, LineTab<float> tb) {
+  constexpr int NY = 2 * M, NT = 32 * YW_L;
+  constexpr int TILE = M * YW_RS * 2;  // floats per tile buffer
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* T = reinterpret_cast<float*>(smem_raw);  // [M][YW_RS] float2
+  float* T = reinterpret_cast<float*>(smem_raw);  // [2][M][YW_RS] float2
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int tiles_x = nx / YW_L, ntiles = tiles_x * nz;
   const size_t plane = (size_t)nx * NY;
-  // copy roles: thread -> column l and rows n = r0 + 16 q (q = 0 .. NY/16 - 1); the tile offset of
-  // (n, l) is then so + q * 8 * 2 * YW_RS and the global offset go + q * 16 nx
-  static_assert(32 * YW_W == 16 * YW_L, "copy roles assume 256 threads and 16 lines");
-  const int cl = threadIdx.x & (YW_L - 1), r0 = threadIdx.x >> 4;
+  // copy roles: thread -> column cl and rows n = r0 + RPP q; tile offset so + q * SSTEP, global offset
+  // go + q * RPP nx
+  constexpr int RPP = NT / YW_L;  // rows per copy pass
+  static_assert(NY % RPP == 0 && RPP % 2 == 0, "rows per copy pass");
+  const int cl = threadIdx.x & (YW_L - 1), r0 = threadIdx.x / YW_L;
   const int so = (r0 >> 1) * (2 * YW_RS) + 2 * cl + (r0 & 1);
-  const size_t go = (size_t)r0 * nx + cl, gstep = (size_t)16 * nx;
-  constexpr int SSTEP = 8 * 2 * YW_RS;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    float* g = w + (size_t)(t / tiles_x) * plane + (t % tiles_x) * YW_L;
-    {
-      const float* gp = g + go;
+  const size_t go = (size_t)r0 * nx + cl, gstep = (size_t)RPP * nx;
+  constexpr int SSTEP = (RPP / 2) * 2 * YW_RS;
+  auto tile_base = [&](int t) { return w + (size_t)(t / tiles_x) * plane + (t % tiles_x) * YW_L; };
+  auto fetch = [&](int t, float* buf) {
+    const float* gp = tile_base(t) + go;
 #pragma unroll 8
-      for (int q = 0; q < NY / 16; ++q, gp += gstep) cp_async4(T + so + q * SSTEP, gp);
-    }
+    for (int q = 0; q < NY / RPP; ++q, gp += gstep) cp_async4(buf + so + q * SSTEP, gp);
     cp_async_commit();
-    cp_async_wait<0>();
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) fetch(t, T);
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    float* cur = T + (it & 1) * TILE;
+    __syncthreads();  // the other buffer's previous tile has been written back
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      fetch(tn, T + ((it + 1) & 1) * TILE);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncthreads();
-#pragma unroll 1
-    for (int c = wid; c < YW_L; c += YW_W) {
-      float* col = T + 2 * c;
+    {
+      float* col = cur + 2 * wid;
       ColSrc src{col};
       ColSnk snk{col};
       const wl::Strided<YW_RS> xb{reinterpret_cast<float2*>(col)};
@@ -72,27 +84,24 @@ __global__ void __launch_bounds__(32 * YW_W, M >= 256 ? 2 : 3) yw_kernel(float* 
         wl::inverse<M, BC>(xb, tb, lane, src, snk);
     }
     __syncthreads();
-    {
-      float* gp = g + go;
+    float* gp = tile_base(t) + go;
 #pragma unroll 8
-      for (int q = 0; q < NY / 16; ++q, gp += gstep) *gp = T[so + q * SSTEP];
-    }
-    __syncthreads();
+    for (int q = 0; q < NY / RPP; ++q, gp += gstep) *gp = cur[so + q * SSTEP];
   }
 }
 
 template <int M, int BC, int DIR>
 cudaError_t yw(const cans_plan_s* P, float* w, cudaStream_t st) {
   auto k = yw_kernel<M, BC, DIR>;
-  const size_t smem = (size_t)M * YW_RS * sizeof(float2);
+  const size_t smem = (size_t)2 * M * YW_RS * sizeof(float2);
   cudaError_t e = set_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * YW_W, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * YW_L, smem);
   const int ntiles = (P->n[0] / YW_L) * P->n[2];
-  k<<<std::max(1, std::min(ntiles, std::max(per_sm, 1) * sms)), 32 * YW_W, smem, st>>>(w, P->n[0], P->n[2], P->ty_f);
+  k<<<std::max(1, std::min(ntiles, std::max(per_sm, 1) * sms)), 32 * YW_L, smem, st>>>(w, P->n[0], P->n[2], P->ty_f);
   return cudaGetLastError();
 }
 

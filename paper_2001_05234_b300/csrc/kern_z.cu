@@ -108,7 +108,11 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   for (int cidx = warp; cidx < ncols; cidx += nwarps) {
     const int i = i0 + cidx;
     if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
-    zsolve_column<MMAX, float, float, false>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
+    if (a.nz == 32 * MMAX)
+      zsolve_column<MMAX, float, float, false, decltype(Z), true>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc,
+                                                                  nullptr, 0.f);
+    else
+      zsolve_column<MMAX, float, float, false>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
   }
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);

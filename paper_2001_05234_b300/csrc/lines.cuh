@@ -46,6 +46,9 @@ struct LineTab {
   const typename V2<T>::t* tw;    // M entries: exp(-2 pi i t / M)
   const typename V2<T>::t* post;  // M+1 entries: exp(-2 pi i k / N)
   const typename V2<T>::t* mak;   // M+1 entries: exp(-i pi k / (2N))
+  // per-stage twiddles of the warp-per-line engine (wline.cuh), stage by stage in [r][k] order so
+  // that the lanes of a warp read consecutive entries; null when the engine does not take M
+  const typename V2<T>::t* wst = nullptr;
   int n, m, bc, nst;
   int radix[16];
 };

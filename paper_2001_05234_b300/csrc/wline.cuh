@@ -1,7 +1,9 @@
 // Warp-per-line real transforms of contiguous lines (the operator F^x of Eq. poi_reduced and its
 // inverse: real DFT for periodic, DCT-II/DST-II for Neumann/Dirichlet walls).
 //
-// One warp owns one line of N = 2M reals (M = 32 V, V = 4, 8 or 16 complex values per lane).
+// One warp (or a group of G warps, then "lane" is the index 0..32G-1 inside the group and the
+// syncs are a named barrier of the group) owns one line of N = 2M reals, M = 32 G V with V = 4, 8
+// or 16 complex values per lane.
 // The line is packed into M complex numbers z_m = (v_2m, v_2m+1) of the (Makhoul-permuted,
 // sign-alternated for Dirichlet) sequence v and transformed by a Stockham FFT whose radices all
 // divide V, so every butterfly of a stage sits in one lane's registers: lane p always holds the
@@ -25,27 +27,46 @@
 namespace cans {
 namespace wl {
 
-// radix schedule: powers of two only, each radix (8, 4 or 2, largest first) dividing V = M/32
-__host__ __device__ constexpr int radix(int M, int s) {
-  int x = M, V = M / 32;
+// radix schedule for a line held by G warps (V = M / (32 G) values per lane): powers of two only,
+// each radix (8, 4 or 2, largest first) dividing V
+__host__ __device__ constexpr int radix(int M, int s, int G = 1) {
+  int x = M, V = M / (32 * G);
   for (int i = 0;; ++i) {
     int r = (x % 8 == 0 && V % 8 == 0) ? 8 : (x % 4 == 0 && V % 4 == 0) ? 4 : 2;
     if (i == s) return r;
     x /= r;
   }
 }
-__host__ __device__ constexpr int nstages(int M) {
+__host__ __device__ constexpr int nstages(int M, int G = 1) {
   int x = M, n = 0;
   while (x > 1) {
-    x /= radix(M, n);
+    x /= radix(M, n, G);
     ++n;
   }
   return n;
 }
-__host__ __device__ constexpr int stride(int M, int s) {
+__host__ __device__ constexpr int stride(int M, int s, int G = 1) {
   int p = 1;
-  for (int i = 0; i < s; ++i) p *= radix(M, i);
+  for (int i = 0; i < s; ++i) p *= radix(M, i, G);
   return p;
+}
+
+// per-stage twiddle table of the schedule (LineTab::wst): stage S >= 1 holds (R-1) x Ns entries,
+// entry (r-1) Ns + k = exp(-2 pi i k r / (R Ns)), stages one after another
+__host__ __device__ constexpr int wst_offset(int M, int S, int G = 1) {
+  int o = 0;
+  for (int s = 1; s < S; ++s) o += (radix(M, s, G) - 1) * stride(M, s, G);
+  return o;
+}
+__host__ __device__ constexpr int wst_size(int M, int G = 1) { return wst_offset(M, nstages(M, G), G); }
+
+// synchronisation of the G warps that share a line: __syncwarp, or named barrier `bar` of 32 G threads
+template <int G>
+__device__ __forceinline__ void gsync(int bar) {
+  if (G == 1)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(32 * G) : "memory");
 }
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
 __host__ __device__ constexpr bool supported(int M) { return M == 128 || M == 256 || M == 512; }
@@ -73,27 +94,30 @@ struct Strided {
 
 // One Stockham stage on the lane's registers.  Exchange (all but the last stage): the outputs are
 // written to xb at their swizzled positions and read back in the lane-p-owns-m=p+32t order.
-template <int M, int S, typename XB>
-__device__ __forceinline__ void stage(float2 (&v)[M / 32], const XB& xb, const float2* __restrict__ tw, int lane) {
-  constexpr int V = M / 32, R = radix(M, S), Ns = stride(M, S), Q = V / R, NST = nstages(M);
-  constexpr int TS = M / (R * Ns);  // twiddle table stride
+template <int M, int S, int G, typename XB>
+__device__ __forceinline__ void stage(float2 (&v)[M / (32 * G)], const XB& xb, const float2* __restrict__ wst,
+                                      int lane, int bar) {
+  constexpr int L = 32 * G;  // lanes per line
+  constexpr int V = M / L, R = radix(M, S, G), Ns = stride(M, S, G), Q = V / R, NST = nstages(M, G);
+  constexpr int OFF = wst_offset(M, S, G);  // this stage's block of the twiddle table
   static_assert(V % R == 0, "radix must divide the values per lane");
+  static_assert(G == 1, "the plan builds the stage twiddle table for one warp per line");
   float2 w[R];
-  if (Ns > 1 && Ns <= 32) {  // k = lane mod Ns for every butterfly of the lane
+  if (Ns > 1 && Ns <= L) {  // k = lane mod Ns for every butterfly of the lane
     const int k = lane & (Ns - 1);
 #pragma unroll
-    for (int r = 1; r < R; ++r) w[r] = ld_tw(tw, k * r * TS);
+    for (int r = 1; r < R; ++r) w[r] = ld_tw(wst, OFF + (r - 1) * Ns + k);
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = v[q + Q * r];
-    const int j = lane + 32 * q;
+    const int j = lane + L * q;
     const int k = j & (Ns - 1);
-    if (Ns > 32) {
+    if (Ns > L) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) w[r] = ld_tw(tw, k * r * TS);
+      for (int r = 1; r < R; ++r) w[r] = ld_tw(wst, OFF + (r - 1) * Ns + k);
     }
     if (Ns > 1) {
 #pragma unroll
@@ -110,25 +134,26 @@ __device__ __forceinline__ void stage(float2 (&v)[M / 32], const XB& xb, const f
     }
   }
   if (S < NST - 1) {
-    __syncwarp();
+    gsync<G>(bar);
 #pragma unroll
-    for (int t = 0; t < V; ++t) v[t] = xb[xpos<Ns, R>(lane + 32 * t)];
-    __syncwarp();
+    for (int t = 0; t < V; ++t) v[t] = xb[xpos<Ns, R>(lane + L * t)];
+    gsync<G>(bar);
   }
 }
 
-template <int M, int S, int NST>
+template <int M, int S, int NST, int G>
 struct Stages {
   template <typename XB>
-  static __device__ __forceinline__ void run(float2 (&v)[M / 32], const XB& xb, const float2* tw, int lane) {
-    stage<M, S>(v, xb, tw, lane);
-    Stages<M, S + 1, NST>::run(v, xb, tw, lane);
+  static __device__ __forceinline__ void run(float2 (&v)[M / (32 * G)], const XB& xb, const float2* wst, int lane,
+                                             int bar) {
+    stage<M, S, G>(v, xb, wst, lane, bar);
+    Stages<M, S + 1, NST, G>::run(v, xb, wst, lane, bar);
   }
 };
-template <int M, int NST>
-struct Stages<M, NST, NST> {
+template <int M, int NST, int G>
+struct Stages<M, NST, NST, G> {
   template <typename XB>
-  static __device__ __forceinline__ void run(float2 (&)[M / 32], const XB&, const float2*, int) {}
+  static __device__ __forceinline__ void run(float2 (&)[M / (32 * G)], const XB&, const float2*, int, int) {}
 };
 
 // sample index of position n of the permuted sequence v (identity for periodic lines)
@@ -156,13 +181,14 @@ __device__ __forceinline__ void put_pair(Snk& snk, int k, float o0, float o1) {
 // Forward transform of one line.
 //   src.pair(n) -> float2 (x_n, x_n+1), n even (periodic lines);  src.one(n) -> x_n (walls).
 //   snk.put(s, y) stores output slot s.
-template <int M, int BC, bool ALIAS = false, typename XB, typename Src, typename Snk>
-__device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
-  constexpr int V = M / 32, N = 2 * M;
+template <int M, int BC, bool ALIAS = false, int G = 1, typename XB, typename Src, typename Snk>
+__device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
+                                        int bar = 0) {
+  constexpr int L = 32 * G, V = M / L, N = 2 * M;
   float2 v[V];
 #pragma unroll
   for (int t = 0; t < V; ++t) {
-    const int m = lane + 32 * t;
+    const int m = lane + L * t;
     if (BC == BC_P) {
       v[t] = src.pair(2 * m);
     } else {
@@ -175,15 +201,15 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
       v[t] = make_float2(a, b);
     }
   }
-  if (ALIAS) __syncwarp();  // every lane has read its inputs before the buffer is overwritten
-  Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
-  // v[t] = Z_k, k = lane + 32 t.  Partner Z_{M-k} through the exchange buffer.
+  if (ALIAS) gsync<G>(bar);  // every lane has read its inputs before the buffer is overwritten
+  Stages<M, 0, nstages(M, G), G>::run(v, xb, tb.wst, lane, bar);
+  // v[t] = Z_k, k = lane + L t.  Partner Z_{M-k} through the exchange buffer.
 #pragma unroll
-  for (int t = 0; t < V; ++t) xb[lane + 32 * t] = v[t];
-  __syncwarp();
+  for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
+  gsync<G>(bar);
 #pragma unroll
   for (int t = 0; t < V; ++t) {
-    const int k = lane + 32 * t;
+    const int k = lane + L * t;
     const float2 zk = v[t];
     float o0, o1;  // the two output values of k (slots below)
     if (k == 0) {
@@ -214,24 +240,25 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
       put_pair<BC, M>(snk, k, o0, o1);
     }
   }
-  __syncwarp();
+  gsync<G>(bar);
   if (ALIAS) {
 #pragma unroll
-    for (int t = 0; t < V; ++t) put_pair<BC, M>(snk, lane + 32 * t, v[t].x, v[t].y);
-    __syncwarp();
+    for (int t = 0; t < V; ++t) put_pair<BC, M>(snk, lane + L * t, v[t].x, v[t].y);
+    gsync<G>(bar);
   }
 }
 
 // Inverse transform of one line (times N).
 //   src.get(s) -> input slot s.   snk.pair(n, x_n, x_n+1) (periodic) or snk.one(n, x_n) (walls).
-template <int M, int BC, bool WAIT_ASYNC = false, typename XB, typename Src, typename Snk>
-__device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk) {
-  constexpr int V = M / 32, N = 2 * M;
+template <int M, int BC, bool WAIT_ASYNC = false, int G = 1, typename XB, typename Src, typename Snk>
+__device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
+                                        int bar = 0) {
+  constexpr int L = 32 * G, V = M / L, N = 2 * M;
   float2 v[V];
-  // X_k (periodic) or V_k = W^-k (Y_k - i Y_N-k)/2 (walls) for the lane's k = lane + 32 t
+  // X_k (periodic) or V_k = W^-k (Y_k - i Y_N-k)/2 (walls) for the lane's k = lane + L t
 #pragma unroll
   for (int t = 0; t < V; ++t) {
-    const int k = lane + 32 * t;
+    const int k = lane + L * t;
     if (BC == BC_P) {
       v[t] = (k == 0) ? make_float2(src.get(0), src.get(N - 1)) : make_float2(src.get(2 * k - 1), src.get(2 * k));
     } else {
@@ -245,13 +272,13 @@ __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, 
     }
   }
   // k = 0 holds (X_0, X_M) packed as real parts; every other k needs X_{M-k} from its partner
-  __syncwarp();  // (the source may be the exchange buffer itself)
+  gsync<G>(bar);  // (the source may be the exchange buffer itself)
 #pragma unroll
-  for (int t = 0; t < V; ++t) xb[lane + 32 * t] = v[t];
-  __syncwarp();
+  for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
+  gsync<G>(bar);
 #pragma unroll
   for (int t = 0; t < V; ++t) {
-    const int k = lane + 32 * t;
+    const int k = lane + L * t;
     const float2 xk = v[t];
     if (k == 0) {
       v[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
@@ -263,16 +290,16 @@ __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, 
       v[t] = cconj(make_float2(A.x - wB.y, A.y + wB.x));  // conj(A + i w B)
     }
   }
-  __syncwarp();
-  Stages<M, 0, nstages(M)>::run(v, xb, tb.tw, lane);
+  gsync<G>(bar);
+  Stages<M, 0, nstages(M, G), G>::run(v, xb, tb.wst, lane, bar);
   if (WAIT_ASYNC) {  // the sink reads data the caller staged with cp.async before the line began
     asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
+    gsync<G>(bar);
   }
-  // v[t] = conj(N x-packed) at m = lane + 32 t: samples 2m, 2m+1 of the permuted sequence
+  // v[t] = conj(N x-packed) at m = lane + L t: samples 2m, 2m+1 of the permuted sequence
 #pragma unroll
   for (int t = 0; t < V; ++t) {
-    const int m = lane + 32 * t;
+    const int m = lane + L * t;
     const float a = v[t].x, b = -v[t].y;
     if (BC == BC_P) {
       snk.pair(2 * m, a, b);

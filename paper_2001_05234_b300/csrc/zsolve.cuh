@@ -74,11 +74,12 @@ __device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& 
   }
 }
 
-// Solve one column (tile column `col`) in precision C with rows staged by stage_zrows.
+// Solve one column (tile column `col`) in precision C with rows staged by stage_zrows.  FULL: the
+// caller guarantees Nz = 32 MMAX (no identity rows), which removes every row-validity test.
 // mu is the x-y eigenvalue term of the mode.  SING: the singular Neumann mode -- the right-hand side
 // is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
 // x = 0, and the result is shifted to the dzf-weighted mean `target`.
-template <int MMAX, typename C, typename T, bool SING, typename ZS>
+template <int MMAX, typename C, typename T, bool SING, typename ZS, bool FULL = false>
 __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int Nz, C mu, const C* sa,
                                               const C* sb, const C* sc, const double* weights, C target) {
   const int lane = threadIdx.x & 31;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
     C sw = 0, swd = 0;
     for (int r = 0; r < m; ++r) {
       const int k = k0 + r;
-      if (k < Nz) {
+      if (FULL || k < Nz) {
         const C w = (C)weights[k];
         sw += w;
         swd += w * cvt<C>(tile[Z.at(k, col, lane)]);
@@ -112,7 +113,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
     if (r < m - 1) {
       const int k = k0 + r;
       C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + mu, c = sc[r * 32 + lane], d = 0;
-      if (k < Nz) d = cvt<C>(tile[Z.at(k, col, lane)]) - proj;
+      if (FULL || k < Nz) d = cvt<C>(tile[Z.at(k, col, lane)]) - proj;
       if (SING && k == Nz - 1) {
         a = 0;
         b = 1;
@@ -159,7 +160,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   const int kl = k0 + m - 1;
   const int rl = m - 1;
   C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + mu, cl = sc[rl * 32 + lane], dl = 0;
-  if (kl < Nz) dl = cvt<C>(tile[Z.at(kl, col, lane)]) - proj;
+  if (FULL || kl < Nz) dl = cvt<C>(tile[Z.at(kl, col, lane)]) - proj;
   if (SING && kl == Nz - 1) {
     al = 0;
     bl = 1;
@@ -195,7 +196,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   C Ep = __shfl_up_sync(full, E, 1);
   if (lane == 0) Ep = 0;
   // back-substitution, written straight into the tile
-  if (lane * m + m - 1 < Nz) tile[Z.at(k0 + m - 1, col, lane)] = cvt<T>(E);
+  if (FULL || lane * m + m - 1 < Nz) tile[Z.at(k0 + m - 1, col, lane)] = cvt<T>(E);
   C xn = E;
 #pragma unroll
   for (int r = MMAX - 1; r >= 0; --r) {
@@ -204,7 +205,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
         xn = dp[r] + lp[r] * Ep + rr * E;
       else
         xn = dp[r] + lp[r] * Ep - cp[r] * xn;
-      if (k0 + r < Nz) tile[Z.at(k0 + r, col, lane)] = cvt<T>(xn);
+      if (FULL || k0 + r < Nz) tile[Z.at(k0 + r, col, lane)] = cvt<T>(xn);
     }
   }
   if (SING) {
@@ -212,7 +213,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
     C sw = 0, swx = 0;
     for (int r = 0; r < m; ++r) {
       const int k = k0 + r;
-      if (k < Nz) {
+      if (FULL || k < Nz) {
         const C w = (C)weights[k];
         sw += w;
         swx += w * cvt<C>(tile[Z.at(k, col, lane)]);
@@ -226,7 +227,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
     const C shift = swx / sw - target;
     for (int r = 0; r < m; ++r) {
       const int k = k0 + r;
-      if (k < Nz) tile[Z.at(k, col, lane)] = cvt<T>(cvt<C>(tile[Z.at(k, col, lane)]) - shift);
+      if (FULL || k < Nz) tile[Z.at(k, col, lane)] = cvt<T>(cvt<C>(tile[Z.at(k, col, lane)]) - shift);
     }
   }
 }
