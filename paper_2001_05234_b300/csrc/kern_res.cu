@@ -35,15 +35,11 @@ __device__ __forceinline__ df df_add_prod(df acc, df coef, df x) {
   return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, p.lo)));
 }
 
-// TILE: the CTA's 32 x 8 columns fill whole tiles of the plane (Nx % 32 == 0, Ny % 8 == 0); each
-// plane's values plus a one-cell halo are then staged in shared memory (double-buffered, one barrier
-// per plane) and the x / y neighbours are read from there instead of through L1.
-template <bool PLO, int BX, int BY, int BZ, bool TILE>
+template <bool PLO, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
                                                       const float* __restrict__ Plo, float* __restrict__ r,
                                                       StencilDF S, int kchunk, double* norm_acc) {
   __shared__ float4 zc[64];  // (c_k hi, c_k lo, a_k hi, a_k lo) of the chunk's planes
-  __shared__ float sp[TILE ? 2 : 1][RY + 2][RX + 2];  // plane tile with halo
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
   const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
   for (int q = threadIdx.y * RX + threadIdx.x; q < k1 - k0; q += RX * RY)
@@ -99,25 +95,10 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             fr[u] = fp[(size_t)PF * sz];
             pr[u] = (k + PF == nz - 1) ? Phi[c0] : pp[(size_t)(PF + 1) * sz];
           }
-          float xm, xp, ym, yp;
-          if (TILE) {
-            const int b = u & 1, tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-            sp[b][ty][tx] = p_cur;
-            if (tx == 1) sp[b][ty][0] = gxm ? ghost<BX>(p_cur) : pp[dxm];
-            if (tx == RX) sp[b][ty][RX + 1] = gxp ? ghost<BX>(p_cur) : pp[dxp];
-            if (ty == 1) sp[b][0][tx] = gym ? ghost<BY>(p_cur) : pp[dym];
-            if (ty == RY) sp[b][RY + 1][tx] = gyp ? ghost<BY>(p_cur) : pp[dyp];
-            __syncthreads();
-            xm = sp[b][ty][tx - 1];
-            xp = sp[b][ty][tx + 1];
-            ym = sp[b][ty - 1][tx];
-            yp = sp[b][ty + 1][tx];
-          } else {
-            xm = gxm ? ghost<BX>(p_cur) : pp[dxm];
-            xp = gxp ? ghost<BX>(p_cur) : pp[dxp];
-            ym = gym ? ghost<BY>(p_cur) : pp[dym];
-            yp = gyp ? ghost<BY>(p_cur) : pp[dyp];
-          }
+          const float xm = gxm ? ghost<BX>(p_cur) : pp[dxm];
+          const float xp = gxp ? ghost<BX>(p_cur) : pp[dxp];
+          const float ym = gym ? ghost<BY>(p_cur) : pp[dym];
+          const float yp = gyp ? ghost<BY>(p_cur) : pp[dyp];
           const float zp = (BZ != BC_P && top) ? ghost<BZ>(p_cur) : p_next;
           const df dp = two_sum(zp, -p_cur);  // Phi_{k+1} - Phi_k exactly
           const float4 co = zc[k - k0];
@@ -184,10 +165,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
 template <bool PLO, int BX, int BY, int BZ>
 cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi, const float* Plo, float* r,
                        const StencilDF& S, int kchunk, double* acc, cudaStream_t st) {
-  if (S.n[0] % RX == 0 && S.n[1] % RY == 0)
-    res_kernel<PLO, BX, BY, BZ, true><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
-  else
-    res_kernel<PLO, BX, BY, BZ, false><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
+  res_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
   return cudaGetLastError();
 }
 
