@@ -149,14 +149,15 @@ int cans_zsolve(cans_plan_t plan, double* field, void* cuda_stream);
 enum cans_pass {
   CANS_PASS_XF = 0, /* forward x (FP64 -> working precision) */
   CANS_PASS_YF = 1, /* forward y */
-  CANS_PASS_Z = 2,  /* tridiagonal z (float and double column kernels together) */
+  CANS_PASS_Z = 2,  /* tridiagonal z (all columns of the FP64 path; the float columns of the mixed path) */
   CANS_PASS_YI = 3, /* inverse y */
   CANS_PASS_XI = 4, /* inverse x of a first solve */
   CANS_PASS_XR = 5, /* forward x fused with the double-float residual (refinement sweep) */
   CANS_PASS_XU = 6, /* inverse x fused with the update of the iterate (refinement sweep) */
   CANS_PASS_RS = 7, /* residual stencil of a refinement sweep, when it runs as its own kernel (then
                        CANS_PASS_XR is the forward x transform of the residual alone) */
-  CANS_PASS_COUNT = 8
+  CANS_PASS_ZD = 8, /* the mixed path's double-precision z columns (lowest |mu| and singular) */
+  CANS_PASS_COUNT = 9
 };
 int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);

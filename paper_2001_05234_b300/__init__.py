@@ -224,7 +224,7 @@ def cans_split_f64(x_ptr: int, n: int, rn_ptr: int = 0, hi_ptr: int = 0, lo_ptr:
 
 
 CANS_PASS_NAMES = ("x_forward", "y_forward", "z_solve", "y_inverse", "x_inverse", "x_forward_residual",
-                   "x_inverse_update", "residual_stencil")
+                   "x_inverse_update", "residual_stencil", "z_solve_double_columns")
 
 
 def cans_plan_profile(plan, enable: bool) -> int:

@@ -762,7 +762,8 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
     TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
-    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st));
+    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st, 0));
+    TIMED(CANS_PASS_ZD, launch_z<float>(P, W, nullptr, st, 1));
     TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
     if (sweeps == 0) {
       TIMED(CANS_PASS_XI, launch_xinv<float, 0>(P, W, p, nullptr, nullptr, inv_scale, nullptr, st));
@@ -781,7 +782,8 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
           TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
         }
         TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
-        TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st));
+        TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st, 0));
+        TIMED(CANS_PASS_ZD, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st, 1));
         TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
         const bool last = (s + 1 == sweeps);
         if (s == 0 && !last)

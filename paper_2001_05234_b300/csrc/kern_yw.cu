@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(32 * YW_L, 1) yw_kernel(float* __restrict__ w,
       ColSnk snk{col};
       const wl::Strided<YW_RS> xb{reinterpret_cast<float2*>(col)};
       if (DIR > 0)
-        wl::forward<M, BC, true>(xb, tb, lane, src, snk);
+        wl::forward<M, BC, true, 1, true>(xb, tb, lane, src, snk);
       else
         wl::inverse<M, BC>(xb, tb, lane, src, snk);
     }

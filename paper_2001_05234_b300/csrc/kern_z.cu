@@ -178,21 +178,25 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
   return a;
 }
 
+// part: -1 both kernels, 0 the float columns only, 1 the marked double columns only (mixed path)
 template <typename T, int MMAX, int TIC>
-static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
   const WLay wl = wlay(P, sizeof(T) == 4);
   const int vec = ((wl.blk || P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
   if (sizeof(T) == 4) {
     // float columns first, then the double columns of the marked bounding box
-    ZArgs a = zargs(P, P->z_ti[1], gauge);
-    a.mask = P->mask_d;
-    const size_t smem = 3 * 32 * a.m * sizeof(float) + P->z_smem[1];
-    cudaError_t e = set_smem((const void*)zpass_f32_kernel<MMAX, TIC>, smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-    zpass_f32_kernel<MMAX, TIC><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (part != 1) {
+      ZArgs a = zargs(P, P->z_ti[1], gauge);
+      a.mask = P->mask_d;
+      const size_t smem = 3 * 32 * a.m * sizeof(float) + P->z_smem[1];
+      e = set_smem((const void*)zpass_f32_kernel<MMAX, TIC>, smem);
+      if (e != cudaSuccess) return e;
+      dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
+      zpass_f32_kernel<MMAX, TIC><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
+      e = cudaGetLastError();
+      if (e != cudaSuccess || part == 0) return e;
+    }
     ZArgs b = zargs(P, P->z_ti[1], gauge);
     b.mask = P->mask_d;
     const size_t smem64 = 3 * 32 * b.m * sizeof(double) + P->z_smem[1];
@@ -213,28 +217,28 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
 
 // compile-time tile widths for the common shapes (the z tile is TI x-slots wide, a power of two)
 template <typename T, int MMAX>
-static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
   switch (P->z_ti[sizeof(T) == 4 ? 1 : 0]) {
-    case 32: return z_mt<T, MMAX, 32>(P, w, gauge, st);
-    case 16: return z_mt<T, MMAX, 16>(P, w, gauge, st);
-    case 8: return z_mt<T, MMAX, 8>(P, w, gauge, st);
-    default: return z_mt<T, MMAX, 0>(P, w, gauge, st);
+    case 32: return z_mt<T, MMAX, 32>(P, w, gauge, st, part);
+    case 16: return z_mt<T, MMAX, 16>(P, w, gauge, st, part);
+    case 8: return z_mt<T, MMAX, 8>(P, w, gauge, st, part);
+    default: return z_mt<T, MMAX, 0>(P, w, gauge, st, part);
   }
 }
 
 template <typename T>
-cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
-  if (P->bc[2] == BC_P) return launch_zspec<T>(P, w, gauge, st);
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
+  if (P->bc[2] == BC_P) return (part == 1) ? cudaSuccess : launch_zspec<T>(P, w, gauge, st);
   switch (P->z_mmax) {
-    case 1: return z_m<T, 1>(P, w, gauge, st);
-    case 2: return z_m<T, 2>(P, w, gauge, st);
-    case 4: return z_m<T, 4>(P, w, gauge, st);
-    case 8: return z_m<T, 8>(P, w, gauge, st);
-    default: return z_m<T, 16>(P, w, gauge, st);
+    case 1: return z_m<T, 1>(P, w, gauge, st, part);
+    case 2: return z_m<T, 2>(P, w, gauge, st, part);
+    case 4: return z_m<T, 4>(P, w, gauge, st, part);
+    case 8: return z_m<T, 8>(P, w, gauge, st, part);
+    default: return z_m<T, 16>(P, w, gauge, st, part);
   }
 }
 
-template cudaError_t launch_z<double>(const cans_plan_s*, double*, const double*, cudaStream_t);
-template cudaError_t launch_z<float>(const cans_plan_s*, float*, const double*, cudaStream_t);
+template cudaError_t launch_z<double>(const cans_plan_s*, double*, const double*, cudaStream_t, int);
+template cudaError_t launch_z<float>(const cans_plan_s*, float*, const double*, cudaStream_t, int);
 
 }  // namespace cans

@@ -133,8 +133,9 @@ cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Ph
                         double* gauge, cudaStream_t st);
 template <typename T, int DIR>
 cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st);
+// part: -1 the whole z pass; in the mixed path 0 = the float columns, 1 = the marked double columns
 template <typename T>
-cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part = -1);
 template <typename T>
 cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
 cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st);

@@ -181,7 +181,12 @@ __device__ __forceinline__ void put_pair(Snk& snk, int k, float o0, float o1) {
 // Forward transform of one line.
 //   src.pair(n) -> float2 (x_n, x_n+1), n even (periodic lines);  src.one(n) -> x_n (walls).
 //   snk.put(s, y) stores output slot s.
-template <int M, int BC, bool ALIAS = false, int G = 1, typename XB, typename Src, typename Snk>
+// PARTNER_SHFL: take Z_{M-k} from lane 32 - p, register V-1-t by warp shuffle (lane 0 pairs within
+// its own registers) instead of through the exchange buffer -- fewer shared-memory operations, all of
+// v[] live through the post-processing (for callers with registers to spare); the sink may then
+// write the exchange buffer directly.
+template <int M, int BC, bool ALIAS = false, int G = 1, bool PARTNER_SHFL = false, typename XB, typename Src,
+          typename Snk>
 __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
                                         int bar = 0) {
   constexpr int L = 32 * G, V = M / L, N = 2 * M;
@@ -201,23 +206,33 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
       v[t] = make_float2(a, b);
     }
   }
-  if (ALIAS) gsync<G>(bar);  // every lane has read its inputs before the buffer is overwritten
+  static_assert(!PARTNER_SHFL || G == 1, "shuffled partners need one warp per line");
+  if (ALIAS || PARTNER_SHFL) gsync<G>(bar);  // every lane has its inputs before the buffer is overwritten
   Stages<M, 0, nstages(M, G), G>::run(v, xb, tb.wst, lane, bar);
-  // v[t] = Z_k, k = lane + L t.  Partner Z_{M-k} through the exchange buffer.
+  // v[t] = Z_k, k = lane + L t.  Partner Z_{M-k}: through the exchange buffer, or by shuffle.
+  if (!PARTNER_SHFL) {
 #pragma unroll
-  for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
-  gsync<G>(bar);
+    for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
+    gsync<G>(bar);
+  }
+  const int src_lane = (32 - lane) & 31;
 #pragma unroll
   for (int t = 0; t < V; ++t) {
     const int k = lane + L * t;
     const float2 zk = v[t];
+    float2 zsh = zk;
+    if (PARTNER_SHFL) {
+      zsh.x = __shfl_sync(0xffffffffu, v[V - 1 - t].x, src_lane);
+      zsh.y = __shfl_sync(0xffffffffu, v[V - 1 - t].y, src_lane);
+      if (lane == 0) zsh = v[(V - t) % V];
+    }
     float o0, o1;  // the two output values of k (slots below)
     if (k == 0) {
       const float v0 = zk.x + zk.y, vm = zk.x - zk.y;
       o0 = (BC == BC_P) ? v0 : 2.f * v0;
       o1 = (BC == BC_P) ? vm : 1.41421356237309504880f * vm;
     } else {
-      const float2 zm = xb[M - k];
+      const float2 zm = PARTNER_SHFL ? zsh : xb[M - k];
       float2 E, O;
       E.x = 0.5f * (zk.x + zm.x);
       E.y = 0.5f * (zk.y - zm.y);
@@ -234,14 +249,14 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
         o1 = -2.f * a.y;
       }
     }
-    if (ALIAS) {
+    if (ALIAS && !PARTNER_SHFL) {
       v[t] = make_float2(o0, o1);  // written after every lane has read its partners
     } else {
       put_pair<BC, M>(snk, k, o0, o1);
     }
   }
   gsync<G>(bar);
-  if (ALIAS) {
+  if (ALIAS && !PARTNER_SHFL) {
 #pragma unroll
     for (int t = 0; t < V; ++t) put_pair<BC, M>(snk, lane + L * t, v[t].x, v[t].y);
     gsync<G>(bar);
