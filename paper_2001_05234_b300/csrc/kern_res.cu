@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
         pr[u] = (k == nz - 1) ? Phi[c0] : pp[(size_t)(u + 1) * sz];  // Phi_{k+1}, periodic wrap
       }
     }
+    // the x / y neighbours of the next plane, loaded one plane ahead of their use
+    float nxm = pp[dxm], nxp = pp[dxp], nym = pp[dym], nyp = pp[dyp];
     for (int kb = k0; kb < k1; kb += PF) {
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
@@ -95,10 +97,16 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             fr[u] = fp[(size_t)PF * sz];
             pr[u] = (k + PF == nz - 1) ? Phi[c0] : pp[(size_t)(PF + 1) * sz];
           }
-          const float xm = gxm ? ghost<BX>(p_cur) : pp[dxm];
-          const float xp = gxp ? ghost<BX>(p_cur) : pp[dxp];
-          const float ym = gym ? ghost<BY>(p_cur) : pp[dym];
-          const float yp = gyp ? ghost<BY>(p_cur) : pp[dyp];
+          const float xm = gxm ? ghost<BX>(p_cur) : nxm;
+          const float xp = gxp ? ghost<BX>(p_cur) : nxp;
+          const float ym = gym ? ghost<BY>(p_cur) : nym;
+          const float yp = gyp ? ghost<BY>(p_cur) : nyp;
+          if (k + 1 < k1) {
+            nxm = pp[sz + dxm];
+            nxp = pp[sz + dxp];
+            nym = pp[sz + dym];
+            nyp = pp[sz + dyp];
+          }
           const float zp = (BZ != BC_P && top) ? ghost<BZ>(p_cur) : p_next;
           const df dp = two_sum(zp, -p_cur);  // Phi_{k+1} - Phi_k exactly
           const float4 co = zc[k - k0];

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(32 * YW_L, 1) yw_kernel(float* __restrict__ w,
       if (DIR > 0)
         wl::forward<M, BC, true, 1, true>(xb, tb, lane, src, snk);
       else
-        wl::inverse<M, BC>(xb, tb, lane, src, snk);
+        wl::inverse<M, BC, false, 1, true>(xb, tb, lane, src, snk);
     }
     __syncthreads();
     float* gp = tile_base(t) + go;

@@ -265,10 +265,23 @@ __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, 
 
 // Inverse transform of one line (times N).
 //   src.get(s) -> input slot s.   snk.pair(n, x_n, x_n+1) (periodic) or snk.one(n, x_n) (walls).
-template <int M, int BC, bool WAIT_ASYNC = false, int G = 1, typename XB, typename Src, typename Snk>
+// Z_k from X_k and its partner X_{M-k} (k > 0): conj(A + i exp(2 pi i k/N) B), A = X_k + conj X_{M-k},
+// B = X_k - conj X_{M-k}
+__device__ __forceinline__ float2 pre_pair(float2 xk, float2 xm, float2 post_k) {
+  const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);
+  const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);
+  const float2 wB = cmul(cconj(post_k), B);
+  return cconj(make_float2(A.x - wB.y, A.y + wB.x));
+}
+
+// PARTNER_SHFL: X_{M-k} by warp shuffle (register pairs t, V-1-t per step; lane 0's partners are
+// its own registers, copied first) instead of through the exchange buffer.
+template <int M, int BC, bool WAIT_ASYNC = false, int G = 1, bool PARTNER_SHFL = false, typename XB, typename Src,
+          typename Snk>
 __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
                                         int bar = 0) {
   constexpr int L = 32 * G, V = M / L, N = 2 * M;
+  static_assert(!PARTNER_SHFL || G == 1, "shuffled partners need one warp per line");
   float2 v[V];
   // X_k (periodic) or V_k = W^-k (Y_k - i Y_N-k)/2 (walls) for the lane's k = lane + L t
 #pragma unroll
@@ -288,21 +301,42 @@ __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, 
   }
   // k = 0 holds (X_0, X_M) packed as real parts; every other k needs X_{M-k} from its partner
   gsync<G>(bar);  // (the source may be the exchange buffer itself)
+  if (PARTNER_SHFL) {
+    const int src_lane = (32 - lane) & 31;
+    float2 own[V];  // lane 0: partner of register t is its own register (V - t) mod V
 #pragma unroll
-  for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
-  gsync<G>(bar);
+    for (int t = 0; t < V; ++t) own[t] = v[(V - t) % V];
 #pragma unroll
-  for (int t = 0; t < V; ++t) {
-    const int k = lane + L * t;
-    const float2 xk = v[t];
-    if (k == 0) {
-      v[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
-    } else {
-      const float2 xm = xb[M - k];
-      const float2 A = make_float2(xk.x + xm.x, xk.y - xm.y);  // X_k + conj X_{M-k}
-      const float2 B = make_float2(xk.x - xm.x, xk.y + xm.y);  // X_k - conj X_{M-k}
-      const float2 wB = cmul(cconj(ld_tw(tb.post, k)), B);
-      v[t] = cconj(make_float2(A.x - wB.y, A.y + wB.x));  // conj(A + i w B)
+    for (int t = 0; t < (V + 1) / 2; ++t) {
+      const int t2 = V - 1 - t;
+      float2 m1, m2;  // partners of registers t and t2: the partner lane's registers t2 and t
+      m1.x = __shfl_sync(0xffffffffu, v[t2].x, src_lane);
+      m1.y = __shfl_sync(0xffffffffu, v[t2].y, src_lane);
+      m2.x = __shfl_sync(0xffffffffu, v[t].x, src_lane);
+      m2.y = __shfl_sync(0xffffffffu, v[t].y, src_lane);
+      if (lane == 0) {
+        m1 = own[t];
+        m2 = own[t2];
+      }
+      const int k1 = lane + L * t, k2 = lane + L * t2;
+      const float2 z1 = (k1 == 0) ? cconj(make_float2(v[t].x + v[t].y, v[t].x - v[t].y))
+                                  : pre_pair(v[t], m1, ld_tw(tb.post, k1));
+      const float2 z2 = pre_pair(v[t2], m2, ld_tw(tb.post, k2));  // k2 >= L (V > 1): never 0
+      v[t] = z1;
+      if (t2 != t) v[t2] = z2;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < V; ++t) xb[lane + L * t] = v[t];
+    gsync<G>(bar);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int k = lane + L * t;
+      const float2 xk = v[t];
+      if (k == 0)
+        v[t] = cconj(make_float2(xk.x + xk.y, xk.x - xk.y));
+      else
+        v[t] = pre_pair(xk, xb[M - k], ld_tw(tb.post, k));
     }
   }
   gsync<G>(bar);
