@@ -120,7 +120,7 @@ const char* cans_status_string(int status);
  *
  * cans_transform_xy: forward (dir = +1) or inverse (dir = -1) transforms along x then y (forward)
  * or y then x (inverse), in double, in place on `field`.  Forward output order per line: periodic
- * -> slot 0 = X_0, slots 2k-1, 2k = Re X_k, Im X_k (1 <= k < N/2), slot N-1 = X_{N/2};
+ * -> slot 0 = X_0, slot 1 = X_{N/2}, slots 2k, 2k+1 = Re X_k, Im X_k (1 <= k < N/2);
  * Neumann -> slot m = DCT-II_m; Dirichlet -> slot m = DST-II_m, all unnormalised (X_k = sum x_n
  * e^{-2 pi i k n/N}, DCT-II_m = 2 sum x_n cos(pi m (2n+1)/(2N)), DST-II_m = 2 sum x_n
  * sin(pi (m+1)(2n+1)/(2N))).  The inverse is the exact inverse times Nx*Ny (so a forward-inverse

@@ -56,8 +56,8 @@ int ilog2(int v) {
 long double slot_lambda(int bc, int N, int s) {
   const long double pi = 3.141592653589793238462643383279502884L;
   long double th;
-  if (bc == BC_P)
-    th = pi * (long double)((s + 1) / 2) / N;
+  if (bc == BC_P)  // slot 0: k = 0, slot 1: k = N/2, slots 2k, 2k+1: k
+    th = pi * (long double)((N > 1 && s == 1) ? N / 2 : s / 2) / N;
   else if (bc == BC_NN)
     th = pi * (long double)s / (2.0L * N);
   else

@@ -67,6 +67,15 @@ __device__ __forceinline__ df df_mul(df a, df b) {
 // exponent field is e - 896; other inputs (zeros, subnormals, tiny or huge values, inf, NaN) take
 // the hardware conversion, whose results these match bit for bit.
 
+// Hardware conversions of the rare inputs outside the integer paths' range, kept out of line so
+// that the compiler branches around them instead of executing them (on the slow pipe) for every
+// element and selecting (measured: the update x-inverse; not d2f_rn, see there).
+static __device__ __noinline__ double f2d_hw(float x) { return (double)x; }
+static __device__ __noinline__ df df_split_hw(double x) {
+  const float h = __double2float_rn(x);
+  return df_make(h, __double2float_rn(x - (double)h));
+}
+
 // nearest float, ties to even (= __double2float_rn)
 __device__ __forceinline__ float d2f_rn(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
@@ -78,7 +87,7 @@ __device__ __forceinline__ float d2f_rn(double x) {
     bits += ((lo & 0x1fffffffu) + (t & 1u) + 0x0fffffffu) >> 29;
     return __uint_as_float(bits);
   }
-  return __double2float_rn(x);
+  return __double2float_rn(x);  // inline: an out-of-line call here costs the x forward pass registers
 }
 
 // x = hi + lo with hi = d2f_rn(x) and lo the remainder to within 2^-46 |x| (exact for |x| >= 2^-80
@@ -99,8 +108,7 @@ __device__ __forceinline__ df df_split(double x) {
     return df_make(h, rf * scale);
   }
   if (((hi << 1) | lo) == 0u) return df_make(__uint_as_float(hi & 0x80000000u), 0.f);
-  const float h = __double2float_rn(x);
-  return df_make(h, __double2float_rn(x - (double)h));
+  return df_split_hw(x);
 }
 
 // x = hi + lo with hi = x truncated to a float (towards zero) and lo the remainder to within
@@ -125,7 +133,7 @@ __device__ __forceinline__ double f2d(float x) {
   if (((b >> 23) & 0xffu) - 1u < 254u)  // normal: rebias the exponent (+896), widen the fraction
     return __hiloint2double((int)((b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20))), (int)(b << 29));
   if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  return (double)x;
+  return f2d_hw(x);
 }
 
 // value conversion between the storage and compute precisions of a kernel

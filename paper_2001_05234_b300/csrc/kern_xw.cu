@@ -73,14 +73,18 @@ struct SrcF32 {  // float input (may be the output line itself: every value is r
 };
 
 struct SnkF {
-  float* __restrict__ o;
+  float* __restrict__ o;  // line start, 8-byte aligned
   __device__ __forceinline__ void put(int s, float y) { o[s] = y; }
+  __device__ __forceinline__ void put2(int s, float a, float b) {  // s even
+    *reinterpret_cast<float2*>(o + s) = make_float2(a, b);
+  }
 };
 
 // ---- source and sinks of the inverse pass ----
 struct SrcSlots {
   const float* __restrict__ s;
   __device__ __forceinline__ float get(int i) { return s[i]; }
+  __device__ __forceinline__ float2 get2(int i) { return *reinterpret_cast<const float2*>(s + i); }  // i even
 };
 
 // MODE 0: p = scale x (double).  1: Phi = scale x (+ dzf-weighted gauge sum).  2 / 4: (Phi, Plo) +=

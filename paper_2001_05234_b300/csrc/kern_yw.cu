@@ -24,10 +24,12 @@ struct ColSrc {  // column w of the tile: sample n = T[n/2][w].(n&1)
   __device__ __forceinline__ float2 pair(int n) { return *reinterpret_cast<const float2*>(c + n * YW_RS); }
   __device__ __forceinline__ float one(int n) { return c[(n >> 1) * (2 * YW_RS) + (n & 1)]; }
   __device__ __forceinline__ float get(int s) { return one(s); }
+  __device__ __forceinline__ float2 get2(int s) { return pair(s); }  // slots s, s+1 (s even)
 };
 struct ColSnk {
   float* c;
   __device__ __forceinline__ void put(int s, float y) { c[(s >> 1) * (2 * YW_RS) + (s & 1)] = y; }
+  __device__ __forceinline__ void put2(int s, float a, float b) { pair(s, a, b); }  // s even
   __device__ __forceinline__ void one(int n, float y) { put(n, y); }
   __device__ __forceinline__ void pair(int n, float a, float b) {
     *reinterpret_cast<float2*>(c + n * YW_RS) = make_float2(a, b);

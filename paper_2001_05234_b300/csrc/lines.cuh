@@ -275,10 +275,10 @@ __device__ __forceinline__ void fft_lines(typename V2<T>::t* buf, const Lay& L, 
 __device__ __forceinline__ void fwd_slots(int bc, int N, int M, int k, int s[4]) {
   s[0] = s[1] = s[2] = s[3] = -1;
   if (bc == BC_P) {
-    if (k == 0) { s[0] = 0; s[1] = N - 1; }
+    if (k == 0) { s[0] = 0; s[1] = 1; }
     else {
-      s[0] = 2 * k - 1; s[1] = 2 * k;
-      if (k != M - k) { s[2] = 2 * (M - k) - 1; s[3] = 2 * (M - k); }
+      s[0] = 2 * k; s[1] = 2 * k + 1;
+      if (k != M - k) { s[2] = 2 * (M - k); s[3] = 2 * (M - k) + 1; }
     }
   } else {
     if (k == 0) { s[0] = 0; s[1] = M; }
@@ -387,10 +387,10 @@ __device__ __forceinline__ void pre_inverse(typename V2<T>::t* buf, const Lay& L
       if (tb.bc == BC_P) {
         if (k == 0) {
           xk = mk2<T>(bufT[L.r(0, l)], (T)0);
-          xm = mk2<T>(bufT[L.r(N - 1, l)], (T)0);  // X_M
+          xm = mk2<T>(bufT[L.r(1, l)], (T)0);  // X_M
         } else {
-          xk = mk2<T>(bufT[L.r(2 * k - 1, l)], bufT[L.r(2 * k, l)]);
-          xm = mk2<T>(bufT[L.r(2 * (M - k) - 1, l)], bufT[L.r(2 * (M - k), l)]);
+          xk = mk2<T>(bufT[L.r(2 * k, l)], bufT[L.r(2 * k + 1, l)]);
+          xm = mk2<T>(bufT[L.r(2 * (M - k), l)], bufT[L.r(2 * (M - k) + 1, l)]);
         }
       } else {
 #define SLOT(q_) (dd ? (N - 1 - (q_)) : (q_))
@@ -571,10 +571,10 @@ __device__ __forceinline__ void pre_inverse_loaded(typename V2<T>::t* buf, const
     if (tb.bc == BC_P) {
       if (k == 0) {
         xk = mk2<T>(loadslot(l, 0), (T)0);
-        xm = mk2<T>(loadslot(l, N - 1), (T)0);
+        xm = mk2<T>(loadslot(l, 1), (T)0);
       } else {
-        xk = mk2<T>(loadslot(l, 2 * k - 1), loadslot(l, 2 * k));
-        xm = mk2<T>(loadslot(l, 2 * (M - k) - 1), loadslot(l, 2 * (M - k)));
+        xk = mk2<T>(loadslot(l, 2 * k), loadslot(l, 2 * k + 1));
+        xm = mk2<T>(loadslot(l, 2 * (M - k)), loadslot(l, 2 * (M - k) + 1));
       }
     } else {
 #define SLOT(q_) (dd ? (N - 1 - (q_)) : (q_))

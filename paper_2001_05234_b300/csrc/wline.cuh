@@ -16,9 +16,9 @@
 // The first stage reads its inputs through the caller's source and the post-processing of the
 // real-FFT split (V_k = E_k + exp(-2 pi i k/N) O_k, then Makhoul's quarter-wave twiddle for the
 // cosine/sine transforms) writes each output slot through the caller's sink, so a pass never
-// stages whole lines in shared memory.  Output slot order: periodic -- slot 0 = X_0, slots
-// 2k-1, 2k = Re, Im X_k (1 <= k < M), slot N-1 = X_M; Neumann -- slot k = Y_k; Dirichlet -- slot
-// N-1-k = Y_k (the order of the plan's eigenvalues).
+// stages whole lines in shared memory.  Output slot order: periodic -- slot 0 = X_0, slot 1 = X_M,
+// slots 2k, 2k+1 = Re, Im X_k (1 <= k < M); Neumann -- slot k = Y_k; Dirichlet -- slot N-1-k = Y_k
+// (the order of the plan's eigenvalues).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -163,14 +163,13 @@ __device__ __forceinline__ int sample_of(int n) {
   return (n < N / 2) ? 2 * n : 2 * (N - 1 - n) + 1;
 }
 
-// output slots of k: periodic (0, N-1) for k = 0 else (2k-1, 2k); Neumann (0, M) / (k, N-k);
-// Dirichlet the Neumann slots s mirrored to N-1-s
+// output slots of k: periodic (2k, 2k+1) (k = 0: X_0 and X_M in slots 0, 1), one aligned pair;
+// Neumann (0, M) / (k, N-k); Dirichlet the Neumann slots s mirrored to N-1-s
 template <int BC, int M, typename Snk>
 __device__ __forceinline__ void put_pair(Snk& snk, int k, float o0, float o1) {
   constexpr int N = 2 * M;
   if (BC == BC_P) {
-    snk.put(k == 0 ? 0 : 2 * k - 1, o0);
-    snk.put(k == 0 ? N - 1 : 2 * k, o1);
+    snk.put2(2 * k, o0, o1);
   } else {
     const int s0 = k, s1 = (k == 0) ? M : N - k;
     snk.put(BC == BC_DD ? N - 1 - s0 : s0, o0);
@@ -288,7 +287,7 @@ __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, 
   for (int t = 0; t < V; ++t) {
     const int k = lane + L * t;
     if (BC == BC_P) {
-      v[t] = (k == 0) ? make_float2(src.get(0), src.get(N - 1)) : make_float2(src.get(2 * k - 1), src.get(2 * k));
+      v[t] = src.get2(2 * k);  // (X_0, X_M) for k = 0
     } else {
       const int s0 = (BC == BC_DD) ? N - 1 : 0;
       if (k == 0) {

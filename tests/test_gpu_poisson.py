@@ -52,13 +52,28 @@ def ref_forward(x, bc, axis):
     X = np.fft.rfft(x, axis=axis)
     X = np.moveaxis(X, axis, -1)
     out = np.empty(X.shape[:-1] + (n,))
-    out[..., 0] = X[..., 0].real
-    for k in range(1, n // 2):
-        out[..., 2 * k - 1] = X[..., k].real
-        out[..., 2 * k] = X[..., k].imag
+    out[..., 0] = X[..., 0].real  # slot 0: X_0, slot 1: X_{n/2}, slots 2k, 2k+1: Re, Im X_k
     if n > 1:
-        out[..., n - 1] = X[..., n // 2].real
+        out[..., 1] = X[..., n // 2].real
+    for k in range(1, n // 2):
+        out[..., 2 * k] = X[..., k].real
+        out[..., 2 * k + 1] = X[..., k].imag
     return np.moveaxis(out, -1, axis)
+
+
+def slot_order(lam, bc):
+    """Oracle eigenvalues (periodic basis columns k = 0, then cos/sin pairs 2k-1, 2k, then the
+    Nyquist column last) rearranged into the library's slot order (slot 0 = mode 0, slot 1 = the
+    Nyquist mode, slots 2k, 2k+1 = mode k).  Cosine / sine bases already match."""
+    if bc != P or lam.shape[0] < 3:
+        return lam
+    n = lam.shape[0]
+    out = np.empty_like(lam)
+    out[0] = lam[0]
+    out[1] = lam[n - 1]
+    for k in range(1, n // 2):
+        out[2 * k], out[2 * k + 1] = lam[2 * k - 1], lam[2 * k]
+    return out
 
 
 def make_plan(cans, n, bc, L=(1.0, 1.0), dzf=None, prec=0, sweeps=2, frac=0.01):
@@ -154,8 +169,8 @@ def test_zsolve_matches_thomas(cans, nz, bcz):
     t = dev(g)
     assert cans.cans_zsolve(h, t.data_ptr(), stream()) == 0
     got = host(t)
-    _, lx = oracle.eigenbasis(bc[0], n[0])
-    _, ly = oracle.eigenbasis(bc[1], n[1])
+    lx = slot_order(oracle.eigenbasis(bc[0], n[0])[1], bc[0])
+    ly = slot_order(oracle.eigenbasis(bc[1], n[1])[1], bc[1])
     mux = lx / (1.3 / n[0]) ** 2
     muy = ly / (0.9 / n[1]) ** 2
     a, b, c = oracle.z_rows(bcz, dzf)
@@ -171,8 +186,8 @@ def test_plan_eigenvalues_match_oracle(cans):
     n = (24, 12, 4)
     h = make_plan(cans, n, (P, DD, NN), (2.0, 3.0))
     mx, my = cans.cans_plan_eigenvalues(h, 24, 12)
-    _, lx = oracle.eigenbasis(P, 24)
-    _, ly = oracle.eigenbasis(DD, 12)
+    lx = slot_order(oracle.eigenbasis(P, 24)[1], P)
+    ly = slot_order(oracle.eigenbasis(DD, 12)[1], DD)
     assert np.abs(mx - lx / (2.0 / 24) ** 2).max() < 1e-12 * np.abs(mx).max()
     assert np.abs(my - ly / (3.0 / 12) ** 2).max() < 1e-12 * np.abs(my).max()
     cans.cans_plan_destroy(h)
