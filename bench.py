@@ -243,6 +243,7 @@ def gpu_arm(args):
     torch.cuda.empty_cache()
 
     rk3 = rk3_measure(cans, I, args)
+    cfg2 = config2_measure(cans, I, args)
     ens = ensemble_measure(cans, I, args)
 
     if rank != 0:
@@ -298,11 +299,99 @@ def gpu_arm(args):
         "clocks": clk,
         "rk3_step": rk3,
         "ensemble": ens,
+        "config2_channel": cfg2,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _dct2_last2(x):
+    """Unnormalised DCT-II along dim -2 (X_k = 2 sum_n x_n cos(pi k (2n+1) / 2N)) via Makhoul's
+    reordering and one complex FFT (cuFFT through torch)."""
+    import torch
+
+    n = x.shape[-2]
+    v = torch.cat([x[..., 0::2, :], x[..., 1::2, :].flip(-2)], dim=-2)
+    V = torch.fft.fft(v, dim=-2)
+    k = torch.arange(n, device=x.device, dtype=torch.float64)
+    W = torch.exp(-1j * torch.pi * k / (2 * n))[:, None]
+    return 2.0 * (W * V).real
+
+
+def _idct2_last2(c):
+    """Inverse of _dct2_last2 along dim -2."""
+    import torch
+
+    n = c.shape[-2]
+    k = torch.arange(n, device=c.device, dtype=torch.float64)
+    cn = torch.cat([torch.zeros_like(c[..., :1, :]), c[..., 1:, :].flip(-2)], dim=-2)  # C_{N-k}, C_N = 0
+    V = 0.5 * torch.exp(1j * torch.pi * k / (2 * n))[:, None] * torch.complex(c, -cn)
+    v = torch.fft.ifft(V, dim=-2).real
+    x = torch.empty_like(c)
+    x[..., 0::2, :] = v[..., : (n + 1) // 2, :]
+    x[..., 1::2, :] = v[..., (n + 1) // 2:, :].flip(-2)
+    return x
+
+
+def config2_measure(cans, I, args):
+    """The FP64 channel solve (1024 x 512 x 256, x periodic, y Dirichlet, z Neumann on tanh faces)
+    with this library, beside a cuFFT comparator: the x real FFT and the y sine transform done with
+    cuFFT (torch.fft) plus Makhoul pre/post-processing as separate passes, this library's z solve in
+    between.  The comparator's result is checked against the library's before its time is used."""
+    import torch
+
+    case = I.case_channel()
+    nx, ny, nz = case.n
+    m = nx // 2
+    f = I.rhs_device(case, "cuda")
+    s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64, autotune=True)
+    p = s.solve(f)
+    stream = torch.cuda.current_stream()
+    sgn = torch.tensor([(-1.0) ** j for j in range(ny)], device="cuda", dtype=torch.float64)[:, None]
+
+    def comparator(rhs):
+        y = _dct2_last2(rhs * sgn).flip(-2)  # DST-II along y (slot N-1-k = mode k)
+        X = torch.fft.rfft(y, dim=-1)  # along x
+        w = torch.empty_like(rhs)  # the library's slot order: 0 = X_0, 1 = X_{N/2}, 2k, 2k+1 = Re, Im X_k
+        w[..., 0] = X[..., 0].real
+        w[..., 1] = X[..., m].real
+        w[..., 2::2] = X[..., 1:m].real
+        w[..., 3::2] = X[..., 1:m].imag
+        st = cans.cans_zsolve(s.plan, w.data_ptr(), stream.cuda_stream)
+        assert st == 0
+        Xs = torch.empty((nz, ny, m + 1), dtype=torch.complex128, device="cuda")
+        Xs[..., 0] = w[..., 0]
+        Xs[..., m] = w[..., 1]
+        Xs[..., 1:m] = torch.complex(w[..., 2::2], w[..., 3::2])
+        y = torch.fft.irfft(Xs, n=nx, dim=-1)
+        return _idct2_last2(y.flip(-2)) * sgn  # inverse sine transform along y
+
+    q = comparator(f)
+    rel = float(torch.linalg.vector_norm(q - p) / torch.linalg.vector_norm(p))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(2, min(args.steps, 5))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_lib = timed(lambda: s.solve(f, p))
+    ms_cufft = timed(lambda: comparator(f))
+    s.close()
+    npts = nx * ny * nz
+    return {"workload": "poisson_channel_1024x512x256_P-DD-NN_tanh1.8_fp64", "unit": "ms/solve",
+            "fp64": ms_lib, "fp64_gpts": npts / (ms_lib * 1e-3) / 1e9,
+            "cufft_comparator": ms_cufft, "cufft_comparator_gpts": npts / (ms_cufft * 1e-3) / 1e9,
+            "comparator_rel_l2_vs_library": rel,
+            "note": "comparator: torch.fft (cuFFT) x rfft + y DST-II via Makhoul + this library's z solve"}
 
 
 def rk3_measure(cans, I, args):

@@ -111,6 +111,21 @@ int cans_poisson_solve(cans_plan_t plan, const double* f, double* p, void* works
 /* Release the plan and its device tables. */
 int cans_plan_destroy(cans_plan_t plan);
 
+/*
+ * cans_poisson_solve_adjoint -- q = S^T g, the transpose (plain Euclidean inner product) of the solve
+ * operator S: f -> p of cans_poisson_solve with this plan (the backward pass of a differentiable
+ * solve; projection-adjoint reading R10).  With D = diag(dzf_k) along z, D A_z is symmetric, so S is
+ * self-adjoint in the dzf-weighted inner product -- in the singular case S is the weighted
+ * pseudo-inverse (compatible projection of f, zero weighted mean of p) -- and S^T = D S D^-1: the
+ * library scales g by 1/dzf_k, solves with the plan's precision, and scales the result by dzf_k.
+ *   g: device, Nx*Ny*Nz doubles, read only.  q: device output (may equal g).
+ *   workspace: cans_poisson_adjoint_workspace_size() bytes, 256-byte aligned (the solve's workspace
+ *   plus one FP64 field).
+ * Asynchronous on cuda_stream, capturable; errors as cans_poisson_solve.
+ */
+int cans_poisson_adjoint_workspace_size(cans_plan_t plan, size_t* bytes);
+int cans_poisson_solve_adjoint(cans_plan_t plan, const double* g, double* q, void* workspace, void* cuda_stream);
+
 /* Static English text for a status code. */
 const char* cans_status_string(int status);
 

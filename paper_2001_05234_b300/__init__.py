@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
         L.cans_poisson_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
+        L.cans_poisson_adjoint_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, vp]
         L.cans_transform_xy.argtypes = [vp, vp, ctypes.c_int, vp]
         L.cans_transform_xy_f32.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.cans_zsolve.argtypes = [vp, vp, vp]
@@ -198,6 +200,16 @@ def cans_plan_destroy(plan) -> int:
     return lib().cans_plan_destroy(plan)
 
 
+def cans_poisson_adjoint_workspace_size(plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_poisson_adjoint_workspace_size(plan, ctypes.byref(b)), "cans_poisson_adjoint_workspace_size")
+    return int(b.value)
+
+
+def cans_poisson_solve_adjoint(plan, g_ptr: int, q_ptr: int, workspace_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_poisson_solve_adjoint(plan, g_ptr, q_ptr, workspace_ptr or None, stream_ptr or None)
+
+
 def cans_transform_xy(plan, field_ptr: int, direction: int, stream_ptr: int) -> int:
     return lib().cans_transform_xy(plan, field_ptr, int(direction), stream_ptr or None)
 
@@ -286,6 +298,19 @@ class PoissonSolver:
             raise CansError(st, "cans_poisson_solve")
         return (out, buf, st) if info else out
 
+    def solve_adjoint(self, g, out=None, stream=None):
+        """q = S^T g (cans_poisson_solve_adjoint); the adjoint workspace is allocated on first use."""
+        import torch
+
+        assert g.dtype == torch.float64 and g.is_cuda and g.is_contiguous() and tuple(g.shape) == self.shape
+        if out is None:
+            out = torch.empty_like(g)
+        if getattr(self, "_adj_ws", None) is None:
+            self._adj_ws, self._adj_ptr = _aligned_workspace(cans_poisson_adjoint_workspace_size(self.plan))
+        _check(cans_poisson_solve_adjoint(self.plan, g.data_ptr(), out.data_ptr(), self._adj_ptr, _stream_ptr(stream)),
+               "cans_poisson_solve_adjoint")
+        return out
+
     def close(self):
         if getattr(self, "plan", None):
             cans_plan_destroy(self.plan)
@@ -296,6 +321,35 @@ class PoissonSolver:
             self.close()
         except Exception:
             pass
+
+
+def _poisson_function():
+    import torch
+
+    class PoissonSolve(torch.autograd.Function):
+        """f -> p = S f (the solver's plan); backward applies S^T through cans_poisson_solve_adjoint."""
+
+        @staticmethod
+        def forward(ctx, solver, f):
+            ctx.solver = solver
+            return solver.solve(f.detach().contiguous())
+
+        @staticmethod
+        def backward(ctx, gp):
+            return None, ctx.solver.solve_adjoint(gp.contiguous())
+
+    return PoissonSolve
+
+
+_Poisson = None
+
+
+def poisson_solve(solver, f):
+    """Differentiable Poisson solve: returns S f; gradients flow through the adjoint solve."""
+    global _Poisson
+    if _Poisson is None:
+        _Poisson = _poisson_function()
+    return _Poisson.apply(solver, f)
 
 
 def _aligned_workspace(nbytes: int):

@@ -475,6 +475,33 @@ int cans_poisson_workspace_size(cans_plan_t P, size_t* bytes) {
   return CANS_OK;
 }
 
+int cans_poisson_adjoint_workspace_size(cans_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return CANS_ERR_ARG;
+  size_t b = 0;
+  cans_poisson_workspace_size(P, &b);
+  *bytes = align256(b) + align256(field_points(P) * sizeof(double));
+  return CANS_OK;
+}
+
+int cans_poisson_solve_adjoint(cans_plan_t P, const double* g, double* q, void* workspace, void* cuda_stream) {
+  if (!P || !g || !q) return CANS_ERR_ARG;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CANS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  size_t b = 0;
+  cans_poisson_workspace_size(P, &b);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* t = reinterpret_cast<double*>(ws + align256(b));
+  // S^T = D S D^-1, D = diag(dzf_k): the solve is self-adjoint in the dzf-weighted inner product
+  if (launch_scale_z(P, g, t, P->dzfi_d, st) != cudaSuccess) return CANS_ERR_CUDA;
+  // a scaled g is generically incompatible in the singular case: project it exactly in FP64 (the
+  // solve projects too, but the mixed path would do it in float); S Pi = S, the result is unchanged
+  if (P->singular && launch_remove_weighted_mean(P, t, P->acc_d + P->nacc - 2, st) != cudaSuccess) return CANS_ERR_CUDA;
+  const int rc = cans_poisson_solve(P, t, q, b ? workspace : nullptr, cuda_stream, nullptr);
+  if (rc != CANS_OK) return rc;
+  if (launch_scale_z(P, q, q, P->dzf_d, st) != cudaSuccess) return CANS_ERR_CUDA;
+  return CANS_OK;
+}
+
 int cans_plan_destroy(cans_plan_t P) {
   if (!P) return CANS_ERR_ARG;
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);

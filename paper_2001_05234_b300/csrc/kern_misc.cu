@@ -74,6 +74,39 @@ cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* a
   return cudaGetLastError();
 }
 
+// out(i, j, k) = in(i, j, k) * wz[k]: the diagonal z weights around the adjoint solve.
+__global__ void scale_z_kernel(const double* __restrict__ in, double* __restrict__ out, size_t plane, size_t n,
+                               const double* __restrict__ wz) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    out[c] = in[c] * wz[c / plane];
+}
+
+// f -= s / total with s = acc[0] (a dzf-weighted sum computed on the device): removes the weighted mean
+__global__ void subtract_mean_kernel(double* __restrict__ f, size_t n, const double* __restrict__ acc,
+                                     double inv_total) {
+  const double m = acc[0] * inv_total;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    f[c] -= m;
+}
+
+cudaError_t launch_remove_weighted_mean(const cans_plan_s* P, double* f, double* acc2, cudaStream_t st) {
+  cudaError_t e = launch_weighted_sum(P, f, acc2, st);
+  if (e != cudaSuccess) return e;
+  const size_t n = (size_t)P->n[0] * P->n[1] * P->n[2];
+  double lz = 0;
+  for (int k = 0; k < P->n[2]; ++k) lz += P->dzf_h[k];
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  subtract_mean_kernel<<<grid, 256, 0, st>>>(f, n, acc2, 1.0 / ((double)P->n[0] * P->n[1] * lz));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_z(const cans_plan_s* P, const double* in, double* out, const double* wz, cudaStream_t st) {
+  const size_t plane = (size_t)P->n[0] * P->n[1], n = plane * P->n[2];
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  scale_z_kernel<<<grid, 256, 0, st>>>(in, out, plane, n, wz);
+  return cudaGetLastError();
+}
+
 // Element-wise double <-> float conversions of the mixed path (integer-arithmetic versions).
 __global__ void split_f64_kernel(const double* __restrict__ x, size_t n, float* rn, float* hi, float* lo,
                                  double* back) {

@@ -163,6 +163,8 @@ Launch line_launch_shape(int N, int count, size_t elem2, int prefer_nl);
 template <int MODE>
 cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
                              double* acc, cudaStream_t st, bool* handled);
+cudaError_t launch_scale_z(const cans_plan_s* P, const double* in, double* out, const double* wz, cudaStream_t st);
+cudaError_t launch_remove_weighted_mean(const cans_plan_s* P, double* f, double* acc2, cudaStream_t st);
 cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
                             float* r, double* norm_acc, cudaStream_t st);
 bool xres_warp_ok(const cans_plan_s* P, const float* W);
