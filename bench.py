@@ -61,11 +61,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()  # the first sample takes a while: start timing only once sampling runs
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.lines.clear()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -102,6 +107,20 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------------
+# DRAM bytes per point (dram__bytes_read.sum + dram__bytes_write.sum / points) of each mixed-path
+# kernel from one ncu --set full capture on a small case of the same recipe (1024x1024x64; the z
+# kernel 256x256x512), scaled to a full launch by the points it processes: every one of these
+# kernels streams its fields once, so traffic grows in proportion to the points.
+NCU_DRAM_BYTES_PER_POINT = {
+    "x_forward": 11.48,
+    "y_forward": 7.20,
+    "y_inverse": 7.19,
+    "x_inverse_update": 15.28,
+    "residual_stencil": 15.87,
+    "z_solve": 6.22,
+}
+
+
 def pass_bytes_mixed(sweeps: int, split_residual: bool):
     """Algorithmic bytes per point each pass kind must move in the mixed solve with `sweeps` sweeps
     (the first sweep knows the iterate's tail Plo is zero, later sweeps read and write it).  With the
@@ -181,14 +200,18 @@ def gpu_arm(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for k in range(args.steps):
         solver.solve(f, p)
+        ev[k + 1].record(stream)
     e1.record(stream)
     barrier()
     cans.cans_plan_profile(solver.plan, False)
     clk = clocks.stop() if rank == 0 else None
     ms_total = e0.elapsed_time(e1)
+    per_solve = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
     ms = replicas.max_over_ranks(ms_total / args.steps, device="cuda")
     # per-pass device times inside the timed region
     split = cans.cans_plan_profile_read(solver.plan, 7)[1] > 0
@@ -242,6 +265,7 @@ def gpu_arm(args):
     del fh, ph, fd, f, p
     torch.cuda.empty_cache()
 
+    small = config1_measure(cans, I, args)
     rk3 = rk3_measure(cans, I, args)
     cfg2 = config2_measure(cans, I, args)
     ens = ensemble_measure(cans, I, args)
@@ -253,6 +277,9 @@ def gpu_arm(args):
         return
 
     cpu = cpu_baseline(seconds_budget=args.cpu_budget)
+    fft_case = I.case_modes(n=(1024, 1024, 64))
+    cpu_fft = cpu_fft_baseline(I.rhs_device(fft_case, "cuda").cpu().numpy(), fft_case,
+                               seconds_budget=args.cpu_budget / 2)
     out = {
         "metric": METRIC,
         "value": replicas.aggregate_gpts(npts, ms, world),
@@ -261,6 +288,8 @@ def gpu_arm(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms,
+        "ms_per_solve_median": per_solve[len(per_solve) // 2],
+        "ms_per_solve_best": per_solve[0],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -287,16 +316,19 @@ def gpu_arm(args):
             "peak_source": peak_src,
             "unit": "GB/s",
             "frac": achieved / hbm_peak,
-            "traffic": None,
+            "traffic": (NCU_DRAM_BYTES_PER_POINT[dominant[0]] * npts
+                        if dominant[0] in NCU_DRAM_BYTES_PER_POINT else None),
             "algorithmic_bytes_per_launch": dom_bytes,
             "whole_solve_frac": (sum(PASS_BYTES_MIXED[v["kind"]] * v["launches"] for v in passes.values())
                                  / args.steps * npts / (ms * 1e-3) / 1e9) / hbm_peak,
         },
         "cpu_baseline": cpu,
+        "cpu_fft_comparator": cpu_fft,
         "e2e": {"value": npts / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8},
         "gpu_launches": kernels_per_solve * args.steps,
         "clocks": clk,
+        "config1_small": small,
         "rk3_step": rk3,
         "ensemble": ens,
         "config2_channel": cfg2,
@@ -392,6 +424,41 @@ def config2_measure(cans, I, args):
             "cufft_comparator": ms_cufft, "cufft_comparator_gpts": npts / (ms_cufft * 1e-3) / 1e9,
             "comparator_rel_l2_vs_library": rel,
             "note": "comparator: torch.fft (cuFFT) x rfft + y DST-II via Makhoul + this library's z solve"}
+
+
+def config1_measure(cans, I, args):
+    """The 32^3 case (x, y periodic, z Neumann, uniform; latency- and L2-bound): microseconds per
+    solve, FP64 and mixed with 2 sweeps, each solve replayed from a CUDA graph."""
+    import torch
+
+    case = I.case_uniform32()
+    f = torch.from_numpy(I.rhs_host(case)).cuda()
+    out = {"workload": "poisson_32x32x32_P-P-NN_uniform", "unit": "us/solve"}
+    for name, prec, sweeps in (("fp64", cans.CANS_FP64, 0), ("mixed_2sweeps", cans.CANS_MIXED, 2)):
+        s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=prec, sweeps=max(sweeps, 1))
+        p = torch.empty_like(f)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            s.solve(f, p)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        reps = 20
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                s.solve(f, p)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) * 1e3 / (5 * reps)
+        s.close()
+    return out
 
 
 def rk3_measure(cans, I, args):
@@ -501,6 +568,102 @@ def cpu_baseline(seconds_budget: float = 20.0):
                       f"FP64 dense-basis oracle, best of {reps}", "seconds": dt}
 
 
+def cpu_fft_solve(f, bc, length_xy, dzf, workers=1):
+    """Fair O(N log N) FP64 CPU solve of L_h p = f (the CPU comparator beside the oracle): scipy.fft
+    transforms along x and y (real DFT for periodic, DCT-II for Neumann, DST-II for Dirichlet
+    directions; eigenvalues -4 sin^2 of the same arguments as the library's), one vectorised Thomas
+    sweep along z over all (x, y) modes (numpy), the inverse transforms.  f: (nz, ny, nx) float64,
+    z non-periodic.  Singular problems (no Dirichlet direction): the (0, 0) mode's last equation is
+    replaced by phi = 0 and the dzf-weighted mean of p is removed, the zero-mean solution."""
+    import scipy.fft as sf
+
+    from paper_2001_05234_b300.inputs import BC_DD, BC_NN, BC_P
+
+    nz, ny, nx = f.shape
+    bx, by, bz = bc
+    assert bz in (BC_NN, BC_DD)
+    a = np.asarray(f, dtype=np.float64)
+    for ax, b in ((-1, bx), (-2, by)):
+        if b == BC_NN:
+            a = sf.dct(a, type=2, axis=ax, workers=workers)
+        elif b == BC_DD:
+            a = sf.dst(a, type=2, axis=ax, workers=workers)
+    kinds = []  # periodic axes in the order transformed: (axis, n, "r" for rfft or "c" for fft)
+    for ax, b, n in ((-1, bx, nx), (-2, by, ny)):
+        if b == BC_P:
+            kind = "c" if kinds else "r"
+            a = (sf.fft if kind == "c" else sf.rfft)(a, axis=ax, workers=workers)
+            kinds.append((ax, n, kind))
+
+    def lam(b, n, m):
+        k = np.arange(m, dtype=np.float64)
+        if b == BC_P:
+            return -4.0 * np.sin(np.pi * k / n) ** 2
+        if b == BC_NN:
+            return -4.0 * np.sin(np.pi * k / (2 * n)) ** 2
+        return -4.0 * np.sin(np.pi * (k + 1) / (2 * n)) ** 2
+
+    dx, dy = length_xy[0] / nx, length_xy[1] / ny
+    mu = lam(bx, nx, a.shape[-1])[None, :] / dx ** 2 + lam(by, ny, a.shape[-2])[:, None] / dy ** 2
+    dzf = np.asarray(dzf, dtype=np.float64)
+    dzc = np.empty(nz + 1)
+    dzc[1:nz] = 0.5 * (dzf[:-1] + dzf[1:])
+    dzc[0], dzc[nz] = dzf[0], dzf[-1]  # wall ghosts mirror the wall cell
+    lo = 1.0 / (dzf * dzc[:nz])
+    up = 1.0 / (dzf * dzc[1:])
+    dg = -(lo + up)
+    if bz == BC_NN:
+        dg[0] += lo[0]
+        dg[-1] += up[-1]
+    else:
+        dg[0] -= lo[0]
+        dg[-1] -= up[-1]
+    lo[0] = up[-1] = 0.0
+    singular = BC_DD not in (bx, by, bz)
+    cp = np.empty((nz,) + mu.shape)
+    den = dg[0] + mu
+    cp[0] = up[0] / den
+    a[0] = a[0] / den
+    for k in range(1, nz):
+        den = (dg[k] + mu) - lo[k] * cp[k - 1]
+        if singular and k == nz - 1:  # the (0, 0) mode: phi_{nz-1} = 0 replaces the last equation
+            den[0, 0] = 1.0
+            a[k, 0, 0] = lo[k] * a[k - 1, 0, 0]
+        cp[k] = up[k] / den
+        a[k] = (a[k] - lo[k] * a[k - 1]) / den
+    for k in range(nz - 2, -1, -1):
+        a[k] -= cp[k] * a[k + 1]
+    for ax, n, kind in reversed(kinds):
+        a = sf.ifft(a, axis=ax, workers=workers) if kind == "c" else sf.irfft(a, n=n, axis=ax, workers=workers)
+    for ax, b in ((-2, by), (-1, bx)):
+        if b == BC_NN:
+            a = sf.idct(a, type=2, axis=ax, workers=workers)
+        elif b == BC_DD:
+            a = sf.idst(a, type=2, axis=ax, workers=workers)
+    if singular:
+        a = a - (np.tensordot(dzf, a, axes=(0, 0)).sum() / (dzf.sum() * nx * ny))
+    return np.ascontiguousarray(a)
+
+
+def cpu_fft_baseline(f_sample, case, seconds_budget: float = 10.0):
+    """The fair CPU solve timed on the host cores on a z-slab of the workload (full x-y planes, so
+    the transforms' cost per point is that of the workload; the z sweep costs the same per point)."""
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    cpu_fft_solve(f_sample, case.bc, case.length_xy, case.dzf, workers=cores)
+    dt = time.perf_counter() - t0
+    reps = 1
+    while dt * (reps + 1) < seconds_budget and reps < 3:
+        t0 = time.perf_counter()
+        cpu_fft_solve(f_sample, case.bc, case.length_xy, case.dzf, workers=cores)
+        dt = min(dt, time.perf_counter() - t0)
+        reps += 1
+    nz, ny, nx = f_sample.shape
+    return {"value": case.points / dt / 1e9, "unit": "Gpts/s", "cores": cores, "kind": "scipy.fft + numpy Thomas",
+            "sample": f"{nx}x{ny}x{nz} slab of the workload recipe (tanh z on {nz} cells), FP64, best of {reps}",
+            "seconds": dt}
+
+
 def reference_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -567,7 +730,7 @@ def solve_once(spec: str, sweeps: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)

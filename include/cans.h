@@ -195,6 +195,18 @@ int cans_batch_solve(cans_batch_t batch, const double* const* f, double* const* 
                      void* cuda_stream);
 int cans_batch_destroy(cans_batch_t batch);
 
+/* cans_poisson_solve_batched -- the same in one call: count problems (plans[i], f[i], p[i] device
+ * pointers as in cans_poisson_solve) solved concurrently on internal streams forked from cuda_stream.
+ * workspace: cans_poisson_batched_workspace_size() bytes (the problems' workspaces, 256-byte aligned
+ * each).  device_status (device, count ints, may be NULL) receives each problem's status, written
+ * on the device after its solve: CANS_ERR_NOT_CONVERGED when a norm the mixed solve accumulates
+ * (|f|^2, the residual of each sweep) is not finite, else CANS_OK (FP64 problems: CANS_OK); when the
+ * call itself fails, every entry receives the returned status.  The internal streams are created and released on every call, so this form is not meant for
+ * stream capture or tight loops: keep a cans_batch_t for those. */
+int cans_poisson_batched_workspace_size(int count, const cans_plan_t* plans, size_t* bytes);
+int cans_poisson_solve_batched(int count, const cans_plan_t* plans, const double* const* f, double* const* p,
+                               void* workspace, void* cuda_stream, int* device_status);
+
 /*
  * Fractional-step pieces for a channel plan (bc = {CANS_BC_P, CANS_BC_P, CANS_BC_NN}: x and y
  * periodic, no-slip walls at z = 0 and z = Lz).  Velocities live on the faces of the staggered grid

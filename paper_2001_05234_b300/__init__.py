@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libcans.so")
 CANS_BC_P, CANS_BC_NN, CANS_BC_DD = 0, 1, 2
 CANS_FP64, CANS_MIXED = 0, 1
 CANS_OK = 0
+CANS_ERR_ARG, CANS_ERR_UNSUPPORTED, CANS_ERR_CUDA, CANS_ERR_WORKSPACE = -1, -2, -3, -4
 STATUS_NAMES = {0: "CANS_OK", -1: "CANS_ERR_ARG", -2: "CANS_ERR_UNSUPPORTED", -3: "CANS_ERR_CUDA",
                 -4: "CANS_ERR_WORKSPACE", -5: "CANS_ERR_INCOMPATIBLE", -6: "CANS_ERR_NOT_CONVERGED",
                 -7: "CANS_ERR_TIMEOUT"}
@@ -72,6 +73,10 @@ def lib() -> ctypes.CDLL:
         L.cans_batch_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
         L.cans_batch_destroy.argtypes = [vp]
+        L.cans_poisson_batched_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(vp),
+                                                           ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_poisson_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                 ctypes.POINTER(vp), vp, vp, vp]
         L.cans_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
         L.cans_project_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -190,6 +195,22 @@ def cans_batch_solve(batch, f_ptrs, p_ptrs, workspace_ptr: int, stream_ptr: int)
 
 def cans_batch_destroy(batch) -> int:
     return lib().cans_batch_destroy(batch)
+
+
+def cans_poisson_batched_workspace_size(plans) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if hasattr(p, "value") else p for p in plans])
+    b = ctypes.c_size_t()
+    _check(lib().cans_poisson_batched_workspace_size(len(plans), arr, ctypes.byref(b)),
+           "cans_poisson_batched_workspace_size")
+    return int(b.value)
+
+
+def cans_poisson_solve_batched(plans, f_ptrs, p_ptrs, workspace_ptr: int, stream_ptr: int, status_ptr: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if hasattr(p, "value") else p for p in plans])
+    fa = (ctypes.c_void_p * len(f_ptrs))(*f_ptrs)
+    pa = (ctypes.c_void_p * len(p_ptrs))(*p_ptrs)
+    return lib().cans_poisson_solve_batched(len(plans), arr, fa, pa, workspace_ptr or None, stream_ptr or None,
+                                            status_ptr or None)
 
 
 def cans_noalloc_scratch_bytes() -> int:

@@ -24,6 +24,45 @@ struct cans_batch_s {
   std::vector<cudaEvent_t> joins;
 };
 
+// Per-problem device status after a solve: CANS_ERR_NOT_CONVERGED when |f|^2 or any residual norm
+// the mixed solve accumulated on the device is not finite, else CANS_OK.  FP64 solves keep no device
+// norms (nacc_used = 0) and report CANS_OK.
+__global__ void solve_status_kernel(const double* acc, int nacc_used, int* status) {
+  bool ok = true;
+  for (int i = threadIdx.x; i < nacc_used; i += 32) ok &= (bool)isfinite(acc[i]);
+  ok = __all_sync(0xffffffffu, ok);
+  if (threadIdx.x == 0) *status = ok ? CANS_OK : CANS_ERR_NOT_CONVERGED;
+}
+
+static int batch_solve_impl(cans_batch_t B, const double* const* f, double* const* p, void* workspace,
+                            void* cuda_stream, int* status) {
+  if (!B || !f || !p) return CANS_ERR_ARG;
+  if (B->ws_bytes > 0 && (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))) return CANS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int ns = (int)B->streams.size();
+  if (cudaEventRecord(B->fork, st) != cudaSuccess) return CANS_ERR_CUDA;
+  for (int s = 0; s < ns; ++s)
+    if (cudaStreamWaitEvent(B->streams[s], B->fork, 0) != cudaSuccess) return CANS_ERR_CUDA;
+  for (int q : B->order) {
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    void* w = (B->ws_bytes > 0) ? ws + B->ws_off[q] : nullptr;
+    cudaStream_t sq = B->streams[B->stream_of[q]];
+    const int rc = cans_poisson_solve(B->plans[q], f[q], p[q], w, sq, nullptr);
+    if (rc != CANS_OK) return rc;
+    if (status) {
+      const cans_plan_s* P = B->plans[q];
+      const int used = (P->opts.prec == CANS_MIXED) ? 1 + P->opts.max_sweeps : 0;
+      solve_status_kernel<<<1, 32, 0, sq>>>(P->acc_d, used, status + q);
+      if (cudaGetLastError() != cudaSuccess) return CANS_ERR_CUDA;
+    }
+  }
+  for (int s = 0; s < ns; ++s) {
+    if (cudaEventRecord(B->joins[s], B->streams[s]) != cudaSuccess) return CANS_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, B->joins[s], 0) != cudaSuccess) return CANS_ERR_CUDA;
+  }
+  return CANS_OK;
+}
+
 extern "C" {
 
 int cans_batch_create(int count, const cans_plan_t* plans, int nstreams, cans_batch_t* out) {
@@ -81,24 +120,7 @@ int cans_batch_workspace_size(cans_batch_t B, size_t* bytes) {
 }
 
 int cans_batch_solve(cans_batch_t B, const double* const* f, double* const* p, void* workspace, void* cuda_stream) {
-  if (!B || !f || !p) return CANS_ERR_ARG;
-  if (B->ws_bytes > 0 && (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))) return CANS_ERR_WORKSPACE;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int ns = (int)B->streams.size();
-  if (cudaEventRecord(B->fork, st) != cudaSuccess) return CANS_ERR_CUDA;
-  for (int s = 0; s < ns; ++s)
-    if (cudaStreamWaitEvent(B->streams[s], B->fork, 0) != cudaSuccess) return CANS_ERR_CUDA;
-  for (int q : B->order) {
-    unsigned char* ws = static_cast<unsigned char*>(workspace);
-    void* w = (B->ws_bytes > 0) ? ws + B->ws_off[q] : nullptr;
-    const int rc = cans_poisson_solve(B->plans[q], f[q], p[q], w, B->streams[B->stream_of[q]], nullptr);
-    if (rc != CANS_OK) return rc;
-  }
-  for (int s = 0; s < ns; ++s) {
-    if (cudaEventRecord(B->joins[s], B->streams[s]) != cudaSuccess) return CANS_ERR_CUDA;
-    if (cudaStreamWaitEvent(st, B->joins[s], 0) != cudaSuccess) return CANS_ERR_CUDA;
-  }
-  return CANS_OK;
+  return batch_solve_impl(B, f, p, workspace, cuda_stream, nullptr);
 }
 
 int cans_batch_destroy(cans_batch_t B) {
@@ -110,6 +132,40 @@ int cans_batch_destroy(cans_batch_t B) {
   if (B->fork) cudaEventDestroy(B->fork);
   delete B;
   return CANS_OK;
+}
+
+int cans_poisson_batched_workspace_size(int count, const cans_plan_t* plans, size_t* bytes) {
+  if (count < 1 || !plans || !bytes) return CANS_ERR_ARG;
+  size_t tot = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!plans[i]) return CANS_ERR_ARG;
+    size_t b = 0;
+    cans_poisson_workspace_size(plans[i], &b);
+    tot += (b + 255) & ~size_t(255);
+  }
+  *bytes = tot;
+  return CANS_OK;
+}
+
+int cans_poisson_solve_batched(int count, const cans_plan_t* plans, const double* const* f, double* const* p,
+                               void* workspace, void* cuda_stream, int* device_status) {
+  if (count < 1 || !plans || !f || !p) return CANS_ERR_ARG;
+  cans_batch_t B = nullptr;
+  int rc = cans_batch_create(count, plans, 8, &B);
+  if (rc != CANS_OK) return rc;
+  rc = batch_solve_impl(B, f, p, workspace, cuda_stream, device_status);
+  if (rc != CANS_OK)  // a failed launch leaves the internal streams unjoined: drain them first
+    for (cudaStream_t s : B->streams) cudaStreamSynchronize(s);
+  cans_batch_destroy(B);  // stream destruction waits for the queued work
+  if (device_status && rc != CANS_OK) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<int> h(count, rc);
+    if (cudaMemcpyAsync(device_status, h.data(), sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return CANS_ERR_CUDA;
+    cudaStreamSynchronize(st);  // h is released on return
+  }
+  return rc;
 }
 
 }  // extern "C"

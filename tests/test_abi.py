@@ -31,7 +31,7 @@ def cans():
 def test_header_declares_entry_points():
     names = declared_symbols()
     for must in ("cans_poisson_plan", "cans_poisson_solve", "cans_poisson_workspace_size", "cans_plan_destroy",
-                 "cans_status_string"):
+                 "cans_status_string", "cans_poisson_solve_batched", "cans_poisson_solve_adjoint"):
         assert must in names
 
 

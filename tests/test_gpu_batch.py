@@ -82,3 +82,62 @@ def test_full_ensemble_64_problems(cans):
         res = oracle.relative_residual(ps[q].cpu().numpy(), fs[q].cpu().numpy(), c.bc, c.length_xy, c.dzf)
         assert res <= 1e-11, (c.n, c.bc, res)
     b.close()
+
+
+def test_solve_batched_one_call_with_status(cans):
+    """cans_poisson_solve_batched: the one-call form writes the same results as the batch object and
+    a zero status per problem; a workspace that is not 256-byte aligned is refused before any launch."""
+    import torch
+
+    cases = I.ensemble_cases(count=6, sizes=(16, 32, 48))
+    fs = [torch.from_numpy(I.rhs_host(c)).cuda() for c in cases]
+    ref = [torch.empty_like(f) for f in fs]
+    b = cans.Batch(cases, prec=cans.CANS_MIXED, sweeps=2, nstreams=8)
+    b.solve(fs, ref)
+    torch.cuda.synchronize()
+    nbytes = cans.cans_poisson_batched_workspace_size(b.plans)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    status = torch.full((len(cases),), -7, dtype=torch.int32, device="cuda")
+    out = [torch.full_like(f, float("nan")) for f in fs]
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = cans.cans_poisson_solve_batched(b.plans, [t.data_ptr() for t in fs], [t.data_ptr() for t in out], base,
+                                         stream, status.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert status.cpu().tolist() == [0] * len(cases)
+    for a, e in zip(out, ref):
+        assert float((a - e).abs().max()) <= 1e-13 * float(e.abs().max())
+    rc = cans.cans_poisson_solve_batched(b.plans, [t.data_ptr() for t in fs], [t.data_ptr() for t in out], base + 8,
+                                         stream, status.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == cans.CANS_ERR_WORKSPACE
+    assert status.cpu().tolist() == [rc] * len(cases)
+    b.close()
+
+
+def test_solve_batched_device_status_flags_nonfinite(cans):
+    """A problem whose right-hand side holds a NaN is flagged CANS_ERR_NOT_CONVERGED in the device status
+    of the one-call batched solve; its neighbours in the batch are unaffected and report CANS_OK."""
+    import torch
+
+    cases = I.ensemble_cases(count=4, sizes=(16, 32))
+    fs = [torch.from_numpy(I.rhs_host(c)).cuda() for c in cases]
+    fs[2].view(-1)[5] = float("nan")
+    b = cans.Batch(cases, prec=cans.CANS_MIXED, sweeps=1, nstreams=4)
+    ref = [torch.empty_like(f) for f in fs]
+    b.solve(fs, ref)
+    torch.cuda.synchronize()
+    nbytes = cans.cans_poisson_batched_workspace_size(b.plans)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    status = torch.full((len(cases),), 99, dtype=torch.int32, device="cuda")
+    out = [torch.empty_like(f) for f in fs]
+    rc = cans.cans_poisson_solve_batched(b.plans, [t.data_ptr() for t in fs], [t.data_ptr() for t in out], base,
+                                         torch.cuda.current_stream().cuda_stream, status.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == 0
+    assert status.cpu().tolist() == [0, 0, -6, 0]
+    for q in (0, 1, 3):
+        assert float((out[q] - ref[q]).abs().max()) <= 1e-13 * float(ref[q].abs().max())
+    b.close()
