@@ -47,6 +47,10 @@ def lib():
         L.oracle_z_rows.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
         L.oracle_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
         L.oracle_set_fault.argtypes = [ctypes.c_int]
+        L.oracle_helmholtz_solve.argtypes = [ctypes.c_int, ip, dp, ip, dp, ctypes.c_double, ctypes.c_int, dp, dp,
+                                             ctypes.c_int]
+        L.oracle_apply_helmholtz.argtypes = [ctypes.c_int, ip, dp, ip, dp, ctypes.c_double, ctypes.c_int, dp, dp,
+                                             ctypes.c_int]
         _lib = L
     return _lib
 
@@ -127,9 +131,45 @@ def set_fault(mode: int) -> None:
     lib().oracle_set_fault(int(mode))
 
 
-def relative_residual(p, f, bc, length_xy=(1.0, 1.0), dzf=None, nthreads=0):
-    r = apply_laplacian(p, bc, length_xy, dzf, nthreads=nthreads) - f
+def relative_residual(p, f, bc, length_xy=(1.0, 1.0), dzf=None, nthreads=0, shift=0.0, z_grid=0):
+    if shift == 0.0 and z_grid == 0:
+        r = apply_laplacian(p, bc, length_xy, dzf, nthreads=nthreads) - f
+    else:
+        r = apply_helmholtz(p, bc, length_xy, dzf, shift=shift, z_grid=z_grid, nthreads=nthreads) - f
     return float(np.linalg.norm(r) / np.linalg.norm(f))
+
+
+# ---- Helmholtz form (Eq. up_id_2) and the face grid of a staggered w ------------------------------
+def _helm_args(shape, bc, length_xy, dzf, z_grid):
+    nu, ny, nx = shape
+    ncell = nu + int(z_grid)
+    n = np.array([nx, ny, ncell], dtype=np.int32)
+    return n, np.array(bc, dtype=np.int32), np.array(length_xy, dtype=np.float64), _dz(n, dzf)
+
+
+def helmholtz_solve(f, bc, length_xy=(1.0, 1.0), dzf=None, shift=0.0, z_grid=0, prec=64, nthreads=0):
+    """p with (L_h + shift) p = f.  z_grid 0: f is (nz, ny, nx) on the cell centres of the nz dzf cells;
+    z_grid 1: f is (nz - 1, ny, nx) on the interior z-faces (w = 0 on the wall faces; bc_z Dirichlet)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n, b, L, dz = _helm_args(f.shape, bc, length_xy, dzf, z_grid)
+    p = np.empty_like(f)
+    rc = lib().oracle_helmholtz_solve(prec, _i(n), _d(L), _i(b), _d(dz), float(shift), int(z_grid), _d(f), _d(p),
+                                      int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_helmholtz_solve rejected its arguments (rc={rc})")
+    return p
+
+
+def apply_helmholtz(p, bc, length_xy=(1.0, 1.0), dzf=None, shift=0.0, z_grid=0, prec=64, nthreads=0):
+    """(L_h + shift) p on the grid of helmholtz_solve."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    n, b, L, dz = _helm_args(p.shape, bc, length_xy, dzf, z_grid)
+    out = np.empty_like(p)
+    rc = lib().oracle_apply_helmholtz(prec, _i(n), _d(L), _i(b), _d(dz), float(shift), int(z_grid), _d(p), _d(out),
+                                      int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_apply_helmholtz rejected its arguments (rc={rc})")
+    return out
 
 
 # ---- fractional-step pieces (channel: x, y periodic, walls in z) --------------------------------

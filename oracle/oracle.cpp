@@ -52,11 +52,28 @@ template <> quad pi_<quad>() { return acosq((quad)-1); }
 // and k+1 (stored with an offset of one so that dzc[0] is the wall ghost distance below cell 0 and
 // dzc[nz] the one above cell nz-1).  At a wall the ghost cell mirrors the first interior cell, so
 // the ghost distance equals the wall cell's width.  A periodic z wraps.
+//
+// Face grid (faces = true; the staggered w of the marker-and-cell grid, Numerical method, solved
+// implicitly by Eq. up_id_2): the unknowns sit on the nz = ncells - 1 interior faces, unknown k on
+// the face between cells k and k+1; w = 0 on both wall faces.  Its second difference at face k is
+//   [ (w_{k+1} - w_k) / dzf_{k+1} - (w_k - w_{k-1}) / dzf_k ] / mid_k,
+// mid_k = (dzf_k + dzf_{k+1}) / 2 the distance between the centres of the two cells, w_{-1} = w_nz = 0.
 template <typename T>
 struct ZGrid {
   int nz, bc;
-  std::vector<T> dzf, dzc;  // dzf[k], k=0..nz-1; dzc[k], k=0..nz (see above)
-  ZGrid(int nz_, int bc_, const double* dzf_in) : nz(nz_), bc(bc_), dzf(nz_), dzc(nz_ + 1) {
+  bool faces;
+  std::vector<T> dzf, dzc;  // cell grid: dzf[k], k=0..nz-1; dzc[k], k=0..nz (see above)
+  std::vector<T> cell, mid;  // face grid: the ncells cell widths and the nz centre distances mid_k
+  ZGrid(int ncells, int bc_, const double* dzf_in, bool faces_ = false)
+      : nz(ncells - (faces_ ? 1 : 0)), bc(bc_), faces(faces_), dzf(nz), dzc(nz + 1) {
+    if (faces) {
+      cell.resize(ncells);
+      mid.resize(nz);
+      for (int k = 0; k < ncells; ++k) cell[k] = (T)dzf_in[k];
+      for (int k = 0; k < nz; ++k) mid[k] = (cell[k] + cell[k + 1]) / 2;
+      for (int k = 0; k < nz; ++k) dzf[k] = mid[k];  // control-volume widths (weights of the mean)
+      return;
+    }
     for (int k = 0; k < nz; ++k) dzf[k] = (T)dzf_in[k];
     for (int k = 1; k < nz; ++k) dzc[k] = (dzf[k - 1] + dzf[k]) / 2;
     if (bc == BC_P) {
@@ -79,9 +96,10 @@ inline T ghost(int bc, T inner, T wrap) {
   return -inner;
 }
 
+// (L_h + shift) p: the Helmholtz form of Eq. up_id_2 when shift != 0.
 template <typename T>
 void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const ZGrid<T>& zg, const T* p, T* out,
-                     int nthreads) {
+                     int nthreads, T shift = 0) {
   const int nx = n[0], ny = n[1], nz = n[2];
   const T dx = len_xy[0] / nx, dy = len_xy[1] / ny;
   const T idx2 = 1 / (dx * dx), idy2 = 1 / (dy * dy);
@@ -100,12 +118,18 @@ void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const Z
         const T zp = (k < nz - 1) ? p[c + sz] : ghost<T>(bc[2], pc, p[c - (nz - 1) * sz]);
         const T lx = (xm - 2 * pc + xp) * idx2;
         const T ly = (ym - 2 * pc + yp) * idy2;
-        // z: (1/dzf_k) [ (p_{k+1}-p_k)/dzc_{k+1/2} - (p_k-p_{k-1})/dzc_{k-1/2} ]  (non-uniform z)
-        T up = (zp - pc) / zg.dzc[k + 1];
-        T dn = (pc - zm) / zg.dzc[k];
-        if (g_fault == 1) dn = (pc - zm) / zg.dzc[k + 1];  // planted: wrong metric index
-        const T lz = (up - dn) / zg.dzf[k];
-        out[c] = lx + ly + lz;
+        T lz;
+        if (zg.faces) {  // w on faces, zero on the wall faces
+          const T wm = (k > 0) ? p[c - sz] : T(0), wp = (k < nz - 1) ? p[c + sz] : T(0);
+          lz = ((wp - pc) / zg.cell[k + 1] - (pc - wm) / zg.cell[k]) / zg.mid[k];
+        } else {
+          // z: (1/dzf_k) [ (p_{k+1}-p_k)/dzc_{k+1/2} - (p_k-p_{k-1})/dzc_{k-1/2} ]  (non-uniform z)
+          T up = (zp - pc) / zg.dzc[k + 1];
+          T dn = (pc - zm) / zg.dzc[k];
+          if (g_fault == 1) dn = (pc - zm) / zg.dzc[k + 1];  // planted: wrong metric index
+          lz = (up - dn) / zg.dzf[k];
+        }
+        out[c] = lx + ly + lz + shift * pc;
       }
     }
   }
@@ -170,6 +194,14 @@ void z_rows(const ZGrid<T>& zg, std::vector<T>& a, std::vector<T>& b, std::vecto
   a.assign(nz, T(0));
   b.assign(nz, T(0));
   c.assign(nz, T(0));
+  if (zg.faces) {  // the face operator above, the zero wall values dropped from the rows
+    for (int k = 0; k < nz; ++k) {
+      a[k] = (k > 0) ? 1 / (zg.cell[k] * zg.mid[k]) : T(0);
+      c[k] = (k < nz - 1) ? 1 / (zg.cell[k + 1] * zg.mid[k]) : T(0);
+      b[k] = -(1 / (zg.cell[k] * zg.mid[k]) + 1 / (zg.cell[k + 1] * zg.mid[k]));
+    }
+    return;
+  }
   for (int k = 0; k < nz; ++k) {
     a[k] = 1 / (zg.dzf[k] * zg.dzc[k]);
     c[k] = 1 / (zg.dzf[k] * zg.dzc[k + 1]);
@@ -210,9 +242,10 @@ void thomas(int n, const T* a, const T* b, const T* c, const T* d, T* x) {
 // Singular case (x, y, z all periodic or Neumann): the (0,0) z-system is singular; its last equation
 // is dropped with phat_{nz-1} = 0, and the result is shifted to zero dzf-weighted mean, which makes
 // the cell-volume-weighted mean of p zero.
+// With a Helmholtz shift (Eq. up_id_2) every diagonal gets + shift and no mode is singular.
 template <typename T>
 int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGrid<T>& zg, const T* f, T* p,
-                  int nthreads) {
+                  int nthreads, T shift = 0) {
   const int nx = n[0], ny = n[1], nz = n[2];
   const size_t plane = (size_t)nx * ny;
   std::vector<T> Ex, lx, Ey, ly, Ez, lz;
@@ -248,7 +281,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
     }
   }
 
-  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD) && shift == 0;
   if (bc[2] == BC_P) {
     // uniform periodic z: diagonalise z as well (checked by the caller)
     eigenbasis<T>(BC_P, nz, Ez, lz);
@@ -262,7 +295,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
       for (int mz = 0; mz < nz; ++mz) {
         T s = 0;
         for (int k = 0; k < nz; ++k) s += Ez[(size_t)k * nz + mz] * g[k];
-        const T den = mu + lz[mz] / (dz * dz);
+        const T den = mu + lz[mz] / (dz * dz) + shift;
         q[mz] = (singular && mx == 0 && my == 0 && mz == 0) ? T(0) : s / den;
       }
       for (int k = 0; k < nz; ++k) {
@@ -282,7 +315,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
       const T mu = lx[mx] / (dx * dx) + ly[my] / (dy * dy);
       std::vector<T> bb(nz), d(nz), x(nz);
       for (int k = 0; k < nz; ++k) {
-        bb[k] = b[k] + mu;
+        bb[k] = b[k] + mu + shift;
         d[k] = hat[col + k * plane];
       }
       if (singular && mx == 0 && my == 0) {
@@ -345,28 +378,31 @@ int check_args(const int n[3], const int bc[3], const double* dzf) {
   return 0;
 }
 
+// n[2] counts the cells of dzf; the unknowns along z are n[2] (cell grid) or n[2] - 1 (face grid).
 template <typename T>
 int solve_t(const int n[3], const double len_xy[2], const int bc[3], const double* dzf, const double* f, double* p,
-            int nthreads) {
-  const size_t N = (size_t)n[0] * n[1] * n[2];
+            int nthreads, double shift = 0, int faces = 0) {
+  ZGrid<T> zg(n[2], bc[2], dzf, faces != 0);
+  const int nu[3] = {n[0], n[1], zg.nz};
+  const size_t N = (size_t)n[0] * n[1] * zg.nz;
   std::vector<T> ft(N), pt(N);
   for (size_t i = 0; i < N; ++i) ft[i] = (T)f[i];
   const T L[2] = {(T)len_xy[0], (T)len_xy[1]};
-  ZGrid<T> zg(n[2], bc[2], dzf);
-  int rc = poisson_solve<T>(n, L, bc, zg, ft.data(), pt.data(), nthreads);
+  int rc = poisson_solve<T>(nu, L, bc, zg, ft.data(), pt.data(), nthreads, (T)shift);
   for (size_t i = 0; i < N; ++i) p[i] = (double)pt[i];
   return rc;
 }
 
 template <typename T>
 int apply_t(const int n[3], const double len_xy[2], const int bc[3], const double* dzf, const double* p, double* out,
-            int nthreads) {
-  const size_t N = (size_t)n[0] * n[1] * n[2];
+            int nthreads, double shift = 0, int faces = 0) {
+  ZGrid<T> zg(n[2], bc[2], dzf, faces != 0);
+  const int nu[3] = {n[0], n[1], zg.nz};
+  const size_t N = (size_t)n[0] * n[1] * zg.nz;
   std::vector<T> pt(N), ot(N);
   for (size_t i = 0; i < N; ++i) pt[i] = (T)p[i];
   const T L[2] = {(T)len_xy[0], (T)len_xy[1]};
-  ZGrid<T> zg(n[2], bc[2], dzf);
-  apply_laplacian<T>(n, L, bc, zg, pt.data(), ot.data(), nthreads);
+  apply_laplacian<T>(nu, L, bc, zg, pt.data(), ot.data(), nthreads, (T)shift);
   for (size_t i = 0; i < N; ++i) out[i] = (double)ot[i];
   return 0;
 }
@@ -406,6 +442,33 @@ int oracle_apply_laplacian(int prec_bits, const int n[3], const double len_xy[2]
   if (prec_bits == 64) return apply_t<double>(n, len_xy, bc, dzf, p, out, nthreads);
   if (prec_bits == 80) return apply_t<long double>(n, len_xy, bc, dzf, p, out, nthreads);
   if (prec_bits == 128) return apply_t<quad>(n, len_xy, bc, dzf, p, out, nthreads);
+  return -1;
+}
+
+// (L_h + shift) p = f (Eq. up_id_2 in Helmholtz form) and its operator, on the cell grid (faces = 0)
+// or on the interior z-faces of the dzf cells (faces = 1, Dirichlet walls only: w = 0 on the wall
+// faces).  n[2] counts the dzf cells; f, p, out hold n[0] n[1] (n[2] - faces) values.
+int oracle_helmholtz_solve(int prec_bits, const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
+                           double shift, int faces, const double* f, double* p, int nthreads) {
+  int rc = check_args(n, bc, dzf);
+  if (rc) return rc;
+  if (faces && (bc[2] != BC_DD || n[2] < 2)) return -1;
+  nthreads = nthreads_or_default(nthreads);
+  if (prec_bits == 64) return solve_t<double>(n, len_xy, bc, dzf, f, p, nthreads, shift, faces);
+  if (prec_bits == 80) return solve_t<long double>(n, len_xy, bc, dzf, f, p, nthreads, shift, faces);
+  if (prec_bits == 128) return solve_t<quad>(n, len_xy, bc, dzf, f, p, nthreads, shift, faces);
+  return -1;
+}
+
+int oracle_apply_helmholtz(int prec_bits, const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
+                           double shift, int faces, const double* p, double* out, int nthreads) {
+  int rc = check_args(n, bc, dzf);
+  if (rc) return rc;
+  if (faces && (bc[2] != BC_DD || n[2] < 2)) return -1;
+  nthreads = nthreads_or_default(nthreads);
+  if (prec_bits == 64) return apply_t<double>(n, len_xy, bc, dzf, p, out, nthreads, shift, faces);
+  if (prec_bits == 80) return apply_t<long double>(n, len_xy, bc, dzf, p, out, nthreads, shift, faces);
+  if (prec_bits == 128) return apply_t<quad>(n, len_xy, bc, dzf, p, out, nthreads, shift, faces);
   return -1;
 }
 
