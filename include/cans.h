@@ -65,9 +65,20 @@ typedef struct {
                                 temporary device scratch of about 12-16 bytes per point during planning;
                                 results cached per device / shape / boundary conditions / precision,
                                 and in the file named by CANS_AUTOTUNE_CACHE when set); 0: built-in */
+  double shift;              /* Helmholtz shift sigma <= 0: the plan solves (L_h + sigma) p = f (the
+                                implicit-diffusion equations of the Numerical method, Eq. up_id_2, are
+                                of this form with sigma = -2 / (gamma_k nu dt)); 0 = Poisson.  Also the
+                                default of cans_helmholtz_solve's per-call shift for the mixed path's
+                                choice of double-precision modes. */
+  int z_grid;                /* 0: unknowns at the cell centres of dzf (pressure, u, v).  1: unknowns on
+                                the Nz - 1 interior z-faces of the dzf cells (a staggered w), with w = 0
+                                on both walls (bc_z must be CANS_BC_DD); the solve then reads and writes
+                                the first Nz - 1 planes of Nx*Ny*Nz arrays and leaves the top plane
+                                (the wall face) alone. */
 } cans_opts;
 
-/* Fill *opts with the defaults: FP64, 2 sweeps, tol 1e-12, fraction 0.01, autotune 0. */
+/* Fill *opts with the defaults: FP64, 2 sweeps, tol 1e-12, fraction 0.01, autotune 0, shift 0,
+ * z_grid 0. */
 void cans_opts_default(cans_opts* opts);
 
 /*
@@ -91,8 +102,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
 int cans_poisson_workspace_size(cans_plan_t plan, size_t* bytes);
 
 /*
- * Solve L_h p = f (Eq. poi) for one right-hand side.
- *   f, p       : device arrays of Nx*Ny*Nz doubles.  CANS_FP64 allows f == p (in place);
+ * Solve L_h p = f (Eq. poi) for one right-hand side ((L_h + opts.shift) p = f for a shifted plan).
+ *   f, p       : device arrays of Nx*Ny*Nz doubles (z_grid 1: only the first Nz - 1 planes are used).  CANS_FP64 allows f == p (in place);
  *                CANS_MIXED needs f != p because f is re-read for the residual.
  *   workspace  : device buffer of at least cans_poisson_workspace_size() bytes, 256-byte aligned
  *                (may be NULL when that size is 0).  Contents on entry are ignored.
@@ -107,6 +118,17 @@ int cans_poisson_workspace_size(cans_plan_t plan, size_t* bytes);
  */
 int cans_poisson_solve(cans_plan_t plan, const double* f, double* p, void* workspace, void* cuda_stream,
                        double* info);
+
+/*
+ * cans_helmholtz_solve -- (L_h + shift) p = f with this plan's grid, boundary conditions and precision
+ * (Eq. up_id_2 written as a Helmholtz problem: the diagonal of every z system is shifted by `shift`
+ * on top of the x-y eigenvalue term; the residual of the mixed path carries the shift).  shift <= 0
+ * and finite, given per call (the plan's opts.shift is the default cans_poisson_solve uses).  A
+ * nonzero shift makes every problem non-singular (no gauge).  Arguments, workspace, asynchrony and
+ * errors as cans_poisson_solve; CANS_ERR_ARG for a positive or non-finite shift.
+ */
+int cans_helmholtz_solve(cans_plan_t plan, const double* f, double* p, double shift, void* workspace,
+                         void* cuda_stream, double* info);
 
 /* Release the plan and its device tables. */
 int cans_plan_destroy(cans_plan_t plan);

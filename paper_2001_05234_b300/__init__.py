@@ -34,7 +34,8 @@ class CansError(RuntimeError):
 
 class cans_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
-                ("fp64_mode_fraction", ctypes.c_double), ("autotune", ctypes.c_int)]
+                ("fp64_mode_fraction", ctypes.c_double), ("autotune", ctypes.c_int), ("shift", ctypes.c_double),
+                ("z_grid", ctypes.c_int)]
 
 
 class cans_rk3_params(ctypes.Structure):
@@ -60,6 +61,7 @@ def lib() -> ctypes.CDLL:
         L.cans_poisson_plan.argtypes = [ip, dp, ip, dp, ctypes.POINTER(cans_opts), ctypes.POINTER(vp)]
         L.cans_poisson_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
+        L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_poisson_adjoint_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, vp]
@@ -139,6 +141,13 @@ def cans_poisson_solve(plan, f_ptr: int, p_ptr: int, workspace_ptr: int, stream_
     """Returns the status; info (numpy float64 array of max_sweeps+2) is filled when given."""
     return lib().cans_poisson_solve(plan, f_ptr, p_ptr, workspace_ptr or None, stream_ptr or None,
                                     _dptr(info) if info is not None else None)
+
+
+def cans_helmholtz_solve(plan, f_ptr: int, p_ptr: int, shift: float, workspace_ptr: int, stream_ptr: int,
+                         info=None) -> int:
+    """(L_h + shift) p = f; returns the status (info as cans_poisson_solve)."""
+    return lib().cans_helmholtz_solve(plan, f_ptr, p_ptr, float(shift), workspace_ptr or None, stream_ptr or None,
+                                      _dptr(info) if info is not None else None)
 
 
 def cans_poisson_solve_noalloc(plan, f_ptr: int, p_ptr: int, stream_ptr: int, info=None) -> int:
@@ -282,10 +291,12 @@ def _stream_ptr(stream=None) -> int:
 
 
 class PoissonSolver:
-    """Owns a plan and its device workspace.  f, p: torch float64 CUDA tensors of shape (Nz, Ny, Nx)."""
+    """Owns a plan and its device workspace.  f, p: torch float64 CUDA tensors of shape (Nz, Ny, Nx).
+    shift: the plan's Helmholtz shift (solves (L_h + shift) p = f); z_grid 1: unknowns on the interior
+    z-faces (a staggered w; the solve uses the first Nz - 1 planes)."""
 
     def __init__(self, n, bc, length_xy=(1.0, 1.0), dzf=None, prec=CANS_FP64, sweeps=2, tol=1e-12,
-                 fp64_fraction=0.01, autotune=False):
+                 fp64_fraction=0.01, autotune=False, shift=0.0, z_grid=0):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -296,6 +307,8 @@ class PoissonSolver:
         o.tol = float(tol)
         o.fp64_mode_fraction = float(fp64_fraction)
         o.autotune = 1 if autotune else 0
+        o.shift = float(shift)
+        o.z_grid = int(z_grid)
         self.opts = o
         _, self.plan = cans_poisson_plan(self.n, length_xy, self.bc, dzf, o)
         nbytes = cans_poisson_workspace_size(self.plan)
@@ -307,16 +320,22 @@ class PoissonSolver:
     def shape(self):
         return (self.n[2], self.n[1], self.n[0])
 
-    def solve(self, f, out=None, stream=None, info: bool = False):
+    def solve(self, f, out=None, stream=None, info: bool = False, shift=None):
+        """p = (L_h + shift)^-1 f; shift None = the plan's own (cans_poisson_solve), else a per-call
+        Helmholtz shift (cans_helmholtz_solve)."""
         import torch
 
         assert f.dtype == torch.float64 and f.is_cuda and f.is_contiguous() and tuple(f.shape) == self.shape
         if out is None:
             out = torch.empty_like(f)
         buf = np.zeros(self.opts.max_sweeps + 2) if info else None
-        st = cans_poisson_solve(self.plan, f.data_ptr(), out.data_ptr(), self._ws_ptr, _stream_ptr(stream), buf)
+        if shift is None:
+            st = cans_poisson_solve(self.plan, f.data_ptr(), out.data_ptr(), self._ws_ptr, _stream_ptr(stream), buf)
+        else:
+            st = cans_helmholtz_solve(self.plan, f.data_ptr(), out.data_ptr(), shift, self._ws_ptr,
+                                      _stream_ptr(stream), buf)
         if st != CANS_OK and not (info and st in (-5, -6)):
-            raise CansError(st, "cans_poisson_solve")
+            raise CansError(st, "cans_helmholtz_solve" if shift is not None else "cans_poisson_solve")
         return (out, buf, st) if info else out
 
     def solve_adjoint(self, g, out=None, stream=None):

@@ -160,6 +160,8 @@ void cans_opts_default(cans_opts* o) {
   o->tol = 1e-12;
   o->fp64_mode_fraction = 0.01;
   o->autotune = 0;
+  o->shift = 0.0;
+  o->z_grid = 0;
 }
 
 const char* cans_status_string(int s) {
@@ -192,11 +194,33 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   if (o.prec != CANS_FP64 && o.prec != CANS_MIXED) return CANS_ERR_ARG;
   if (o.max_sweeps < 0 || o.max_sweeps > 8) return CANS_ERR_ARG;
   if (!(o.fp64_mode_fraction >= 0 && o.fp64_mode_fraction <= 1)) return CANS_ERR_ARG;
-  const int nz = n[2];
-  std::vector<double> dz(nz);
-  for (int k = 0; k < nz; ++k) {
-    dz[k] = dzf ? dzf[k] : 1.0 / nz;
-    if (!(dz[k] > 0) || !std::isfinite(dz[k])) return CANS_ERR_ARG;
+  if (!std::isfinite(o.shift) || o.shift > 0) return CANS_ERR_ARG;
+  if (o.z_grid != 0 && o.z_grid != 1) return CANS_ERR_ARG;
+  if (o.z_grid == 1 && (bc[2] != BC_DD || n[2] < 2)) return CANS_ERR_ARG;
+  const int ncell = n[2];
+  std::vector<double> dzcell(ncell);
+  for (int k = 0; k < ncell; ++k) {
+    dzcell[k] = dzf ? dzf[k] : 1.0 / ncell;
+    if (!(dzcell[k] > 0) || !std::isfinite(dzcell[k])) return CANS_ERR_ARG;
+  }
+  // The solved z grid: widths dz of its control volumes and the distances dzc between consecutive
+  // unknowns (dzc[k] between k-1 and k, k = 0..nz; dzc[0] and dzc[nz] reach the mirrored wall
+  // ghosts).  Cell centres: the wall ghost mirrors the wall cell, dzc = dzf there.  Interior faces
+  // (z_grid 1): unknown k sits on the face between cells k and k+1, its control volume spans the two
+  // half cells, neighbouring faces are one cell apart, and a ghost at twice the wall distance with
+  // the Dirichlet sign puts w = 0 exactly on the wall face.
+  const int nz = ncell - o.z_grid;
+  std::vector<double> dz(nz), dzc(nz + 1);
+  if (o.z_grid == 0) {
+    dz = dzcell;
+    for (int k = 1; k < nz; ++k) dzc[k] = 0.5 * (dz[k - 1] + dz[k]);
+    dzc[0] = dz[0];
+    dzc[nz] = dz[nz - 1];
+  } else {
+    for (int k = 0; k < nz; ++k) dz[k] = 0.5 * (dzcell[k] + dzcell[k + 1]);
+    for (int k = 1; k < nz; ++k) dzc[k] = dzcell[k];
+    dzc[0] = 2.0 * dzcell[0];
+    dzc[nz] = 2.0 * dzcell[ncell - 1];
   }
   if (bc[2] == BC_P) {
     for (int k = 1; k < nz; ++k)
@@ -214,12 +238,16 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   cans_plan_s* P = new (std::nothrow) cans_plan_s();
   if (!P) return CANS_ERR_ARG;
   std::memcpy(P->n, n, sizeof(P->n));
+  P->n[2] = nz;
+  P->nz_cells = ncell;
   std::memcpy(P->len, len_xy, sizeof(P->len));
   std::memcpy(P->bc, bc, sizeof(P->bc));
   P->opts = o;
   P->wblk = 0;  // the blocked work-field layout measured no faster on B300; kept selectable
   cudaGetDevice(&P->device);
-  P->singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+  P->sing_bc = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+  P->shift = o.shift;
+  P->singular = P->sing_bc && P->shift == 0.0;
 
   DirHost* dirs[2] = {&P->dx, &P->dy};
   for (int d = 0; d < 2; ++d) {
@@ -252,11 +280,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->idx2 = 1.0 / (hx * hx);
   P->idy2 = 1.0 / (hy * hy);
 
-  // z grid: centre distances with mirrored wall ghosts; stencil and tridiagonal rows
-  std::vector<double> dzc(nz + 1);  // dzc[k] = distance between centres k-1 and k (k = 0..nz)
-  for (int k = 1; k < nz; ++k) dzc[k] = 0.5 * (dz[k - 1] + dz[k]);
-  dzc[0] = dz[0];
-  dzc[nz] = dz[nz - 1];
+  // z stencil and tridiagonal rows on the solved grid (dzc with the wall ghosts from above)
   std::vector<double> sa(nz), sc(nz), za(nz), zb(nz), zc(nz);
   for (int k = 0; k < nz; ++k) {
     sa[k] = 1.0 / (dz[k] * dzc[k]);
@@ -362,7 +386,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
         const size_t c = (size_t)j * n[0] + i;
-        keyed[c] = {std::fabs(P->mux_h[i] + P->muy_h[j]), (uint32_t)c};
+        keyed[c] = {std::fabs(P->mux_h[i] + P->muy_h[j] + o.shift), (uint32_t)c};
       }
     std::nth_element(keyed.begin(), keyed.begin() + (want - 1), keyed.end());
     std::vector<unsigned char> mask(ncol, 0);
@@ -432,7 +456,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->acc_d = reinterpret_cast<double*>(base + o_acc);
 
   // launch shapes
-  const int nlines = n[1] * n[2];
+  const int nlines = n[1] * nz;
   P->x_l[0] = line_launch(n[0], nlines, sizeof(double2), 16);
   P->x_l[1] = line_launch(n[0], nlines, sizeof(float2), 32);
   P->y_l[0] = line_launch(n[1], n[0], sizeof(double2), 8);
@@ -845,6 +869,19 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     if (P->opts.prec == CANS_MIXED && info[sweeps] > P->opts.tol) return CANS_ERR_NOT_CONVERGED;
   }
   return CANS_OK;
+}
+
+int cans_helmholtz_solve(cans_plan_t P, const double* f, double* p, double shift, void* workspace,
+                         void* cuda_stream, double* info) {
+  if (!P) return CANS_ERR_ARG;
+  if (!std::isfinite(shift) || shift > 0) return CANS_ERR_ARG;
+  const double shift0 = P->shift;
+  P->shift = shift;  // read by the launches of this call (kernel arguments), restored after
+  P->singular = P->sing_bc && shift == 0.0;
+  const int rc = cans_poisson_solve(P, f, p, workspace, cuda_stream, info);
+  P->shift = shift0;
+  P->singular = P->sing_bc && shift0 == 0.0;
+  return rc;
 }
 
 int cans_transform_xy(cans_plan_t P, double* field, int dir, void* cuda_stream) {

@@ -1,5 +1,5 @@
-// Reporting kernels (only run when the caller asks for residual norms): ||f - L_h p||^2 in FP64
-// (Eq. poi with a non-uniform z) and the dzf-weighted sum of f for the compatibility check of a
+// Reporting kernels (only run when the caller asks for residual norms): ||f - (L_h + shift) p||^2
+// in FP64 (Eq. poi with a non-uniform z) and the dzf-weighted sum of f for the compatibility check of a
 // singular problem.
 #include <algorithm>
 
@@ -9,7 +9,7 @@ namespace cans {
 
 __global__ void residual_norm_kernel(const double* __restrict__ f, const double* __restrict__ p, int nx, int ny, int nz,
                                      int bx, int by, int bz, double idx2, double idy2, const double* __restrict__ sa,
-                                     const double* __restrict__ sc, double* out) {
+                                     const double* __restrict__ sc, double shift, double* out) {
   const size_t N = (size_t)nx * ny * nz;
   double rr = 0, ff = 0;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
@@ -25,7 +25,8 @@ __global__ void residual_norm_kernel(const double* __restrict__ f, const double*
     const double xm = nb(bx, i == 0, c - 1, c + (nx - 1)), xp = nb(bx, i == nx - 1, c + 1, c - (nx - 1));
     const double ym = nb(by, j == 0, c - sy, c + (ny - 1) * sy), yp = nb(by, j == ny - 1, c + sy, c - (ny - 1) * sy);
     const double zm = nb(bz, k == 0, c - sz, c + (nz - 1) * sz), zp = nb(bz, k == nz - 1, c + sz, c - (nz - 1) * sz);
-    const double Lp = (xm - 2 * pc + xp) * idx2 + (ym - 2 * pc + yp) * idy2 + sc[k] * (zp - pc) + sa[k] * (zm - pc);
+    const double Lp = (xm - 2 * pc + xp) * idx2 + (ym - 2 * pc + yp) * idy2 + sc[k] * (zp - pc) + sa[k] * (zm - pc) +
+                      shift * pc;
     const double r = f[c] - Lp;
     rr += r * r;
     ff += f[c] * f[c];
@@ -63,7 +64,7 @@ cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const d
   cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   residual_norm_kernel<<<148 * 8, 256, 0, st>>>(f, p, P->n[0], P->n[1], P->n[2], P->bc[0], P->bc[1], P->bc[2], P->idx2,
-                                                 P->idy2, P->sa_d, P->sc_d, acc2);
+                                                 P->idy2, P->sa_d, P->sc_d, P->shift, acc2);
   return cudaGetLastError();
 }
 

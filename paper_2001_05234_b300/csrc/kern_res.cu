@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
           }
           L = df_add_prod(L, df_make(co.x, co.y), dp);
           L = df_add_prod(L, df_make(co.z, co.w), dm);
+          if (S.shift.hi != 0.f) L = df_add_prod(L, S.shift, df_make(p_cur, 0.f));
           // r = (f_hi - L_hi) + (f_lo - L_lo): the first difference is exact when r is small against
           // f (Sterbenz), and otherwise rounds relative to r itself
           const df fs = df_split_rz(fk);
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             const float qzm = (BZ != BC_P && k == 0) ? ghost<BZ>(q_cur) : q_prev;
             const float qzp = (BZ != BC_P && top) ? ghost<BZ>(q_cur) : q_next;
             rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
-                  co.x * (qzp - q_cur) + co.z * (qzm - q_cur);
+                  co.x * (qzp - q_cur) + co.z * (qzm - q_cur) + S.shift.hi * q_cur;
             q_prev = q_cur;
             q_cur = q_next;
             qp += sz;

@@ -349,6 +349,8 @@ StencilDF stencil_df(const cans_plan_s* P) {
   StencilDF S;
   S.idx2.hi = (float)P->idx2;
   S.idx2.lo = (float)(P->idx2 - (double)S.idx2.hi);
+  S.shift.hi = (float)P->shift;
+  S.shift.lo = (float)(P->shift - (double)S.shift.hi);
   S.idy2.hi = (float)P->idy2;
   S.idy2.lo = (float)(P->idy2 - (double)S.idy2.hi);
   S.sa_hi = P->sa_hi;

@@ -171,7 +171,8 @@ cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st) {
 }
 
 // Periodic (uniform) z: the z operator is diagonalised too.  A CTA takes nl consecutive x-slots of one
-// y-slot, transforms each column along z (real DFT), divides slot s by mu_x(i) + mu_y(j) + mu_z(s),
+// y-slot, transforms each column along z (real DFT), divides slot s by mu_x(i) + mu_y(j) + mu_z(s)
+// (+ the Helmholtz shift),
 // and transforms back (scaled by 1/Nz).  The singular (0,0,0) mode gets Nz * target, which makes the
 // column mean `target` (0, or the gauge correction of the mixed path's first sweep).
 template <typename T, int MC>
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(512, 2) zspec_kernel(T* __restrict__ w, int nx
                                                        LineTab<T> tb, const T* __restrict__ mux,
                                                        const T* __restrict__ muy, const T* __restrict__ muz,
                                                        int singular, const double* gauge, double gauge_scale,
-                                                       WLay wl) {
+                                                       T shift, WLay wl) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(512, 2) zspec_kernel(T* __restrict__ w, int nx
   }
   __syncthreads();
   line_forward<MAXV, T, MC>(buf, L, lognl, tb);
-  const T my = muy[j];
+  const T my = muy[j] + shift;
   for (int e = threadIdx.x; e < nl * NZ; e += blockDim.x) {
     const int l = e & (nl - 1), s = e >> lognl;
     const int i = i0 + l;
@@ -244,7 +245,7 @@ static cudaError_t zspec_m(const cans_plan_s* P, T* w, const double* gauge, cuda
   const T* muz = sizeof(T) == 8 ? (const T*)P->muz_d : (const T*)P->muz_f;
   zspec_kernel<T, MC><<<grid, L.threads, L.smem, st>>>(w, P->n[0], P->n[1], P->n[2], L.lognl, tab_z<T>(P), mux, muy,
                                                        muz, P->singular ? 1 : 0, gauge, P->gauge_scale,
-                                                       wlay(P, sizeof(T) == 4));
+                                                       (T)P->shift, wlay(P, sizeof(T) == 4));
   return cudaGetLastError();
 }
 

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const float muy = a.muy_f[j];
+  const float muy = a.muy_f[j] + (float)a.shift;
   for (int cidx = warp; cidx < ncols; cidx += nwarps) {
     const int i = i0 + cidx;
     if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
   tile_load<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const double muy = a.muy_d[j];
+  const double muy = a.muy_d[j] + a.shift;
   for (int cidx = warp; cidx < ncols; cidx += nwarps) {
     const int i = i0 + cidx;
     if (a.mask != nullptr && !a.mask[(size_t)j * a.nx + i]) continue;
@@ -165,6 +165,7 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
   a.ti = ti;
   a.m = P->z_m;
   a.singular = P->singular ? 1 : 0;
+  a.shift = P->shift;
   a.mask = nullptr;
   a.mux_d = P->mux_d;
   a.muy_d = P->muy_d;

@@ -24,6 +24,7 @@ struct Launch {
 // Stencil coefficients for the residual r = f - L_h p (Eq. poi with a non-uniform z).
 struct StencilDF {
   df idx2, idy2;
+  df shift;  // Helmholtz shift sigma of (L_h + sigma): 0 for Poisson
   const float *sa_hi, *sa_lo, *sc_hi, *sc_lo;  // z: a_k (to k-1), c_k (to k+1), wall ghosts included
   int bc[3];
   int n[3];
@@ -55,7 +56,8 @@ struct XArgs {
 
 struct ZArgs {
   int nx, ny, nz, ti, m;
-  int singular;               // the (0,0) mode is singular (Neumann z, no Dirichlet direction)
+  int singular;               // the (0,0) mode is singular (Neumann z, no Dirichlet direction, no shift)
+  double shift;               // Helmholtz shift added to every diagonal (0 for Poisson)
   const unsigned char* mask;  // mixed: 1 = solve this column in double
   const double* mux_d;
   const double* muy_d;
@@ -75,7 +77,10 @@ struct cans_plan_s {
   int bc[3];
   cans_opts opts;
   int device = 0;
-  bool singular = false;
+  bool sing_bc = false;   // no Dirichlet direction: singular unless shifted
+  bool singular = false;  // sing_bc and a zero shift for the solve in progress
+  double shift = 0;       // Helmholtz shift of the solve in progress (opts.shift by default)
+  int nz_cells = 0;       // cells of the caller's dzf (n[2] + 1 on the face grid)
   cans::DirHost dx, dy, dz;  // dz only for a periodic z
   std::vector<double> mux_h, muy_h;
   void* dtab = nullptr;

@@ -1,5 +1,5 @@
-// The 7-point operator of Eq. poi applied to the mixed path's iterate Phi + Plo (two float
-// fields) and subtracted from f (double): the residual of a refinement sweep, evaluated in
+// The 7-point operator of Eq. poi (plus the Helmholtz shift of Eq. up_id_2, when set) applied to
+// the mixed path's iterate Phi + Plo (two float fields) and subtracted from f (double): the residual of a refinement sweep, evaluated in
 // double-float arithmetic so that it carries about 47 significant bits although every operand is
 // read as a float (f is split on the fly).
 #pragma once
@@ -60,6 +60,7 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
   acc = df_sub_prod(acc, S.idy2, second_difference(ym, yp, pc));
   acc = df_sub_prod(acc, df_make(S.sc_hi[k], S.sc_lo[k]), two_sum(zp, -pc));
   acc = df_sub_prod(acc, df_make(S.sa_hi[k], S.sa_lo[k]), two_sum(zm, -pc));
+  if (S.shift.hi != 0.f) acc = df_sub_prod(acc, S.shift, df_make(pc, 0.f));
   float r = acc.hi + acc.lo;
   if (PLO) {
     const float* o = Plo + c;
@@ -78,7 +79,7 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
       if (k == nz - 1) qzp = wall_ghost(S.bc[2], qc);
     }
     r -= S.idx2.hi * (qxm + qxp - 2.f * qc) + S.idy2.hi * (qym + qyp - 2.f * qc) + S.sc_hi[k] * (qzp - qc) +
-         S.sa_hi[k] * (qzm - qc);
+         S.sa_hi[k] * (qzm - qc) + S.shift.hi * qc;
   }
   return r;
 }
@@ -131,6 +132,7 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
       }
       acc = df_sub_prod(acc, df_make(sca, scl), two_sum(zp, -c0));
       acc = df_sub_prod(acc, df_make(saa, sal), two_sum(zm, -c0));
+      if (S.shift.hi != 0.f) acc = df_sub_prod(acc, S.shift, df_make(c0, 0.f));
       r[e] = acc.hi + acc.lo;
     }
   }
@@ -150,7 +152,7 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
       const float zm = (wz && k == 0) ? wall_ghost(S.bc[2], c0) : zms[e];
       const float zp = (wz && k == nz - 1) ? wall_ghost(S.bc[2], c0) : zps[e];
       r[e] -= S.idx2.hi * (xms[e] + xps[e] - 2.f * c0) + S.idy2.hi * (ym + yp - 2.f * c0) + sca * (zp - c0) +
-              saa * (zm - c0);
+              saa * (zm - c0) + S.shift.hi * c0;
     }
   }
   return make_float2(r[0], r[1]);

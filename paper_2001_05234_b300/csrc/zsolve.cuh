@@ -112,7 +112,8 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   for (int r = 0; r < MMAX; ++r) {
     if (r < m - 1) {
       const int k = k0 + r;
-      C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + mu, c = sc[r * 32 + lane], d = 0;
+      // identity rows past Nz keep b = 1 (with mu added, 1 + mu could vanish)
+      C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + ((FULL || k < Nz) ? mu : (C)0), c = sc[r * 32 + lane], d = 0;
       if (FULL || k < Nz) d = cvt<C>(tile[Z.at(k, col, lane)]) - proj;
       if (SING && k == Nz - 1) {
         a = 0;
@@ -159,7 +160,8 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   // this segment's last row ties the interface unknowns together
   const int kl = k0 + m - 1;
   const int rl = m - 1;
-  C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + mu, cl = sc[rl * 32 + lane], dl = 0;
+  C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + ((FULL || kl < Nz) ? mu : (C)0), cl = sc[rl * 32 + lane];
+  C dl = 0;
   if (FULL || kl < Nz) dl = cvt<C>(tile[Z.at(kl, col, lane)]) - proj;
   if (SING && kl == Nz - 1) {
     al = 0;
