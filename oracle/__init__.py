@@ -195,6 +195,8 @@ def _bind_chan():
     L.oracle_project.argtypes = [ip, dp, dp, dp, dp, dp, dp, dp, dp, dp, ctypes.c_int]
     L.oracle_rk3_step.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   dp, dp, dp, dp, dp, ctypes.c_int]
+    L.oracle_rk3_step_implicit.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int]
     L._chan_bound = True
     return L
 
@@ -259,6 +261,20 @@ def rk3_step(u, v, w, p, nu, cfl, ubulk, length_xy, dzf, dt=0.0, nthreads=0):
     dt_out = ctypes.c_double()
     rc = L.oracle_rk3_step(_i(n), _d(Lxy), _d(dz), float(nu), float(cfl), float(ubulk), float(dt), _d(u), _d(v),
                            _d(w), _d(p), ctypes.byref(dt_out), int(nthreads))
+    if rc:
+        raise ValueError(rc)
+    return u, v, w, p, float(dt_out.value)
+
+
+def rk3_step_implicit(u, v, w, p, nu, cfl, ubulk, length_xy, dzf, dt=0.0, forcing=True, nthreads=0):
+    """One RK3 step with Crank-Nicolson diffusion (Eq. up_id, Eq. up_id_2, the projection and the
+    pressure update with -gamma nu dt/2 L Phi); returns (u, v, w, p, dt) (copies)."""
+    L = _bind_chan()
+    u, v, w, p = (_c(a).copy() for a in (u, v, w, p))
+    n, Lxy, dz = _chan_args(u.shape, length_xy, dzf)
+    dt_out = ctypes.c_double()
+    rc = L.oracle_rk3_step_implicit(_i(n), _d(Lxy), _d(dz), float(nu), float(cfl), float(ubulk), int(bool(forcing)),
+                                    float(dt), _d(u), _d(v), _d(w), _d(p), ctypes.byref(dt_out), int(nthreads))
     if rc:
         raise ValueError(rc)
     return u, v, w, p, float(dt_out.value)

@@ -679,6 +679,28 @@ double bulk_u(const Chan& g, const double* u) {
 const double RK_A[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double RK_B[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
+// The viscous operator L of the momentum equations alone: lap_t for u and v (no-slip ghosts), the
+// face-grid second difference for w (zero on both walls; the top wall face stays 0).
+void velocity_laplacian(const Chan& g, const double* u, const double* v, const double* w, double* lu, double* lv,
+                        double* lw) {
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const size_t c = g.id(i, j, k);
+        lu[c] = lap_t(g, u, i, j, k);
+        lv[c] = lap_t(g, v, i, j, k);
+        if (k == g.nz - 1) {
+          lw[c] = 0.0;
+          continue;
+        }
+        const double wc = w[c];
+        const double lx = (W(g, w, i - 1, j, k) - 2 * wc + W(g, w, i + 1, j, k)) / (g.dx * g.dx);
+        const double ly = (W(g, w, i, j - 1, k) - 2 * wc + W(g, w, i, j + 1, k)) / (g.dy * g.dy);
+        const double lz = ((W(g, w, i, j, k + 1) - wc) / g.dzf[k + 1] - (wc - W(g, w, i, j, k - 1)) / g.dzf[k]) / g.dzc[k + 1];
+        lw[c] = lx + ly + lz;
+      }
+}
+
 }  // namespace
 
 extern "C" {
@@ -768,6 +790,74 @@ int oracle_rk3_step(const int n[3], const double len_xy[2], const double* dzf, d
     pu.swap(ru);
     pv.swap(rv);
     pw.swap(rw);
+  }
+  if (dt_out) *dt_out = dt;
+  return 0;
+}
+
+// One RK3 step with implicit (Crank-Nicolson) viscous diffusion, the second form of the Numerical
+// method: per substage
+//   u** = u^k + dt (alpha A u^k + beta A u^{k-1} + gamma (-G p + nu L u^k))            (Eq. up_id)
+//   u* - gamma nu dt/2 L u* = u** - gamma nu dt/2 L u^k                                (Eq. up_id_2)
+//   L Phi = D u* / (gamma dt),  u^{k+1} = u* - gamma dt G Phi,
+//   p^{k+1/2} = p^{k-1/2} + Phi - gamma nu dt/2 L Phi,
+// A the advection alone.  Eq. up_id_2 is solved per component as the Helmholtz problem
+// (L + s) u* = s rhs with s = -2/(gamma nu dt): u and v on the cell grid with no-slip ghosts (x, y
+// periodic, z Dirichlet), w on the interior z-faces.  The pressure Laplacian of Phi has the Neumann
+// walls of the pressure.  dt as oracle_rk3_step; forcing shifts u to ubulk when forcing != 0.
+int oracle_rk3_step_implicit(const int n[3], const double len_xy[2], const double* dzf, double nu, double cfl,
+                             double ubulk, int forcing, double dt_in, double* u, double* v, double* w, double* p,
+                             double* dt_out, int nthreads) {
+  Chan g(n, len_xy, dzf);
+  const size_t N = g.size();
+  const size_t NW = (size_t)g.nx * g.ny * (g.nz - 1);  // interior z-faces
+  const double dt = (dt_in > 0) ? dt_in : stable_dt(g, nu, cfl, u, v, w);
+  std::vector<double> au(N), av(N), aw(N), pu(N, 0.0), pv(N, 0.0), pw(N, 0.0), lu(N), lv(N), lw(N);
+  std::vector<double> gx(N), gy(N), gz(N), d(N), phi(N), lphi(N), ru(N), rv(N), rw(N), z0(N, 0.0);
+  const int bcp[3] = {BC_P, BC_P, BC_NN};
+  const int bcv[3] = {BC_P, BC_P, BC_DD};
+  nthreads = nthreads_or_default(nthreads);
+  for (int s = 0; s < 3; ++s) {
+    const double a = RK_A[s], b = RK_B[s], gm = a + b;
+    const double h = gm * nu * dt / 2, sh = -1.0 / h;
+    momentum_rhs(g, 0.0, u, v, w, au.data(), av.data(), aw.data());  // advection only
+    velocity_laplacian(g, u, v, w, lu.data(), lv.data(), lw.data());
+    gradient(g, p, gx.data(), gy.data(), gz.data());
+    for (size_t c = 0; c < N; ++c) {
+      const double uss = u[c] + dt * (a * au[c] + b * pu[c] + gm * (-gx[c] + nu * lu[c]));
+      const double vss = v[c] + dt * (a * av[c] + b * pv[c] + gm * (-gy[c] + nu * lv[c]));
+      const double wss = w[c] + dt * (a * aw[c] + b * pw[c] + gm * (-gz[c] + nu * lw[c]));
+      ru[c] = sh * (uss - h * lu[c]);
+      rv[c] = sh * (vss - h * lv[c]);
+      rw[c] = sh * (wss - h * lw[c]);
+    }
+    int rc = solve_t<double>(n, len_xy, bcv, dzf, ru.data(), u, nthreads, sh, 0);
+    if (rc) return rc;
+    rc = solve_t<double>(n, len_xy, bcv, dzf, rv.data(), v, nthreads, sh, 0);
+    if (rc) return rc;
+    rc = solve_t<double>(n, len_xy, bcv, dzf, rw.data(), w, nthreads, sh, 1);  // the first Nz-1 planes
+    if (rc) return rc;
+    for (size_t c = NW; c < N; ++c) w[c] = 0.0;  // top wall face
+    divergence(g, u, v, w, d.data());
+    for (size_t c = 0; c < N; ++c) d[c] /= gm * dt;
+    rc = solve_t<double>(n, len_xy, bcp, dzf, d.data(), phi.data(), nthreads);
+    if (rc) return rc;
+    gradient(g, phi.data(), gx.data(), gy.data(), gz.data());
+    rc = apply_t<double>(n, len_xy, bcp, dzf, phi.data(), lphi.data(), nthreads);
+    if (rc) return rc;
+    for (size_t c = 0; c < N; ++c) {
+      u[c] -= gm * dt * gx[c];
+      v[c] -= gm * dt * gy[c];
+      w[c] -= gm * dt * gz[c];
+      p[c] += phi[c] - h * lphi[c];
+    }
+    if (forcing) {
+      const double shift = ubulk - bulk_u(g, u);
+      for (size_t c = 0; c < N; ++c) u[c] += shift;
+    }
+    pu.swap(au);
+    pv.swap(av);
+    pw.swap(aw);
   }
   if (dt_out) *dt_out = dt;
   return 0;
