@@ -473,19 +473,27 @@ def rk3_measure(cans, I, args):
     npts = n[0] * n[1] * n[2]
     seed = I.SEED_BASE + 4
     out = {"workload": "channel_512x256x192_Re5600_tanh1.8", "unit": "ms/step"}
-    for name, prec in (("mixed", cans.CANS_MIXED), ("fp64", cans.CANS_FP64)):
+    for name, prec, implicit in (("mixed", cans.CANS_MIXED, False), ("fp64", cans.CANS_FP64, False),
+                                 ("implicit_mixed", cans.CANS_MIXED, True)):
         u = (1.5 * (1 - (zc - 1) ** 2))[:, None, None] + 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=11).view(shape) - 1)
         v = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=12).view(shape) - 1)
         w = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=13).view(shape) - 1)
         w[-1] = 0
         p = torch.zeros_like(u)
-        ch = cans.Channel(n, L, dzf, prec=prec, sweeps=1)
+        ch = cans.Channel(n, L, dzf, prec=prec, sweeps=1, implicit=implicit)
         dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+        def step():
+            if implicit:  # fixed dt: the explicit step's CFL dt
+                ch.rk3_step_implicit(u, v, w, p, 2.0 / 5600, out["mixed_dt"], ubulk=1.0, dt_out=dt)
+            else:
+                ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0, dt_out=dt)
+
         for _ in range(2):
-            ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0, dt_out=dt)
+            step()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0, dt_out=dt)
+            step()
         g.replay()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -500,7 +508,9 @@ def rk3_measure(cans, I, args):
         ch.close()
         del u, v, w, p, g
     torch.cuda.empty_cache()
-    out["note"] = "one CUDA graph per step; mixed = Poisson solves mixed precision with 1 refinement sweep"
+    out["note"] = ("one CUDA graph per step; mixed = Poisson solves mixed precision with 1 refinement sweep; "
+                   "implicit_mixed = Crank-Nicolson diffusion (three Helmholtz solves + the Poisson solve per "
+                   "substage, mixed, 1 sweep) at the explicit step's dt")
     return out
 
 

@@ -257,6 +257,25 @@ int cans_rk3_step(cans_plan_t plan, double* u, double* v, double* w, double* p, 
                   double* dt_dev, void* workspace, void* cuda_stream);
 
 /*
+ * cans_rk3_step_implicit: one RK3 step with Crank-Nicolson viscous diffusion (the implicit variant of
+ * the Numerical method): per substage u** of Eq. up_id (advection with alpha, beta; -G p and
+ * nu L u^k with gamma), then Eq. up_id_2, u* - gamma nu dt/2 L u* = u** - gamma nu dt/2 L u^k, solved
+ * per component as (L + sigma) u* = sigma (...), sigma = -2/(gamma nu dt), with the same direct
+ * solver; then Eq. poi_ns_id, the correction, and p += Phi - gamma nu dt/2 L Phi.
+ *   plan    : the pressure plan (x, y periodic, z Neumann), as for cans_rk3_step.
+ *   uv_plan : x, y periodic, z Dirichlet, z_grid 0, same grid (the no-slip u and v).
+ *   w_plan  : x, y periodic, z Dirichlet, z_grid 1 over the same dzf (w on the interior faces).
+ *   params  : as cans_rk3_step, but params->dt must be > 0 (a fixed step: the shifts enter the
+ *             solves as launch arguments).  Plans of either precision.
+ *   workspace: cans_rk3_implicit_workspace_size() bytes, 256-byte aligned.
+ * CANS_ERR_ARG for plans that do not describe the same grid or a non-positive dt.  Asynchronous.
+ */
+int cans_rk3_implicit_workspace_size(cans_plan_t plan, cans_plan_t uv_plan, cans_plan_t w_plan, size_t* bytes);
+int cans_rk3_step_implicit(cans_plan_t plan, cans_plan_t uv_plan, cans_plan_t w_plan, double* u, double* v,
+                           double* w, double* p, const cans_rk3_params* params, double* dt_dev, void* workspace,
+                           void* cuda_stream);
+
+/*
  * cans_project: in place, u <- P u = u - G L^-1 D u, the discretely divergence-free part of a face field
  * (the correction of Eq. poi_ns with gamma dt cancelled).  cans_project_adjoint: u <- P^T u =
  * W_f P W_f^-1 u with W_f the face volumes (dzf for u and v faces, the centre distance for w faces),

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
                                                  ctypes.POINTER(vp), vp, vp, vp]
         L.cans_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
+        L.cans_rk3_implicit_workspace_size.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_rk3_step_implicit.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
         L.cans_project_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_project.argtypes = [vp, vp, vp, vp, vp, vp]
         L.cans_project_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -161,6 +163,19 @@ def cans_rk3_workspace_size(plan) -> int:
     b = ctypes.c_size_t()
     _check(lib().cans_rk3_workspace_size(plan, ctypes.byref(b)), "cans_rk3_workspace_size")
     return int(b.value)
+
+
+def cans_rk3_implicit_workspace_size(plan, uv_plan, w_plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().cans_rk3_implicit_workspace_size(plan, uv_plan, w_plan, ctypes.byref(b)),
+           "cans_rk3_implicit_workspace_size")
+    return int(b.value)
+
+
+def cans_rk3_step_implicit(plan, uv_plan, w_plan, u_ptr: int, v_ptr: int, w_ptr: int, p_ptr: int,
+                           params: cans_rk3_params, dt_dev_ptr: int, workspace_ptr: int, stream_ptr: int) -> int:
+    return lib().cans_rk3_step_implicit(plan, uv_plan, w_plan, u_ptr, v_ptr, w_ptr, p_ptr, ctypes.byref(params),
+                                        dt_dev_ptr or None, workspace_ptr, stream_ptr or None)
 
 
 def cans_rk3_step(plan, u_ptr: int, v_ptr: int, w_ptr: int, p_ptr: int, params: cans_rk3_params, dt_dev_ptr: int,
@@ -403,7 +418,7 @@ class Channel:
     """Channel flow (x, y periodic, no-slip walls in z) on one GPU: plan + workspaces for the RK3 step
     and the projection.  Velocities u, v, w and pressure p are float64 CUDA tensors (Nz, Ny, Nx)."""
 
-    def __init__(self, n, length_xy, dzf, prec=CANS_FP64, sweeps=2):
+    def __init__(self, n, length_xy, dzf, prec=CANS_FP64, sweeps=2, implicit=False):
         self.n = tuple(int(v) for v in n)
         o = cans_opts_default()
         o.prec = int(prec)
@@ -411,6 +426,23 @@ class Channel:
         _, self.plan = cans_poisson_plan(self.n, length_xy, (CANS_BC_P, CANS_BC_P, CANS_BC_NN), dzf, o)
         self._rk_buf, self._rk_ws = _aligned_workspace(cans_rk3_workspace_size(self.plan))
         self._pj_buf, self._pj_ws = _aligned_workspace(cans_project_workspace_size(self.plan))
+        self.uv_plan = self.w_plan = None
+        if implicit:  # the velocity Helmholtz plans of the Crank-Nicolson step
+            vel = (CANS_BC_P, CANS_BC_P, CANS_BC_DD)
+            _, self.uv_plan = cans_poisson_plan(self.n, length_xy, vel, dzf, o)
+            ow = cans_opts_default()
+            ow.prec, ow.max_sweeps, ow.z_grid = int(prec), int(sweeps), 1
+            _, self.w_plan = cans_poisson_plan(self.n, length_xy, vel, dzf, ow)
+            self._im_buf, self._im_ws = _aligned_workspace(
+                cans_rk3_implicit_workspace_size(self.plan, self.uv_plan, self.w_plan))
+
+    def rk3_step_implicit(self, u, v, w, p, nu, dt, ubulk=1.0, forcing=True, dt_out=None, stream=None):
+        """One RK3 step with Crank-Nicolson diffusion (cans_rk3_step_implicit); dt fixed (> 0)."""
+        prm = cans_rk3_params(float(nu), 1.0, float(ubulk), float(dt), 1 if forcing else 0)
+        st = cans_rk3_step_implicit(self.plan, self.uv_plan, self.w_plan, u.data_ptr(), v.data_ptr(), w.data_ptr(),
+                                    p.data_ptr(), prm, dt_out.data_ptr() if dt_out is not None else 0, self._im_ws,
+                                    _stream_ptr(stream))
+        _check(st, "cans_rk3_step_implicit")
 
     def rk3_step(self, u, v, w, p, nu, cfl=0.9, ubulk=1.0, dt=0.0, forcing=True, dt_out=None, stream=None):
         prm = cans_rk3_params(float(nu), float(cfl), float(ubulk), float(dt), 1 if forcing else 0)
@@ -425,9 +457,10 @@ class Channel:
         return u, v, w
 
     def close(self):
-        if getattr(self, "plan", None):
-            cans_plan_destroy(self.plan)
-            self.plan = None
+        for name in ("plan", "uv_plan", "w_plan"):
+            if getattr(self, name, None):
+                cans_plan_destroy(getattr(self, name))
+                setattr(self, name, None)
 
     def __del__(self):
         try:

@@ -9,6 +9,9 @@
 // 3-point Laplacian with no-slip ghosts (ghost = -interior).  Everything in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+
 #include "plan.cuh"
 
 namespace cans {
@@ -52,11 +55,15 @@ __device__ __forceinline__ double lap_t(const Chan& g, const double* a, int i, i
 
 // Momentum right-hand side A(u) + nu L(u) (Eq. up) and the predictor
 //   u* = u + dt (alpha rhs + beta rhs_prev - gamma G p).  rhs replaces rhs_prev in place.
+// IMPL (Crank-Nicolson diffusion, Eq. up_id and Eq. up_id_2): rhs = A(u) alone, and us receives the
+// right-hand side of the Helmholtz problem (L + sigma) u* = sigma (u** - gamma nu dt/2 L u), sigma =
+// -2/(gamma nu dt), which is sigma (u + dt (alpha A + beta A_prev - gamma G p)) - L u.
+template <bool IMPL>
 __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const double* __restrict__ v,
                                 const double* __restrict__ w, const double* __restrict__ p, double* __restrict__ ru,
                                 double* __restrict__ rv, double* __restrict__ rw, double* __restrict__ us,
                                 double* __restrict__ vs, double* __restrict__ ws, double nu, double alpha, double beta,
-                                double gamma, const double* __restrict__ dt_dev) {
+                                double gamma, const double* __restrict__ dt_dev, double sigma) {
   // The same discrete operator as written term by term (two-point averages, products, differences),
   // arranged for fewer FP64 operations (B300 issues FP64 at 1/64 of FP32): the 1/2 x 1/2 factors of
   // the averaged products and 1/dx^2 are folded into constants, (ue^2 - uw^2) is formed as
@@ -68,7 +75,7 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((size_t)g.nx * g.ny));
     const double qdz = 0.25 * g.dzfi[k], dzfi = g.dzfi[k], dzc_up = g.dzci[k], dzc_dn = dzc_inv_below(g, k);
     const double uc = u[c], vc = v[c];
-    double r_u, r_v, r_w;
+    double r_u, r_v, r_w, l_u, l_v, l_w = 0.0;
     {  // u at (i+1/2, j, k)
       const double ue = u[g.id(i + 1, j, k)], uw = u[g.id(i - 1, j, k)];
       const double un = u[g.id(i, j + 1, k)], uS = u[g.id(i, j - 1, k)];
@@ -81,7 +88,8 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
       const double adv = fma(qdx, ax, fma(qdy, ay, qdz * az));
       const double lz = fma(ut - uc, dzc_up, -(uc - ub) * dzc_dn) * dzfi;
       const double lap = fma(dx2, fma(-2.0, uc, ue + uw), fma(dy2, fma(-2.0, uc, un + uS), lz));
-      r_u = fma(nu, lap, -adv);
+      r_u = IMPL ? -adv : fma(nu, lap, -adv);
+      l_u = lap;
     }
     {  // v at (i, j+1/2, k)
       const double ve = v[g.id(i + 1, j, k)], vw = v[g.id(i - 1, j, k)];
@@ -95,7 +103,8 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
       const double adv = fma(qdx, ax, fma(qdy, ay, qdz * az));
       const double lz = fma(vt - vc, dzc_up, -(vc - vb) * dzc_dn) * dzfi;
       const double lap = fma(dx2, fma(-2.0, vc, ve + vw), fma(dy2, fma(-2.0, vc, vn + vS), lz));
-      r_v = fma(nu, lap, -adv);
+      r_v = IMPL ? -adv : fma(nu, lap, -adv);
+      l_v = lap;
     }
     if (k == g.nz - 1) {
       r_w = 0.0;
@@ -113,7 +122,8 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
       const double adv = fma(qdx, ax, fma(qdy, ay, qdzc * az));
       const double lz = fma(wt - wc, g.dzfi[k + 1], -(wc - wb) * dzfi) * dzc_up;
       const double lap = fma(dx2, fma(-2.0, wc, we + ww), fma(dy2, fma(-2.0, wc, wn + wS), lz));
-      r_w = fma(nu, lap, -adv);
+      r_w = IMPL ? -adv : fma(nu, lap, -adv);
+      l_w = lap;
     }
     const double pc = p[c];
     const double gx = (p[g.id(i + 1, j, k)] - pc) * g.dxi;
@@ -125,9 +135,15 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
       sv = fma(beta, rv[c], sv);
       sw = fma(beta, rw[c], sw);
     }
-    us[c] = fma(dt, fma(-gamma, gx, su), uc);
-    vs[c] = fma(dt, fma(-gamma, gy, sv), vc);
-    ws[c] = (k < g.nz - 1) ? fma(dt, fma(-gamma, gz, sw), w[c]) : 0.0;
+    if (IMPL) {
+      us[c] = fma(sigma, fma(dt, fma(-gamma, gx, su), uc), -l_u);
+      vs[c] = fma(sigma, fma(dt, fma(-gamma, gy, sv), vc), -l_v);
+      ws[c] = (k < g.nz - 1) ? fma(sigma, fma(dt, fma(-gamma, gz, sw), w[c]), -l_w) : 0.0;
+    } else {
+      us[c] = fma(dt, fma(-gamma, gx, su), uc);
+      vs[c] = fma(dt, fma(-gamma, gy, sv), vc);
+      ws[c] = (k < g.nz - 1) ? fma(dt, fma(-gamma, gz, sw), w[c]) : 0.0;
+    }
     ru[c] = r_u;
     rv[c] = r_v;
     rw[c] = r_w;
@@ -159,10 +175,12 @@ __global__ void divergence_kernel(Chan g, const double* __restrict__ u, const do
 // u = u* - gamma dt G Phi (Eq. poi_ns correction), p += Phi when p != nullptr, and the dzf-weighted
 // sum of the new u into *bulk (for the constant-flow-rate forcing).  Adjoint use (weighted): the
 // gradient is multiplied by the face weight.
+// Crank-Nicolson diffusion (Eq. up_id_2): p += Phi + lcoef L_p Phi with lcoef = -gamma nu dt/2 and L_p
+// the pressure Laplacian (periodic x, y; Neumann walls).
 __global__ void correct_kernel(Chan g, const double* __restrict__ us, const double* __restrict__ vs,
                                const double* __restrict__ ws, const double* __restrict__ phi, double* __restrict__ u,
                                double* __restrict__ v, double* __restrict__ w, double* __restrict__ p, double gamma,
-                               const double* __restrict__ dt_dev, int weighted, double* bulk) {
+                               const double* __restrict__ dt_dev, int weighted, double* bulk, double lcoef) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const double f = (dt_dev != nullptr) ? gamma * (*dt_dev) : 1.0;
   double acc = 0.0;
@@ -181,7 +199,19 @@ __global__ void correct_kernel(Chan g, const double* __restrict__ us, const doub
     u[c] = un;
     v[c] = vs[c] - f * gy;
     w[c] = (k < g.nz - 1) ? ws[c] - f * gz : 0.0;
-    if (p != nullptr) p[c] += pc;
+    if (p != nullptr) {
+      double dp = pc;
+      if (lcoef != 0.0) {
+        const double pxm = phi[g.id(i - 1, j, k)], pxp = phi[g.id(i + 1, j, k)];
+        const double pym = phi[g.id(i, j - 1, k)], pyp = phi[g.id(i, j + 1, k)];
+        const double fup = (k < g.nz - 1) ? (phi[g.id(i, j, k + 1)] - pc) * g.dzci[k] : 0.0;
+        const double fdn = (k > 0) ? (pc - phi[g.id(i, j, k - 1)]) * g.dzci[k - 1] : 0.0;
+        const double lap = (pxm - 2 * pc + pxp) * g.dxi * g.dxi + (pym - 2 * pc + pyp) * g.dyi * g.dyi +
+                           (fup - fdn) * g.dzfi[k];
+        dp = fma(lcoef, lap, pc);
+      }
+      p[c] += dp;
+    }
     acc += g.dzf[k] * un;
   }
   if (bulk != nullptr) {
@@ -260,10 +290,16 @@ static int grid_for(size_t N) {
 
 cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double* v, const double* w, const double* p,
                             double* ru, double* rv, double* rw, double* us, double* vs, double* ws, double nu,
-                            double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st) {
+                            double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st,
+                            double sigma) {
   const Chan g = chan(P);
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  momentum_kernel<<<grid_for(N), 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma, dt_dev);
+  if (sigma != 0.0)
+    momentum_kernel<true><<<grid_for(N), 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
+                                                       dt_dev, sigma);
+  else
+    momentum_kernel<false><<<grid_for(N), 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
+                                                        dt_dev, 0.0);
   return cudaGetLastError();
 }
 
@@ -277,10 +313,10 @@ cudaError_t launch_divergence(const cans_plan_s* P, const double* u, const doubl
 
 cudaError_t launch_correct(const cans_plan_s* P, const double* us, const double* vs, const double* ws,
                            const double* phi, double* u, double* v, double* w, double* p, double gamma,
-                           const double* dt_dev, int weighted, double* bulk, cudaStream_t st) {
+                           const double* dt_dev, int weighted, double* bulk, cudaStream_t st, double lcoef) {
   const Chan g = chan(P);
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  correct_kernel<<<grid_for(N), 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gamma, dt_dev, weighted, bulk);
+  correct_kernel<<<grid_for(N), 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gamma, dt_dev, weighted, bulk, lcoef);
   return cudaGetLastError();
 }
 
@@ -373,6 +409,78 @@ int cans_rk3_step(cans_plan_t P, double* u, double* v, double* w, double* p, con
     double* bulk = prm->forcing ? small + 1 : nullptr;
     if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
     RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st));
+    if (bulk) RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
+  }
+  return CANS_OK;
+}
+
+// The velocity plans of the implicit step must describe the pressure plan's grid: (P, P, DD) with
+// the same Nx, Ny, lengths; uv on the cell grid of the same dzf, w on its interior faces.
+static bool implicit_plans_match(const cans_plan_s* P, const cans_plan_s* U, const cans_plan_s* W) {
+  if (!U || !W) return false;
+  const int nz = P->n[2];
+  for (const cans_plan_s* Q : {U, W}) {
+    if (Q->n[0] != P->n[0] || Q->n[1] != P->n[1] || Q->len[0] != P->len[0] || Q->len[1] != P->len[1]) return false;
+    if (Q->bc[0] != BC_P || Q->bc[1] != BC_P || Q->bc[2] != BC_DD) return false;
+  }
+  if (U->opts.z_grid != 0 || U->n[2] != nz || W->opts.z_grid != 1 || W->nz_cells != nz) return false;
+  for (int k = 0; k < nz; ++k)
+    if (std::fabs(U->dzf_h[k] - P->dzf_h[k]) > 1e-14 * P->dzf_h[k]) return false;
+  for (int k = 0; k + 1 < nz; ++k) {
+    const double mid = 0.5 * (P->dzf_h[k] + P->dzf_h[k + 1]);
+    if (std::fabs(W->dzf_h[k] - mid) > 1e-14 * mid) return false;
+  }
+  return true;
+}
+
+int cans_rk3_implicit_workspace_size(cans_plan_t P, cans_plan_t U, cans_plan_t W, size_t* bytes) {
+  if (!P || !U || !W || !bytes) return CANS_ERR_ARG;
+  const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+  size_t pws = 0, b = 0;
+  for (const cans_plan_s* Q : {P, U, W}) {
+    cans_poisson_workspace_size(const_cast<cans_plan_t>(Q), &b);
+    pws = std::max(pws, b);
+  }
+  *bytes = 10 * a256(N * sizeof(double)) + 256 + a256(pws);
+  return CANS_OK;
+}
+
+int cans_rk3_step_implicit(cans_plan_t P, cans_plan_t U, cans_plan_t W, double* u, double* v, double* w, double* p,
+                           const cans_rk3_params* prm, double* dt_dev, void* workspace, void* cuda_stream) {
+  if (!P || !u || !v || !w || !p || !prm || !workspace) return CANS_ERR_ARG;
+  if (!is_channel(P)) return CANS_ERR_UNSUPPORTED;
+  if (!implicit_plans_match(P, U, W)) return CANS_ERR_ARG;
+  if (!(prm->nu > 0) || !(prm->dt > 0) || !std::isfinite(prm->dt)) return CANS_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return CANS_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t N = (size_t)P->n[0] * P->n[1] * P->n[2];
+  const size_t fb = a256(N * sizeof(double));
+  unsigned char* base = static_cast<unsigned char*>(workspace);
+  double* F[10];
+  for (int q = 0; q < 10; ++q) F[q] = reinterpret_cast<double*>(base + q * fb);
+  double *us = F[0], *vs = F[1], *ws = F[2], *ru = F[3], *rv = F[4], *rw = F[5], *fu = F[6], *fv = F[7], *fw = F[8];
+  double* phi = F[9];
+  double* f = fu;  // the divergence reuses the first Helmholtz right-hand side
+  double* small = reinterpret_cast<double*>(base + 10 * fb);  // [0] dt, [1] bulk sum, [2] dti bits
+  void* pws = base + 10 * fb + 256;
+  double* dt = dt_dev ? dt_dev : small;
+  RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt, st));
+  for (int s = 0; s < 3; ++s) {
+    const double a = RK_ALPHA[s], b = RK_BETA[s], g = a + b;
+    const double h = g * prm->nu * prm->dt / 2, sigma = -1.0 / h;
+    RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, fu, fv, fw, prm->nu, a, b, g, dt, st, sigma));
+    int rc = cans_helmholtz_solve(U, fu, us, sigma, pws, cuda_stream, nullptr);
+    if (rc == CANS_OK) rc = cans_helmholtz_solve(U, fv, vs, sigma, pws, cuda_stream, nullptr);
+    if (rc == CANS_OK) rc = cans_helmholtz_solve(W, fw, ws, sigma, pws, cuda_stream, nullptr);
+    if (rc != CANS_OK) return rc;
+    RK_CK(cudaMemsetAsync(ws + (size_t)P->n[0] * P->n[1] * (P->n[2] - 1), 0,
+                          sizeof(double) * P->n[0] * P->n[1], st));  // the top wall face
+    RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
+    rc = cans_poisson_solve(P, f, phi, pws, cuda_stream, nullptr);
+    if (rc != CANS_OK) return rc;
+    double* bulk = prm->forcing ? small + 1 : nullptr;
+    if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
+    RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st, -h));
     if (bulk) RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
   }
   return CANS_OK;

@@ -147,12 +147,13 @@ cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const d
 cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st);
 cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double* v, const double* w, const double* p,
                             double* ru, double* rv, double* rw, double* us, double* vs, double* ws, double nu,
-                            double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st);
+                            double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st,
+                            double sigma = 0.0);
 cudaError_t launch_divergence(const cans_plan_s* P, const double* u, const double* v, const double* w, double* f,
                               double scale_num, const double* dt_dev, double gamma, int weighted, cudaStream_t st);
 cudaError_t launch_correct(const cans_plan_s* P, const double* us, const double* vs, const double* ws,
                            const double* phi, double* u, double* v, double* w, double* p, double gamma,
-                           const double* dt_dev, int weighted, double* bulk, cudaStream_t st);
+                           const double* dt_dev, int weighted, double* bulk, cudaStream_t st, double lcoef = 0.0);
 cudaError_t launch_forcing(const cans_plan_s* P, double* u, const double* bulk, double ubulk, cudaStream_t st);
 cudaError_t launch_chkdt(const cans_plan_s* P, const double* u, const double* v, const double* w,
                          unsigned long long* dti_bits, double* dt_dev, double cfl, double nu, double dt_fixed,

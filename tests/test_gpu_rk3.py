@@ -231,3 +231,54 @@ def test_config4_channel_step_matches_oracle(cans):
     for got, want in zip(t[:3], (ou, ov, ow)):
         assert rel(host(got), want) <= 1e-11
     ch.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-10)])
+def test_rk3_step_implicit_matches_oracle(cans, prec, tol):
+    """cans_rk3_step_implicit (Crank-Nicolson diffusion, Eq. up_id / up_id_2: three Helmholtz solves per
+    substage, w on the interior z-faces) against the oracle's implicit step, a low-Reynolds channel
+    with a fixed dt ten times the explicit viscous limit."""
+    import torch
+
+    shape, L = (16, 12, 24), (2.0, 1.0)
+    dzf = I.tanh_dzf(16, 1.8, 2.0)
+    u, v, w = channel_state(shape, L, dzf, 21)
+    u, v, w = oracle.project(u, v, w, L, dzf)[:3]
+    p = 0.05 * I.uniform(22, shape, -1, 1)
+    nu = 0.05
+    dl = min(L[0] / 24, L[1] / 12, float(dzf.min()))
+    dt = 10 * 1.65 * dl * dl / nu
+    ch = cans.Channel((24, 12, 16), L, dzf, prec=prec, implicit=True)
+    tu, tv, tw, tp = dev(u), dev(v), dev(w), dev(p)
+    for _ in range(2):
+        ch.rk3_step_implicit(tu, tv, tw, tp, nu, dt, ubulk=1.0)
+    ou, ov, ow, op = u, v, w, p
+    for _ in range(2):
+        ou, ov, ow, op, _ = oracle.rk3_step_implicit(ou, ov, ow, op, nu, 0.5, 1.0, L, dzf, dt=dt)
+    for got, want in ((host(tu), ou), (host(tv), ov), (host(tw), ow)):
+        assert rel(got, want) <= tol, rel(got, want)
+    assert np.all(host(tw)[-1] == 0.0)
+    gp, wp = host(tp), op
+    wgt = dzf[:, None, None] * np.ones(shape)
+    gp = gp - (gp * wgt).sum() / wgt.sum()
+    wp = wp - (wp * wgt).sum() / wgt.sum()
+    assert rel(gp, wp) <= 100 * tol, rel(gp, wp)
+    d = oracle.divergence(host(tu), host(tv), host(tw), L, dzf)
+    assert np.abs(d).max() <= 1e-9
+    ch.close()
+
+
+def test_rk3_step_implicit_argument_checks(cans):
+    import torch
+
+    shape, L = (8, 8, 8), (1.0, 1.0)
+    dzf = I.tanh_dzf(8, 1.5, 2.0)
+    ch = cans.Channel((8, 8, 8), L, dzf, implicit=True)
+    t = [torch.zeros(shape, dtype=torch.float64, device="cuda") for _ in range(4)]
+    prm = cans.cans_rk3_params(0.1, 0.5, 1.0, 0.0, 1)  # dt = 0: the implicit step needs a fixed dt
+    st = cans.cans_rk3_step_implicit(ch.plan, ch.uv_plan, ch.w_plan, *(x.data_ptr() for x in t), prm, 0, ch._im_ws, 0)
+    assert st == cans.CANS_ERR_ARG
+    prm = cans.cans_rk3_params(0.1, 0.5, 1.0, 1e-3, 1)
+    st = cans.cans_rk3_step_implicit(ch.plan, ch.w_plan, ch.uv_plan, *(x.data_ptr() for x in t), prm, 0, ch._im_ws, 0)
+    assert st == cans.CANS_ERR_ARG  # plans swapped
+    ch.close()
