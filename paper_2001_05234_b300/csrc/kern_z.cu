@@ -91,16 +91,18 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
                                                            WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
+  constexpr bool CL = MMAX >= 4;  // lane-contiguous coefficient rows, four per 16-byte load
+  const int rs = CL ? 32 * (m + 4) : 32 * m;
   float* sa = reinterpret_cast<float*>(smem_raw);
-  float* sb = sa + 32 * m;
-  float* sc = sb + 32 * m;
-  float* tile = sc + 32 * m;
+  float* sb = sa + rs;
+  float* sc = sb + rs;
+  float* tile = sc + rs;
   const int i0 = blockIdx.x * TI, j = blockIdx.y;
   const size_t plane = wl.zstride();
   float* col0 = w + wl.zbase(i0, j);
   const int ncols = min(TI, a.nx - i0);
   const auto Z = make_zswz<TIC, MMAX>(TI, m);
-  stage_zrows<float, float>(sa, sb, sc, zf, a.nz, m);
+  stage_zrows<CL>(sa, sb, sc, zf, a.nz, m);
   tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -109,10 +111,11 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
     const int i = i0 + cidx;
     if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
     if (a.nz == 32 * MMAX)
-      zsolve_column<MMAX, float, float, false, decltype(Z), true>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc,
-                                                                  nullptr, 0.f);
+      zsolve_column<MMAX, float, float, false, decltype(Z), true, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
+                                                                      sc, nullptr, 0.f);
     else
-      zsolve_column<MMAX, float, float, false>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc, nullptr, 0.f);
+      zsolve_column<MMAX, float, float, false, decltype(Z), false, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
+                                                                       sc, nullptr, 0.f);
   }
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     if (!any) return;
   }
   const auto Z = make_zswz<TIC, MMAX>(TI, m);
-  stage_zrows<double, double>(sa, sb, sc, zd, a.nz, m);
+  stage_zrows<false>(sa, sb, sc, zd, a.nz, m);
   tile_load<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -190,7 +193,7 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
     if (part != 1) {
       ZArgs a = zargs(P, P->z_ti[1], gauge);
       a.mask = P->mask_d;
-      const size_t smem = 3 * 32 * a.m * sizeof(float) + P->z_smem[1];
+      const size_t smem = 3 * 32 * (a.m + 4) * sizeof(float) + P->z_smem[1];
       e = set_smem((const void*)zpass_f32_kernel<MMAX, TIC>, smem);
       if (e != cudaSuccess) return e;
       dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);

@@ -60,18 +60,26 @@ __device__ __forceinline__ ZSwz<TI_, M_> make_zswz(int TI, int m) {
   return s;
 }
 
-// Per-CTA copy of the z rows in lane-major order: row k = lane*m + r sits at [r*32 + lane], so the 32
-// lanes of a warp read 32 consecutive words.  Rows past Nz become identity rows (a = c = 0, b = 1).
-template <typename C, typename S>
+// Per-CTA copy of the z rows.  Row k = lane*m + r of a lane's segment sits at [r*32 + lane] (the 32
+// lanes of a warp read 32 consecutive words), or, with CL (float rows, m >= 4), at
+// [lane*(m+4) + r]: each lane's rows are contiguous, so four rows come in one 16-byte load, and the
+// padded lane stride keeps every quarter-warp's 16-byte loads on distinct banks.  Rows past Nz become
+// identity rows (a = c = 0, b = 1).
+template <bool CL = false, typename C, typename S>
 __device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& zt, int Nz, int m) {
   for (int q = threadIdx.x; q < 32 * m; q += blockDim.x) {
     const int lane = q & 31, r = q >> 5;
     const int k = lane * m + r;
     const bool in = k < Nz;
-    sa[q] = in ? (C)zt.a[k] : (C)0;
-    sb[q] = in ? (C)zt.b[k] : (C)1;
-    sc[q] = in ? (C)zt.c[k] : (C)0;
+    const int at = CL ? lane * (m + 4) + r : q;
+    sa[at] = in ? (C)zt.a[k] : (C)0;
+    sb[at] = in ? (C)zt.b[k] : (C)1;
+    sc[at] = in ? (C)zt.c[k] : (C)0;
   }
+}
+
+__device__ __forceinline__ float f4_get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
 // Solve one column (tile column `col`) in precision C with rows staged by stage_zrows.  FULL: the
@@ -79,11 +87,30 @@ __device__ __forceinline__ void stage_zrows(C* sa, C* sb, C* sc, const ZTab<S>& 
 // mu is the x-y eigenvalue term of the mode.  SING: the singular Neumann mode -- the right-hand side
 // is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
 // x = 0, and the result is shifted to the dzf-weighted mean `target`.
-template <int MMAX, typename C, typename T, bool SING, typename ZS, bool FULL = false>
+template <int MMAX, typename C, typename T, bool SING, typename ZS, bool FULL = false, bool CL = false>
 __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int Nz, C mu, const C* sa,
                                               const C* sb, const C* sc, const double* weights, C target) {
   const int lane = threadIdx.x & 31;
   constexpr int m = MMAX;  // rows per lane (compile time: keeps the row arrays in registers)
+  static_assert(!CL || (MMAX >= 4 && sizeof(C) == 4), "lane-contiguous rows: float, four rows per load");
+  constexpr int LS = MMAX + 4;
+  float4 A4, B4, C4;  // CL: rows r .. r+3 of this lane's coefficients
+  auto coefs = [&](int r, C& a, C& b, C& c) {
+    if constexpr (CL) {
+      if ((r & 3) == 0) {
+        A4 = *reinterpret_cast<const float4*>(sa + lane * LS + r);
+        B4 = *reinterpret_cast<const float4*>(sb + lane * LS + r);
+        C4 = *reinterpret_cast<const float4*>(sc + lane * LS + r);
+      }
+      a = f4_get(A4, r & 3);
+      b = f4_get(B4, r & 3);
+      c = f4_get(C4, r & 3);
+    } else {
+      a = sa[r * 32 + lane];
+      b = sb[r * 32 + lane];
+      c = sc[r * 32 + lane];
+    }
+  };
   const int k0 = lane * m;
   const unsigned full = 0xffffffffu;
   C proj = 0;
@@ -113,7 +140,9 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
     if (r < m - 1) {
       const int k = k0 + r;
       // identity rows past Nz keep b = 1 (with mu added, 1 + mu could vanish)
-      C a = sa[r * 32 + lane], b = sb[r * 32 + lane] + ((FULL || k < Nz) ? mu : (C)0), c = sc[r * 32 + lane], d = 0;
+      C a, b, c, d = 0;
+      coefs(r, a, b, c);
+      b += (FULL || k < Nz) ? mu : (C)0;
       if (FULL || k < Nz) d = cvt<C>(tile[Z.at(k, col, lane)]) - proj;
       if (SING && k == Nz - 1) {
         a = 0;
@@ -160,8 +189,15 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   // this segment's last row ties the interface unknowns together
   const int kl = k0 + m - 1;
   const int rl = m - 1;
-  C al = sa[rl * 32 + lane], bl = sb[rl * 32 + lane] + ((FULL || kl < Nz) ? mu : (C)0), cl = sc[rl * 32 + lane];
-  C dl = 0;
+  C al, bl, cl, dl = 0;
+  if (CL && ((m - 1) & 3) != 0) {  // the last row's group of four was loaded by the forward loop
+    al = f4_get(A4, rl & 3);
+    bl = f4_get(B4, rl & 3);
+    cl = f4_get(C4, rl & 3);
+  } else {
+    coefs(rl, al, bl, cl);
+  }
+  bl += (FULL || kl < Nz) ? mu : (C)0;
   if (FULL || kl < Nz) dl = cvt<C>(tile[Z.at(kl, col, lane)]) - proj;
   if (SING && kl == Nz - 1) {
     al = 0;
