@@ -20,6 +20,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.cpp")
 
 BC_P, BC_NN, BC_DD = 0, 1, 2
+BC_ND, BC_DN = 3, 4  # z only: Neumann low / Dirichlet high wall, and the reverse
 
 
 def build(force: bool = False) -> str:

@@ -24,7 +24,13 @@
 
 namespace {
 
-enum { BC_P = 0, BC_NN = 1, BC_DD = 2 };
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };
+// ND / DN (z only): Neumann at the low wall and Dirichlet at the high wall, or the reverse -- the
+// remaining cell-centred wall combinations of the Numerical method's transform list.  The wall rule
+// of each end of a direction:
+inline int bc_low(int bc) { return (bc == BC_ND) ? BC_NN : (bc == BC_DN ? BC_DD : bc); }
+inline int bc_high(int bc) { return (bc == BC_ND) ? BC_DD : (bc == BC_DN ? BC_NN : bc); }
+inline bool has_dirichlet(int bc) { return bc == BC_DD || bc == BC_ND || bc == BC_DN; }
 
 // Deliberate-mistake switch used only by the mutation tests (tests/test_oracle_mutations.py): each
 // value plants one plausible error so the tests can show that some pin catches it.  0 = correct.
@@ -114,8 +120,8 @@ void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const Z
         const T xp = (i < nx - 1) ? p[c + sx] : ghost<T>(bc[0], pc, p[c - (nx - 1) * sx]);
         const T ym = (j > 0) ? p[c - sy] : ghost<T>(bc[1], pc, p[c + (ny - 1) * sy]);
         const T yp = (j < ny - 1) ? p[c + sy] : ghost<T>(bc[1], pc, p[c - (ny - 1) * sy]);
-        const T zm = (k > 0) ? p[c - sz] : ghost<T>(bc[2], pc, p[c + (nz - 1) * sz]);
-        const T zp = (k < nz - 1) ? p[c + sz] : ghost<T>(bc[2], pc, p[c - (nz - 1) * sz]);
+        const T zm = (k > 0) ? p[c - sz] : ghost<T>(bc_low(bc[2]), pc, p[c + (nz - 1) * sz]);
+        const T zp = (k < nz - 1) ? p[c + sz] : ghost<T>(bc_high(bc[2]), pc, p[c - (nz - 1) * sz]);
         const T lx = (xm - 2 * pc + xp) * idx2;
         const T ly = (ym - 2 * pc + yp) * idy2;
         T lz;
@@ -207,12 +213,11 @@ void z_rows(const ZGrid<T>& zg, std::vector<T>& a, std::vector<T>& b, std::vecto
     c[k] = 1 / (zg.dzf[k] * zg.dzc[k + 1]);
     b[k] = -(a[k] + c[k]);
   }
-  if (zg.bc == BC_NN) {  // ghost equals the wall cell: that flux vanishes
-    b[0] += a[0];
-    b[nz - 1] += c[nz - 1];
-  } else if (zg.bc == BC_DD) {  // ghost is minus the wall cell
-    b[0] -= a[0];
-    b[nz - 1] -= c[nz - 1];
+  if (zg.bc != BC_P) {
+    // Neumann end: the ghost equals the wall cell and that flux vanishes; Dirichlet end: the ghost is
+    // minus the wall cell
+    b[0] += (bc_low(zg.bc) == BC_NN) ? a[0] : -a[0];
+    b[nz - 1] += (bc_high(zg.bc) == BC_NN) ? c[nz - 1] : -c[nz - 1];
   }
   if (zg.bc != BC_P) {
     a[0] = 0;
@@ -281,7 +286,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
     }
   }
 
-  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD) && shift == 0;
+  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && !has_dirichlet(bc[2]) && shift == 0;
   if (bc[2] == BC_P) {
     // uniform periodic z: diagonalise z as well (checked by the caller)
     eigenbasis<T>(BC_P, nz, Ez, lz);
@@ -368,7 +373,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
 int check_args(const int n[3], const int bc[3], const double* dzf) {
   for (int d = 0; d < 3; ++d) {
     if (n[d] < 1) return -1;
-    if (bc[d] < 0 || bc[d] > 2) return -1;
+    if (bc[d] < 0 || bc[d] > (d == 2 ? 4 : 2)) return -1;  // the mixed wall pairs along z only
   }
   for (int k = 0; k < n[2]; ++k)
     if (!(dzf[k] > 0) || !std::isfinite(dzf[k])) return -1;
@@ -485,7 +490,7 @@ int oracle_eigenbasis(int bc, int n, double* E, double* lam) {
 
 // Rows of the z operator for one mode: a_k p_{k-1} + b_k p_k + c_k p_{k+1}; a_0 = c_{nz-1} = 0 at walls.
 int oracle_z_rows(int bc_z, int nz, const double* dzf, double* a, double* b, double* c) {
-  if (nz < 1 || bc_z < 0 || bc_z > 2) return -1;
+  if (nz < 1 || bc_z < 0 || bc_z > 4) return -1;
   ZGrid<double> zg(nz, bc_z, dzf);
   std::vector<double> va, vb, vc;
   z_rows<double>(zg, va, vb, vc);

@@ -22,6 +22,7 @@ M2 = 0x94D049BB133111EB
 MASK64 = (1 << 64) - 1
 
 BC_P, BC_NN, BC_DD = 0, 1, 2
+BC_ND, BC_DN = 3, 4  # z only: Neumann low / Dirichlet high wall, and the reverse
 BC_NAMES = {BC_P: "P", BC_NN: "NN", BC_DD: "DD"}
 
 SEED_BASE = 2001052340  # config c draws from seed SEED_BASE + c

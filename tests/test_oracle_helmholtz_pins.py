@@ -1,10 +1,12 @@
 """Pins of the oracle's Helmholtz form (L_h + sigma) p = f (Eq. up_id_2, the implicit-diffusion step
 solved "with the same type of direct solver" as the pressure) and of its face grid for a staggered
-w (unknowns on the interior z-faces, w = 0 on the wall faces).
+w (unknowns on the interior z-faces, w = 0 on the wall faces), and of the mixed Neumann / Dirichlet
+wall pairs along z.
 
 Independent facts used: closed-form discrete eigenpairs (periodic cosines, the cell-centred
 Neumann / Dirichlet cosines and sines, and the node-Dirichlet sines of the face grid, whose
-eigenvalues are -4 sin^2(pi m / 2N) / h^2), numpy dense LU of the operator assembled from the
+eigenvalues are -4 sin^2(pi m / 2N) / h^2, and the quarter-wave cosines / sines of a mixed wall
+pair), numpy dense LU of the operator assembled from the
 stencil, the oracle's separate channel w-diffusion (the viscous part of the momentum right-hand
 side), and a re-run in __float128.
 """
@@ -127,3 +129,50 @@ def test_zero_shift_is_the_poisson_solve():
     a = oracle.helmholtz_solve(f, (P, P, NN), (1.0, 1.0), dzf, shift=0.0)
     b = oracle.poisson_solve(f, (P, P, NN), (1.0, 1.0), dzf)
     np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------------------------
+# mixed walls along z: Neumann at the low wall and Dirichlet at the high wall (ND), or the reverse
+# ---------------------------------------------------------------------------------------------
+ND, DN = oracle.BC_ND, oracle.BC_DN
+
+
+@pytest.mark.parametrize("bcz", [ND, DN])
+@pytest.mark.parametrize("m", [0, 3])
+def test_mixed_wall_quarter_wave_eigenfunction(bcz, m):
+    """Uniform z with a Neumann and a Dirichlet wall: the eigenvectors are the quarter-wave cosines
+    cos(pi (m + 1/2)(k + 1/2) / N) (ND) or sines sin(...) (DN), eigenvalues -4 sin^2(pi (2m+1) / 4N) / h^2."""
+    nx, ny, nz = 6, 4, 10
+    h = 1.0 / nz
+    k = np.arange(nz)
+    th = np.pi * (m + 0.5) * (k + 0.5) / nz
+    fz = np.cos(th) if bcz == ND else np.sin(th)
+    fx = np.cos(2 * np.pi * np.arange(nx) / nx)
+    f = fz[:, None, None] * np.ones((1, ny, 1)) * fx[None, None, :]
+    lam = -4 * np.sin(np.pi / nx) ** 2 * nx ** 2 - 4 * np.sin(np.pi * (2 * m + 1) / (4 * nz)) ** 2 / h ** 2
+    p = oracle.poisson_solve(f, (P, P, bcz), (1.0, 1.0), np.full(nz, h))
+    np.testing.assert_allclose(p, f / lam, rtol=0, atol=1e-13 * np.abs(f / lam).max())
+
+
+@pytest.mark.parametrize("bcz", [ND, DN])
+@pytest.mark.parametrize("bxy", [(P, P), (NN, NN), (P, DD), (NN, P)])
+def test_dense_lu_mixed_walls(bcz, bxy):
+    shape = (6, 4, 5)
+    dzf = I.uniform(15, (shape[0],), 0.5, 1.5)
+    f = I.uniform(16, shape, -1, 1)
+    bc = (bxy[0], bxy[1], bcz)
+    A = dense_helmholtz(shape, bc, (1.0, 1.3), dzf, 0.0, 0)
+    ref = np.linalg.solve(A, f.ravel()).reshape(shape)  # a Dirichlet wall: never singular
+    got = oracle.poisson_solve(f, bc, (1.0, 1.3), dzf)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_mixed_walls_are_the_two_ends_of_nn_and_dd():
+    """Row by row, the ND rows are the NN rows near the low wall and the DD rows near the high wall."""
+    dzf = I.uniform(17, (9,), 0.5, 1.5)
+    nn, dd, nd, dn = (oracle.z_rows(b, dzf) for b in (NN, DD, ND, DN))
+    for q in range(3):
+        np.testing.assert_array_equal(nd[q][:4], nn[q][:4])
+        np.testing.assert_array_equal(nd[q][-4:], dd[q][-4:])
+        np.testing.assert_array_equal(dn[q][:4], dd[q][:4])
+        np.testing.assert_array_equal(dn[q][-4:], nn[q][-4:])
