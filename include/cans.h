@@ -37,7 +37,10 @@ extern "C" {
 
 typedef struct cans_plan_s* cans_plan_t;
 
-enum cans_bc { CANS_BC_P = 0, CANS_BC_NN = 1, CANS_BC_DD = 2 };
+/* Boundary conditions of a direction (cell-centred unknowns, walls half a cell beyond the first and
+ * last cell): periodic, Neumann at both walls, Dirichlet at both walls; along z also the mixed pairs
+ * Neumann at the low wall with Dirichlet at the high wall (ND) and the reverse (DN). */
+enum cans_bc { CANS_BC_P = 0, CANS_BC_NN = 1, CANS_BC_DD = 2, CANS_BC_ND = 3, CANS_BC_DN = 4 };
 
 /* CANS_FP64: every pass in IEEE double.
  * CANS_MIXED: transforms and most z-solves in float; the z-solves of the smallest-|mu| modes in
@@ -93,7 +96,8 @@ void cans_opts_default(cans_opts* opts);
  *   opts    : NULL for the defaults.
  *   out     : receives the plan.  The plan uploads its coefficient tables to the current device.
  * Errors: CANS_ERR_ARG (bad n, bc, lengths, dzf non-positive or non-finite, periodic z not
- * uniform), CANS_ERR_UNSUPPORTED (sizes outside the list above), CANS_ERR_CUDA.
+ * uniform), CANS_ERR_UNSUPPORTED (sizes outside the list above; CANS_BC_ND / CANS_BC_DN along x or
+ * y, whose quarter-wave transforms this build does not have), CANS_ERR_CUDA.
  */
 int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
                       const cans_opts* opts, cans_plan_t* out);

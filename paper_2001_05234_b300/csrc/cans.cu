@@ -184,8 +184,9 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   *out = nullptr;
   for (int d = 0; d < 3; ++d) {
     if (n[d] < 1) return CANS_ERR_ARG;
-    if (bc[d] < 0 || bc[d] > 2) return CANS_ERR_ARG;
+    if (bc[d] < 0 || bc[d] > 4) return CANS_ERR_ARG;
   }
+  if (bc[0] > 2 || bc[1] > 2) return CANS_ERR_UNSUPPORTED;  // mixed wall pairs along z only
   for (int d = 0; d < 2; ++d)
     if (!(len_xy[d] > 0) || !std::isfinite(len_xy[d])) return CANS_ERR_ARG;
   cans_opts o;
@@ -245,7 +246,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->opts = o;
   P->wblk = 0;  // the blocked work-field layout measured no faster on B300; kept selectable
   cudaGetDevice(&P->device);
-  P->sing_bc = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] != BC_DD);
+  P->sing_bc = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] == BC_P || bc[2] == BC_NN);
   P->shift = o.shift;
   P->singular = P->sing_bc && P->shift == 0.0;
 
@@ -289,13 +290,9 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     zc[k] = sc[k];
     zb[k] = -(sa[k] + sc[k]);
   }
-  if (bc[2] == BC_NN) {
-    zb[0] += sa[0];
-    zb[nz - 1] += sc[nz - 1];
-  } else {  // Dirichlet
-    zb[0] -= sa[0];
-    zb[nz - 1] -= sc[nz - 1];
-  }
+  // per wall: a Neumann ghost mirrors the wall cell (that flux vanishes), a Dirichlet ghost is its negative
+  zb[0] += (bc_lo(bc[2]) == BC_NN) ? sa[0] : -sa[0];
+  zb[nz - 1] += (bc_hi(bc[2]) == BC_NN) ? sc[nz - 1] : -sc[nz - 1];
   za[0] = 0;
   zc[nz - 1] = 0;
 

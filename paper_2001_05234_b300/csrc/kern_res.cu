@@ -63,7 +63,9 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
     const float p_first_prev = Phi[(size_t)kprev * sz + c0];
     float p_cur = pp[0];
     // Phi_{k-1} - Phi_k exactly (k = k0; a wall ghost at k = 0)
-    df dm = two_sum((BZ != BC_P && k0 == 0) ? ghost<BZ>(p_cur) : p_first_prev, -p_cur);
+    // z wall ghosts: Neumann mirrors, Dirichlet negates (each wall its own rule)
+    const float zsl = (S.zlo == BC_NN) ? 1.f : -1.f, zsh = (S.zhi == BC_NN) ? 1.f : -1.f;
+    df dm = two_sum((BZ != BC_P && k0 == 0) ? zsl * p_cur : p_first_prev, -p_cur);
     const float* qp = PLO ? Plo + (size_t)k0 * sz + c0 : nullptr;
     float q_prev = 0.f, q_cur = 0.f;
     if (PLO) {
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             nym = pp[sz + dym];
             nyp = pp[sz + dyp];
           }
-          const float zp = (BZ != BC_P && top) ? ghost<BZ>(p_cur) : p_next;
+          const float zp = (BZ != BC_P && top) ? zsh * p_cur : p_next;
           const df dp = two_sum(zp, -p_cur);  // Phi_{k+1} - Phi_k exactly
           const float4 co = zc[k - k0];
           // L_h Phi as a double-float
@@ -136,8 +138,8 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             const float qxp = gxp ? ghost<BX>(q_cur) : qp[dxp];
             const float qym = gym ? ghost<BY>(q_cur) : qp[dym];
             const float qyp = gyp ? ghost<BY>(q_cur) : qp[dyp];
-            const float qzm = (BZ != BC_P && k == 0) ? ghost<BZ>(q_cur) : q_prev;
-            const float qzp = (BZ != BC_P && top) ? ghost<BZ>(q_cur) : q_next;
+            const float qzm = (BZ != BC_P && k == 0) ? zsl * q_cur : q_prev;
+            const float qzp = (BZ != BC_P && top) ? zsh * q_cur : q_next;
             rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
                   co.x * (qzp - q_cur) + co.z * (qzm - q_cur) + S.shift.hi * q_cur;
             q_prev = q_cur;
@@ -181,9 +183,9 @@ cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi,
 template <bool PLO, int BX, int BY>
 cudaError_t res_bz(int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
+  // walled z: one instantiation, the rule of each wall from S.zlo / S.zhi
   if (bz == BC_P) return res_launch<PLO, BX, BY, BC_P>(g, b, f, Phi, Plo, r, S, kc, acc, st);
-  if (bz == BC_NN) return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st);
-  return res_launch<PLO, BX, BY, BC_DD>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st);
 }
 template <bool PLO, int BX>
 cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,

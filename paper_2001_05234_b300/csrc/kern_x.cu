@@ -349,6 +349,8 @@ StencilDF stencil_df(const cans_plan_s* P) {
   StencilDF S;
   S.idx2.hi = (float)P->idx2;
   S.idx2.lo = (float)(P->idx2 - (double)S.idx2.hi);
+  S.zlo = bc_lo(P->bc[2]);
+  S.zhi = bc_hi(P->bc[2]);
   S.shift.hi = (float)P->shift;
   S.shift.lo = (float)(P->shift - (double)S.shift.hi);
   S.idy2.hi = (float)P->idy2;

@@ -16,7 +16,10 @@
 
 namespace cans {
 
-enum { BC_P = 0, BC_NN = 1, BC_DD = 2 };
+enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };  // ND / DN: z only (mixed walls)
+// wall rule at the low and the high end of a walled direction
+__host__ __device__ __forceinline__ int bc_lo(int bc) { return bc == BC_ND ? BC_NN : (bc == BC_DN ? BC_DD : bc); }
+__host__ __device__ __forceinline__ int bc_hi(int bc) { return bc == BC_ND ? BC_DD : (bc == BC_DN ? BC_NN : bc); }
 
 template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };

@@ -52,8 +52,8 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
     if (j == ny - 1) yp = wall_ghost(S.bc[1], pc);
   }
   if (S.bc[2] != BC_P) {
-    if (k == 0) zm = wall_ghost(S.bc[2], pc);
-    if (k == nz - 1) zp = wall_ghost(S.bc[2], pc);
+    if (k == 0) zm = wall_ghost(S.zlo, pc);
+    if (k == nz - 1) zp = wall_ghost(S.zhi, pc);
   }
   df acc = df_from_double(f[c]);
   acc = df_sub_prod(acc, S.idx2, second_difference(xm, xp, pc));
@@ -75,8 +75,8 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
       if (j == ny - 1) qyp = wall_ghost(S.bc[1], qc);
     }
     if (S.bc[2] != BC_P) {
-      if (k == 0) qzm = wall_ghost(S.bc[2], qc);
-      if (k == nz - 1) qzp = wall_ghost(S.bc[2], qc);
+      if (k == 0) qzm = wall_ghost(S.zlo, qc);
+      if (k == nz - 1) qzp = wall_ghost(S.zhi, qc);
     }
     r -= S.idx2.hi * (qxm + qxp - 2.f * qc) + S.idy2.hi * (qym + qyp - 2.f * qc) + S.sc_hi[k] * (qzp - qc) +
          S.sa_hi[k] * (qzm - qc) + S.shift.hi * qc;
@@ -117,8 +117,8 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
       const float c0 = pcs[e];
       const float ym = (wy && j == 0) ? wall_ghost(S.bc[1], c0) : yms[e];
       const float yp = (wy && j == ny - 1) ? wall_ghost(S.bc[1], c0) : yps[e];
-      const float zm = (wz && k == 0) ? wall_ghost(S.bc[2], c0) : zms[e];
-      const float zp = (wz && k == nz - 1) ? wall_ghost(S.bc[2], c0) : zps[e];
+      const float zm = (wz && k == 0) ? wall_ghost(S.zlo, c0) : zms[e];
+      const float zp = (wz && k == nz - 1) ? wall_ghost(S.zhi, c0) : zps[e];
       df acc = df_split(fs[e]);
       if (S.iso) {
         const df a = two_sum(xms[e], xps[e]);
@@ -149,8 +149,8 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
       const float c0 = qcs[e];
       const float ym = (wy && j == 0) ? wall_ghost(S.bc[1], c0) : yms[e];
       const float yp = (wy && j == ny - 1) ? wall_ghost(S.bc[1], c0) : yps[e];
-      const float zm = (wz && k == 0) ? wall_ghost(S.bc[2], c0) : zms[e];
-      const float zp = (wz && k == nz - 1) ? wall_ghost(S.bc[2], c0) : zps[e];
+      const float zm = (wz && k == 0) ? wall_ghost(S.zlo, c0) : zms[e];
+      const float zp = (wz && k == nz - 1) ? wall_ghost(S.zhi, c0) : zps[e];
       r[e] -= S.idx2.hi * (xms[e] + xps[e] - 2.f * c0) + S.idy2.hi * (ym + yp - 2.f * c0) + sca * (zp - c0) +
               saa * (zm - c0) + S.shift.hi * c0;
     }

@@ -66,6 +66,9 @@ def test_opts_defaults(cans):
         ((7, 8, 4), (1, 1), (0, 0, 1), None, -2),  # odd periodic N
         ((8, 10, 4), (1, 1), (0, 1, 1), None, -2),  # N/2 = 5 does not factor into 2s and 3s
         ((8, 8, 600), (1, 1), (0, 0, 1), None, -2),  # Nz above 512
+        ((8, 8, 8), (1, 1), (3, 0, 1), None, -2),  # mixed wall pair along x: z only in this build
+        ((8, 8, 8), (1, 1), (0, 4, 1), None, -2),  # mixed wall pair along y
+        ((8, 8, 8), (1, 1), (0, 0, 6), None, -1),  # no such boundary condition
     ],
 )
 def test_plan_rejects_bad_arguments_on_the_host(cans, n, L, bc, dzf, want):
@@ -80,3 +83,15 @@ def test_null_arguments(cans):
     assert L.cans_poisson_solve(None, None, None, None, None, None) == -1
     assert L.cans_plan_destroy(None) == -1
     assert L.cans_poisson_workspace_size(None, None) == -1
+
+
+@pytest.mark.parametrize("field,value,bc", [("shift", 1.0, (0, 0, 2)), ("shift", float("inf"), (0, 0, 2)),
+                                            ("z_grid", 2, (0, 0, 2)), ("z_grid", 1, (0, 0, 1)),
+                                            ("z_grid", 1, (0, 0, 3))])
+def test_plan_rejects_bad_helmholtz_options_on_the_host(cans, field, value, bc):
+    """A positive or non-finite shift, an unknown z grid, and the face grid without Dirichlet walls at
+    both ends are refused before any device work."""
+    o = cans.cans_opts_default()
+    setattr(o, field, value)
+    st, h = cans.cans_poisson_plan((8, 8, 8), (1, 1), bc, None, o, check=False)
+    assert st == -1 and not h.value

@@ -176,3 +176,39 @@ def test_adjoint_with_shift(cans, z_grid):
     b = float((f[:nu] * STg[:nu]).sum())
     assert abs(a - b) <= 1e-12 * max(abs(a), abs(b)), (a, b)
     s.close()
+
+
+ND, DN = 3, 4
+
+
+@pytest.mark.parametrize("bcz", [ND, DN])
+@pytest.mark.parametrize("bcx,bcy", [(P, P), (NN, DD), (DD, NN), (P, NN)])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shift", [0.0, -30.0])
+def test_mixed_z_walls_match_oracle(cans, bcz, bcx, bcy, prec, shift):
+    """Neumann at one z wall and Dirichlet at the other (the z rows, the residual stencils' ghosts and
+    the FP64 norms take each wall's own rule); never singular."""
+    n = (24, 18, 21)
+    bc = (bcx, bcy, bcz)
+    dzf = I.tanh_dzf(n[2], 1.8)
+    f = I.uniform(91 + bcx + 3 * bcy + 9 * bcz, (n[2], n[1], n[0]), -1, 1)
+    ref = oracle.helmholtz_solve(f, bc, (1.0, 1.0), dzf, shift=shift)
+    got, info, st = run(cans, f, n, bc, (1.0, 1.0), dzf, prec, shift)
+    assert st == 0, (st, info)
+    assert rel(got, ref) <= (1e-12 if prec == 0 else 1e-11), rel(got, ref)
+    res = oracle.relative_residual(got, f, bc, (1.0, 1.0), dzf, shift=shift)
+    assert res <= 1e-12, res
+    if prec == 0:
+        assert abs(info[0] - res) <= 1e-3 * res + 1e-16  # the library's own FP64 norm of the same residual
+
+
+@pytest.mark.parametrize("bcz", [ND, DN])
+def test_mixed_z_walls_warp_engine_and_streaming_residual(cans, bcz):
+    n = (256, 256, 40)
+    bc = (P, P, bcz)
+    dzf = I.tanh_dzf(n[2], 1.8)
+    f = I.uniform(101 + bcz, (n[2], n[1], n[0]), -1, 1)
+    got, info, st = run(cans, f, n, bc, (1.0, 1.0), dzf, 1, 0.0, sweeps=2)
+    assert st == 0, (st, info)
+    res = oracle.relative_residual(got, f, bc, (1.0, 1.0), dzf, nthreads=8)
+    assert res <= 1e-12, (res, info)
