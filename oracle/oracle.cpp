@@ -25,9 +25,9 @@
 namespace {
 
 enum { BC_P = 0, BC_NN = 1, BC_DD = 2, BC_ND = 3, BC_DN = 4 };
-// ND / DN (z only): Neumann at the low wall and Dirichlet at the high wall, or the reverse -- the
-// remaining cell-centred wall combinations of the Numerical method's transform list.  The wall rule
-// of each end of a direction:
+// ND / DN: Neumann at the low wall and Dirichlet at the high wall, or the reverse -- the remaining
+// cell-centred wall combinations of the Numerical method's transform list.  The wall rule of each
+// end of a direction:
 inline int bc_low(int bc) { return (bc == BC_ND) ? BC_NN : (bc == BC_DN ? BC_DD : bc); }
 inline int bc_high(int bc) { return (bc == BC_ND) ? BC_DD : (bc == BC_DN ? BC_NN : bc); }
 inline bool has_dirichlet(int bc) { return bc == BC_DD || bc == BC_ND || bc == BC_DN; }
@@ -116,10 +116,10 @@ void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const Z
       for (int i = 0; i < nx; ++i) {
         const size_t c = i * sx + j * sy + k * sz;
         const T pc = p[c];
-        const T xm = (i > 0) ? p[c - sx] : ghost<T>(bc[0], pc, p[c + (nx - 1) * sx]);
-        const T xp = (i < nx - 1) ? p[c + sx] : ghost<T>(bc[0], pc, p[c - (nx - 1) * sx]);
-        const T ym = (j > 0) ? p[c - sy] : ghost<T>(bc[1], pc, p[c + (ny - 1) * sy]);
-        const T yp = (j < ny - 1) ? p[c + sy] : ghost<T>(bc[1], pc, p[c - (ny - 1) * sy]);
+        const T xm = (i > 0) ? p[c - sx] : ghost<T>(bc_low(bc[0]), pc, p[c + (nx - 1) * sx]);
+        const T xp = (i < nx - 1) ? p[c + sx] : ghost<T>(bc_high(bc[0]), pc, p[c - (nx - 1) * sx]);
+        const T ym = (j > 0) ? p[c - sy] : ghost<T>(bc_low(bc[1]), pc, p[c + (ny - 1) * sy]);
+        const T yp = (j < ny - 1) ? p[c + sy] : ghost<T>(bc_high(bc[1]), pc, p[c - (ny - 1) * sy]);
         const T zm = (k > 0) ? p[c - sz] : ghost<T>(bc_low(bc[2]), pc, p[c + (nz - 1) * sz]);
         const T zp = (k < nz - 1) ? p[c + sz] : ghost<T>(bc_high(bc[2]), pc, p[c - (nz - 1) * sz]);
         const T lx = (xm - 2 * pc + xp) * idx2;
@@ -149,6 +149,9 @@ void apply_laplacian(const int n[3], const T len_xy[2], const int bc[3], const Z
 //              lam = -4 sin^2(pi k/n), which equals 2(cos(2 pi k/n) - 1).
 //   Neumann  : sqrt(2/n) c_m cos(pi m (i+1/2)/n), c_0 = 1/sqrt(2); lam = -4 sin^2(pi m/(2n)).
 //   Dirichlet: sqrt(2/n) c_m sin(pi (m+1)(i+1/2)/n), c_{n-1} = 1/sqrt(2); lam = -4 sin^2(pi (m+1)/(2n)).
+//   Neumann-Dirichlet: sqrt(2/n) cos(pi (m+1/2)(i+1/2)/n); Dirichlet-Neumann: sqrt(2/n) sin(pi (m+1/2)(i+1/2)/n);
+//              both lam = -4 sin^2(pi (2m+1)/(4n)) (quarter waves: zero slope at one wall, zero value
+//              half a cell beyond the other).
 template <typename T>
 void eigenbasis(int bc, int n, std::vector<T>& E, std::vector<T>& lam) {
   E.assign((size_t)n * n, T(0));
@@ -179,11 +182,20 @@ void eigenbasis(int bc, int n, std::vector<T>& E, std::vector<T>& lam) {
       const T s = sin_(pi * T(m) / (2 * T(n)));
       lam[m] = -4 * s * s;
     }
-  } else {
+  } else if (bc == BC_DD) {
     for (int m = 0; m < n; ++m) {
       const T cm = (m == n - 1) ? sqrt_(T(0.5)) : T(1);
       for (int i = 0; i < n; ++i) E[(size_t)i * n + m] = s2n * cm * sin_(pi * T(m + 1) * (T(i) + T(0.5)) / T(n));
       const T s = sin_(pi * T(m + 1) / (2 * T(n)));
+      lam[m] = -4 * s * s;
+    }
+  } else {  // BC_ND, BC_DN
+    for (int m = 0; m < n; ++m) {
+      for (int i = 0; i < n; ++i) {
+        const T th = pi * (T(m) + T(0.5)) * (T(i) + T(0.5)) / T(n);
+        E[(size_t)i * n + m] = s2n * ((bc == BC_ND) ? cos_(th) : sin_(th));
+      }
+      const T s = sin_(pi * T(2 * m + 1) / (4 * T(n)));
       lam[m] = -4 * s * s;
     }
   }
@@ -286,7 +298,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
     }
   }
 
-  const bool singular = (bc[0] != BC_DD) && (bc[1] != BC_DD) && !has_dirichlet(bc[2]) && shift == 0;
+  const bool singular = !has_dirichlet(bc[0]) && !has_dirichlet(bc[1]) && !has_dirichlet(bc[2]) && shift == 0;
   if (bc[2] == BC_P) {
     // uniform periodic z: diagonalise z as well (checked by the caller)
     eigenbasis<T>(BC_P, nz, Ez, lz);
@@ -373,7 +385,7 @@ int poisson_solve(const int n[3], const T len_xy[2], const int bc[3], const ZGri
 int check_args(const int n[3], const int bc[3], const double* dzf) {
   for (int d = 0; d < 3; ++d) {
     if (n[d] < 1) return -1;
-    if (bc[d] < 0 || bc[d] > (d == 2 ? 4 : 2)) return -1;  // the mixed wall pairs along z only
+    if (bc[d] < 0 || bc[d] > 4) return -1;
   }
   for (int k = 0; k < n[2]; ++k)
     if (!(dzf[k] > 0) || !std::isfinite(dzf[k])) return -1;
@@ -480,7 +492,7 @@ int oracle_apply_helmholtz(int prec_bits, const int n[3], const double len_xy[2]
 // Dense orthonormal eigenbasis E (row-major n x n, columns = eigenvectors) and unit-spacing
 // eigenvalues lam of the 1-D operator with boundary condition bc.
 int oracle_eigenbasis(int bc, int n, double* E, double* lam) {
-  if (n < 1 || bc < 0 || bc > 2) return -1;
+  if (n < 1 || bc < 0 || bc > 4) return -1;
   std::vector<double> e, l;
   eigenbasis<double>(bc, n, e, l);
   std::memcpy(E, e.data(), sizeof(double) * e.size());

@@ -176,3 +176,36 @@ def test_mixed_walls_are_the_two_ends_of_nn_and_dd():
         np.testing.assert_array_equal(nd[q][-4:], dd[q][-4:])
         np.testing.assert_array_equal(dn[q][:4], dd[q][:4])
         np.testing.assert_array_equal(dn[q][-4:], nn[q][-4:])
+
+
+@pytest.mark.parametrize("bc", [ND, DN])
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 12])
+def test_quarter_wave_basis_is_the_dct4_dst4(bc, n):
+    """The oracle's x / y basis for a mixed wall pair: orthonormal, E^T x equal to scipy's DCT-IV
+    (ND) / DST-IV (DN) up to its factor 2 sqrt(n/2), and eigenpairs of the 1-D stencil matrix with a
+    mirrored (Neumann) ghost at one end and a negated (Dirichlet) ghost at the other."""
+    import scipy.fft
+
+    E, lam = oracle.eigenbasis(bc, n)
+    np.testing.assert_allclose(E.T @ E, np.eye(n), atol=1e-13)
+    x = I.uniform(18 + n, (n,), -1, 1)
+    t = scipy.fft.dct(x, type=4) if bc == ND else scipy.fft.dst(x, type=4)
+    np.testing.assert_allclose(E.T @ x, t / 2 * np.sqrt(2.0 / n), atol=1e-13)
+    T = np.diag(np.full(n, -2.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    lo, hi = (1.0, -1.0) if bc == ND else (-1.0, 1.0)
+    T[0, 0] += lo
+    T[-1, -1] += hi
+    np.testing.assert_allclose(T @ E, E * lam[None, :], atol=1e-12)
+
+
+@pytest.mark.parametrize("bx,by", [(ND, P), (DN, NN), (P, ND), (ND, DN), (DN, DD)])
+@pytest.mark.parametrize("bz", [NN, DD, ND])
+def test_dense_lu_mixed_walls_in_x_and_y(bx, by, bz):
+    shape = (4, 5, 6)
+    dzf = I.uniform(19, (shape[0],), 0.5, 1.5)
+    f = I.uniform(20, shape, -1, 1)
+    bc = (bx, by, bz)
+    A = dense_helmholtz(shape, bc, (1.2, 0.8), dzf, 0.0, 0)
+    ref = np.linalg.solve(A, f.ravel()).reshape(shape)
+    got = oracle.poisson_solve(f, bc, (1.2, 0.8), dzf)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
