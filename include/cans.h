@@ -38,8 +38,8 @@ extern "C" {
 typedef struct cans_plan_s* cans_plan_t;
 
 /* Boundary conditions of a direction (cell-centred unknowns, walls half a cell beyond the first and
- * last cell): periodic, Neumann at both walls, Dirichlet at both walls; along z also the mixed pairs
- * Neumann at the low wall with Dirichlet at the high wall (ND) and the reverse (DN). */
+ * last cell): periodic, Neumann at both walls, Dirichlet at both walls, and the mixed pairs Neumann
+ * at the low wall with Dirichlet at the high wall (ND) and the reverse (DN). */
 enum cans_bc { CANS_BC_P = 0, CANS_BC_NN = 1, CANS_BC_DD = 2, CANS_BC_ND = 3, CANS_BC_DN = 4 };
 
 /* CANS_FP64: every pass in IEEE double.
@@ -96,8 +96,9 @@ void cans_opts_default(cans_opts* opts);
  *   opts    : NULL for the defaults.
  *   out     : receives the plan.  The plan uploads its coefficient tables to the current device.
  * Errors: CANS_ERR_ARG (bad n, bc, lengths, dzf non-positive or non-finite, periodic z not
- * uniform), CANS_ERR_UNSUPPORTED (sizes outside the list above; CANS_BC_ND / CANS_BC_DN along x or
- * y, whose quarter-wave transforms this build does not have), CANS_ERR_CUDA.
+ * uniform), CANS_ERR_UNSUPPORTED (sizes outside the list above), CANS_ERR_CUDA.
+ * Along x and y the mixed pairs use the quarter-wave transforms (DCT-IV / DST-IV; output slot s =
+ * mode s, eigenvalue -4 sin^2(pi (2s+1) / 4N)) of the shared-memory line engine.
  */
 int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], const double* dzf,
                       const cans_opts* opts, cans_plan_t* out);
@@ -164,8 +165,9 @@ const char* cans_status_string(int status);
  * -> slot 0 = X_0, slot 1 = X_{N/2}, slots 2k, 2k+1 = Re X_k, Im X_k (1 <= k < N/2);
  * Neumann -> slot m = DCT-II_m; Dirichlet -> slot m = DST-II_m, all unnormalised (X_k = sum x_n
  * e^{-2 pi i k n/N}, DCT-II_m = 2 sum x_n cos(pi m (2n+1)/(2N)), DST-II_m = 2 sum x_n
- * sin(pi (m+1)(2n+1)/(2N))).  The inverse is the exact inverse times Nx*Ny (so a forward-inverse
- * round trip multiplies by Nx*Ny).
+ * sin(pi (m+1)(2n+1)/(2N))); Neumann-Dirichlet -> slot m = DCT-IV_m = 2 sum x_n
+ * cos(pi (2m+1)(2n+1)/(4N)); Dirichlet-Neumann -> slot m = DST-IV_m (sin).  The inverse is the
+ * exact inverse times Nx*Ny (so a forward-inverse round trip multiplies by Nx*Ny).
  */
 int cans_transform_xy(cans_plan_t plan, double* field, int dir, void* cuda_stream);
 

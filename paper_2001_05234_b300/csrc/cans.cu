@@ -60,8 +60,10 @@ long double slot_lambda(int bc, int N, int s) {
     th = pi * (long double)((N > 1 && s == 1) ? N / 2 : s / 2) / N;
   else if (bc == BC_NN)
     th = pi * (long double)s / (2.0L * N);
-  else
+  else if (bc == BC_DD)
     th = pi * (long double)(s + 1) / (2.0L * N);
+  else  // quarter-wave (ND, DN): slot s = mode s
+    th = pi * (long double)(2 * s + 1) / (4.0L * N);
   const long double sn = sinl(th);
   return -4.0L * sn * sn;
 }
@@ -118,6 +120,17 @@ void dir_tables(const DirHost& d, std::vector<double>& tw, std::vector<double>& 
     const long double th = -2.0L * pi * t / M;
     tw[2 * t] = (double)cosl(th);
     tw[2 * t + 1] = (double)sinl(th);
+  }
+  if (d.bc == BC_ND || d.bc == BC_DN) {  // quarter-wave: post-twiddle exp(-i pi k/N), pre-twiddle exp(-i pi (4m+1)/4N)
+    for (int k = 0; k < M; ++k) {
+      const long double th = -pi * k / N;
+      post[2 * k] = (double)cosl(th);
+      post[2 * k + 1] = (double)sinl(th);
+      const long double tm = -pi * (4.0L * k + 1.0L) / (4.0L * N);
+      mak[2 * k] = (double)cosl(tm);
+      mak[2 * k + 1] = (double)sinl(tm);
+    }
+    return;
   }
   for (int k = 0; k <= M; ++k) {
     const long double th = -2.0L * pi * k / N;
@@ -186,7 +199,6 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     if (n[d] < 1) return CANS_ERR_ARG;
     if (bc[d] < 0 || bc[d] > 4) return CANS_ERR_ARG;
   }
-  if (bc[0] > 2 || bc[1] > 2) return CANS_ERR_UNSUPPORTED;  // mixed wall pairs along z only
   for (int d = 0; d < 2; ++d)
     if (!(len_xy[d] > 0) || !std::isfinite(len_xy[d])) return CANS_ERR_ARG;
   cans_opts o;
@@ -246,7 +258,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->opts = o;
   P->wblk = 0;  // the blocked work-field layout measured no faster on B300; kept selectable
   cudaGetDevice(&P->device);
-  P->sing_bc = (bc[0] != BC_DD) && (bc[1] != BC_DD) && (bc[2] == BC_P || bc[2] == BC_NN);
+  P->sing_bc = (bc[0] == BC_P || bc[0] == BC_NN) && (bc[1] == BC_P || bc[1] == BC_NN) && (bc[2] == BC_P || bc[2] == BC_NN);
   P->shift = o.shift;
   P->singular = P->sing_bc && P->shift == 0.0;
 
@@ -276,8 +288,10 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   P->muy_h.resize(n[1]);
   for (int s = 0; s < n[0]; ++s) P->mux_h[s] = (double)(slot_lambda(bc[0], n[0], s) / ((long double)hx * hx));
   for (int s = 0; s < n[1]; ++s) P->muy_h[s] = (double)(slot_lambda(bc[1], n[1], s) / ((long double)hy * hy));
-  if (n[0] == 1) P->mux_h[0] = (bc[0] == BC_DD) ? -4.0 / (hx * hx) : 0.0;
-  if (n[1] == 1) P->muy_h[0] = (bc[1] == BC_DD) ? -4.0 / (hy * hy) : 0.0;
+  // one cell: the ghosts alone (Dirichlet -c, Neumann c, periodic c itself) give -4, -2 or 0
+  auto one_cell = [](int b) { return b == BC_DD ? -4.0 : ((b == BC_ND || b == BC_DN) ? -2.0 : 0.0); };
+  if (n[0] == 1) P->mux_h[0] = one_cell(bc[0]) / (hx * hx);
+  if (n[1] == 1) P->muy_h[0] = one_cell(bc[1]) / (hy * hy);
   P->idx2 = 1.0 / (hx * hx);
   P->idy2 = 1.0 / (hy * hy);
 

@@ -22,8 +22,9 @@ __global__ void residual_norm_kernel(const double* __restrict__ f, const double*
       return -pc;
     };
     const size_t sy = nx, sz = (size_t)nx * ny;
-    const double xm = nb(bx, i == 0, c - 1, c + (nx - 1)), xp = nb(bx, i == nx - 1, c + 1, c - (nx - 1));
-    const double ym = nb(by, j == 0, c - sy, c + (ny - 1) * sy), yp = nb(by, j == ny - 1, c + sy, c - (ny - 1) * sy);
+    const double xm = nb(bc_lo(bx), i == 0, c - 1, c + (nx - 1)), xp = nb(bc_hi(bx), i == nx - 1, c + 1, c - (nx - 1));
+    const double ym = nb(bc_lo(by), j == 0, c - sy, c + (ny - 1) * sy);
+    const double yp = nb(bc_hi(by), j == ny - 1, c + sy, c - (ny - 1) * sy);
     const double zm = nb(bc_lo(bz), k == 0, c - sz, c + (nz - 1) * sz);
     const double zp = nb(bc_hi(bz), k == nz - 1, c + sz, c - (nz - 1) * sz);
     const double Lp = (xm - 2 * pc + xp) * idx2 + (ym - 2 * pc + yp) * idy2 + sc[k] * (zp - pc) + sa[k] * (zm - pc) +

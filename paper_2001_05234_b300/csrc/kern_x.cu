@@ -349,6 +349,10 @@ StencilDF stencil_df(const cans_plan_s* P) {
   StencilDF S;
   S.idx2.hi = (float)P->idx2;
   S.idx2.lo = (float)(P->idx2 - (double)S.idx2.hi);
+  S.xlo = bc_lo(P->bc[0]);
+  S.xhi = bc_hi(P->bc[0]);
+  S.ylo = bc_lo(P->bc[1]);
+  S.yhi = bc_hi(P->bc[1]);
   S.zlo = bc_lo(P->bc[2]);
   S.zhi = bc_hi(P->bc[2]);
   S.shift.hi = (float)P->shift;

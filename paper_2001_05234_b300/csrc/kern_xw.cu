@@ -299,7 +299,7 @@ template <int MODE>
 cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
                              double* acc, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || !aligned16(f) || !aligned16(dst)) return cudaSuccess;
+  if (P->wblk || !aligned16(f) || !aligned16(dst) || quarter(P->bc[0])) return cudaSuccess;  // quarter-wave: CTA engine
   const int bc = P->bc[0];
   *handled = true;
 #define XW_CASE(MM)                                                            \
@@ -320,7 +320,7 @@ template <int MODE>
 cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
                              double* gauge, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || !aligned16(src)) return cudaSuccess;
+  if (P->wblk || !aligned16(src) || quarter(P->bc[0])) return cudaSuccess;
   if ((MODE == 0 || MODE == 3 || MODE == 5) && !aligned16(p)) return cudaSuccess;
   if (upd_reads<MODE>() > 0 && !aligned16(Phi)) return cudaSuccess;
   if (upd_reads<MODE>() == 2 && !aligned16(Plo)) return cudaSuccess;
@@ -343,7 +343,8 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
 // Residual sweep, split form: the streaming residual stencil (kern_res.cu) writes r into W, then
 // this x-forward transforms W in place.  Taken whenever the x lines fit the warp engine.
 bool xres_warp_ok(const cans_plan_s* P, const float* W) {
-  return !P->wblk && aligned16(W) && wl::supported(P->dx.m);
+  // the streaming stencil takes one rule for both x walls and both y walls
+  return !P->wblk && aligned16(W) && wl::supported(P->dx.m) && !quarter(P->bc[0]) && !quarter(P->bc[1]);
 }
 
 cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st) {

@@ -112,7 +112,7 @@ cudaError_t yw(const cans_plan_s* P, float* w, cudaStream_t st) {
 template <int DIR>
 cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || P->n[0] % YW_L != 0 || (reinterpret_cast<uintptr_t>(w) & 15)) return cudaSuccess;
+  if (P->wblk || P->n[0] % YW_L != 0 || (reinterpret_cast<uintptr_t>(w) & 15) || quarter(P->bc[1])) return cudaSuccess;
   const int bc = P->bc[1];
   *handled = true;
 #define YW_CASE(MM)                                                  \

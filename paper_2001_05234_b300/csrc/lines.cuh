@@ -1,6 +1,7 @@
 // Shared-memory line transforms for the x and y passes of the eigenfunction-expansion solver
 // (the operator F^{x_i} of Eq. poi_reduced: real DFT for periodic, DCT-II/DST-II for Neumann /
-// Dirichlet walls, with the inverses DFT^-1, DCT-III, DST-III).
+// Dirichlet walls, with the inverses DFT^-1, DCT-III, DST-III; DCT-IV / DST-IV, their own inverses,
+// for a Neumann wall paired with a Dirichlet wall).
 //
 // A CTA holds `nl` lines (nl a power of two) of N = 2M reals in shared memory.  Each real line is
 // packed into M complex numbers (even -> real part, odd -> imaginary part), transformed by a
@@ -63,12 +64,39 @@ struct Lay {
   __device__ __forceinline__ int r(int s, int l) const { return 2 * c(s >> 1, l) + (s & 1); }
 };
 
+// Quarter-wave lines (a Neumann wall paired with a Dirichlet wall).  The cosine transform
+//   Y_k = 2 sum_n x_n cos(pi (2n+1)(2k+1) / 4N)  (DCT-IV)
+// runs as one half-length complex FFT between two twiddles:
+//   z_m = (x_2m + i x_{N-1-2m}) exp(-i pi (4m+1)/4N),  Z = FFT_M(z),  u_k = Z_k exp(-i pi k/N),
+//   Y_2k = 2 Re u_k,  Y_{N-1-2k} = -2 Im u_k.
+// The sine transform (DST-IV, Dirichlet wall first) is the cosine one of (-1)^n x_n read backwards.
+// Both are their own inverses up to 2N, so the inverse pass (times N) is the same routine with
+// factor 1.  The direction's tables then hold mak[m] = exp(-i pi (4m+1)/4N) (pre) and
+// post[k] = exp(-i pi k/N) (post).
+__host__ __device__ __forceinline__ bool quarter(int bc) { return bc == BC_ND || bc == BC_DN; }
+// sign of sample (or slot) n on the way into the half-length FFT: Dirichlet-first lines alternate
+__host__ __device__ __forceinline__ bool neg_in(int bc, int n) { return (bc == BC_DD || bc == BC_DN) && (n & 1); }
+
 // position of input sample n inside the sequence fed to the half-length FFT
 //   periodic: identity.  Neumann / Dirichlet (Makhoul): even samples first in order, odd samples
-//   after them in reverse order.
+//   after them in reverse order.  Quarter-wave: x_2m is the real part of z_m, x_{N-1-2m} its
+//   imaginary part (odd n sits at position N - n).
 __device__ __forceinline__ int perm_in(int bc, int N, int n) {
   if (bc == BC_P) return n;
+  if (quarter(bc)) return (n & 1) ? N - n : n;
   return (n & 1) ? (N - 1 - (n >> 1)) : (n >> 1);
+}
+
+// the two samples (or slots) that pack into complex element m of a quarter-wave line, and the two
+// that complex output k of the half-length FFT produces (in the same order: real, imaginary part)
+__device__ __forceinline__ void qw_pair(int bc, int N, int m, int& a, int& b) {
+  a = 2 * m;
+  b = N - 1 - 2 * m;
+  if (bc == BC_DN) {  // read backwards
+    const int t = a;
+    a = b;
+    b = t;
+  }
 }
 
 // ---- small DFTs (forward sign) --------------------------------------------------------------
@@ -437,7 +465,14 @@ __device__ __forceinline__ void pre_inverse(typename V2<T>::t* buf, const Lay& L
 template <typename T, int MC = 0>
 __device__ __forceinline__ T inverse_sample(const typename V2<T>::t* buf, const Lay& L, const LineTab<T>& tb, int n,
                                             int l) {
-  const int s = perm_in(tb.bc, MC > 0 ? 2 * MC : tb.n, n);
+  const int N = MC > 0 ? 2 * MC : tb.n;
+  if (quarter(tb.bc) && N >= 2) {  // post-twiddle of the complex output that carries sample n
+    const int nn = (tb.bc == BC_DN) ? N - 1 - n : n;  // its index in the cosine form
+    const int k = (nn & 1) ? (N - 1 - nn) >> 1 : nn >> 1;
+    const typename V2<T>::t u = cmul(buf[L.c(k, l)], __ldg(&tb.post[k]));
+    return (nn & 1) ? -u.y : u.x;
+  }
+  const int s = perm_in(tb.bc, N, n);
   const T* bufT = reinterpret_cast<const T*>(buf);
   T v = bufT[L.r(s, l)];
   if (s & 1) v = -v;  // conjugate back
@@ -450,7 +485,7 @@ template <typename T, int MC = 0>
 __device__ __forceinline__ void forward_store(typename V2<T>::t* buf, const Lay& L, const LineTab<T>& tb, int n, int l,
                                               T v) {
   const int s = perm_in(tb.bc, MC > 0 ? 2 * MC : tb.n, n);
-  if (tb.bc == BC_DD && (n & 1)) v = -v;
+  if (neg_in(tb.bc, n)) v = -v;
   reinterpret_cast<T*>(buf)[L.r(s, l)] = v;
 }
 
@@ -465,7 +500,7 @@ __device__ __forceinline__ int perm_out(int bc, int N, int s) {
 // the packed complex z_m = (v_2m, v_2m+1) of the permuted sequence v is assembled on the fly.
 template <int R, int MAXV, typename T, int M, typename LoadF>
 __device__ __forceinline__ void fft_stage1_loaded(typename V2<T>::t* buf, const Lay& L, int lognl, int bc,
-                                                  LoadF load) {
+                                                  LoadF load, const typename V2<T>::t* __restrict__ qpre) {
   typedef typename V2<T>::t C;
   constexpr int Q = (MAXV + R - 1) / R;
   constexpr int nb = M / R;
@@ -480,13 +515,19 @@ __device__ __forceinline__ void fft_stage1_loaded(typename V2<T>::t* buf, const 
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = j + r * nb;
-        const int n0 = perm_out(bc, N, 2 * m), n1 = perm_out(bc, N, 2 * m + 1);
-        T x0 = load(l, n0), x1 = load(l, n1);
-        if (bc == BC_DD) {
-          if (n0 & 1) x0 = -x0;
-          if (n1 & 1) x1 = -x1;
+        int n0, n1;
+        if (quarter(bc)) {
+          n0 = 2 * m;
+          n1 = N - 1 - 2 * m;
+        } else {
+          n0 = perm_out(bc, N, 2 * m);
+          n1 = perm_out(bc, N, 2 * m + 1);
         }
+        T x0 = load(l, n0), x1 = load(l, n1);
+        if (neg_in(bc, n0)) x0 = -x0;
+        if (neg_in(bc, n1)) x1 = -x1;
         v[q][r] = mk2<T>(x0, x1);
+        if (quarter(bc)) v[q][r] = cmul(v[q][r], __ldg(&qpre[m]));
       }
       Dft<R, C>::run(v[q]);
     }
@@ -511,6 +552,18 @@ __device__ __forceinline__ void post_forward_store(const typename V2<T>::t* buf,
                                                    const LineTab<T>& tb, StoreF store) {
   typedef typename V2<T>::t C;
   constexpr int N = 2 * M, half = M >> 1;
+  if (quarter(tb.bc)) {
+    for (int t = threadIdx.x; t < (M << lognl); t += blockDim.x) {
+      const int l = JFAST ? t / M : (t & (L.nl - 1));
+      const int k = JFAST ? t - l * M : (t >> lognl);
+      const C u = cmul(buf[L.c(k, l)], __ldg(&tb.post[k]));
+      int a, b;
+      qw_pair(tb.bc, N, k, a, b);
+      store(l, a, (T)2 * u.x);
+      store(l, b, (T)-2 * u.y);
+    }
+    return;
+  }
   const int total = (half + 1) << lognl;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int l = JFAST ? t / (half + 1) : (t & (L.nl - 1));
@@ -566,6 +619,18 @@ __device__ __forceinline__ void pre_inverse_loaded(typename V2<T>::t* buf, const
                                                    const LineTab<T>& tb, LoadF loadslot) {
   typedef typename V2<T>::t C;
   constexpr int N = 2 * M, half = M >> 1;
+  if (quarter(tb.bc)) {
+    for (int t = threadIdx.x; t < (M << lognl); t += blockDim.x) {
+      const int l = t & (L.nl - 1), m = t >> lognl;
+      const int a = 2 * m, b = N - 1 - 2 * m;
+      T xa = loadslot(l, a), xb = loadslot(l, b);
+      if (neg_in(tb.bc, a)) xa = -xa;
+      if (neg_in(tb.bc, b)) xb = -xb;
+      buf[L.c(m, l)] = cmul(mk2<T>(xa, xb), __ldg(&tb.mak[m]));
+    }
+    __syncthreads();
+    return;
+  }
   const int total = (half + 1) << lognl;
   const bool dd = (tb.bc == BC_DD);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -610,7 +675,8 @@ __device__ __forceinline__ void pre_inverse_loaded(typename V2<T>::t* buf, const
 // conjugate-back and the unpacking of z_m into samples 2m, 2m+1 of v (and v -> x) are fused.
 template <int R, int MAXV, typename T, int M, int Ns, bool JFAST = false, typename StoreF>
 __device__ __forceinline__ void fft_last_stage_store(const typename V2<T>::t* buf, const Lay& L, int lognl, int bc,
-                                                     const typename V2<T>::t* __restrict__ tw, StoreF store) {
+                                                     const typename V2<T>::t* __restrict__ tw, StoreF store,
+                                                     const typename V2<T>::t* __restrict__ qpost) {
   typedef typename V2<T>::t C;
   constexpr int Q = (MAXV + R - 1) / R;
   constexpr int nb = M / R;
@@ -637,6 +703,14 @@ __device__ __forceinline__ void fft_last_stage_store(const typename V2<T>::t* bu
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int m = base + r * Ns;
+        if (quarter(bc)) {  // post-twiddle; the FFT ran forward on the pre-twiddled slots
+          const C u = cmul(v[r], __ldg(&qpost[m]));
+          int a, b;
+          qw_pair(bc, N, m, a, b);
+          store(l, a, u.x);
+          store(l, b, -u.y);
+          continue;
+        }
         const int n0 = perm_out(bc, N, 2 * m), n1 = perm_out(bc, N, 2 * m + 1);
         T x0 = v[r].x, x1 = -v[r].y;  // conjugate back
         if (bc == BC_DD) {
@@ -670,7 +744,7 @@ template <int MAXV, typename T, int M, bool JFAST = false, typename LoadF, typen
 __device__ __forceinline__ void line_forward_fused(typename V2<T>::t* buf, const Lay& L, int lognl,
                                                    const LineTab<T>& tb, LoadF load, StoreF store) {
   constexpr int NST = m_nst(M);
-  fft_stage1_loaded<m_radix(M, 0), MAXV, T, M>(buf, L, lognl, tb.bc, load);
+  fft_stage1_loaded<m_radix(M, 0), MAXV, T, M>(buf, L, lognl, tb.bc, load, tb.mak);
   FftStages<MAXV, T, M, 1, NST>::run(buf, L, lognl, tb.tw);
   post_forward_store<MAXV, T, M, JFAST>(buf, L, lognl, tb, store);
 }
@@ -683,12 +757,95 @@ __device__ __forceinline__ void line_inverse_fused(typename V2<T>::t* buf, const
   pre_inverse_loaded<MAXV, T, M>(buf, L, lognl, tb, loadslot);
   FftStagesButLast<MAXV, T, M, 0, NST>::run(buf, L, lognl, tb.tw);
   fft_last_stage_store<m_radix(M, NST - 1), MAXV, T, M, m_ns(M, NST - 1), JFAST>(buf, L, lognl, tb.bc, tb.tw,
-                                                                                 store);
+                                                                                 store, tb.post);
+}
+
+// ---- quarter-wave steps on a staged tile ----------------------------------------------------------
+// pre-twiddle of the packed elements (each thread scales its own cells)
+template <typename T, int MC = 0>
+__device__ __forceinline__ void qw_pretwiddle(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  const int M = MC > 0 ? MC : tb.m;
+  for (int t = threadIdx.x; t < (M << lognl); t += blockDim.x) {
+    const int l = t & (L.nl - 1), m = t >> lognl;
+    buf[L.c(m, l)] = cmul(buf[L.c(m, l)], __ldg(&tb.mak[m]));
+  }
+  __syncthreads();
+}
+
+// forward post-twiddle: the N slots of the line, every k written after every thread has read
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void qw_post_forward(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  typedef typename V2<T>::t C;
+  constexpr int J = MAXV + 1;
+  const int M = MC > 0 ? MC : tb.m, N = 2 * M;
+  const int total = M << lognl;
+  C u[J];
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      u[q] = cmul(buf[L.c(k, l)], __ldg(&tb.post[k]));
+    }
+  }
+  __syncthreads();
+  T* bufT = reinterpret_cast<T*>(buf);
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), k = t >> lognl;
+      int a, b;
+      qw_pair(tb.bc, N, k, a, b);
+      bufT[L.r(a, l)] = (T)2 * u[q].x;
+      bufT[L.r(b, l)] = (T)-2 * u[q].y;
+    }
+  }
+  __syncthreads();
+}
+
+// inverse pre-step: the slots of the line (in the real storage) packed and pre-twiddled into buf
+template <int MAXV, typename T, int MC = 0>
+__device__ __forceinline__ void qw_pre_inverse(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
+  typedef typename V2<T>::t C;
+  constexpr int J = MAXV + 1;
+  const int M = MC > 0 ? MC : tb.m, N = 2 * M;
+  const int total = M << lognl;
+  const T* bufT = reinterpret_cast<const T*>(buf);
+  C z[J];
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), m = t >> lognl;
+      const int a = 2 * m, b = N - 1 - 2 * m;
+      T xa = bufT[L.r(a, l)], xb = bufT[L.r(b, l)];
+      if (neg_in(tb.bc, a)) xa = -xa;
+      if (neg_in(tb.bc, b)) xb = -xb;
+      z[q] = cmul(mk2<T>(xa, xb), __ldg(&tb.mak[m]));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < J; ++q) {
+    const int t = threadIdx.x + q * blockDim.x;
+    if (t < total) {
+      const int l = t & (L.nl - 1), m = t >> lognl;
+      buf[L.c(m, l)] = z[q];
+    }
+  }
+  __syncthreads();
 }
 
 template <int MAXV, typename T, int MC = 0>
 __device__ __forceinline__ void line_forward(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
   if (MC == 0 && tb.n < 2) return;
+  if (quarter(tb.bc)) {
+    qw_pretwiddle<T, MC>(buf, L, lognl, tb);
+    fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
+    qw_post_forward<MAXV, T, MC>(buf, L, lognl, tb);
+    return;
+  }
   fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
   post_forward<MAXV, T, MC>(buf, L, lognl, tb);
 }
@@ -696,6 +853,11 @@ __device__ __forceinline__ void line_forward(typename V2<T>::t* buf, const Lay& 
 template <int MAXV, typename T, int MC = 0>
 __device__ __forceinline__ void line_inverse(typename V2<T>::t* buf, const Lay& L, int lognl, const LineTab<T>& tb) {
   if (MC == 0 && tb.n < 2) return;
+  if (quarter(tb.bc)) {
+    qw_pre_inverse<MAXV, T, MC>(buf, L, lognl, tb);
+    fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
+    return;
+  }
   pre_inverse<MAXV, T, MC>(buf, L, lognl, tb);
   fft_lines<MAXV, T, MC>(buf, L, lognl, tb);
 }

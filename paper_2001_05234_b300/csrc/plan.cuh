@@ -27,7 +27,7 @@ struct StencilDF {
   df shift;  // Helmholtz shift sigma of (L_h + sigma): 0 for Poisson
   const float *sa_hi, *sa_lo, *sc_hi, *sc_lo;  // z: a_k (to k-1), c_k (to k+1), wall ghosts included
   int bc[3];
-  int zlo, zhi;  // wall rule (BC_NN or BC_DD) at the low and the high z wall (walled z only)
+  int xlo, xhi, ylo, yhi, zlo, zhi;  // wall rule (BC_NN or BC_DD) at the low and the high wall of each walled direction
   int n[3];
   int iso;  // 1/dx^2 == 1/dy^2 exactly
 };

@@ -44,12 +44,12 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
   const float pc = q[0];
   float xm = q[oxm], xp = q[oxp], ym = q[oym], yp = q[oyp], zm = q[ozm], zp = q[ozp];
   if (S.bc[0] != BC_P) {
-    if (i == 0) xm = wall_ghost(S.bc[0], pc);
-    if (i == nx - 1) xp = wall_ghost(S.bc[0], pc);
+    if (i == 0) xm = wall_ghost(S.xlo, pc);
+    if (i == nx - 1) xp = wall_ghost(S.xhi, pc);
   }
   if (S.bc[1] != BC_P) {
-    if (j == 0) ym = wall_ghost(S.bc[1], pc);
-    if (j == ny - 1) yp = wall_ghost(S.bc[1], pc);
+    if (j == 0) ym = wall_ghost(S.ylo, pc);
+    if (j == ny - 1) yp = wall_ghost(S.yhi, pc);
   }
   if (S.bc[2] != BC_P) {
     if (k == 0) zm = wall_ghost(S.zlo, pc);
@@ -67,12 +67,12 @@ __device__ __forceinline__ float residual_point(const double* __restrict__ f, co
     const float qc = o[0];
     float qxm = o[oxm], qxp = o[oxp], qym = o[oym], qyp = o[oyp], qzm = o[ozm], qzp = o[ozp];
     if (S.bc[0] != BC_P) {
-      if (i == 0) qxm = wall_ghost(S.bc[0], qc);
-      if (i == nx - 1) qxp = wall_ghost(S.bc[0], qc);
+      if (i == 0) qxm = wall_ghost(S.xlo, qc);
+      if (i == nx - 1) qxp = wall_ghost(S.xhi, qc);
     }
     if (S.bc[1] != BC_P) {
-      if (j == 0) qym = wall_ghost(S.bc[1], qc);
-      if (j == ny - 1) qyp = wall_ghost(S.bc[1], qc);
+      if (j == 0) qym = wall_ghost(S.ylo, qc);
+      if (j == ny - 1) qyp = wall_ghost(S.yhi, qc);
     }
     if (S.bc[2] != BC_P) {
       if (k == 0) qzm = wall_ghost(S.zlo, qc);
@@ -107,16 +107,16 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
     const float* q = Phi + c;
     const float2 pc = ld_f2(q), ym2 = ld_f2(q + oym), yp2 = ld_f2(q + oyp), zm2 = ld_f2(q + ozm), zp2 = ld_f2(q + ozp);
     float xl = q[oxm], xr = q[oxp];
-    if (wx && i == 0) xl = wall_ghost(S.bc[0], pc.x);
-    if (wx && i + 1 == nx - 1) xr = wall_ghost(S.bc[0], pc.y);
+    if (wx && i == 0) xl = wall_ghost(S.xlo, pc.x);
+    if (wx && i + 1 == nx - 1) xr = wall_ghost(S.xhi, pc.y);
     const float pcs[2] = {pc.x, pc.y}, xms[2] = {xl, pc.x}, xps[2] = {pc.y, xr};
     const float yms[2] = {ym2.x, ym2.y}, yps[2] = {yp2.x, yp2.y}, zms[2] = {zm2.x, zm2.y}, zps[2] = {zp2.x, zp2.y};
     const double fs[2] = {fd.x, fd.y};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const float c0 = pcs[e];
-      const float ym = (wy && j == 0) ? wall_ghost(S.bc[1], c0) : yms[e];
-      const float yp = (wy && j == ny - 1) ? wall_ghost(S.bc[1], c0) : yps[e];
+      const float ym = (wy && j == 0) ? wall_ghost(S.ylo, c0) : yms[e];
+      const float yp = (wy && j == ny - 1) ? wall_ghost(S.yhi, c0) : yps[e];
       const float zm = (wz && k == 0) ? wall_ghost(S.zlo, c0) : zms[e];
       const float zp = (wz && k == nz - 1) ? wall_ghost(S.zhi, c0) : zps[e];
       df acc = df_split(fs[e]);
@@ -140,15 +140,15 @@ __device__ __forceinline__ float2 residual_pair(const double* __restrict__ f, co
     const float* o = Plo + c;
     const float2 qc = ld_f2(o), ym2 = ld_f2(o + oym), yp2 = ld_f2(o + oyp), zm2 = ld_f2(o + ozm), zp2 = ld_f2(o + ozp);
     float xl = o[oxm], xr = o[oxp];
-    if (wx && i == 0) xl = wall_ghost(S.bc[0], qc.x);
-    if (wx && i + 1 == nx - 1) xr = wall_ghost(S.bc[0], qc.y);
+    if (wx && i == 0) xl = wall_ghost(S.xlo, qc.x);
+    if (wx && i + 1 == nx - 1) xr = wall_ghost(S.xhi, qc.y);
     const float qcs[2] = {qc.x, qc.y}, xms[2] = {xl, qc.x}, xps[2] = {qc.y, xr};
     const float yms[2] = {ym2.x, ym2.y}, yps[2] = {yp2.x, yp2.y}, zms[2] = {zm2.x, zm2.y}, zps[2] = {zp2.x, zp2.y};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const float c0 = qcs[e];
-      const float ym = (wy && j == 0) ? wall_ghost(S.bc[1], c0) : yms[e];
-      const float yp = (wy && j == ny - 1) ? wall_ghost(S.bc[1], c0) : yps[e];
+      const float ym = (wy && j == 0) ? wall_ghost(S.ylo, c0) : yms[e];
+      const float yp = (wy && j == ny - 1) ? wall_ghost(S.yhi, c0) : yps[e];
       const float zm = (wz && k == 0) ? wall_ghost(S.zlo, c0) : zms[e];
       const float zp = (wz && k == nz - 1) ? wall_ghost(S.zhi, c0) : zps[e];
       r[e] -= S.idx2.hi * (xms[e] + xps[e] - 2.f * c0) + S.idy2.hi * (ym + yp - 2.f * c0) + sca * (zp - c0) +
