@@ -35,10 +35,13 @@ __device__ __forceinline__ df df_add_prod(df acc, df coef, df x) {
   return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, p.lo)));
 }
 
-template <bool PLO, int BX, int BY, int BZ>
+// PM bit 0: Plo is nonzero (later sweeps); bit 1: the Helmholtz shift term (kept out of the Poisson
+// instantiations' inner loop)
+template <int PM, int BX, int BY, int BZ>
 __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
                                                       const float* __restrict__ Plo, float* __restrict__ r,
                                                       StencilDF S, int kchunk, double* norm_acc) {
+  constexpr bool PLO = (PM & 1) != 0, SHIFT = (PM & 2) != 0;
   __shared__ float4 zc[64];  // (c_k hi, c_k lo, a_k hi, a_k lo) of the chunk's planes
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
   const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
@@ -63,8 +66,10 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
     const float p_first_prev = Phi[(size_t)kprev * sz + c0];
     float p_cur = pp[0];
     // Phi_{k-1} - Phi_k exactly (k = k0; a wall ghost at k = 0)
-    // z wall ghosts: Neumann mirrors, Dirichlet negates (each wall its own rule)
-    const float zsl = (S.zlo == BC_NN) ? 1.f : -1.f, zsh = (S.zhi == BC_NN) ? 1.f : -1.f;
+    // z wall ghosts: Neumann mirrors, Dirichlet negates; BZ = NN / DD fix both walls at compile time,
+    // BZ = BC_ND takes each wall's own rule from S (the mixed pairs)
+    const float zsl = (BZ == BC_NN) ? 1.f : (BZ == BC_DD) ? -1.f : ((S.zlo == BC_NN) ? 1.f : -1.f);
+    const float zsh = (BZ == BC_NN) ? 1.f : (BZ == BC_DD) ? -1.f : ((S.zhi == BC_NN) ? 1.f : -1.f);
     df dm = two_sum((BZ != BC_P && k0 == 0) ? zsl * p_cur : p_first_prev, -p_cur);
     const float* qp = PLO ? Plo + (size_t)k0 * sz + c0 : nullptr;
     float q_prev = 0.f, q_cur = 0.f;
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
           }
           L = df_add_prod(L, df_make(co.x, co.y), dp);
           L = df_add_prod(L, df_make(co.z, co.w), dm);
-          if (S.shift.hi != 0.f) L = df_add_prod(L, S.shift, df_make(p_cur, 0.f));
+          if (SHIFT) L = df_add_prod(L, S.shift, df_make(p_cur, 0.f));
           // r = (f_hi - L_hi) + (f_lo - L_lo): the first difference is exact when r is small against
           // f (Sterbenz), and otherwise rounds relative to r itself
           const df fs = df_split_rz(fk);
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             const float qzm = (BZ != BC_P && k == 0) ? zsl * q_cur : q_prev;
             const float qzp = (BZ != BC_P && top) ? zsh * q_cur : q_next;
             rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
-                  co.x * (qzp - q_cur) + co.z * (qzm - q_cur) + S.shift.hi * q_cur;
+                  co.x * (qzp - q_cur) + co.z * (qzm - q_cur) + (SHIFT ? S.shift.hi * q_cur : 0.f);
             q_prev = q_cur;
             q_cur = q_next;
             qp += sz;
@@ -173,28 +178,29 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
   }
 }
 
-template <bool PLO, int BX, int BY, int BZ>
+template <int PLO, int BX, int BY, int BZ>
 cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi, const float* Plo, float* r,
                        const StencilDF& S, int kchunk, double* acc, cudaStream_t st) {
   res_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
   return cudaGetLastError();
 }
 
-template <bool PLO, int BX, int BY>
+template <int PLO, int BX, int BY>
 cudaError_t res_bz(int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
-  // walled z: one instantiation, the rule of each wall from S.zlo / S.zhi
   if (bz == BC_P) return res_launch<PLO, BX, BY, BC_P>(g, b, f, Phi, Plo, r, S, kc, acc, st);
-  return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (bz == BC_NN) return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (bz == BC_DD) return res_launch<PLO, BX, BY, BC_DD>(g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_launch<PLO, BX, BY, BC_ND>(g, b, f, Phi, Plo, r, S, kc, acc, st);  // either mixed pair
 }
-template <bool PLO, int BX>
+template <int PLO, int BX>
 cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
   if (by == BC_P) return res_bz<PLO, BX, BC_P>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
   if (by == BC_NN) return res_bz<PLO, BX, BC_NN>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
   return res_bz<PLO, BX, BC_DD>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
 }
-template <bool PLO>
+template <int PLO>
 cudaError_t res_bx(const int* bc, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
   if (bc[0] == BC_P) return res_by<PLO, BC_P>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
@@ -211,8 +217,13 @@ cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* 
   dim3 grid((nx + RX - 1) / RX, (ny + RY - 1) / RY, (nz + kchunk - 1) / kchunk);
   dim3 block(RX, RY);
   const StencilDF S = stencil_df(P);
-  if (plo) return res_bx<true>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
-  return res_bx<false>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+  const int pm = (plo ? 1 : 0) | (S.shift.hi != 0.f ? 2 : 0);
+  switch (pm) {
+    case 0: return res_bx<0>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+    case 1: return res_bx<1>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+    case 2: return res_bx<2>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+    default: return res_bx<3>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st);
+  }
 }
 
 }  // namespace cans
