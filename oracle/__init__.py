@@ -198,6 +198,12 @@ def _bind_chan():
                                   dp, dp, dp, dp, dp, ctypes.c_int]
     L.oracle_rk3_step_implicit.argtypes = [ip, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp, ctypes.c_int]
+    L.oracle_box_project.argtypes = [ip, ip, dp, dp, dp, dp, dp, ctypes.c_int]
+    L.oracle_box_divergence.argtypes = [ip, ip, dp, dp, dp, dp, dp, dp]
+    L.oracle_box_operators.argtypes = [ip, ip, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+    L.oracle_box_rk3_step.argtypes = [ip, ip, ctypes.c_double, dp, dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp, dp, dp,
+                                      ctypes.c_int]
     L._chan_bound = True
     return L
 
@@ -276,6 +282,56 @@ def rk3_step_implicit(u, v, w, p, nu, cfl, ubulk, length_xy, dzf, dt=0.0, forcin
     dt_out = ctypes.c_double()
     rc = L.oracle_rk3_step_implicit(_i(n), _d(Lxy), _d(dz), float(nu), float(cfl), float(ubulk), int(bool(forcing)),
                                     float(dt), _d(u), _d(v), _d(w), _d(p), ctypes.byref(dt_out), int(nthreads))
+    if rc:
+        raise ValueError(rc)
+    return u, v, w, p, float(dt_out.value)
+
+
+# ---- the box: each direction periodic or bounded by no-slip walls, optional lid on the top z wall --
+def _box_args(shape, walls, length_xy, dzf):
+    n, Lxy, dz = _chan_args(shape, length_xy, dzf)
+    return n, np.array([int(bool(x)) for x in walls], dtype=np.int32), Lxy, dz
+
+
+def box_project(u, v, w, walls, length_xy, dzf, nthreads=0):
+    L = _bind_chan()
+    u, v, w = (_c(a).copy() for a in (u, v, w))
+    n, wl, Lxy, dz = _box_args(u.shape, walls, length_xy, dzf)
+    rc = L.oracle_box_project(_i(n), _i(wl), _d(Lxy), _d(dz), _d(u), _d(v), _d(w), int(nthreads))
+    if rc:
+        raise ValueError(rc)
+    return u, v, w
+
+
+def box_divergence(u, v, w, walls, length_xy, dzf):
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, wl, Lxy, dz = _box_args(u.shape, walls, length_xy, dzf)
+    out = np.empty_like(u)
+    L.oracle_box_divergence(_i(n), _i(wl), _d(Lxy), _d(dz), _d(u), _d(v), _d(w), _d(out))
+    return out
+
+
+def box_operators(u, v, w, walls, length_xy, dzf, lid=0.0):
+    """(advection, viscous operator) of the momentum equations, each a (u, v, w) triple."""
+    L = _bind_chan()
+    u, v, w = _c(u), _c(v), _c(w)
+    n, wl, Lxy, dz = _box_args(u.shape, walls, length_xy, dzf)
+    out = [np.empty_like(u) for _ in range(6)]
+    L.oracle_box_operators(_i(n), _i(wl), float(lid), _d(Lxy), _d(dz), _d(u), _d(v), _d(w), *(_d(o) for o in out))
+    return tuple(out[:3]), tuple(out[3:])
+
+
+def box_rk3_step(u, v, w, p, walls, nu, length_xy, dzf, cfl=0.5, ubulk=0.0, forcing=False, dt=0.0, lid=0.0,
+                 nthreads=0):
+    """One explicit RK3 fractional step in the box; returns (u, v, w, p, dt) (copies)."""
+    L = _bind_chan()
+    u, v, w, p = (_c(a).copy() for a in (u, v, w, p))
+    n, wl, Lxy, dz = _box_args(u.shape, walls, length_xy, dzf)
+    dt_out = ctypes.c_double()
+    rc = L.oracle_box_rk3_step(_i(n), _i(wl), float(lid), _d(Lxy), _d(dz), float(nu), float(cfl), float(ubulk),
+                               int(bool(forcing)), float(dt), _d(u), _d(v), _d(w), _d(p), ctypes.byref(dt_out),
+                               int(nthreads))
     if rc:
         raise ValueError(rc)
     return u, v, w, p, float(dt_out.value)

@@ -881,3 +881,295 @@ int oracle_rk3_step_implicit(const int n[3], const double len_xy[2], const doubl
 }
 
 }  // extern "C"
+
+// =================================================================================================
+// The same fractional step in a box whose every direction is either periodic or bounded by no-slip
+// walls, with an optional moving lid (the top z wall moving with velocity lid along x): the flows the
+// paper lists for its solver -- lid-driven cavity (walls everywhere), square duct (x periodic),
+// channel (z walls), decaying Taylor-Green vortex (periodic everywhere).  Written separately from
+// the channel code above from the same marker-and-cell definitions, so that the two cross-check:
+//   * a velocity component normal to a walled direction lives on that direction's faces and is zero
+//     on both wall faces (the high wall face is its last stored face);
+//   * a tangential component beyond a wall takes the ghost 2 U_wall - (value at the wall cell), with
+//     U_wall = lid for u at the top z wall and 0 otherwise;
+//   * the pressure is Neumann at walls, periodic elsewhere.
+// =================================================================================================
+namespace {
+
+struct Box {
+  int n[3];
+  bool wall[3];
+  double lid;
+  double dx, dy;
+  std::vector<double> dzf, dzc;  // dzc[k]: centre distance between k-1 and k, k = 0..nz (wall ghosts: dzf)
+  Box(const int n_[3], const int wall_[3], double lid_, const double len_xy[2], const double* dz)
+      : lid(lid_), dzf(n_[2]), dzc(n_[2] + 1) {
+    for (int d = 0; d < 3; ++d) {
+      n[d] = n_[d];
+      wall[d] = wall_[d] != 0;
+    }
+    dx = len_xy[0] / n[0];
+    dy = len_xy[1] / n[1];
+    const int nz = n[2];
+    for (int k = 0; k < nz; ++k) dzf[k] = dz[k];
+    for (int k = 1; k < nz; ++k) dzc[k] = 0.5 * (dzf[k - 1] + dzf[k]);
+    dzc[0] = wall[2] ? dzf[0] : 0.5 * (dzf[nz - 1] + dzf[0]);
+    dzc[nz] = wall[2] ? dzf[nz - 1] : dzc[0];
+  }
+  size_t size() const { return (size_t)n[0] * n[1] * n[2]; }
+  size_t at(int i, int j, int k) const { return (size_t)i + (size_t)n[0] * ((size_t)j + (size_t)n[1] * k); }
+  // component c (0 u, 1 v, 2 w) of face field a at (i, j, k), each index at most one cell outside
+  double V(const double* a, int c, int i, int j, int k) const {
+    int id[3] = {i, j, k};
+    double sgn = 1.0, add = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      int& x = id[d];
+      if (wall[d] && d == c && (x < 0 || x >= n[d] - 1)) return 0.0;  // normal velocity at / beyond a wall
+      if (x >= 0 && x < n[d]) continue;
+      if (!wall[d]) {
+        x = (x + n[d]) % n[d];
+        continue;
+      }
+      // crossing a wall maps the value v to 2 U_wall - v (a corner ghost crosses two walls, x first)
+      const bool high = x >= n[d];
+      x = high ? n[d] - 1 : 0;
+      add = -add + ((high && d == 2 && c == 0) ? 2.0 * lid : 0.0);
+      sgn = -sgn;
+    }
+    return sgn * a[at(id[0], id[1], id[2])] + add;
+  }
+  double P(const double* q, int i, int j, int k) const {  // pressure-like cell field, Neumann at walls
+    int id[3] = {i, j, k};
+    for (int d = 0; d < 3; ++d) {
+      int& x = id[d];
+      if (x >= 0 && x < n[d]) continue;
+      x = wall[d] ? (x < 0 ? 0 : n[d] - 1) : (x + n[d]) % n[d];
+    }
+    return q[at(id[0], id[1], id[2])];
+  }
+  bool wall_face(int c, int i, int j, int k) const {
+    const int x = (c == 0) ? i : (c == 1 ? j : k);
+    return wall[c] && x == n[c] - 1;
+  }
+};
+
+void box_divergence(const Box& g, const double* u, const double* v, const double* w, double* out) {
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i)
+        out[g.at(i, j, k)] = (g.V(u, 0, i, j, k) - g.V(u, 0, i - 1, j, k)) / g.dx +
+                             (g.V(v, 1, i, j, k) - g.V(v, 1, i, j - 1, k)) / g.dy +
+                             (g.V(w, 2, i, j, k) - g.V(w, 2, i, j, k - 1)) / g.dzf[k];
+}
+
+void box_gradient(const Box& g, const double* q, double* gx, double* gy, double* gz) {
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const size_t c = g.at(i, j, k);
+        const double qc = q[c];
+        gx[c] = g.wall_face(0, i, j, k) ? 0.0 : (g.P(q, i + 1, j, k) - qc) / g.dx;
+        gy[c] = g.wall_face(1, i, j, k) ? 0.0 : (g.P(q, i, j + 1, k) - qc) / g.dy;
+        gz[c] = g.wall_face(2, i, j, k) ? 0.0 : (g.P(q, i, j, k + 1) - qc) / g.dzc[k + 1];
+      }
+}
+
+// viscous operator of each component at its own faces (3-point differences; z metrics of cell
+// centres for u, v and of faces for w)
+void box_laplacian(const Box& g, const double* u, const double* v, const double* w, double* lu, double* lv,
+                   double* lw) {
+  const double idx2 = 1.0 / (g.dx * g.dx), idy2 = 1.0 / (g.dy * g.dy);
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const size_t c = g.at(i, j, k);
+        const double* F[3] = {u, v, w};
+        double* L[3] = {lu, lv, lw};
+        for (int q = 0; q < 3; ++q) {
+          if (g.wall_face(q, i, j, k)) {
+            L[q][c] = 0.0;
+            continue;
+          }
+          const double* a = F[q];
+          const double ac = g.V(a, q, i, j, k);
+          const double lx = (g.V(a, q, i - 1, j, k) - 2 * ac + g.V(a, q, i + 1, j, k)) * idx2;
+          const double ly = (g.V(a, q, i, j - 1, k) - 2 * ac + g.V(a, q, i, j + 1, k)) * idy2;
+          double lz;
+          if (q < 2) {
+            lz = ((g.V(a, q, i, j, k + 1) - ac) / g.dzc[k + 1] - (ac - g.V(a, q, i, j, k - 1)) / g.dzc[k]) / g.dzf[k];
+          } else {
+            const double dzu = g.dzf[(k + 1) % g.n[2]], mid = g.dzc[k + 1];
+            lz = ((g.V(a, q, i, j, k + 1) - ac) / dzu - (ac - g.V(a, q, i, j, k - 1)) / g.dzf[k]) / mid;
+          }
+          L[q][c] = lx + ly + lz;
+        }
+      }
+}
+
+// conservative advection -div(u u) with two-point averages at each component's faces
+void box_advection(const Box& g, const double* u, const double* v, const double* w, double* au, double* av,
+                   double* aw) {
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const size_t c = g.at(i, j, k);
+        auto U = [&](int a, int b, int e) { return g.V(u, 0, a, b, e); };
+        auto Vv = [&](int a, int b, int e) { return g.V(v, 1, a, b, e); };
+        auto Ww = [&](int a, int b, int e) { return g.V(w, 2, a, b, e); };
+        if (g.wall_face(0, i, j, k)) {
+          au[c] = 0.0;
+        } else {  // u at (i+1/2, j, k)
+          const double ue = 0.5 * (U(i, j, k) + U(i + 1, j, k)), uw = 0.5 * (U(i - 1, j, k) + U(i, j, k));
+          const double un = 0.5 * (U(i, j, k) + U(i, j + 1, k)) * 0.5 * (Vv(i, j, k) + Vv(i + 1, j, k));
+          const double us = 0.5 * (U(i, j - 1, k) + U(i, j, k)) * 0.5 * (Vv(i, j - 1, k) + Vv(i + 1, j - 1, k));
+          const double ut = 0.5 * (U(i, j, k) + U(i, j, k + 1)) * 0.5 * (Ww(i, j, k) + Ww(i + 1, j, k));
+          const double ub = 0.5 * (U(i, j, k - 1) + U(i, j, k)) * 0.5 * (Ww(i, j, k - 1) + Ww(i + 1, j, k - 1));
+          au[c] = -((ue * ue - uw * uw) / g.dx + (un - us) / g.dy + (ut - ub) / g.dzf[k]);
+        }
+        if (g.wall_face(1, i, j, k)) {
+          av[c] = 0.0;
+        } else {  // v at (i, j+1/2, k)
+          const double ve = 0.5 * (Vv(i, j, k) + Vv(i + 1, j, k)) * 0.5 * (U(i, j, k) + U(i, j + 1, k));
+          const double vw = 0.5 * (Vv(i - 1, j, k) + Vv(i, j, k)) * 0.5 * (U(i - 1, j, k) + U(i - 1, j + 1, k));
+          const double vn = 0.5 * (Vv(i, j, k) + Vv(i, j + 1, k)), vs = 0.5 * (Vv(i, j - 1, k) + Vv(i, j, k));
+          const double vt = 0.5 * (Vv(i, j, k) + Vv(i, j, k + 1)) * 0.5 * (Ww(i, j, k) + Ww(i, j + 1, k));
+          const double vb = 0.5 * (Vv(i, j, k - 1) + Vv(i, j, k)) * 0.5 * (Ww(i, j, k - 1) + Ww(i, j + 1, k - 1));
+          av[c] = -((ve - vw) / g.dx + (vn * vn - vs * vs) / g.dy + (vt - vb) / g.dzf[k]);
+        }
+        if (g.wall_face(2, i, j, k)) {
+          aw[c] = 0.0;
+        } else {  // w at (i, j, k+1/2)
+          const double we = 0.5 * (Ww(i, j, k) + Ww(i + 1, j, k)) * 0.5 * (U(i, j, k) + U(i, j, k + 1));
+          const double ww = 0.5 * (Ww(i - 1, j, k) + Ww(i, j, k)) * 0.5 * (U(i - 1, j, k) + U(i - 1, j, k + 1));
+          const double wn = 0.5 * (Ww(i, j, k) + Ww(i, j + 1, k)) * 0.5 * (Vv(i, j, k) + Vv(i, j, k + 1));
+          const double ws = 0.5 * (Ww(i, j - 1, k) + Ww(i, j, k)) * 0.5 * (Vv(i, j - 1, k) + Vv(i, j - 1, k + 1));
+          const double wt = 0.5 * (Ww(i, j, k) + Ww(i, j, k + 1)), wb = 0.5 * (Ww(i, j, k - 1) + Ww(i, j, k));
+          aw[c] = -((we - ww) / g.dx + (wn - ws) / g.dy + (wt * wt - wb * wb) / g.dzc[k + 1]);
+        }
+      }
+}
+
+double box_max_dti(const Box& g, const double* u, const double* v, const double* w) {
+  double dti = 0;
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        auto U = [&](int a, int b, int e) { return g.V(u, 0, a, b, e); };
+        auto Vv = [&](int a, int b, int e) { return g.V(v, 1, a, b, e); };
+        auto Ww = [&](int a, int b, int e) { return g.V(w, 2, a, b, e); };
+        const double dtix = std::fabs(U(i, j, k)) / g.dx +
+                            0.25 * std::fabs(Vv(i, j, k) + Vv(i, j - 1, k) + Vv(i + 1, j, k) + Vv(i + 1, j - 1, k)) / g.dy +
+                            0.25 * std::fabs(Ww(i, j, k) + Ww(i, j, k - 1) + Ww(i + 1, j, k) + Ww(i + 1, j, k - 1)) / g.dzf[k];
+        const double dtiy = 0.25 * std::fabs(U(i, j, k) + U(i - 1, j, k) + U(i, j + 1, k) + U(i - 1, j + 1, k)) / g.dx +
+                            std::fabs(Vv(i, j, k)) / g.dy +
+                            0.25 * std::fabs(Ww(i, j, k) + Ww(i, j, k - 1) + Ww(i, j + 1, k) + Ww(i, j + 1, k - 1)) / g.dzf[k];
+        const double dtiz = 0.25 * std::fabs(U(i, j, k) + U(i - 1, j, k) + U(i, j, k + 1) + U(i - 1, j, k + 1)) / g.dx +
+                            0.25 * std::fabs(Vv(i, j, k) + Vv(i, j - 1, k) + Vv(i, j, k + 1) + Vv(i, j - 1, k + 1)) / g.dy +
+                            std::fabs(Ww(i, j, k)) / g.dzc[k + 1];
+        dti = std::max(dti, std::max(dtix, std::max(dtiy, dtiz)));
+      }
+  return dti;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Projection u - G L^-1 D u in the box (pressure Neumann at walls, periodic elsewhere).
+int oracle_box_project(const int n[3], const int wall[3], const double len_xy[2], const double* dzf, double* u,
+                       double* v, double* w, int nthreads) {
+  Box g(n, wall, 0.0, len_xy, dzf);
+  const size_t N = g.size();
+  std::vector<double> d(N), phi(N), gx(N), gy(N), gz(N);
+  box_divergence(g, u, v, w, d.data());
+  const int bc[3] = {wall[0] ? BC_NN : BC_P, wall[1] ? BC_NN : BC_P, wall[2] ? BC_NN : BC_P};
+  int rc = solve_t<double>(n, len_xy, bc, dzf, d.data(), phi.data(), nthreads_or_default(nthreads));
+  if (rc) return rc;
+  box_gradient(g, phi.data(), gx.data(), gy.data(), gz.data());
+  for (size_t c = 0; c < N; ++c) {
+    u[c] -= gx[c];
+    v[c] -= gy[c];
+    w[c] -= gz[c];
+  }
+  return 0;
+}
+
+int oracle_box_divergence(const int n[3], const int wall[3], const double len_xy[2], const double* dzf,
+                          const double* u, const double* v, const double* w, double* out) {
+  Box g(n, wall, 0.0, len_xy, dzf);
+  box_divergence(g, u, v, w, out);
+  return 0;
+}
+
+// advection (a*) and viscous (l*) operators of the momentum equations in the box
+int oracle_box_operators(const int n[3], const int wall[3], double lid, const double len_xy[2], const double* dzf,
+                         const double* u, const double* v, const double* w, double* au, double* av, double* aw,
+                         double* lu, double* lv, double* lw) {
+  Box g(n, wall, lid, len_xy, dzf);
+  box_advection(g, u, v, w, au, av, aw);
+  box_laplacian(g, u, v, w, lu, lv, lw);
+  return 0;
+}
+
+// One explicit RK3 fractional step in the box (Eq. up, Eq. poi_ns, correction, p += Phi); dt from
+// Eq. dt unless dt_in > 0; forcing != 0 shifts u to the bulk velocity ubulk after each substage.
+int oracle_box_rk3_step(const int n[3], const int wall[3], double lid, const double len_xy[2], const double* dzf,
+                        double nu, double cfl, double ubulk, int forcing, double dt_in, double* u, double* v,
+                        double* w, double* p, double* dt_out, int nthreads) {
+  Box g(n, wall, lid, len_xy, dzf);
+  const size_t N = g.size();
+  double dt = dt_in;
+  if (!(dt_in > 0)) {
+    double dl = std::min(g.dx, g.dy);
+    for (int k = 0; k < g.n[2]; ++k) dl = std::min(dl, g.dzf[k]);
+    const double dti = box_max_dti(g, u, v, w);
+    dt = 1.65 * dl * dl / nu;
+    if (dti > 0) dt = std::min(dt, std::sqrt(3.0) / dti);
+    dt *= cfl;
+  }
+  std::vector<double> au(N), av(N), aw(N), lu(N), lv(N), lw(N), pu(N, 0.0), pv(N, 0.0), pw(N, 0.0);
+  std::vector<double> gx(N), gy(N), gz(N), d(N), phi(N);
+  const int bc[3] = {wall[0] ? BC_NN : BC_P, wall[1] ? BC_NN : BC_P, wall[2] ? BC_NN : BC_P};
+  nthreads = nthreads_or_default(nthreads);
+  for (int s = 0; s < 3; ++s) {
+    const double a = RK_A[s], b = RK_B[s], gm = a + b;
+    box_advection(g, u, v, w, au.data(), av.data(), aw.data());
+    box_laplacian(g, u, v, w, lu.data(), lv.data(), lw.data());
+    box_gradient(g, p, gx.data(), gy.data(), gz.data());
+    for (size_t c = 0; c < N; ++c) {
+      const double ru = au[c] + nu * lu[c], rv = av[c] + nu * lv[c], rw = aw[c] + nu * lw[c];
+      u[c] += dt * (a * ru + b * pu[c] - gm * gx[c]);
+      v[c] += dt * (a * rv + b * pv[c] - gm * gy[c]);
+      w[c] += dt * (a * rw + b * pw[c] - gm * gz[c]);
+      pu[c] = ru;
+      pv[c] = rv;
+      pw[c] = rw;
+    }
+    box_divergence(g, u, v, w, d.data());
+    for (size_t c = 0; c < N; ++c) d[c] /= gm * dt;
+    const int rc = solve_t<double>(n, len_xy, bc, dzf, d.data(), phi.data(), nthreads);
+    if (rc) return rc;
+    box_gradient(g, phi.data(), gx.data(), gy.data(), gz.data());
+    for (size_t c = 0; c < N; ++c) {
+      u[c] -= gm * dt * gx[c];
+      v[c] -= gm * dt * gy[c];
+      w[c] -= gm * dt * gz[c];
+      p[c] += phi[c];
+    }
+    if (forcing) {
+      double sum = 0, vol = 0;
+      for (int k = 0; k < g.n[2]; ++k)
+        for (int j = 0; j < g.n[1]; ++j)
+          for (int i = 0; i < g.n[0]; ++i) {
+            sum += g.dzf[k] * u[g.at(i, j, k)];
+            vol += g.dzf[k];
+          }
+      const double shift = ubulk - sum / vol;
+      for (size_t c = 0; c < N; ++c) u[c] += shift;
+    }
+  }
+  if (dt_out) *dt_out = dt;
+  return 0;
+}
+
+}  // extern "C"
