@@ -66,9 +66,8 @@ def test_opts_defaults(cans):
         ((7, 8, 4), (1, 1), (0, 0, 1), None, -2),  # odd periodic N
         ((8, 10, 4), (1, 1), (0, 1, 1), None, -2),  # N/2 = 5 does not factor into 2s and 3s
         ((8, 8, 600), (1, 1), (0, 0, 1), None, -2),  # Nz above 512
-        ((8, 8, 8), (1, 1), (3, 0, 1), None, -2),  # mixed wall pair along x: z only in this build
-        ((8, 8, 8), (1, 1), (0, 4, 1), None, -2),  # mixed wall pair along y
         ((8, 8, 8), (1, 1), (0, 0, 6), None, -1),  # no such boundary condition
+        ((7, 8, 8), (1, 1), (3, 0, 1), None, -2),  # odd N along a quarter-wave direction
     ],
 )
 def test_plan_rejects_bad_arguments_on_the_host(cans, n, L, bc, dzf, want):
