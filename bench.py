@@ -186,8 +186,11 @@ def gpu_arm(args):
             break
     if sweeps_used is None:
         sweeps_used, info_used = 3, info
+    t_plan = time.perf_counter()
     solver = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sweeps_used,
                                 autotune=True)
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t_plan) * 1e3  # includes the autotuning (or its cache hit) and workspace
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -290,6 +293,7 @@ def gpu_arm(args):
         "ms_per_step": ms,
         "ms_per_solve_median": per_solve[len(per_solve) // 2],
         "ms_per_solve_best": per_solve[0],
+        "plan_ms_autotuned": plan_ms,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -419,8 +423,15 @@ def config2_measure(cans, I, args):
     ms_cufft = timed(lambda: comparator(f))
     s.close()
     npts = nx * ny * nz
+    hbm, _ = _peaks()
+    # FP64 flop model: ~2.5 log2 N flops per point per real transform direction and pass (4 passes)
+    # plus ~6 for the Makhoul twiddles and ~9 for the z elimination; FP64 peak 1.13 TFLOP/s (the
+    # measured 0.57 T FMA/s of this GPU)
+    flops = npts * (2 * (2.5 * np.log2(nx) + 6) + 2 * (2.5 * np.log2(ny) + 6) + 9)
+    out_frac = {"hbm_frac_80B_model": 80.0 * npts / (ms_lib * 1e-3) / 1e9 / hbm,
+                "fp64_flop_frac": flops / (ms_lib * 1e-3) / 1.13e12}
     return {"workload": "poisson_channel_1024x512x256_P-DD-NN_tanh1.8_fp64", "unit": "ms/solve",
-            "fp64": ms_lib, "fp64_gpts": npts / (ms_lib * 1e-3) / 1e9,
+            "fp64": ms_lib, "fp64_gpts": npts / (ms_lib * 1e-3) / 1e9, **out_frac,
             "cufft_comparator": ms_cufft, "cufft_comparator_gpts": npts / (ms_cufft * 1e-3) / 1e9,
             "comparator_rel_l2_vs_library": rel,
             "note": "comparator: torch.fft (cuFFT) x rfft + y DST-II via Makhoul + this library's z solve"}
@@ -540,8 +551,14 @@ def ensemble_measure(cans, I, args):
     ms = e0.elapsed_time(e1) / reps
     pts = sum(c.points for c in cases)
     b.close()
+    hbm, _ = _peaks()
+    # pass models (per point): five passes per solve and sweep -- mixed first solve 48 B, each sweep 64
+    # B; three passes when a plane fits on chip (x-y fused) -- first solve 32 B, each sweep 48 B
+    five, three = (48 + 2 * 64) * pts, (32 + 2 * 48) * pts
     return {"workload": "ensemble64_dims32-192_mixed_2sweeps", "problems": len(cases), "points": pts,
-            "ms_per_batch": ms, "value": pts / (ms * 1e-3) / 1e9, "unit": "Gpts/s"}
+            "ms_per_batch": ms, "value": pts / (ms * 1e-3) / 1e9, "unit": "Gpts/s",
+            "hbm_frac_5pass_model": five / (ms * 1e-3) / 1e9 / hbm,
+            "hbm_frac_3pass_model": three / (ms * 1e-3) / 1e9 / hbm}
 
 
 # ------------------------------------------------------------------------------------------------

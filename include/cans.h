@@ -282,6 +282,22 @@ int cans_rk3_step_implicit(cans_plan_t plan, cans_plan_t uv_plan, cans_plan_t w_
                            void* cuda_stream);
 
 /*
+ * cans_box_rk3_step: the explicit RK3 step of cans_rk3_step in a box whose directions are periodic or
+ * bounded by no-slip walls, read from the plan's boundary conditions: CANS_BC_P = periodic,
+ * CANS_BC_NN = walls (the pressure is Neumann there).  It covers the flows the paper lists for its
+ * solver: lid-driven cavity (NN, NN, NN with a lid), square duct (P, NN, NN with forcing), channel
+ * (P, P, NN) and the periodic Taylor-Green box (P, P, P, uniform z).  A velocity component normal to
+ * a walled direction lives on that direction's faces and stays 0 on its last stored face (the high
+ * wall); tangential components take the no-slip ghost 2 U_wall - u, U_wall = lid for u at the top z
+ * wall (lid != 0 needs z walls).  params as cans_rk3_step (forcing shifts u to ubulk).  Plans with
+ * other boundary conditions, a shift or z_grid 1 return CANS_ERR_UNSUPPORTED.  workspace:
+ * cans_box_rk3_workspace_size() bytes, 256-byte aligned.  Asynchronous.
+ */
+int cans_box_rk3_workspace_size(cans_plan_t plan, size_t* bytes);
+int cans_box_rk3_step(cans_plan_t plan, double* u, double* v, double* w, double* p, const cans_rk3_params* params,
+                      double lid, double* dt_dev, void* workspace, void* cuda_stream);
+
+/*
  * cans_project: in place, u <- P u = u - G L^-1 D u, the discretely divergence-free part of a face field
  * (the correction of Eq. poi_ns with gamma dt cancelled).  cans_project_adjoint: u <- P^T u =
  * W_f P W_f^-1 u with W_f the face volumes (dzf for u and v faces, the centre distance for w faces),

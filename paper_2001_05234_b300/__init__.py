@@ -82,6 +82,9 @@ def lib() -> ctypes.CDLL:
         L.cans_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
         L.cans_rk3_implicit_workspace_size.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_box_rk3_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_box_rk3_step.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), ctypes.c_double, vp,
+                                        vp, vp]
         L.cans_rk3_step_implicit.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(cans_rk3_params), vp, vp, vp]
         L.cans_project_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_project.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -461,6 +464,40 @@ class Channel:
             if getattr(self, name, None):
                 cans_plan_destroy(getattr(self, name))
                 setattr(self, name, None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Box:
+    """Fractional-step flow in a box: each direction periodic (False) or bounded by no-slip walls (True),
+    an optional lid (the top z wall moving along x).  u, v, w, p: float64 CUDA tensors (Nz, Ny, Nx)."""
+
+    def __init__(self, n, length_xy, dzf, walls, prec=CANS_FP64, sweeps=2):
+        self.n = tuple(int(v) for v in n)
+        self.walls = tuple(bool(x) for x in walls)
+        o = cans_opts_default()
+        o.prec, o.max_sweeps = int(prec), int(sweeps)
+        bc = tuple(CANS_BC_NN if wl else CANS_BC_P for wl in self.walls)
+        _, self.plan = cans_poisson_plan(self.n, length_xy, bc, dzf, o)
+        b = ctypes.c_size_t()
+        _check(lib().cans_box_rk3_workspace_size(self.plan, ctypes.byref(b)), "cans_box_rk3_workspace_size")
+        self._buf, self._ws = _aligned_workspace(int(b.value))
+
+    def rk3_step(self, u, v, w, p, nu, cfl=0.5, ubulk=0.0, dt=0.0, forcing=False, lid=0.0, dt_out=None, stream=None):
+        prm = cans_rk3_params(float(nu), float(cfl), float(ubulk), float(dt), 1 if forcing else 0)
+        st = lib().cans_box_rk3_step(self.plan, u.data_ptr(), v.data_ptr(), w.data_ptr(), p.data_ptr(),
+                                     ctypes.byref(prm), float(lid), dt_out.data_ptr() if dt_out is not None else None,
+                                     self._ws, _stream_ptr(stream) or None)
+        _check(st, "cans_box_rk3_step")
+
+    def close(self):
+        if getattr(self, "plan", None):
+            cans_plan_destroy(self.plan)
+            self.plan = None
 
     def __del__(self):
         try:
