@@ -321,6 +321,7 @@ def gpu_arm(args):
             "peak_source": peak_src,
             "unit": "GB/s",
             "frac": achieved / hbm_peak,
+            "frac_of_nominal_7700GBs": achieved / 7700.0,
             "traffic": (NCU_DRAM_BYTES_PER_POINT[dominant[0]] * npts
                         if dominant[0] in NCU_DRAM_BYTES_PER_POINT else None),
             "algorithmic_bytes_per_launch": dom_bytes,

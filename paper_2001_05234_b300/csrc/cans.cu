@@ -5,6 +5,7 @@
 // FP64 in place in p; mixed mode runs the passes in FP32 with a double-float residual / iterate and
 // FP64 z-solves for the smallest-|mu| modes.  The pass kernels live in kern_*.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -612,11 +613,18 @@ cudaError_t cans::set_smem(const void* fn, size_t bytes) {
 namespace {
 
 // Event pair around one pass launch when profiling is on.
+// Each pass is an NVTX range (seen by Nsight tools attached to the process; a no-op otherwise) and,
+// while cans_plan_profile is on, a pair of CUDA events on the solve's stream.
+const char* const kPassName[CANS_PASS_COUNT] = {"x_forward",          "y_forward",        "z_solve",
+                                                "y_inverse",          "x_inverse",        "x_forward_residual",
+                                                "x_inverse_update",   "residual_stencil", "z_solve_double_columns"};
+
 struct PassTimer {
   cans_plan_s* P;
   cudaStream_t st;
   int rec = -1;
   PassTimer(cans_plan_s* P_, int kind, cudaStream_t st_) : P(P_), st(st_) {
+    nvtxRangePushA(kPassName[kind]);
     if (!P->profiling) return;
     if ((size_t)(2 * P->ev_used + 2) > P->ev_pool.size()) {
       for (int q = 0; q < 64; ++q) {
@@ -631,6 +639,7 @@ struct PassTimer {
   }
   ~PassTimer() {
     if (rec >= 0) cudaEventRecord(P->ev_pool[2 * rec + 1], st);
+    nvtxRangePop();
   }
 };
 

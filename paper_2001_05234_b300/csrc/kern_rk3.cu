@@ -8,6 +8,7 @@
 // cell centres.  Advection: conservative divergence of u (x) u with two-point averages; diffusion:
 // 3-point Laplacian with no-slip ghosts (ghost = -interior).  Everything in FP64.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -352,6 +353,12 @@ using namespace cans;
 
 namespace {
 
+// NVTX range of one RK3 substage (host timeline of its enqueued work; a no-op without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 const double RK_ALPHA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double RK_BETA[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
 
@@ -401,6 +408,7 @@ int cans_rk3_step(cans_plan_t P, double* u, double* v, double* w, double* p, con
   double* dt = dt_dev ? dt_dev : small;
   RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt, st));
   for (int s = 0; s < 3; ++s) {
+    NvtxRange substage(s == 0 ? "rk3_substage_1" : (s == 1 ? "rk3_substage_2" : "rk3_substage_3"));
     const double a = RK_ALPHA[s], b = RK_BETA[s], g = a + b;
     RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, g, dt, st));
     RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
@@ -466,6 +474,7 @@ int cans_rk3_step_implicit(cans_plan_t P, cans_plan_t U, cans_plan_t W, double* 
   double* dt = dt_dev ? dt_dev : small;
   RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt, st));
   for (int s = 0; s < 3; ++s) {
+    NvtxRange substage(s == 0 ? "rk3_implicit_substage_1" : (s == 1 ? "rk3_implicit_substage_2" : "rk3_implicit_substage_3"));
     const double a = RK_ALPHA[s], b = RK_BETA[s], g = a + b;
     const double h = g * prm->nu * prm->dt / 2, sigma = -1.0 / h;
     RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, fu, fv, fw, prm->nu, a, b, g, dt, st, sigma));
