@@ -477,7 +477,7 @@ def config1_measure(cans, I, args):
 
 def next_rows_measure(cans, I, args):
     """The widened rows at scale: the mixed solve of the headline grid with quarter-wave x / y walls
-    (Neumann-Dirichlet in x, Dirichlet-Neumann in y: the shared-memory line engine), the Helmholtz solve
+    (Neumann-Dirichlet in x, Dirichlet-Neumann in y), the Helmholtz solve
     (shift -2 / (gamma nu dt) of a Re_b = 5600 step) of the headline grid, and ms per RK3 step of the box
     flows (one CUDA graph per step, mixed Poisson with 2 sweeps): lid-driven cavity 256^3, square duct
     512 x 256 x 256 (forced), Taylor-Green box 256^3."""
@@ -557,8 +557,7 @@ def next_rows_measure(cans, I, args):
         box.close()
         del u, v, w, pr, g
         torch.cuda.empty_cache()
-    out["note"] = ("quarter-wave directions run on the shared-memory line engine; Helmholtz shift -1e4; box "
-                   "steps FP64 momentum / projection kernels, mixed Poisson (2 sweeps)")
+    out["note"] = ("Helmholtz shift -1e4; box steps FP64 momentum / projection kernels, mixed Poisson (2 sweeps)")
     return out
 
 

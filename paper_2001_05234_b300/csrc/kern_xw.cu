@@ -299,13 +299,15 @@ template <int MODE>
 cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
                              double* acc, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || !aligned16(f) || !aligned16(dst) || quarter(P->bc[0])) return cudaSuccess;  // quarter-wave: CTA engine
+  if (P->wblk || !aligned16(f) || !aligned16(dst)) return cudaSuccess;
   const int bc = P->bc[0];
   *handled = true;
 #define XW_CASE(MM)                                                            \
   if (P->dx.m == MM) {                                                         \
     if (bc == BC_P) return xfwd_w<MM, BC_P, MODE>(P, f, Phi, Plo, dst, acc, st);   \
     if (bc == BC_NN) return xfwd_w<MM, BC_NN, MODE>(P, f, Phi, Plo, dst, acc, st); \
+    if (bc == BC_ND) return xfwd_w<MM, BC_ND, MODE>(P, f, Phi, Plo, dst, acc, st); \
+    if (bc == BC_DN) return xfwd_w<MM, BC_DN, MODE>(P, f, Phi, Plo, dst, acc, st); \
     return xfwd_w<MM, BC_DD, MODE>(P, f, Phi, Plo, dst, acc, st);                  \
   }
   XW_CASE(128)
@@ -320,7 +322,7 @@ template <int MODE>
 cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
                              double* gauge, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || !aligned16(src) || quarter(P->bc[0])) return cudaSuccess;
+  if (P->wblk || !aligned16(src)) return cudaSuccess;
   if ((MODE == 0 || MODE == 3 || MODE == 5) && !aligned16(p)) return cudaSuccess;
   if (upd_reads<MODE>() > 0 && !aligned16(Phi)) return cudaSuccess;
   if (upd_reads<MODE>() == 2 && !aligned16(Plo)) return cudaSuccess;
@@ -330,6 +332,8 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
   if (P->dx.m == MM) {                                                                    \
     if (bc == BC_P) return xinv_w<MM, BC_P, MODE>(P, src, p, Phi, Plo, scale, gauge, st);   \
     if (bc == BC_NN) return xinv_w<MM, BC_NN, MODE>(P, src, p, Phi, Plo, scale, gauge, st); \
+    if (bc == BC_ND) return xinv_w<MM, BC_ND, MODE>(P, src, p, Phi, Plo, scale, gauge, st); \
+    if (bc == BC_DN) return xinv_w<MM, BC_DN, MODE>(P, src, p, Phi, Plo, scale, gauge, st); \
     return xinv_w<MM, BC_DD, MODE>(P, src, p, Phi, Plo, scale, gauge, st);                  \
   }
   XW_CASE(128)

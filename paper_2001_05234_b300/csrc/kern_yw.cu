@@ -112,13 +112,15 @@ cudaError_t yw(const cans_plan_s* P, float* w, cudaStream_t st) {
 template <int DIR>
 cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (P->wblk || P->n[0] % YW_L != 0 || (reinterpret_cast<uintptr_t>(w) & 15) || quarter(P->bc[1])) return cudaSuccess;
+  if (P->wblk || P->n[0] % YW_L != 0 || (reinterpret_cast<uintptr_t>(w) & 15)) return cudaSuccess;
   const int bc = P->bc[1];
   *handled = true;
 #define YW_CASE(MM)                                                  \
   if (P->dy.m == MM) {                                               \
     if (bc == BC_P) return yw<MM, BC_P, DIR>(P, w, st);              \
     if (bc == BC_NN) return yw<MM, BC_NN, DIR>(P, w, st);            \
+    if (bc == BC_ND) return yw<MM, BC_ND, DIR>(P, w, st);            \
+    if (bc == BC_DN) return yw<MM, BC_DN, DIR>(P, w, st);            \
     return yw<MM, BC_DD, DIR>(P, w, st);                             \
   }
   YW_CASE(128)

@@ -177,6 +177,43 @@ __device__ __forceinline__ void put_pair(Snk& snk, int k, float o0, float o1) {
   }
 }
 
+// Quarter-wave line (a Neumann wall paired with a Dirichlet wall; the direction's tables hold the
+// pre-twiddle exp(-i pi (4m+1)/4N) in mak and the post-twiddle exp(-i pi k/N) in post): z_m =
+// (x_2m + i x_{N-1-2m}) times the pre-twiddle (sine lines: the odd sample negated), the stages, then
+// u_k = Z_k times the post-twiddle gives F Re u_k and -F Im u_k at positions 2k and N-1-2k (sine
+// lines: swapped).  The forward transform (DCT-IV / DST-IV) has F = 2; as both are their own
+// inverses up to 2N, the inverse (times N) is the same line with F = 1 -- get/put read input
+// positions and write output positions in either direction.  No partner pairing is needed.
+template <int M, int BC, bool ALIAS, bool WAIT_ASYNC, int G, typename XB, typename Get, typename Put>
+__device__ __forceinline__ void quarter_line(const XB& xb, const LineTab<float>& tb, int lane, float F, Get get,
+                                             Put put, int bar) {
+  constexpr int L = 32 * G, V = M / L, N = 2 * M;
+  float2 v[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int m = lane + L * t;
+    const float a = get(2 * m);
+    float b = get(N - 1 - 2 * m);
+    if (BC == BC_DN) b = -b;  // N - 1 - 2m is odd
+    v[t] = cmul(make_float2(a, b), ld_tw(tb.mak, m));
+  }
+  if (ALIAS) gsync<G>(bar);  // every lane has its inputs before the buffer is overwritten
+  Stages<M, 0, nstages(M, G), G>::run(v, xb, tb.wst, lane, bar);
+  if (WAIT_ASYNC) {  // the sink reads data the caller staged with cp.async before the line began
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    gsync<G>(bar);
+  }
+#pragma unroll
+  for (int t = 0; t < V; ++t) {
+    const int k = lane + L * t;
+    const float2 u = cmul(v[t], ld_tw(tb.post, k));
+    const int pa = (BC == BC_DN) ? N - 1 - 2 * k : 2 * k, pb = (BC == BC_DN) ? 2 * k : N - 1 - 2 * k;
+    put(pa, F * u.x);
+    put(pb, -F * u.y);
+  }
+  gsync<G>(bar);
+}
+
 // Forward transform of one line.
 //   src.pair(n) -> float2 (x_n, x_n+1), n even (periodic lines);  src.one(n) -> x_n (walls).
 //   snk.put(s, y) stores output slot s.
@@ -188,6 +225,11 @@ template <int M, int BC, bool ALIAS = false, int G = 1, bool PARTNER_SHFL = fals
           typename Snk>
 __device__ __forceinline__ void forward(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
                                         int bar = 0) {
+  if constexpr (BC == BC_ND || BC == BC_DN) {
+    quarter_line<M, BC, ALIAS || PARTNER_SHFL, false, G>(
+        xb, tb, lane, 2.f, [&](int n) { return src.one(n); }, [&](int s, float y) { snk.put(s, y); }, bar);
+    return;
+  }
   constexpr int L = 32 * G, V = M / L, N = 2 * M;
   float2 v[V];
 #pragma unroll
@@ -279,6 +321,11 @@ template <int M, int BC, bool WAIT_ASYNC = false, int G = 1, bool PARTNER_SHFL =
           typename Snk>
 __device__ __forceinline__ void inverse(const XB& xb, const LineTab<float>& tb, int lane, Src& src, Snk& snk,
                                         int bar = 0) {
+  if constexpr (BC == BC_ND || BC == BC_DN) {
+    quarter_line<M, BC, true, WAIT_ASYNC, G>(
+        xb, tb, lane, 1.f, [&](int s) { return src.get(s); }, [&](int n, float y) { snk.one(n, y); }, bar);
+    return;
+  }
   constexpr int L = 32 * G, V = M / L, N = 2 * M;
   static_assert(!PARTNER_SHFL || G == 1, "shuffled partners need one warp per line");
   float2 v[V];

@@ -1,6 +1,6 @@
 """GPU parity of the mixed Neumann / Dirichlet wall pairs along x and y: the quarter-wave transforms
-(DCT-IV, DST-IV) of the shared-memory line engine against scipy, and the FP64 / mixed solves
-against the CPU oracle."""
+(DCT-IV, DST-IV) of the shared-memory line engine and of the warp-per-line kernels against scipy, and
+the FP64 / mixed solves against the CPU oracle."""
 import itertools
 
 import numpy as np
@@ -91,10 +91,10 @@ def test_quarter_wave_fp64_transforms(cans, bcx, bcy, n):
 
 
 @pytest.mark.parametrize("bcx,bcy", [(ND, P), (DN, NN), (P, ND), (NN, DN), (ND, DN), (DN, ND), (DD, ND)])
-@pytest.mark.parametrize("n", [(256, 512, 2), (512, 256, 1), (64, 48, 2), (24, 256, 2)])
+@pytest.mark.parametrize("n", [(256, 512, 2), (512, 256, 1), (1024, 256, 1), (64, 48, 2), (24, 256, 2)])
 def test_quarter_wave_f32_transforms(cans, bcx, bcy, n):
-    """The mixed path's float x / y passes: quarter-wave lines take the shared-memory engine even at
-    the sizes where the other boundary conditions take the warp-per-line kernels."""
+    """The mixed path's float x / y passes: quarter-wave lines on the warp-per-line kernels for N in
+    {256, 512, 1024} (Nx a multiple of 16 for y), the shared-memory engine otherwise."""
     import torch
 
     h = make_plan(cans, n, (bcx, bcy, NN), prec=1)
@@ -136,8 +136,8 @@ def test_quarter_wave_solves_match_oracle(cans, bcx, bcy, bcz, prec):
                                   ((256, 128, 16), (ND, P, NN)), ((128, 256, 16), (P, DN, NN))])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_quarter_wave_edge_and_large_shapes(cans, n, bc, prec):
-    """One-cell and two-cell directions, and warp-engine-sized shapes whose quarter-wave direction
-    falls back to the shared-memory engine (and the mixed residual to the fused x pass)."""
+    """One-cell and two-cell directions, and warp-engine-sized shapes (quarter-wave lines on the
+    warp-per-line kernels; the mixed residual in the fused warp x pass)."""
     import torch
 
     dzf = I.tanh_dzf(n[2], 1.5)
