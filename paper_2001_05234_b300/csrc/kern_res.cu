@@ -16,12 +16,6 @@ namespace {
 
 constexpr int RX = 32, RY = 8;  // CTA tile of columns
 
-// compile-time boundary kinds: ghost of a wall neighbour (Neumann mirrors, Dirichlet flips sign)
-template <int BC>
-__device__ __forceinline__ float ghost(float c) {
-  return (BC == BC_NN) ? c : -c;
-}
-
 // coef * x as a double-float (coef and x double-float): the product's exact head and a float tail
 __device__ __forceinline__ df df_prod(df coef, df x) {
   df p = two_prod(coef.hi, x.hi);
@@ -57,6 +51,11 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
     const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
     const bool gxm = BX != BC_P && i == 0, gxp = BX != BC_P && i == nx - 1;
     const bool gym = BY != BC_P && j == 0, gyp = BY != BC_P && j == ny - 1;
+    // x / y wall ghosts: the sign of each wall (compile time for NN / DD, from S for a mixed pair, BC_ND)
+    const float sxm = (BX == BC_NN) ? 1.f : (BX == BC_DD) ? -1.f : ((S.xlo == BC_NN) ? 1.f : -1.f);
+    const float sxp = (BX == BC_NN) ? 1.f : (BX == BC_DD) ? -1.f : ((S.xhi == BC_NN) ? 1.f : -1.f);
+    const float sym = (BY == BC_NN) ? 1.f : (BY == BC_DD) ? -1.f : ((S.ylo == BC_NN) ? 1.f : -1.f);
+    const float syp = (BY == BC_NN) ? 1.f : (BY == BC_DD) ? -1.f : ((S.yhi == BC_NN) ? 1.f : -1.f);
     const int c0 = j * nx + i;
     const int dxm = j * nx + im - c0, dxp = j * nx + ip - c0, dym = jm * nx + i - c0, dyp = jp * nx + i - c0;
     const int kprev = (k0 == 0) ? nz - 1 : k0 - 1;
@@ -104,10 +103,10 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
             fr[u] = fp[(size_t)PF * sz];
             pr[u] = (k + PF == nz - 1) ? Phi[c0] : pp[(size_t)(PF + 1) * sz];
           }
-          const float xm = gxm ? ghost<BX>(p_cur) : nxm;
-          const float xp = gxp ? ghost<BX>(p_cur) : nxp;
-          const float ym = gym ? ghost<BY>(p_cur) : nym;
-          const float yp = gyp ? ghost<BY>(p_cur) : nyp;
+          const float xm = gxm ? sxm * p_cur : nxm;
+          const float xp = gxp ? sxp * p_cur : nxp;
+          const float ym = gym ? sym * p_cur : nym;
+          const float yp = gyp ? syp * p_cur : nyp;
           if (k + 1 < k1) {
             nxm = pp[sz + dxm];
             nxp = pp[sz + dxp];
@@ -139,10 +138,10 @@ __global__ void __launch_bounds__(RX * RY, 4) res_kernel(const double* __restric
           if (PLO) {
             const long long dzp = top ? -(long long)(nz - 1) * sz : (long long)sz;
             const float q_next = qp[dzp];
-            const float qxm = gxm ? ghost<BX>(q_cur) : qp[dxm];
-            const float qxp = gxp ? ghost<BX>(q_cur) : qp[dxp];
-            const float qym = gym ? ghost<BY>(q_cur) : qp[dym];
-            const float qyp = gyp ? ghost<BY>(q_cur) : qp[dyp];
+            const float qxm = gxm ? sxm * q_cur : qp[dxm];
+            const float qxp = gxp ? sxp * q_cur : qp[dxp];
+            const float qym = gym ? sym * q_cur : qp[dym];
+            const float qyp = gyp ? syp * q_cur : qp[dyp];
             const float qzm = (BZ != BC_P && k == 0) ? zsl * q_cur : q_prev;
             const float qzp = (BZ != BC_P && top) ? zsh * q_cur : q_next;
             rr -= S.idx2.hi * (qxm + qxp - 2.f * q_cur) + S.idy2.hi * (qym + qyp - 2.f * q_cur) +
@@ -198,14 +197,16 @@ cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float*
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
   if (by == BC_P) return res_bz<PLO, BX, BC_P>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
   if (by == BC_NN) return res_bz<PLO, BX, BC_NN>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
-  return res_bz<PLO, BX, BC_DD>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (by == BC_DD) return res_bz<PLO, BX, BC_DD>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_bz<PLO, BX, BC_ND>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st);  // either mixed pair
 }
 template <int PLO>
 cudaError_t res_bx(const int* bc, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
                    const StencilDF& S, int kc, double* acc, cudaStream_t st) {
   if (bc[0] == BC_P) return res_by<PLO, BC_P>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
   if (bc[0] == BC_NN) return res_by<PLO, BC_NN>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
-  return res_by<PLO, BC_DD>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
+  if (bc[0] == BC_DD) return res_by<PLO, BC_DD>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
+  return res_by<PLO, BC_ND>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st);
 }
 
 }  // namespace

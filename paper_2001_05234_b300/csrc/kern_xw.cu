@@ -347,8 +347,7 @@ cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, 
 // Residual sweep, split form: the streaming residual stencil (kern_res.cu) writes r into W, then
 // this x-forward transforms W in place.  Taken whenever the x lines fit the warp engine.
 bool xres_warp_ok(const cans_plan_s* P, const float* W) {
-  // the streaming stencil takes one rule for both x walls and both y walls
-  return !P->wblk && aligned16(W) && wl::supported(P->dx.m) && !quarter(P->bc[0]) && !quarter(P->bc[1]);
+  return !P->wblk && aligned16(W) && wl::supported(P->dx.m);
 }
 
 cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st) {
@@ -357,6 +356,8 @@ cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st) 
   if (P->dx.m == MM) {                                             \
     if (bc == BC_P) return xfwd32_w<MM, BC_P>(P, W, W, st);        \
     if (bc == BC_NN) return xfwd32_w<MM, BC_NN>(P, W, W, st);      \
+    if (bc == BC_ND) return xfwd32_w<MM, BC_ND>(P, W, W, st);      \
+    if (bc == BC_DN) return xfwd32_w<MM, BC_DN>(P, W, W, st);      \
     return xfwd32_w<MM, BC_DD>(P, W, W, st);                       \
   }
   XW_CASE(128)
