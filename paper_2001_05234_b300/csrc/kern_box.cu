@@ -76,16 +76,48 @@ __device__ __forceinline__ bool wall_face(const BoxG& g, int i, int j, int k) {
   return wl[C] && x == g.n[C] - 1;
 }
 
+// Neighbour access policies: Gen applies every wall and wrap rule; Fast reads at fixed offsets from
+// the cell (i0, j0, k0), valid when every neighbour used lies inside the arrays and off the last
+// index of each direction (1 <= i <= n - 3 and likewise: then no wrap, no ghost and no wall face
+// is touched).
+template <int WX, int WY, int WZ>
+struct Gen {
+  const BoxG& g;
+  template <int C>
+  __device__ __forceinline__ double vel(const double* a, int i, int j, int k) const {
+    return V<C, WX, WY, WZ>(g, a, i, j, k);
+  }
+  __device__ __forceinline__ double cell(const double* q, int i, int j, int k) const {
+    return Pc<WX, WY, WZ>(g, q, i, j, k);
+  }
+};
+struct Fast {
+  const BoxG& g;
+  int i0, j0, k0;
+  size_t c0;
+  __device__ __forceinline__ size_t at(int i, int j, int k) const {
+    return c0 + (ptrdiff_t)(i - i0) + (ptrdiff_t)(j - j0) * g.n[0] + (ptrdiff_t)(k - k0) * ((ptrdiff_t)g.n[0] * g.n[1]);
+  }
+  template <int C>
+  __device__ __forceinline__ double vel(const double* a, int i, int j, int k) const {
+    return a[at(i, j, k)];
+  }
+  __device__ __forceinline__ double cell(const double* q, int i, int j, int k) const { return q[at(i, j, k)]; }
+};
+__device__ __forceinline__ bool interior(const BoxG& g, int i, int j, int k) {
+  return i >= 1 && i <= g.n[0] - 3 && j >= 1 && j <= g.n[1] - 3 && k >= 1 && k <= g.n[2] - 3;
+}
+
 // advection -div(u u) (two-point averages) + nu L at the faces of component C
-template <int C, int WX, int WY, int WZ>
-__device__ __forceinline__ double box_rhs(const BoxG& g, const double* u, const double* v, const double* w, double nu,
-                                          int i, int j, int k) {
+template <int C, int WX, int WY, int WZ, typename Acc>
+__device__ __forceinline__ double box_rhs(const BoxG& g, const Acc& X, const double* u, const double* v,
+                                          const double* w, double nu, int i, int j, int k) {
   if (wall_face<C, WX, WY, WZ>(g, i, j, k)) return 0.0;
-  auto U = [&](int a, int b, int e) { return V<0, WX, WY, WZ>(g, u, a, b, e); };
-  auto Vv = [&](int a, int b, int e) { return V<1, WX, WY, WZ>(g, v, a, b, e); };
-  auto Ww = [&](int a, int b, int e) { return V<2, WX, WY, WZ>(g, w, a, b, e); };
+  auto U = [&](int a, int b, int e) { return X.template vel<0>(u, a, b, e); };
+  auto Vv = [&](int a, int b, int e) { return X.template vel<1>(v, a, b, e); };
+  auto Ww = [&](int a, int b, int e) { return X.template vel<2>(w, a, b, e); };
   const double* F = (C == 0) ? u : (C == 1 ? v : w);
-  auto A = [&](int a, int b, int e) { return V<C, WX, WY, WZ>(g, F, a, b, e); };
+  auto A = [&](int a, int b, int e) { return X.template vel<C>(F, a, b, e); };
   double adv;
   if (C == 0) {
     const double ue = 0.5 * (U(i, j, k) + U(i + 1, j, k)), uw = 0.5 * (U(i - 1, j, k) + U(i, j, k));
@@ -122,13 +154,13 @@ __device__ __forceinline__ double box_rhs(const BoxG& g, const double* u, const 
   return fma(nu, lx + ly + lz, -adv);
 }
 
-template <int C, int WX, int WY, int WZ>
-__device__ __forceinline__ double grad(const BoxG& g, const double* q, int i, int j, int k) {
+template <int C, int WX, int WY, int WZ, typename Acc>
+__device__ __forceinline__ double grad(const BoxG& g, const Acc& X, const double* q, int i, int j, int k) {
   if (wall_face<C, WX, WY, WZ>(g, i, j, k)) return 0.0;
   const double qc = q[g.at(i, j, k)];
-  if (C == 0) return (Pc<WX, WY, WZ>(g, q, i + 1, j, k) - qc) * g.dxi;
-  if (C == 1) return (Pc<WX, WY, WZ>(g, q, i, j + 1, k) - qc) * g.dyi;
-  return (Pc<WX, WY, WZ>(g, q, i, j, k + 1) - qc) * g.dzci[k];
+  if (C == 0) return (X.cell(q, i + 1, j, k) - qc) * g.dxi;
+  if (C == 1) return (X.cell(q, i, j + 1, k) - qc) * g.dyi;
+  return (X.cell(q, i, j, k + 1) - qc) * g.dzci[k];
 }
 
 template <int WX, int WY, int WZ>
@@ -141,21 +173,27 @@ __global__ void box_momentum_kernel(BoxG g, const double* __restrict__ u, const 
   const double dt = *dt_dev;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((size_t)g.n[0] * g.n[1]));
-    const double r0 = box_rhs<0, WX, WY, WZ>(g, u, v, w, nu, i, j, k);
-    const double r1 = box_rhs<1, WX, WY, WZ>(g, u, v, w, nu, i, j, k);
-    const double r2 = box_rhs<2, WX, WY, WZ>(g, u, v, w, nu, i, j, k);
-    double s0 = alpha * r0, s1 = alpha * r1, s2 = alpha * r2;
-    if (beta != 0.0) {
-      s0 = fma(beta, ru[c], s0);
-      s1 = fma(beta, rv[c], s1);
-      s2 = fma(beta, rw[c], s2);
-    }
-    us[c] = fma(dt, fma(-gamma, grad<0, WX, WY, WZ>(g, p, i, j, k), s0), u[c]);
-    vs[c] = fma(dt, fma(-gamma, grad<1, WX, WY, WZ>(g, p, i, j, k), s1), v[c]);
-    ws[c] = fma(dt, fma(-gamma, grad<2, WX, WY, WZ>(g, p, i, j, k), s2), w[c]);
-    ru[c] = r0;
-    rv[c] = r1;
-    rw[c] = r2;
+    auto body = [&](const auto& X) {
+      const double r0 = box_rhs<0, WX, WY, WZ>(g, X, u, v, w, nu, i, j, k);
+      const double r1 = box_rhs<1, WX, WY, WZ>(g, X, u, v, w, nu, i, j, k);
+      const double r2 = box_rhs<2, WX, WY, WZ>(g, X, u, v, w, nu, i, j, k);
+      double s0 = alpha * r0, s1 = alpha * r1, s2 = alpha * r2;
+      if (beta != 0.0) {
+        s0 = fma(beta, ru[c], s0);
+        s1 = fma(beta, rv[c], s1);
+        s2 = fma(beta, rw[c], s2);
+      }
+      us[c] = fma(dt, fma(-gamma, grad<0, WX, WY, WZ>(g, X, p, i, j, k), s0), u[c]);
+      vs[c] = fma(dt, fma(-gamma, grad<1, WX, WY, WZ>(g, X, p, i, j, k), s1), v[c]);
+      ws[c] = fma(dt, fma(-gamma, grad<2, WX, WY, WZ>(g, X, p, i, j, k), s2), w[c]);
+      ru[c] = r0;
+      rv[c] = r1;
+      rw[c] = r2;
+    };
+    if (interior(g, i, j, k))
+      body(Fast{g, i, j, k, c});
+    else
+      body(Gen<WX, WY, WZ>{g});
   }
 }
 
@@ -167,9 +205,12 @@ __global__ void box_divergence_kernel(BoxG g, const double* __restrict__ u, cons
   const double scale = 1.0 / (gamma * (*dt_dev));
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((size_t)g.n[0] * g.n[1]));
-    const double d = (V<0, WX, WY, WZ>(g, u, i, j, k) - V<0, WX, WY, WZ>(g, u, i - 1, j, k)) * g.dxi +
-                     (V<1, WX, WY, WZ>(g, v, i, j, k) - V<1, WX, WY, WZ>(g, v, i, j - 1, k)) * g.dyi +
-                     (V<2, WX, WY, WZ>(g, w, i, j, k) - V<2, WX, WY, WZ>(g, w, i, j, k - 1)) * g.dzfi[k];
+    auto div = [&](const auto& X) {
+      return (X.template vel<0>(u, i, j, k) - X.template vel<0>(u, i - 1, j, k)) * g.dxi +
+             (X.template vel<1>(v, i, j, k) - X.template vel<1>(v, i, j - 1, k)) * g.dyi +
+             (X.template vel<2>(w, i, j, k) - X.template vel<2>(w, i, j, k - 1)) * g.dzfi[k];
+    };
+    const double d = interior(g, i, j, k) ? div(Fast{g, i, j, k, c}) : div(Gen<WX, WY, WZ>{g});
     f[c] = scale * d;
   }
 }
@@ -185,10 +226,20 @@ __global__ void box_correct_kernel(BoxG g, const double* __restrict__ us, const 
   double acc = 0.0;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((size_t)g.n[0] * g.n[1]));
-    const double un = us[c] - f * grad<0, WX, WY, WZ>(g, phi, i, j, k);
+    double gx, gy, gz;
+    auto grads = [&](const auto& X) {
+      gx = grad<0, WX, WY, WZ>(g, X, phi, i, j, k);
+      gy = grad<1, WX, WY, WZ>(g, X, phi, i, j, k);
+      gz = grad<2, WX, WY, WZ>(g, X, phi, i, j, k);
+    };
+    if (interior(g, i, j, k))
+      grads(Fast{g, i, j, k, c});
+    else
+      grads(Gen<WX, WY, WZ>{g});
+    const double un = us[c] - f * gx;
     u[c] = un;
-    v[c] = vs[c] - f * grad<1, WX, WY, WZ>(g, phi, i, j, k);
-    w[c] = ws[c] - f * grad<2, WX, WY, WZ>(g, phi, i, j, k);
+    v[c] = vs[c] - f * gy;
+    w[c] = ws[c] - f * gz;
     p[c] += phi[c];
     acc += g.dzf[k] * un;
   }
@@ -205,9 +256,10 @@ __global__ void box_chkdt_kernel(BoxG g, const double* __restrict__ u, const dou
   double dti = 0.0;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]), k = (int)(c / ((size_t)g.n[0] * g.n[1]));
-    auto U = [&](int a, int b, int e) { return V<0, WX, WY, WZ>(g, u, a, b, e); };
-    auto Vv = [&](int a, int b, int e) { return V<1, WX, WY, WZ>(g, v, a, b, e); };
-    auto Ww = [&](int a, int b, int e) { return V<2, WX, WY, WZ>(g, w, a, b, e); };
+    auto dti_at = [&](const auto& X) {
+    auto U = [&](int a, int b, int e) { return X.template vel<0>(u, a, b, e); };
+    auto Vv = [&](int a, int b, int e) { return X.template vel<1>(v, a, b, e); };
+    auto Ww = [&](int a, int b, int e) { return X.template vel<2>(w, a, b, e); };
     const double dtix = fabs(U(i, j, k)) * g.dxi +
                         0.25 * fabs(Vv(i, j, k) + Vv(i, j - 1, k) + Vv(i + 1, j, k) + Vv(i + 1, j - 1, k)) * g.dyi +
                         0.25 * fabs(Ww(i, j, k) + Ww(i, j, k - 1) + Ww(i + 1, j, k) + Ww(i + 1, j, k - 1)) * g.dzfi[k];
@@ -217,7 +269,9 @@ __global__ void box_chkdt_kernel(BoxG g, const double* __restrict__ u, const dou
     const double dtiz = 0.25 * fabs(U(i, j, k) + U(i - 1, j, k) + U(i, j, k + 1) + U(i - 1, j, k + 1)) * g.dxi +
                         0.25 * fabs(Vv(i, j, k) + Vv(i, j - 1, k) + Vv(i, j, k + 1) + Vv(i, j - 1, k + 1)) * g.dyi +
                         fabs(Ww(i, j, k)) * g.dzci[k];
-    dti = fmax(dti, fmax(dtix, fmax(dtiy, dtiz)));
+    return fmax(dtix, fmax(dtiy, dtiz));
+    };
+    dti = fmax(dti, interior(g, i, j, k) ? dti_at(Fast{g, i, j, k, c}) : dti_at(Gen<WX, WY, WZ>{g}));
   }
   for (int o = 16; o > 0; o >>= 1) dti = fmax(dti, __shfl_xor_sync(0xffffffffu, dti, o));
   if ((threadIdx.x & 31) == 0) atomicMax(dti_bits, (unsigned long long)__double_as_longlong(dti));

@@ -16,13 +16,6 @@ template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
 
-__device__ __forceinline__ float ghost_or(int bc, int at_edge, float inner_c, float wrap, float nb) {
-  if (!at_edge) return nb;
-  if (bc == BC_P) return wrap;
-  if (bc == BC_NN) return inner_c;
-  return -inner_c;
-}
-
 __device__ __forceinline__ void block_accumulate(float v, double* dst) {
   __shared__ float red[32];
 #pragma unroll
