@@ -26,15 +26,34 @@ def nvcc() -> str:
     return "nvcc"
 
 
+def _obj(src: str) -> str:
+    return os.path.join(OBJDIR, os.path.basename(src) + ".o")
+
+
+def _stale_objects() -> list[str]:
+    """Objects left behind by sources that no longer exist."""
+    want = {_obj(s) for s in SOURCES}
+    return [o for o in glob.glob(os.path.join(OBJDIR, "*.o")) if o not in want]
+
+
+def _out_of_date(src: str) -> bool:
+    """An object is rebuilt when its source or any shared header is newer than it."""
+    obj = _obj(src)
+    if not os.path.exists(obj):
+        return True
+    t = os.path.getmtime(obj)
+    return any(os.path.getmtime(d) > t for d in [src, *DEPS[len(SOURCES):]])
+
+
 def needs_build() -> bool:
-    if not os.path.exists(SO):
+    if not os.path.exists(SO) or _stale_objects():
         return True
     t = os.path.getmtime(SO)
     return any(os.path.getmtime(d) > t for d in DEPS)
 
 
 def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+    obj = _obj(src)
     cmd = [nvcc(), *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-c", "-o", obj, src]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
@@ -43,13 +62,18 @@ def _compile(src: str, verbose: bool) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile each translation unit in parallel, then link one shared library (static cudart)."""
+    """Compile the out-of-date translation units in parallel, then link one shared library (static
+    cudart)."""
     if force or needs_build():
         from concurrent.futures import ThreadPoolExecutor
 
         os.makedirs(OBJDIR, exist_ok=True)
-        with ThreadPoolExecutor(max_workers=max(1, min(len(SOURCES), os.cpu_count() or 1))) as ex:
-            objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        for o in _stale_objects():
+            os.remove(o)
+        todo = [s for s in SOURCES if force or verbose or _out_of_date(s)]
+        with ThreadPoolExecutor(max_workers=max(1, min(len(todo) or 1, os.cpu_count() or 1))) as ex:
+            list(ex.map(lambda s: _compile(s, verbose), todo))
+        objs = [_obj(s) for s in SOURCES]
         cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
                "-o", SO + ".tmp", *objs]
         subprocess.check_call(cmd)

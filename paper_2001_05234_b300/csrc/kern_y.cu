@@ -158,7 +158,7 @@ cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st) {
   if (P->n[1] < 2) return cudaSuccess;
   if (sizeof(T) == 4) {
     bool handled = false;
-    const cudaError_t e = launch_y_warp<DIR>(P, reinterpret_cast<float*>(w), st, &handled);
+    const cudaError_t e = launch_y_cols<DIR>(P, reinterpret_cast<float*>(w), st, &handled);
     if (handled) return e;
   }
   switch (P->dy.m) {

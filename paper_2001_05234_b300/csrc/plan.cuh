@@ -176,8 +176,9 @@ cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* 
                             float* r, double* norm_acc, cudaStream_t st);
 bool xres_warp_ok(const cans_plan_s* P, const float* W);
 cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st);
+// y-pass with the x-slots across the lanes (kern_yc.cu): taken first where the shape allows it
 template <int DIR>
-cudaError_t launch_y_warp(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled);
+cudaError_t launch_y_cols(const cans_plan_s* P, float* w, cudaStream_t st, bool* handled);
 template <int MODE>
 cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
                              double* gauge, cudaStream_t st, bool* handled);

@@ -80,16 +80,10 @@ __device__ __forceinline__ int xpos(int m) {
 
 __device__ __forceinline__ float2 ld_tw(const float2* __restrict__ t, int i) { return __ldg(&t[i]); }
 
-// Exchange buffer of M float2 cells: contiguous (Plain) or one column of a row-padded tile whose
-// rows are RS cells apart (Strided; conflict-free whenever Plain is, for odd RS).
+// Exchange buffer of M contiguous float2 cells.
 struct Plain {
   float2* p;
   __device__ __forceinline__ float2& operator[](int i) const { return p[i]; }
-};
-template <int RS>
-struct Strided {
-  float2* p;
-  __device__ __forceinline__ float2& operator[](int i) const { return p[i * RS]; }
 };
 
 // One Stockham stage on the lane's registers.  Exchange (all but the last stage): the outputs are

@@ -107,10 +107,13 @@ def test_transform_xy_matches_library_transforms(cans, bcx, bcy, n):
 
 
 @pytest.mark.parametrize("bcx,bcy", list(itertools.product((P, NN, DD), (P, NN, DD))))
-@pytest.mark.parametrize("n", [(256, 512, 2), (1024, 128, 1), (512, 1024, 1), (64, 48, 2), (24, 256, 2)])
+@pytest.mark.parametrize(
+    "n", [(256, 512, 2), (1024, 128, 1), (512, 1024, 1), (64, 48, 2), (24, 256, 2), (32, 256, 3), (48, 1024, 2)]
+)
 def test_transform_xy_f32_matches_library_transforms(cans, bcx, bcy, n):
-    """The mixed path's FP32 x/y passes: warp-per-line kernels for N in {256, 512, 1024} (Nx a
-    multiple of 16 for y), CTA-wide kernels otherwise; agreement to FP32 rounding."""
+    """The mixed path's FP32 x/y passes: warp-per-line x kernels for N in {256, 512, 1024}, the
+    lanes-across-x-slots y kernel for Ny in {256, 512, 1024} (Nx a multiple of 16; several tiles per
+    plane and several planes), CTA-wide kernels otherwise; agreement to FP32 rounding."""
     import torch
 
     h = make_plan(cans, n, (bcx, bcy, NN), prec=1)
