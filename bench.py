@@ -113,8 +113,8 @@ class ClockSampler:
 # kernels streams its fields once, so traffic grows in proportion to the points.
 NCU_DRAM_BYTES_PER_POINT = {
     "x_forward": 11.48,
-    "y_forward": 7.20,
-    "y_inverse": 7.19,
+    "y_forward": 7.18,
+    "y_inverse": 7.21,
     "x_inverse_update": 15.28,
     "residual_stencil": 15.87,
     "z_solve": 6.21,

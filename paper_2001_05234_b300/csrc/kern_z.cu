@@ -86,9 +86,11 @@ __device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane,
   }
 }
 
-template <int MMAX, int TIC>
-__global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, int vec,
-                                                           WLay wl) {
+// PAIR: x periodic, so x-slots 2q and 2q+1 (q >= 1) share their eigenvalue; a warp solves such a pair
+// with one factorisation (zsolve_pair) unless the plan marks one of the two as a double column.
+template <int MMAX, int TIC, bool PAIR>
+__global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf,
+                                                                      int vec, WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
   constexpr bool CL = MMAX >= 4;  // lane-contiguous coefficient rows, four per 16-byte load
@@ -107,15 +109,32 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const float muy = a.muy_f[j] + (float)a.shift;
-  for (int cidx = warp; cidx < ncols; cidx += nwarps) {
+  auto single = [&](int cidx) {
     const int i = i0 + cidx;
-    if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) continue;
+    if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) return;
     if (a.nz == 32 * MMAX)
       zsolve_column<MMAX, float, float, false, decltype(Z), true, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
                                                                       sc, nullptr, 0.f);
     else
       zsolve_column<MMAX, float, float, false, decltype(Z), false, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
                                                                        sc, nullptr, 0.f);
+  };
+  if constexpr (PAIR) {  // i0 and ncols are even (checked at launch)
+    for (int q = warp; 2 * q < ncols; q += nwarps) {
+      const int c0 = 2 * q, i = i0 + c0;
+      const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
+      const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
+      if (i == 0 || m0 || m1) {  // slots 0 and 1 (X_0, X_M) differ; a marked column goes to the double kernel
+        single(c0);
+        single(c0 + 1);
+      } else if (a.nz == 32 * MMAX) {
+        zsolve_pair<MMAX, decltype(Z), true, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+      } else {
+        zsolve_pair<MMAX, decltype(Z), false, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+      }
+    }
+  } else {
+    for (int cidx = warp; cidx < ncols; cidx += nwarps) single(cidx);
   }
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
@@ -194,10 +213,13 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
       ZArgs a = zargs(P, P->z_ti[1], gauge);
       a.mask = P->mask_d;
       const size_t smem = 3 * 32 * (a.m + 4) * sizeof(float) + P->z_smem[1];
-      e = set_smem((const void*)zpass_f32_kernel<MMAX, TIC>, smem);
-      if (e != cudaSuccess) return e;
       dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-      zpass_f32_kernel<MMAX, TIC><<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
+      // pairs of equal eigenvalues: periodic x, every tile an even number of whole pairs
+      const bool pair = MMAX >= 4 && P->bc[0] == BC_P && a.nx % 2 == 0 && a.ti % 2 == 0;
+      auto kern = pair ? zpass_f32_kernel<MMAX, TIC, (MMAX >= 4)> : zpass_f32_kernel<MMAX, TIC, false>;
+      e = set_smem((const void*)kern, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
       e = cudaGetLastError();
       if (e != cudaSuccess || part == 0) return e;
     }

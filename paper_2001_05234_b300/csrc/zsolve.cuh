@@ -270,4 +270,175 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
   }
 }
 
+
+// Two columns with the same shift mu (the Re and Im slots of one periodic x wavenumber): the
+// coefficient-only parts of the partitioned solve above (pivots, spikes, the reduced system's
+// matrix and its cyclic reduction) are computed once and applied to both right-hand sides.  Float,
+// non-singular columns only.
+template <int MMAX, typename ZS, bool FULL, bool CL>
+__device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, const ZS& Z, int Nz, float mu,
+                                            const float* sa, const float* sb, const float* sc) {
+  const int lane = threadIdx.x & 31;
+  constexpr int m = MMAX;
+  static_assert(MMAX >= 2, "two or more rows per lane");
+  static_assert(!CL || MMAX >= 4, "lane-contiguous rows: four rows per load");
+  constexpr int LS = MMAX + 4;
+  float4 A4, B4, C4;
+  auto coefs = [&](int r, float& a, float& b, float& c) {
+    if constexpr (CL) {
+      if ((r & 3) == 0) {
+        A4 = *reinterpret_cast<const float4*>(sa + lane * LS + r);
+        B4 = *reinterpret_cast<const float4*>(sb + lane * LS + r);
+        C4 = *reinterpret_cast<const float4*>(sc + lane * LS + r);
+      }
+      a = f4_get(A4, r & 3);
+      b = f4_get(B4, r & 3);
+      c = f4_get(C4, r & 3);
+    } else {
+      a = sa[r * 32 + lane];
+      b = sb[r * 32 + lane];
+      c = sc[r * 32 + lane];
+    }
+  };
+  const int k0 = lane * m;
+  const unsigned full = 0xffffffffu;
+  // the second column's forward values go back into its own tile rows instead of registers
+  float cp[MMAX], lp[MMAX], dp0[MMAX];
+  float rr = 0.f, cprev = 0.f, lprev = 0.f, d0prev = 0.f, d1prev = 0.f;
+  auto t1 = [&](int k) -> float& { return tile[Z.at(k, col1, lane)]; };
+#pragma unroll
+  for (int r = 0; r < m - 1; ++r) {
+    const int k = k0 + r;
+    float a, b, c, d0 = 0.f, d1 = 0.f;
+    coefs(r, a, b, c);
+    b += (FULL || k < Nz) ? mu : 0.f;
+    if (FULL || k < Nz) {
+      d0 = tile[Z.at(k, col0, lane)];
+      d1 = tile[Z.at(k, col1, lane)];
+    }
+    const float inv = rcp_(b - a * cprev);
+    const bool last_inner = (r == m - 2);
+    cp[r] = last_inner ? 0.f : c * inv;
+    if (last_inner) rr = -c * inv;
+    dp0[r] = (d0 - a * d0prev) * inv;
+    const float dp1r = (d1 - a * d1prev) * inv;
+    if (FULL || k < Nz) t1(k) = dp1r;
+    lp[r] = ((r == 0) ? -a : -a * lprev) * inv;
+    cprev = c * inv;
+    d0prev = dp0[r];
+    d1prev = dp1r;
+    lprev = lp[r];
+  }
+  float Dl0, Dl1, Vl, Wl, Df0, Df1, Vf, Wf;
+  {
+    float D0 = 0.f, D1 = 0.f, V = 0.f, W = 0.f;
+#pragma unroll
+    for (int r = m - 2; r >= 0; --r) {
+      const float dp1r = (FULL || k0 + r < Nz) ? t1(k0 + r) : 0.f;
+      if (r == m - 2) {
+        D0 = dp0[r];
+        D1 = dp1r;
+        V = lp[r];
+        W = rr;
+        Dl0 = D0;
+        Dl1 = D1;
+        Vl = V;
+        Wl = W;
+      } else {
+        D0 = dp0[r] - cp[r] * D0;
+        D1 = dp1r - cp[r] * D1;
+        V = lp[r] - cp[r] * V;
+        W = -cp[r] * W;
+      }
+    }
+    Df0 = D0;
+    Df1 = D1;
+    Vf = V;
+    Wf = W;
+  }
+  const int kl = k0 + m - 1;
+  const int rl = m - 1;
+  float al, bl, cl, dl0 = 0.f, dl1 = 0.f;
+  if (CL && ((m - 1) & 3) != 0) {  // the last row's group of four was loaded by the forward loop
+    al = f4_get(A4, rl & 3);
+    bl = f4_get(B4, rl & 3);
+    cl = f4_get(C4, rl & 3);
+  } else {
+    coefs(rl, al, bl, cl);
+  }
+  bl += (FULL || kl < Nz) ? mu : 0.f;
+  if (FULL || kl < Nz) {
+    dl0 = tile[Z.at(kl, col0, lane)];
+    dl1 = tile[Z.at(kl, col1, lane)];
+  }
+  const float Dfn0 = __shfl_down_sync(full, Df0, 1);
+  const float Dfn1 = __shfl_down_sync(full, Df1, 1);
+  const float Vfn = __shfl_down_sync(full, Vf, 1);
+  const float Wfn = __shfl_down_sync(full, Wf, 1);
+  const bool hasn = lane < 31;
+  float alpha = (lane == 0) ? 0.f : al * Vl;
+  float beta = bl + al * Wl + (hasn ? cl * Vfn : 0.f);
+  float gamma = hasn ? cl * Wfn : 0.f;
+  float delta0 = dl0 - al * Dl0 - (hasn ? cl * Dfn0 : 0.f);
+  float delta1 = dl1 - al * Dl1 - (hasn ? cl * Dfn1 : 0.f);
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    float am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
+    float gm = __shfl_up_sync(full, gamma, s);
+    float dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
+    float ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
+    float gp = __shfl_down_sync(full, gamma, s);
+    float dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
+    if (lane < s) {
+      am = 0.f;
+      bm = 1.f;
+      gm = 0.f;
+      dm0 = 0.f;
+      dm1 = 0.f;
+    }
+    if (lane + s > 31) {
+      ap = 0.f;
+      bp = 1.f;
+      gp = 0.f;
+      dq0 = 0.f;
+      dq1 = 0.f;
+    }
+    const float k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
+    const float na = -am * k1, ng = -gp * k2;
+    const float nb = beta - gm * k1 - ap * k2;
+    delta0 = delta0 - dm0 * k1 - dq0 * k2;
+    delta1 = delta1 - dm1 * k1 - dq1 * k2;
+    alpha = na;
+    beta = nb;
+    gamma = ng;
+  }
+  const float ib = rcp_(beta);
+  const float E0 = delta0 * ib, E1 = delta1 * ib;
+  float Ep0 = __shfl_up_sync(full, E0, 1), Ep1 = __shfl_up_sync(full, E1, 1);
+  if (lane == 0) {
+    Ep0 = 0.f;
+    Ep1 = 0.f;
+  }
+  if (FULL || kl < Nz) {
+    tile[Z.at(kl, col0, lane)] = E0;
+    tile[Z.at(kl, col1, lane)] = E1;
+  }
+  float x0 = E0, x1 = E1;
+#pragma unroll
+  for (int r = m - 2; r >= 0; --r) {
+    const float dp1r = (FULL || k0 + r < Nz) ? t1(k0 + r) : 0.f;
+    if (r == m - 2) {
+      x0 = dp0[r] + lp[r] * Ep0 + rr * E0;
+      x1 = dp1r + lp[r] * Ep1 + rr * E1;
+    } else {
+      x0 = dp0[r] + lp[r] * Ep0 - cp[r] * x0;
+      x1 = dp1r + lp[r] * Ep1 - cp[r] * x1;
+    }
+    if (FULL || k0 + r < Nz) {
+      tile[Z.at(k0 + r, col0, lane)] = x0;
+      tile[Z.at(k0 + r, col1, lane)] = x1;
+    }
+  }
+}
+
 }  // namespace cans
