@@ -112,6 +112,10 @@ struct SnkUpd {
         gacc = df_add(gacc, tt);
       }
       return d;
+    } else if (MODE == 5) {
+      // Plo is zero: the exact widenings of Phi and d and one rounded FP64 add give the correctly
+      // rounded Phi + d
+      pd = f2d(sphi[(int)(o - base)]) + f2d(d);
     } else {
       const int n = (int)(o - base);
       df s2 = two_sum(sphi[n], d);
