@@ -128,9 +128,10 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
         single(c0);
         single(c0 + 1);
       } else if (a.nz == 32 * MMAX) {
-        zsolve_pair<MMAX, decltype(Z), true, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+        zsolve_pair<MMAX, float, float, decltype(Z), true, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
       } else {
-        zsolve_pair<MMAX, decltype(Z), false, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+        zsolve_pair<MMAX, float, float, decltype(Z), false, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb,
+                                                                 sc);
       }
     }
   } else {
@@ -164,9 +165,10 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
   __syncthreads();
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const double muy = a.muy_d[j] + a.shift;
-  for (int cidx = warp; cidx < ncols; cidx += nwarps) {
+  auto marked = [&](int i) { return a.mask == nullptr || a.mask[(size_t)j * a.nx + i]; };
+  auto single = [&](int cidx) {
     const int i = i0 + cidx;
-    if (a.mask != nullptr && !a.mask[(size_t)j * a.nx + i]) continue;
+    if (!marked(i)) return;
     const double mu = a.mux_d[i] + muy;
     if (a.singular && i == 0 && j == 0) {
       const double target = (a.gauge != nullptr) ? a.gauge_scale * (*a.gauge) : 0.0;
@@ -174,6 +176,20 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     } else {
       zsolve_column<MMAX, double, T, false>(tile, cidx, Z, a.nz, mu, sa, sb, sc, nullptr, 0.0);
     }
+  };
+  if (MMAX >= 2 && a.xpairs) {  // x periodic: slots 2q, 2q+1 (q >= 1) share their shift, one factorisation
+    for (int q = warp; 2 * q < ncols; q += nwarps) {
+      const int c0 = 2 * q, i = i0 + c0;
+      if (i == 0 || !marked(i) || !marked(i + 1)) {
+        single(c0);
+        single(c0 + 1);
+      } else if constexpr (MMAX >= 2) {
+        zsolve_pair<MMAX, double, T, decltype(Z), false, false>(tile, c0, c0 + 1, Z, a.nz, a.mux_d[i] + muy, sa, sb,
+                                                                 sc);
+      }
+    }
+  } else {
+    for (int cidx = warp; cidx < ncols; cidx += nwarps) single(cidx);
   }
   __syncthreads();
   tile_store<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
@@ -198,6 +214,9 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
   a.gauge_scale = P->gauge_scale;
   a.i_end = P->n[0];
   a.j_end = P->n[1];
+  // periodic x: slots 2q, 2q+1 hold one wavenumber's Re / Im parts (equal shift); tiles of an even
+  // width hold whole pairs
+  a.xpairs = (P->bc[0] == BC_P && P->n[0] % 2 == 0 && ti % 2 == 0) ? 1 : 0;
   return a;
 }
 

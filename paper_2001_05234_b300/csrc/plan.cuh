@@ -68,6 +68,7 @@ struct ZArgs {
   const double* gauge;  // optional: target weighted column mean = gauge_scale * (*gauge)
   double gauge_scale;
   int j_end, i_end;     // FP64-column kernel: bounding box of the columns it owns
+  int xpairs;           // x periodic, even widths: column pairs of equal shift
 };
 
 }  // namespace cans

@@ -273,18 +273,20 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
 
 // Two columns with the same shift mu (the Re and Im slots of one periodic x wavenumber): the
 // coefficient-only parts of the partitioned solve above (pivots, spikes, the reduced system's
-// matrix and its cyclic reduction) are computed once and applied to both right-hand sides.  Float,
-// non-singular columns only.
-template <int MMAX, typename ZS, bool FULL, bool CL>
-__device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, const ZS& Z, int Nz, float mu,
-                                            const float* sa, const float* sb, const float* sc) {
+// matrix and its cyclic reduction) are computed once and applied to both right-hand sides.
+// Non-singular columns; compute type C, storage type T.  When C is T, the second column's forward
+// values go back into its own tile rows instead of registers (register budget of the float kernel).
+template <int MMAX, typename C, typename T, typename ZS, bool FULL, bool CL>
+__device__ __forceinline__ void zsolve_pair(T* tile, int col0, int col1, const ZS& Z, int Nz, C mu, const C* sa,
+                                            const C* sb, const C* sc) {
+  constexpr bool IN_TILE = sizeof(C) == sizeof(T);
   const int lane = threadIdx.x & 31;
   constexpr int m = MMAX;
   static_assert(MMAX >= 2, "two or more rows per lane");
-  static_assert(!CL || MMAX >= 4, "lane-contiguous rows: four rows per load");
+  static_assert(!CL || (MMAX >= 4 && sizeof(C) == 4), "lane-contiguous rows: float, four rows per load");
   constexpr int LS = MMAX + 4;
   float4 A4, B4, C4;
-  auto coefs = [&](int r, float& a, float& b, float& c) {
+  auto coefs = [&](int r, C& a, C& b, C& c) {
     if constexpr (CL) {
       if ((r & 3) == 0) {
         A4 = *reinterpret_cast<const float4*>(sa + lane * LS + r);
@@ -302,39 +304,51 @@ __device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, con
   };
   const int k0 = lane * m;
   const unsigned full = 0xffffffffu;
-  // the second column's forward values go back into its own tile rows instead of registers
-  float cp[MMAX], lp[MMAX], dp0[MMAX];
-  float rr = 0.f, cprev = 0.f, lprev = 0.f, d0prev = 0.f, d1prev = 0.f;
-  auto t1 = [&](int k) -> float& { return tile[Z.at(k, col1, lane)]; };
+  C cp[MMAX], lp[MMAX], dp0[MMAX], dp1[IN_TILE ? 1 : MMAX];
+  C rr = 0, cprev = 0, lprev = 0, d0prev = 0, d1prev = 0;
+  auto t1 = [&](int k) -> T& { return tile[Z.at(k, col1, lane)]; };
+  auto put1 = [&](int r, int k, C v) {
+    if constexpr (IN_TILE) {
+      if (FULL || k < Nz) t1(k) = (T)v;
+    } else {
+      dp1[r] = v;
+    }
+  };
+  auto get1 = [&](int r, int k) -> C {
+    if constexpr (IN_TILE)
+      return (FULL || k < Nz) ? (C)t1(k) : (C)0;
+    else
+      return dp1[r];
+  };
 #pragma unroll
   for (int r = 0; r < m - 1; ++r) {
     const int k = k0 + r;
-    float a, b, c, d0 = 0.f, d1 = 0.f;
+    C a, b, c, d0 = 0, d1 = 0;
     coefs(r, a, b, c);
-    b += (FULL || k < Nz) ? mu : 0.f;
+    b += (FULL || k < Nz) ? mu : (C)0;
     if (FULL || k < Nz) {
-      d0 = tile[Z.at(k, col0, lane)];
-      d1 = tile[Z.at(k, col1, lane)];
+      d0 = cvt<C>(tile[Z.at(k, col0, lane)]);
+      d1 = cvt<C>(t1(k));
     }
-    const float inv = rcp_(b - a * cprev);
+    const C inv = rcp_(b - a * cprev);
     const bool last_inner = (r == m - 2);
-    cp[r] = last_inner ? 0.f : c * inv;
+    cp[r] = last_inner ? (C)0 : c * inv;
     if (last_inner) rr = -c * inv;
     dp0[r] = (d0 - a * d0prev) * inv;
-    const float dp1r = (d1 - a * d1prev) * inv;
-    if (FULL || k < Nz) t1(k) = dp1r;
+    const C dp1r = (d1 - a * d1prev) * inv;
+    put1(r, k, dp1r);
     lp[r] = ((r == 0) ? -a : -a * lprev) * inv;
     cprev = c * inv;
     d0prev = dp0[r];
     d1prev = dp1r;
     lprev = lp[r];
   }
-  float Dl0, Dl1, Vl, Wl, Df0, Df1, Vf, Wf;
+  C Dl0, Dl1, Vl, Wl, Df0, Df1, Vf, Wf;
   {
-    float D0 = 0.f, D1 = 0.f, V = 0.f, W = 0.f;
+    C D0 = 0, D1 = 0, V = 0, W = 0;
 #pragma unroll
     for (int r = m - 2; r >= 0; --r) {
-      const float dp1r = (FULL || k0 + r < Nz) ? t1(k0 + r) : 0.f;
+      const C dp1r = get1(r, k0 + r);
       if (r == m - 2) {
         D0 = dp0[r];
         D1 = dp1r;
@@ -358,7 +372,7 @@ __device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, con
   }
   const int kl = k0 + m - 1;
   const int rl = m - 1;
-  float al, bl, cl, dl0 = 0.f, dl1 = 0.f;
+  C al, bl, cl, dl0 = 0, dl1 = 0;
   if (CL && ((m - 1) & 3) != 0) {  // the last row's group of four was loaded by the forward loop
     al = f4_get(A4, rl & 3);
     bl = f4_get(B4, rl & 3);
@@ -366,67 +380,67 @@ __device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, con
   } else {
     coefs(rl, al, bl, cl);
   }
-  bl += (FULL || kl < Nz) ? mu : 0.f;
+  bl += (FULL || kl < Nz) ? mu : (C)0;
   if (FULL || kl < Nz) {
-    dl0 = tile[Z.at(kl, col0, lane)];
-    dl1 = tile[Z.at(kl, col1, lane)];
+    dl0 = cvt<C>(tile[Z.at(kl, col0, lane)]);
+    dl1 = cvt<C>(t1(kl));
   }
-  const float Dfn0 = __shfl_down_sync(full, Df0, 1);
-  const float Dfn1 = __shfl_down_sync(full, Df1, 1);
-  const float Vfn = __shfl_down_sync(full, Vf, 1);
-  const float Wfn = __shfl_down_sync(full, Wf, 1);
+  const C Dfn0 = __shfl_down_sync(full, Df0, 1);
+  const C Dfn1 = __shfl_down_sync(full, Df1, 1);
+  const C Vfn = __shfl_down_sync(full, Vf, 1);
+  const C Wfn = __shfl_down_sync(full, Wf, 1);
   const bool hasn = lane < 31;
-  float alpha = (lane == 0) ? 0.f : al * Vl;
-  float beta = bl + al * Wl + (hasn ? cl * Vfn : 0.f);
-  float gamma = hasn ? cl * Wfn : 0.f;
-  float delta0 = dl0 - al * Dl0 - (hasn ? cl * Dfn0 : 0.f);
-  float delta1 = dl1 - al * Dl1 - (hasn ? cl * Dfn1 : 0.f);
+  C alpha = (lane == 0) ? (C)0 : al * Vl;
+  C beta = bl + al * Wl + (hasn ? cl * Vfn : (C)0);
+  C gamma = hasn ? cl * Wfn : (C)0;
+  C delta0 = dl0 - al * Dl0 - (hasn ? cl * Dfn0 : (C)0);
+  C delta1 = dl1 - al * Dl1 - (hasn ? cl * Dfn1 : (C)0);
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
-    float am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
-    float gm = __shfl_up_sync(full, gamma, s);
-    float dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
-    float ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
-    float gp = __shfl_down_sync(full, gamma, s);
-    float dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
+    C am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
+    C gm = __shfl_up_sync(full, gamma, s);
+    C dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
+    C ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
+    C gp = __shfl_down_sync(full, gamma, s);
+    C dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
     if (lane < s) {
-      am = 0.f;
-      bm = 1.f;
-      gm = 0.f;
-      dm0 = 0.f;
-      dm1 = 0.f;
+      am = 0;
+      bm = 1;
+      gm = 0;
+      dm0 = 0;
+      dm1 = 0;
     }
     if (lane + s > 31) {
-      ap = 0.f;
-      bp = 1.f;
-      gp = 0.f;
-      dq0 = 0.f;
-      dq1 = 0.f;
+      ap = 0;
+      bp = 1;
+      gp = 0;
+      dq0 = 0;
+      dq1 = 0;
     }
-    const float k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
-    const float na = -am * k1, ng = -gp * k2;
-    const float nb = beta - gm * k1 - ap * k2;
+    const C k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
+    const C na = -am * k1, ng = -gp * k2;
+    const C nb = beta - gm * k1 - ap * k2;
     delta0 = delta0 - dm0 * k1 - dq0 * k2;
     delta1 = delta1 - dm1 * k1 - dq1 * k2;
     alpha = na;
     beta = nb;
     gamma = ng;
   }
-  const float ib = rcp_(beta);
-  const float E0 = delta0 * ib, E1 = delta1 * ib;
-  float Ep0 = __shfl_up_sync(full, E0, 1), Ep1 = __shfl_up_sync(full, E1, 1);
+  const C ib = rcp_(beta);
+  const C E0 = delta0 * ib, E1 = delta1 * ib;
+  C Ep0 = __shfl_up_sync(full, E0, 1), Ep1 = __shfl_up_sync(full, E1, 1);
   if (lane == 0) {
-    Ep0 = 0.f;
-    Ep1 = 0.f;
+    Ep0 = 0;
+    Ep1 = 0;
   }
   if (FULL || kl < Nz) {
-    tile[Z.at(kl, col0, lane)] = E0;
-    tile[Z.at(kl, col1, lane)] = E1;
+    tile[Z.at(kl, col0, lane)] = cvt<T>(E0);
+    t1(kl) = cvt<T>(E1);
   }
-  float x0 = E0, x1 = E1;
+  C x0 = E0, x1 = E1;
 #pragma unroll
   for (int r = m - 2; r >= 0; --r) {
-    const float dp1r = (FULL || k0 + r < Nz) ? t1(k0 + r) : 0.f;
+    const C dp1r = get1(r, k0 + r);
     if (r == m - 2) {
       x0 = dp0[r] + lp[r] * Ep0 + rr * E0;
       x1 = dp1r + lp[r] * Ep1 + rr * E1;
@@ -435,8 +449,8 @@ __device__ __forceinline__ void zsolve_pair(float* tile, int col0, int col1, con
       x1 = dp1r + lp[r] * Ep1 - cp[r] * x1;
     }
     if (FULL || k0 + r < Nz) {
-      tile[Z.at(k0 + r, col0, lane)] = x0;
-      tile[Z.at(k0 + r, col1, lane)] = x1;
+      tile[Z.at(k0 + r, col0, lane)] = cvt<T>(x0);
+      t1(k0 + r) = cvt<T>(x1);
     }
   }
 }
