@@ -98,6 +98,7 @@ struct SnkUpd {
   df gw;  // gauge weight dzf_k of the line (MODE 1)
   bool gauge;
   df gacc;
+  df lacc;  // MODE 1: the lane's share of the line's sum, weighted by gw once per line
   const float* sphi;  // the line's Phi (and Plo) staged in shared memory (MODE >= 2)
   const float* splo;
   size_t base;
@@ -107,9 +108,8 @@ struct SnkUpd {
       pd = f2d(d);
     } else if (MODE == 1) {
       if (gauge) {
-        df tt = two_prod(d, gw.hi);
-        tt.lo = __fmaf_rn(d, gw.lo, tt.lo);
-        gacc = df_add(gacc, tt);
+        const df s2 = two_sum(lacc.hi, d);
+        lacc = df_make(s2.hi, __fadd_rn(lacc.lo, s2.lo));
       }
       return d;
     } else if (MODE == 5) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32 * XW_WARPS, upd_reads<MODE>() == 2 ? 2 : 3)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float2* xb = reinterpret_cast<float2*>(xw_smem) + wid * M;
   float* stg = reinterpret_cast<float*>(xw_smem + (size_t)XW_WARPS * M * sizeof(float2)) + (size_t)wid * NR * N;
-  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f),
+  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f), df_make(0.f, 0.f),
                  stg, stg + (NR == 2 ? N : 0), 0};
   for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
     const size_t base = (size_t)line * N;
@@ -233,6 +233,10 @@ __global__ void __launch_bounds__(32 * XW_WARPS, upd_reads<MODE>() == 2 ? 2 : 3)
     SnkLine<MODE> out{&u, base};
     wl::inverse<M, BC, true>(wl::Plain{xb}, tb, lane, in, out);
     if (NR > 0) __syncwarp();  // the staged iterate is read before the next line overwrites it
+    if (MODE == 1 && gauge != nullptr) {  // the line's dzf_k-weighted share of the gauge sum
+      u.gacc = df_add(u.gacc, df_mul(u.lacc, u.gw));
+      u.lacc = df_make(0.f, 0.f);
+    }
   }
   if (MODE == 1 && gauge != nullptr) {
     __shared__ double red[XW_WARPS];
