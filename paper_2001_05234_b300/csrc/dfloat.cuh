@@ -90,6 +90,18 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __double2float_rn(x);  // inline: an out-of-line call here costs the x forward pass registers
 }
 
+// d2f_rn on the integer path only: *ok is false (and the result meaningless) outside its range, so
+// that a caller can take the hardware conversion in a branch of its own (see SrcF in kern_xw.cu)
+__device__ __forceinline__ float d2f_rn_int(double x, bool* ok) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  *ok = e - 897u < 254u;
+  const unsigned t = __funnelshift_l(lo, hi, 3);
+  unsigned bits = (t - (896u << 23)) | (hi & 0x80000000u);
+  bits += ((lo & 0x1fffffffu) + (t & 1u) + 0x0fffffffu) >> 29;
+  return __uint_as_float(bits);
+}
+
 // x = hi + lo with hi = d2f_rn(x) and lo the remainder to within 2^-46 |x| (exact for |x| >= 2^-80
 // up to the 6 lowest of its 29 remainder bits).  Outside 2^-80 <= |x| < 2^127 the FP64 route is used.
 __device__ __forceinline__ df df_split(double x) {

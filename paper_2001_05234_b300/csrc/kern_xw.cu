@@ -32,9 +32,17 @@ __device__ __forceinline__ void warp_block_accumulate(float v, double* dst) {
 struct SrcF {  // f (double) rounded to float; accumulates sum f^2
   const double* __restrict__ f;  // line start, 16-byte aligned
   float acc;
+  // called by all 32 lanes together (the first stage of a line): the rare inputs outside the integer
+  // path's range (zeros, subnormal, tiny or huge values) take the hardware conversion in a
+  // warp-uniform branch, so that the slow FP64-class conversion is not executed for every element
   __device__ __forceinline__ float2 pair(int n) {
     const double2 d = *reinterpret_cast<const double2*>(f + n);
-    const float a = d2f_rn(d.x), b = d2f_rn(d.y);
+    bool oka, okb;
+    float a = d2f_rn_int(d.x, &oka), b = d2f_rn_int(d.y, &okb);
+    if (!__all_sync(0xffffffffu, oka && okb)) {
+      if (!oka) a = __double2float_rn(d.x);
+      if (!okb) b = __double2float_rn(d.y);
+    }
     acc = __fmaf_rn(a, a, __fmaf_rn(b, b, acc));
     return make_float2(a, b);
   }

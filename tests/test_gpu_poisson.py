@@ -130,6 +130,31 @@ def test_transform_xy_f32_matches_library_transforms(cans, bcx, bcy, n):
     cans.cans_plan_destroy(h)
 
 
+@pytest.mark.parametrize("n", [(512, 256, 2), (48, 32, 3)])
+def test_transform_xy_f32_special_inputs(cans, n):
+    """Inputs the integer double -> float rounding leaves to the hardware conversion (exact zeros,
+    values below the float range, signed zeros) mixed into ordinary ones: the forward x-y transform
+    of the float-rounded field, to FP32 rounding."""
+    import torch
+
+    h = make_plan(cans, n, (P, NN, NN), prec=1)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((n[2], n[1], n[0]))
+    sel = rng.random(x.shape)
+    x[sel < 0.02] = 0.0
+    x[(sel >= 0.02) & (sel < 0.03)] = 1e-300
+    x[(sel >= 0.03) & (sel < 0.035)] = -0.0
+    x[(sel >= 0.035) & (sel < 0.04)] = 3e-39  # a float subnormal
+    t = dev(x)
+    w = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+    assert cans.cans_transform_xy_f32(h, t.data_ptr(), w.data_ptr(), 1, stream()) == 0
+    xf = x.astype(np.float32).astype(np.float64)
+    want = ref_forward(ref_forward(xf, P, 2), NN, 1)
+    got = host(w).astype(np.float64)
+    assert np.abs(got - want).max() <= 4e-6 * np.abs(want).max()
+    cans.cans_plan_destroy(h)
+
+
 def test_transform_xy_f32_rejects_fp64_plans(cans):
     import torch
 
