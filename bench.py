@@ -261,7 +261,7 @@ def gpu_arm(args):
     fd = [torch.empty_like(f), f]
     pd = [torch.empty_like(p), p]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    e2e_steps = max(4, min(args.steps, 6))
+    e2e_steps = max(4, min(args.steps, 10))  # the pipeline's fill and drain are spread over the steps
     ev = lambda: torch.cuda.Event()  # noqa: E731
     ev_in, ev_done, ev_out = [ev() for _ in range(e2e_steps)], [ev() for _ in range(e2e_steps)], \
         [ev() for _ in range(e2e_steps)]

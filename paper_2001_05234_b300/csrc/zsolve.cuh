@@ -29,7 +29,17 @@ __device__ __forceinline__ float rcp_(float x) {
   asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+// 1/x in double: the hardware's approximate reciprocal refined by two Newton steps
+// y <- y + y (1 - x y), each squaring the relative error; the pivots of the z systems are normal,
+// nonzero numbers (diagonal dominance), so the flush-to-zero approximation is safe here.
+__device__ __forceinline__ double rcp_(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
 
 // Swizzled position of (row k, column i) inside the [Nz][TI] tile.  Every lane owns m = 2^sh rows
 // (rows past Nz are identity rows), so row k belongs to lane seg = k >> sh; the column index is
