@@ -91,10 +91,13 @@ def test_quarter_wave_fp64_transforms(cans, bcx, bcy, n):
 
 
 @pytest.mark.parametrize("bcx,bcy", [(ND, P), (DN, NN), (P, ND), (NN, DN), (ND, DN), (DN, ND), (DD, ND)])
-@pytest.mark.parametrize("n", [(256, 512, 2), (512, 256, 1), (1024, 256, 1), (64, 48, 2), (24, 256, 2)])
+@pytest.mark.parametrize(
+    "n", [(256, 512, 2), (512, 256, 1), (1024, 256, 1), (64, 48, 2), (24, 256, 2), (32, 1024, 2), (48, 256, 3)]
+)
 def test_quarter_wave_f32_transforms(cans, bcx, bcy, n):
-    """The mixed path's float x / y passes: quarter-wave lines on the warp-per-line kernels for N in
-    {256, 512, 1024} (Nx a multiple of 16 for y), the shared-memory engine otherwise."""
+    """The mixed path's float x / y passes: quarter-wave lines on the warp-per-line x kernels for N in
+    {256, 512, 1024}, the lanes-across-x-slots y kernel for Ny in {256, 512, 1024} (Nx a multiple of
+    16; several tiles and planes), the shared-memory engine otherwise."""
     import torch
 
     h = make_plan(cans, n, (bcx, bcy, NN), prec=1)
