@@ -355,6 +355,30 @@ def test_mixed_refined_reaches_fp64_accuracy(cans, bc):
     assert st == 0
 
 
+def test_mixed_refined_with_special_rhs_values(cans):
+    """A right-hand side with exact zeros, signed zeros and values below the float range (the inputs
+    the residual stencil's integer split of f leaves to its general path): the mixed solve still
+    reaches the FP64 accuracy of the oracle."""
+    bc = (P, DD, NN)
+    n = (64, 48, 40)
+    dzf = I.tanh_dzf(40, 1.8)
+    case = I.case_modes(n=n)
+    case.bc = bc
+    case.dzf = dzf
+    f = I.rhs_host(case).copy()
+    sel = np.random.default_rng(6).random(f.shape)
+    f[sel < 0.03] = 0.0
+    f[(sel >= 0.03) & (sel < 0.04)] = -0.0
+    f[(sel >= 0.04) & (sel < 0.05)] = 1e-300
+    p, st, info = solve_gpu(cans, f, n, bc, (1.0, 1.0), dzf, prec=1, sweeps=2, info=True)
+    ref = oracle.poisson_solve(f, bc, (1.0, 1.0), dzf)
+    res = oracle.relative_residual(p, f, bc, (1.0, 1.0), dzf)
+    floor = oracle.relative_residual(ref, f, bc, (1.0, 1.0), dzf)
+    assert res <= max(1e-12, 2 * floor), (res, floor, info)
+    assert rel(p, ref) <= 1e-11
+    assert st == 0
+
+
 def test_mixed_first_solve_only(cans):
     case = I.case_modes(n=(32, 32, 16))
     f = I.rhs_host(case)
