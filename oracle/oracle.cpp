@@ -615,7 +615,9 @@ void momentum_rhs(const Chan& g, double nu, const double* u, const double* v, co
           const double us = 0.5 * (u[g.id(i, j - 1, k)] + u[c]) * 0.5 * (v[g.id(i, j - 1, k)] + v[g.id(i + 1, j - 1, k)]);
           const double ut = 0.5 * (u[c] + U(g, u, i, j, k + 1)) * 0.5 * (W(g, w, i, j, k) + W(g, w, i + 1, j, k));
           const double ub = 0.5 * (U(g, u, i, j, k - 1) + u[c]) * 0.5 * (W(g, w, i, j, k - 1) + W(g, w, i + 1, j, k - 1));
-          const double adv = (ue * ue - uw * uw) / g.dx + (un - us) / g.dy + (ut - ub) / g.dzf[k];
+          // planted 4: the u z-flux divided by the centre distance instead of the cell width
+          const double hz = (g_fault == 4) ? g.dzc[k + 1] : g.dzf[k];
+          const double adv = (ue * ue - uw * uw) / g.dx + (un - us) / g.dy + (ut - ub) / hz;
           ru[c] = -adv + nu * lap_t(g, u, i, j, k);
         }
         // v on the face (i, j+1/2, k)
@@ -638,7 +640,9 @@ void momentum_rhs(const Chan& g, double nu, const double* u, const double* v, co
           const double wn = 0.5 * (wc + W(g, w, i, j + 1, k)) * 0.5 * (v[c] + v[g.id(i, j, k + 1)]);
           const double ws = 0.5 * (W(g, w, i, j - 1, k) + wc) * 0.5 * (v[g.id(i, j - 1, k)] + v[g.id(i, j - 1, k + 1)]);
           const double wt = 0.5 * (wc + W(g, w, i, j, k + 1)), wb = 0.5 * (W(g, w, i, j, k - 1) + wc);
-          const double adv = (we - ww) / g.dx + (wn - ws) / g.dy + (wt * wt - wb * wb) / g.dzc[k + 1];
+          // planted 5: the w z-flux divided by the cell width instead of the centre distance
+          const double hz = (g_fault == 5) ? g.dzf[k] : g.dzc[k + 1];
+          const double adv = (we - ww) / g.dx + (wn - ws) / g.dy + (wt * wt - wb * wb) / hz;
           const double lx = (W(g, w, i - 1, j, k) - 2 * wc + W(g, w, i + 1, j, k)) / (g.dx * g.dx);
           const double ly = (W(g, w, i, j - 1, k) - 2 * wc + W(g, w, i, j + 1, k)) / (g.dy * g.dy);
           const double lz = ((W(g, w, i, j, k + 1) - wc) / g.dzf[k + 1] - (wc - W(g, w, i, j, k - 1)) / g.dzf[k]) / g.dzc[k + 1];
@@ -656,16 +660,17 @@ double max_dti(const Chan& g, const double* u, const double* v, const double* w)
         const size_t c = g.id(i, j, k);
         const double ux = std::fabs(u[c]);
         const double vx = 0.25 * std::fabs(v[c] + v[g.id(i, j - 1, k)] + v[g.id(i + 1, j, k)] + v[g.id(i + 1, j - 1, k)]);
-        const double wx = 0.25 * std::fabs(W(g, w, i, j, k) + W(g, w, i, j, k - 1) + W(g, w, i + 1, j, k) + W(g, w, i + 1, j, k - 1));
+        const int kb = (g_fault == 7) ? k + 1 : k - 1;  // planted 7: the wrong pair of w faces
+        const double wx = 0.25 * std::fabs(W(g, w, i, j, k) + W(g, w, i, j, kb) + W(g, w, i + 1, j, k) + W(g, w, i + 1, j, kb));
         const double dtix = ux / g.dx + vx / g.dy + wx / g.dzf[k];
         const double uy = 0.25 * std::fabs(u[c] + u[g.id(i - 1, j, k)] + u[g.id(i, j + 1, k)] + u[g.id(i - 1, j + 1, k)]);
         const double vy = std::fabs(v[c]);
         const double wy = 0.25 * std::fabs(W(g, w, i, j, k) + W(g, w, i, j, k - 1) + W(g, w, i, j + 1, k) + W(g, w, i, j + 1, k - 1));
-        const double dtiy = uy / g.dx + vy / g.dy + wy / g.dzf[k];
+        const double dtiy = uy / g.dx + vy / ((g_fault == 8) ? g.dx : g.dy) + wy / g.dzf[k];  // planted 8: x spacing
         const double uz = 0.25 * std::fabs(u[c] + u[g.id(i - 1, j, k)] + U(g, u, i, j, k + 1) + U(g, u, i - 1, j, k + 1));
         const double vz = 0.25 * std::fabs(v[c] + v[g.id(i, j - 1, k)] + U(g, v, i, j, k + 1) + U(g, v, i, j - 1, k + 1));
         const double wz = std::fabs(W(g, w, i, j, k));
-        const double dtiz = uz / g.dx + vz / g.dy + wz / g.dzc[k + 1];
+        const double dtiz = uz / g.dx + vz / g.dy + wz / ((g_fault == 6) ? g.dzf[k] : g.dzc[k + 1]);  // planted 6: cell width
         dti = std::max(dti, std::max(dtix, std::max(dtiy, dtiz)));
       }
   return dti;

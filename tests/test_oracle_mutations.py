@@ -1,8 +1,8 @@
 """Plant plausible mistakes in the oracle (on the CPU) and check that the pins notice each one.
 
 Fault 1 uses the wrong z metric index in the stencil, fault 2 pairs each mode with its neighbour's
-eigenvalue, fault 3 transposes the x basis on the way back.  The correct oracle is restored after
-every case.
+eigenvalue, fault 3 transposes the x basis on the way back; faults 4-8 (below) sit in the advection
+term and the stable time step.  The correct oracle is restored after every case.
 """
 import numpy as np
 import pytest
@@ -56,4 +56,26 @@ def test_correct_oracle_passes_all_checks():
 def test_planted_mistake_is_caught(faulty, mode):
     faulty(mode)
     caught = (_lu_mismatch() > 1e-6) or (_manufactured_mismatch() > 1e-6) or (_stencil_eigen_mismatch() > 1e-6)
+    assert caught, f"fault {mode} slipped through the pins"
+
+
+# Faults 4-8 sit in the fractional-step pieces: 4 and 5 swap the z metric of the advection term's
+# z-flux divergence (u: cell width -> centre distance; w: the reverse), 6 puts the cell width in the
+# z row of the inverse time scale, 7 averages the wrong pair of w faces in its x row, 8 divides the
+# y row's v term by the x spacing.
+from tests.test_oracle_rk3_pins import _continuum_advection, advection_orders, dt_mismatches  # noqa: E402
+
+
+def test_correct_oracle_passes_the_step_pins():
+    orders, _ = advection_orders()
+    assert (orders > 1.75).all()
+    assert max(dt_mismatches().values()) < 1e-14
+
+
+@pytest.mark.parametrize("mode", [4, 5, 6, 7, 8])
+def test_planted_step_mistake_is_caught(faulty, mode):
+    fields = _continuum_advection()
+    faulty(mode)
+    orders, _ = advection_orders(fields)
+    caught = (orders < 1.75).any() or max(dt_mismatches().values()) > 1e-6
     assert caught, f"fault {mode} slipped through the pins"

@@ -105,6 +105,119 @@ def test_stable_dt_closed_form():
     assert abs(oracle.stable_dt(u * 1e-9, z, z, 10.0, 0.9, L, dzf) - 0.9 * 1.65 * dl * dl / 10.0) < 1e-15
 
 
+# ---------------------------------------------------------------------------------------------
+# Advection on the stretched grid: second-order convergence to the continuum -div(u u)
+# ---------------------------------------------------------------------------------------------
+ADV_L = (1.0, 0.7, 2.0)  # Lx, Ly, Lz
+
+
+def _continuum_advection():
+    """A smooth divergence-free channel field and its exact advection term -div(u u).
+
+    With s(z) = 1 - cos(2 pi z / Lz) (s and s' vanish on both walls), a = 2 pi / Lx, b = 2 pi / Ly:
+    w = s sin(ax) cos(by), u = U0(z) + s'/(2a) cos(ax) cos(by), v = V0(z) - s'/(2b) sin(ax) sin(by),
+    so u_x + v_y = -s' sin(ax) cos(by) = -w_z, and u = v = w = 0 on the walls (no slip).  The exact
+    derivatives come from sympy, independently of the oracle's stencils."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    lx, ly, lz = ADV_L
+    a, b = 2 * sp.pi / lx, 2 * sp.pi / ly
+    s = 1 - sp.cos(2 * sp.pi * z / lz)
+    ds = sp.diff(s, z)
+    u = sp.sin(sp.pi * z / lz) + ds / (2 * a) * sp.cos(a * x) * sp.cos(b * y)
+    v = sp.Rational(3, 10) * sp.sin(2 * sp.pi * z / lz) - ds / (2 * b) * sp.sin(a * x) * sp.sin(b * y)
+    w = s * sp.sin(a * x) * sp.cos(b * y)
+    assert sp.simplify(sp.diff(u, x) + sp.diff(v, y) + sp.diff(w, z)) == 0
+    adv = [-(sp.diff(c * u, x) + sp.diff(c * v, y) + sp.diff(c * w, z)) for c in (u, v, w)]
+    f = lambda e: sp.lambdify((x, y, z), e, "numpy")
+    return [f(e) for e in (u, v, w)], [f(e) for e in adv]
+
+
+def advection_errors(n, fields=None):
+    """Max error of the oracle's advection term (nu = 0) against the continuum one on an n^3 tanh grid
+    (alpha 1.8), each component sampled at its own staggered location."""
+    (fu, fv, fw), (au, av, aw) = fields or _continuum_advection()
+    lx, ly, lz = ADV_L
+    dzf = I.tanh_dzf(n, 1.8, lz)
+    zf = np.concatenate([[0.0], np.cumsum(dzf)])
+    zc = 0.5 * (zf[:-1] + zf[1:])
+    xc, xf = (np.arange(n) + 0.5) * lx / n, (np.arange(n) + 1.0) * lx / n
+    yc, yf = (np.arange(n) + 0.5) * ly / n, (np.arange(n) + 1.0) * ly / n
+
+    def at(fn, zz, yy, xx):
+        return np.broadcast_to(fn(xx[None, None, :], yy[None, :, None], zz[:, None, None]), (n, n, n)).copy()
+
+    u, eu = at(fu, zc, yc, xf), at(au, zc, yc, xf)
+    v, ev = at(fv, zc, yf, xc), at(av, zc, yf, xc)
+    w, ew = at(fw, zf[1:], yc, xc), at(aw, zf[1:], yc, xc)
+    w[-1] = 0.0
+    ru, rv, rw = oracle.momentum_rhs(u, v, w, 0.0, ADV_L[:2], dzf)
+    return np.array([np.abs(ru - eu).max(), np.abs(rv - ev).max(), np.abs(rw[:-1] - ew[:-1]).max()])
+
+
+def advection_orders(fields=None):
+    e = [advection_errors(n, fields) for n in (16, 32, 64)]
+    return np.log2(e[1] / e[2]), e[2]
+
+
+def test_advection_is_second_order_on_stretched_grid():
+    """Every component of the advection term converges at second order on the tanh-stretched grid.
+
+    A swapped z metric (cell width dzf where the centre distance dzc belongs, or the reverse) leaves a
+    first-order error on a stretched grid, which this catches and the uniform-grid energy pin cannot."""
+    orders, err64 = advection_orders()
+    assert (orders > 1.75).all(), orders
+    assert (err64 < 0.06).all(), err64
+
+
+# ---------------------------------------------------------------------------------------------
+# Stable time step: closed forms that isolate each row and each term of the inverse time scale
+# ---------------------------------------------------------------------------------------------
+DT_SHAPE = (10, 6, 8)  # (nz, ny, nx)
+
+
+def dt_cases():
+    """(name, (u, v, w), exact dt / cfl) on the stretched grid, cfl = 1 and negligible viscosity.
+
+    A field alternating in sign along two directions cancels in every four-point average that spans
+    one of them, so only the chosen row of Eq. dt's inverse time scale survives.  A w spike on one
+    face k0 gives |w| / (distance between centres k0, k0+1) in the z row and |w| / (2 dzf) in the x and
+    y rows of the two cells that share the face."""
+    dzf = I.tanh_dzf(DT_SHAPE[0], 1.8, 2.0)
+    dzc = 0.5 * (dzf[:-1] + dzf[1:])
+    dx, dy = L[0] / DT_SHAPE[2], L[1] / DT_SHAPE[1]
+    k, j, i = np.meshgrid(*(np.arange(n) for n in DT_SHAPE), indexing="ij")
+    alt_jk, alt_ik = (-1.0) ** (j + k), (-1.0) ** (i + k)
+    z = np.zeros(DT_SHAPE)
+    k0 = 2  # lower half: dzf[k0] < dzf[k0 + 1]
+
+    def spike(amp):
+        w = np.zeros(DT_SHAPE)
+        w[k0] = amp
+        return w
+
+    r3 = np.sqrt(3.0)
+    return dzf, [
+        ("v only", (z, 3 * alt_ik, z), r3 * dy / 3),
+        ("w only", (z, z, spike(2.0)), r3 * dzc[k0] / 2),
+        ("x row: u, v", (40 * alt_jk, np.full(DT_SHAPE, 3.0), z), r3 / (40 / dx + 3 / dy)),
+        ("x row: u, w", (40 * alt_jk, z, spike(2.0)), r3 / (40 / dx + 1 / dzf[k0])),
+        ("y row: v, w", (z, 40 * alt_ik, spike(2.0)), r3 / (40 / dy + 1 / dzf[k0])),
+        ("y row: u, v", (np.full(DT_SHAPE, 2.0), 5 * alt_ik, z), r3 / (2 / dx + 5 / dy)),
+        ("z row: u, w", (np.full(DT_SHAPE, 2.0), z, spike(2.0)), r3 / (2 / dx + 2 / dzc[k0])),
+    ]
+
+
+def dt_mismatches():
+    dzf, cases = dt_cases()
+    return {name: abs(oracle.stable_dt(*f, 1e-9, 1.0, L, dzf) - want) / want for name, f, want in cases}
+
+
+def test_stable_dt_closed_forms_for_each_row():
+    bad = {k: v for k, v in dt_mismatches().items() if v > 1e-14}
+    assert not bad, bad
+
+
 def test_rk3_step_keeps_flow_divergence_free_and_bulk_velocity():
     dzf = I.tanh_dzf(SHAPE[0], 1.6, 2.0)
     zc = I.z_centres(dzf)
