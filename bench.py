@@ -302,7 +302,9 @@ def gpu_arm(args):
             dist.destroy_process_group()
         return
 
-    cpu = cpu_baseline(seconds_budget=args.cpu_budget)
+    slab = {}
+    cpu = cpu_baseline(seconds_budget=args.cpu_budget, keep=slab)
+    err_sweeps = error_per_sweep(cans, slab, sweeps_used + 1)
     fft_case = I.case_modes(n=(1024, 1024, 64))
     cpu_fft = cpu_fft_baseline(I.rhs_device(fft_case, "cuda").cpu().numpy(), fft_case,
                                seconds_budget=args.cpu_budget / 2)
@@ -329,6 +331,7 @@ def gpu_arm(args):
             "z_grid": "tanh faces, alpha 1.8",
             "sweeps": sweeps_used,
             "residual_per_sweep": [float(v) for v in info_used],
+            "rel_err_vs_fp64_oracle_per_sweep": err_sweeps,
             "l2": "inputs larger than L2 (f and p 4.3 GB each, work fields 6.4 GB)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
         },
@@ -629,12 +632,62 @@ def rk3_measure(cans, I, args):
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / steps
         out[name + "_dt"] = float(dt.item())
+        if not implicit:
+            out[name + "_breakdown"] = rk3_breakdown(cans, ch, step, npts, out[name])
         ch.close()
         del u, v, w, p, g
     torch.cuda.empty_cache()
     out["note"] = ("one CUDA graph per step; mixed = Poisson solves mixed precision with 1 refinement sweep; "
                    "implicit_mixed = Crank-Nicolson diffusion (three Helmholtz solves + the Poisson solve per "
                    "substage, mixed, 1 sweep) at the explicit step's dt")
+    return out
+
+
+# Algorithmic bytes per point per launch of the step's kernels (FP64 fields): momentum reads u, v, w,
+# p and the previous right-hand sides (7 fields; substage 1 skips those 3) and writes the right-hand
+# sides and u*, v*, w* (6); the divergence reads u*, v*, w* and writes f; the correction reads u*,
+# v*, w*, Phi, p and writes u, v, w, p; chkdt reads u, v, w; the forcing reads and writes u.
+RK3_BYTES = {"momentum": (32 + 56 + 56) / 3 + 48, "divergence": 32, "correction": 72, "chkdt": 24, "forcing": 16}
+# FP64 operations per point of the momentum kernel (an FMA counts 2), counted from its source: per
+# velocity component 42 (advection 24, diffusion 16, nu L - A 2), the pressure gradient 6, the RK3
+# combination 21 (substages 2 and 3), two metric products
+MOMENTUM_FP64_FLOPS = 155
+
+
+def rk3_breakdown(cans, ch, step, npts, ms_step):
+    """Per-kernel device times of one RK3 step from the plan's CUDA-event profile (three eager steps,
+    after the graph-timed ones), with each kernel's HBM fraction by its algorithmic bytes and the
+    momentum kernel's FP64 rate."""
+    import torch
+
+    cans.cans_plan_profile(ch.plan, True)
+    reps = 3
+    for _ in range(reps):
+        step()
+    torch.cuda.synchronize()
+    hbm, _ = _peaks()
+    names = cans.CANS_PASS_NAMES
+    out, solve_ms = {}, 0.0
+    for k, nm in enumerate(names):
+        tot, n = cans.cans_plan_profile_read(ch.plan, k)
+        if not n:
+            continue
+        if nm in RK3_BYTES:
+            ms = tot / reps
+            per_launch = tot / n
+            ent = {"ms_per_step": ms, "launches_per_step": n // reps, "ms_per_launch": per_launch,
+                   "bytes_per_pt": RK3_BYTES[nm],
+                   "hbm_frac": RK3_BYTES[nm] * npts / (per_launch * 1e-3) / 1e9 / hbm,
+                   "share_of_step": ms / ms_step}
+            if nm == "momentum":
+                ent["fp64_tflops"] = MOMENTUM_FP64_FLOPS * npts / (per_launch * 1e-3) / 1e12
+            out[nm] = ent
+        else:
+            solve_ms += tot / reps
+    cans.cans_plan_profile(ch.plan, False)
+    out["poisson_passes"] = {"ms_per_step": solve_ms, "share_of_step": solve_ms / ms_step}
+    out["note"] = ("eager steps with the plan's CUDA-event profile (the graph-timed step has the same "
+                   "launches); shares are of the graph-timed step")
     return out
 
 
@@ -677,6 +730,25 @@ def ensemble_measure(cans, I, args):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle: the baseline leg and the reference arm
 # ------------------------------------------------------------------------------------------------
+def error_per_sweep(cans, slab, max_sweeps: int):
+    """Relative L2 error of the mixed solve against the FP64 oracle after 0 .. max_sweeps refinement
+    sweeps, on the oracle's slab of the workload (the same 1024 x 1024 planes, so the same x-y
+    kernels; the z pass on its 2-cell columns)."""
+    import torch
+
+    case, f, ref = slab["case"], slab["f"], slab["ref"]
+    ft = torch.from_numpy(f).cuda()
+    out = {"sample": f"{case.n[0]}x{case.n[1]}x{case.n[2]} slab of the workload, mixed, plan as the bench's"}
+    for sw in range(max_sweeps + 1):
+        s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_MIXED, sweeps=sw,
+                               autotune=True)
+        p = s.solve(ft)
+        torch.cuda.synchronize()
+        s.close()
+        out[f"sweeps_{sw}"] = float(np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref))
+    return out
+
+
 def _oracle_sample(nz_sample: int):
     from paper_2001_05234_b300 import inputs as I
 
@@ -684,7 +756,7 @@ def _oracle_sample(nz_sample: int):
     return case, I.rhs_host(case)
 
 
-def cpu_baseline(seconds_budget: float = 20.0):
+def cpu_baseline(seconds_budget: float = 20.0, keep=None):
     """The oracle as it stands, on the host cores, on a slab of the workload: full 1024 x 1024 x-y
     planes (the oracle's cost per point depends on Nx + Ny, so a slab keeps the per-point cost) and
     a few z-levels."""
@@ -695,8 +767,10 @@ def cpu_baseline(seconds_budget: float = 20.0):
     nz = 2
     case, f = _oracle_sample(nz)
     t0 = time.perf_counter()
-    oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
+    ref = oracle.poisson_solve(f, case.bc, case.length_xy, case.dzf, nthreads=cores)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(case=case, f=f, ref=ref)
     reps = 1
     while dt * (reps + 1) < seconds_budget and reps < 3:
         t0 = time.perf_counter()

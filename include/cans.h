@@ -78,10 +78,15 @@ typedef struct {
                                 on both walls (bc_z must be CANS_BC_DD); the solve then reads and writes
                                 the first Nz - 1 planes of Nx*Ny*Nz arrays and leaves the top plane
                                 (the wall face) alone. */
+  int verify;                /* 1: every solve ends with ||f - L_h p||_2 / ||f||_2 evaluated on the
+                                device (one more read of f and p, no host synchronisation) and a value
+                                above tol recorded as CANS_ERR_NOT_CONVERGED in the plan's status word
+                                (cans_plan_status); skipped for in-place FP64 solves (f == p), whose f is
+                                gone.  0: only the checks that cost no extra pass (see cans_plan_status). */
 } cans_opts;
 
 /* Fill *opts with the defaults: FP64, 2 sweeps, tol 1e-12, fraction 0.01, autotune 0, shift 0,
- * z_grid 0. */
+ * z_grid 0, verify 0. */
 void cans_opts_default(cans_opts* opts);
 
 /*
@@ -118,7 +123,9 @@ int cans_poisson_workspace_size(cans_plan_t plan, size_t* bytes);
  *                and after every sweep, and the call synchronises the stream; with info the call
  *                returns CANS_ERR_NOT_CONVERGED when the last value exceeds opts.tol (mixed only),
  *                and CANS_ERR_INCOMPATIBLE when a singular problem's f has a weighted mean above
- *                1e-10 of mean|f|.
+ *                1e-10 of mean|f|; errors the device checks recorded in the plan's status word
+ *                (cans_plan_status) are returned as well, and the word is cleared.  An in-place
+ *                FP64 solve (f == p) has no f left to measure: its info values are NaN.
  * Singular problems always return the zero-mean solution of the compatible part of f.
  */
 int cans_poisson_solve(cans_plan_t plan, const double* f, double* p, void* workspace, void* cuda_stream,
@@ -137,6 +144,30 @@ int cans_helmholtz_solve(cans_plan_t plan, const double* f, double* p, double sh
 
 /* Release the plan and its device tables. */
 int cans_plan_destroy(cans_plan_t plan);
+
+/*
+ * cans_plan_status -- the plan's device status word: the first error that any solve on this plan
+ * (cans_poisson_solve, cans_helmholtz_solve, cans_poisson_solve_adjoint, the solves inside the RK3
+ * steps and batches) detected on the device since the last call, written by the solve's last kernel
+ * without a host synchronisation -- so it also covers solves replayed from a CUDA graph and solves
+ * called without `info`.  The call synchronises the plan's device, stores the word in *status (or
+ * CANS_OK) and clears it.  Checks, in this order:
+ *   CANS_ERR_INCOMPATIBLE  singular problem whose f has a dzf-weighted mean above 1e-9 (FP64) or
+ *                          1e-5 (mixed: the transforms round to float) of sqrt(Nx Ny sum_k dzf_k^2)
+ *                          ||f||_2 -- the mean relative to the root-mean-square of f;
+ *   CANS_ERR_NOT_CONVERGED a norm the solve accumulated (||f||^2, each sweep's residual) is not finite;
+ *                          a refinement sweep (mixed, from the second on) that reduced the residual by
+ *                          less than half while it was still above tol; with opts.verify = 1, a final
+ *                          relative residual above tol;
+ *   CANS_ERR_TIMEOUT       a bounded device-side wait of a persistent kernel gave up.
+ * The return value is CANS_OK, or CANS_ERR_ARG / CANS_ERR_CUDA when the word could not be read.
+ *
+ * A plan serves one solve at a time: its device accumulators, its status word and (for
+ * cans_helmholtz_solve, which sets the plan's shift for the duration of the call and restores it)
+ * its shift are per plan, so solves that overlap on the GPU (several streams) or on the host
+ * (several threads) must use separate plans.
+ */
+int cans_plan_status(cans_plan_t plan, int* status);
 
 /*
  * cans_poisson_solve_adjoint -- q = S^T g, the transpose (plain Euclidean inner product) of the solve
@@ -200,7 +231,14 @@ enum cans_pass {
   CANS_PASS_RS = 7, /* residual stencil of a refinement sweep, when it runs as its own kernel (then
                        CANS_PASS_XR is the forward x transform of the residual alone) */
   CANS_PASS_ZD = 8, /* the mixed path's double-precision z columns (lowest |mu| and singular) */
-  CANS_PASS_COUNT = 9
+  /* the fractional-step kernels around the solve (cans_rk3_step, cans_rk3_step_implicit,
+   * cans_box_rk3_step, cans_project), recorded on the pressure plan */
+  CANS_PASS_MOMENTUM = 9,    /* advection + diffusion + RK3 combination (Eq. up) */
+  CANS_PASS_DIVERGENCE = 10, /* right-hand side of Eq. poi_ns */
+  CANS_PASS_CORRECT = 11,    /* projection correction and pressure update (+ bulk-velocity sum) */
+  CANS_PASS_CHKDT = 12,      /* stable time step: max reduction of the inverse time scale + dt */
+  CANS_PASS_FORCING = 13,    /* constant-flow-rate shift of u */
+  CANS_PASS_COUNT = 14
 };
 int cans_plan_profile(cans_plan_t plan, int enable);
 int cans_plan_profile_read(cans_plan_t plan, int pass, double* total_ms, int* launches);
@@ -227,9 +265,11 @@ int cans_batch_destroy(cans_batch_t batch);
  * pointers as in cans_poisson_solve) solved concurrently on internal streams forked from cuda_stream.
  * workspace: cans_poisson_batched_workspace_size() bytes (the problems' workspaces, 256-byte aligned
  * each).  device_status (device, count ints, may be NULL) receives each problem's status, written
- * on the device after its solve: CANS_ERR_NOT_CONVERGED when a norm the mixed solve accumulates
- * (|f|^2, the residual of each sweep) is not finite, else CANS_OK (FP64 problems: CANS_OK); when the
- * call itself fails, every entry receives the returned status.  The internal streams are created and released on every call, so this form is not meant for
+ * on the device after its solve: the checks of cans_plan_status for that problem alone --
+ * CANS_ERR_INCOMPATIBLE (singular problem, f with a weighted mean), CANS_ERR_NOT_CONVERGED (a norm
+ * the solve accumulated is not finite, a stalled refinement sweep, or, with the plan's opts.verify,
+ * a final relative residual above its tol) -- else CANS_OK; when the call itself fails, every entry
+ * receives the returned status.  The internal streams are created and released on every call, so this form is not meant for
  * stream capture or tight loops: keep a cans_batch_t for those. */
 int cans_poisson_batched_workspace_size(int count, const cans_plan_t* plans, size_t* bytes);
 int cans_poisson_solve_batched(int count, const cans_plan_t* plans, const double* const* f, double* const* p,
@@ -322,7 +362,10 @@ int cans_project_adjoint(cans_plan_t plan, double* u, double* v, double* w, void
  *   - A plan whose workspace exceeds the scratch size is rejected with CANS_ERR_WORKSPACE before any
  *     work is enqueued.  FP64 plans need no scratch and always fit.
  *   - The first call on each device looks up the scratch array's device address (with that device
- *     current); make that first call before any stream capture begins.
+ *     current); make that first call before any stream capture begins.  Under CUDA's lazy module
+ *     loading (the default) that first call is also when the device commits the 48 MiB, so a caller
+ *     whose memory pool will take the rest of the device makes it before the pool does.  A device
+ *     reset in between is noticed and the address looked up again.
  *   - All calls share the one array: calls whose work overlaps on the GPU (several streams or threads
  *     at once) race on it and must be serialised by the caller.
  *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.

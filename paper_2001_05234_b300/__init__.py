@@ -35,7 +35,7 @@ class CansError(RuntimeError):
 class cans_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
                 ("fp64_mode_fraction", ctypes.c_double), ("autotune", ctypes.c_int), ("shift", ctypes.c_double),
-                ("z_grid", ctypes.c_int)]
+                ("z_grid", ctypes.c_int), ("verify", ctypes.c_int)]
 
 
 class cans_rk3_params(ctypes.Structure):
@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
         L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
         L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
+        L.cans_plan_status.argtypes = [vp, ip]
         L.cans_poisson_adjoint_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, vp]
         L.cans_transform_xy.argtypes = [vp, vp, ctypes.c_int, vp]
@@ -248,6 +249,13 @@ def cans_plan_destroy(plan) -> int:
     return lib().cans_plan_destroy(plan)
 
 
+def cans_plan_status(plan) -> int:
+    """The plan's device status word (synchronises the device, then clears the word)."""
+    word = ctypes.c_int(0)
+    _check(lib().cans_plan_status(plan, ctypes.byref(word)), "cans_plan_status")
+    return int(word.value)
+
+
 def cans_poisson_adjoint_workspace_size(plan) -> int:
     b = ctypes.c_size_t()
     _check(lib().cans_poisson_adjoint_workspace_size(plan, ctypes.byref(b)), "cans_poisson_adjoint_workspace_size")
@@ -284,7 +292,8 @@ def cans_split_f64(x_ptr: int, n: int, rn_ptr: int = 0, hi_ptr: int = 0, lo_ptr:
 
 
 CANS_PASS_NAMES = ("x_forward", "y_forward", "z_solve", "y_inverse", "x_inverse", "x_forward_residual",
-                   "x_inverse_update", "residual_stencil", "z_solve_double_columns")
+                   "x_inverse_update", "residual_stencil", "z_solve_double_columns", "momentum", "divergence",
+                   "correction", "chkdt", "forcing")
 
 
 def cans_plan_profile(plan, enable: bool) -> int:
@@ -314,7 +323,7 @@ class PoissonSolver:
     z-faces (a staggered w; the solve uses the first Nz - 1 planes)."""
 
     def __init__(self, n, bc, length_xy=(1.0, 1.0), dzf=None, prec=CANS_FP64, sweeps=2, tol=1e-12,
-                 fp64_fraction=0.01, autotune=False, shift=0.0, z_grid=0):
+                 fp64_fraction=0.01, autotune=False, shift=0.0, z_grid=0, verify=False):
         import torch
 
         self.n = tuple(int(v) for v in n)
@@ -327,6 +336,7 @@ class PoissonSolver:
         o.autotune = 1 if autotune else 0
         o.shift = float(shift)
         o.z_grid = int(z_grid)
+        o.verify = 1 if verify else 0
         self.opts = o
         _, self.plan = cans_poisson_plan(self.n, length_xy, self.bc, dzf, o)
         nbytes = cans_poisson_workspace_size(self.plan)
@@ -355,6 +365,10 @@ class PoissonSolver:
         if st != CANS_OK and not (info and st in (-5, -6)):
             raise CansError(st, "cans_helmholtz_solve" if shift is not None else "cans_poisson_solve")
         return (out, buf, st) if info else out
+
+    def status(self) -> int:
+        """The plan's device status word since the last read (cans_plan_status; synchronises)."""
+        return cans_plan_status(self.plan)
 
     def solve_adjoint(self, g, out=None, stream=None):
         """q = S^T g (cans_poisson_solve_adjoint); the adjoint workspace is allocated on first use."""

@@ -24,14 +24,11 @@ struct cans_batch_s {
   std::vector<cudaEvent_t> joins;
 };
 
-// Per-problem device status after a solve: CANS_ERR_NOT_CONVERGED when |f|^2 or any residual norm
-// the mixed solve accumulated on the device is not finite, else CANS_OK.  FP64 solves keep no device
-// norms (nacc_used = 0) and report CANS_OK.
-__global__ void solve_status_kernel(const double* acc, int nacc_used, int* status) {
-  bool ok = true;
-  for (int i = threadIdx.x; i < nacc_used; i += 32) ok &= (bool)isfinite(acc[i]);
-  ok = __all_sync(0xffffffffu, ok);
-  if (threadIdx.x == 0) *status = ok ? CANS_OK : CANS_ERR_NOT_CONVERGED;
+// Per-problem device status after a solve: the checks of the plan's status word (cans::solve_check:
+// incompatible singular right-hand side, non-finite norms, a stalled refinement sweep, and with
+// opts.verify the final residual against tol), written for this problem alone.
+__global__ void batch_status_kernel(const double* acc, cans::SolveCheck c, int* status) {
+  if (threadIdx.x == 0) *status = cans::solve_check(acc, c);
 }
 
 static int batch_solve_impl(cans_batch_t B, const double* const* f, double* const* p, void* workspace,
@@ -51,8 +48,8 @@ static int batch_solve_impl(cans_batch_t B, const double* const* f, double* cons
     if (rc != CANS_OK) return rc;
     if (status) {
       const cans_plan_s* P = B->plans[q];
-      const int used = (P->opts.prec == CANS_MIXED) ? 1 + P->opts.max_sweeps : 0;
-      solve_status_kernel<<<1, 32, 0, sq>>>(P->acc_d, used, status + q);
+      batch_status_kernel<<<1, 32, 0, sq>>>(P->acc_d, cans::solve_check_args(P, P->singular, P->opts.verify != 0),
+                                            status + q);
       if (cudaGetLastError() != cudaSuccess) return CANS_ERR_CUDA;
     }
   }

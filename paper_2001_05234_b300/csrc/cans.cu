@@ -176,6 +176,7 @@ void cans_opts_default(cans_opts* o) {
   o->autotune = 0;
   o->shift = 0.0;
   o->z_grid = 0;
+  o->verify = 0;
 }
 
 const char* cans_status_string(int s) {
@@ -211,6 +212,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   if (!std::isfinite(o.shift) || o.shift > 0) return CANS_ERR_ARG;
   if (o.z_grid != 0 && o.z_grid != 1) return CANS_ERR_ARG;
   if (o.z_grid == 1 && (bc[2] != BC_DD || n[2] < 2)) return CANS_ERR_ARG;
+  if (o.verify != 0 && o.verify != 1) return CANS_ERR_ARG;
   const int ncell = n[2];
   std::vector<double> dzcell(ncell);
   for (int k = 0; k < ncell; ++k) {
@@ -411,9 +413,18 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     o_mask = B.add(mask.data(), ncol);
     has_mask = true;
   }
-  P->nacc = 2 * (o.max_sweeps + 4);  // [0] |f|^2, [1+s] |r_s|^2, [nacc-5] gauge sum, [nacc-4..] reports
+  // [0] |f|^2, [1+s] |r_s|^2 (s < max_sweeps), [nacc-7] compatibility sum, [nacc-5] gauge sum,
+  // [nacc-4..] reports: slots 1 + max_sweeps .. nacc-8 stay free for every max_sweeps >= 0
+  P->nacc = 2 * (o.max_sweeps + 4);
   std::vector<double> zeros(P->nacc, 0.0);
   const size_t o_acc = B.add(zeros.data(), P->nacc * 8);
+  const int status0 = CANS_OK;
+  const size_t o_status = B.add(&status0, sizeof(int));
+  {
+    double w2 = 0;
+    for (int k = 0; k < nz; ++k) w2 += dz[k] * dz[k];
+    P->compat_scale = std::sqrt((double)n[0] * (double)n[1] * w2);
+  }
 
   if (cudaMalloc(&P->dtab, B.host.size()) != cudaSuccess ||
       cudaMemcpy(P->dtab, B.host.data(), B.host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -466,6 +477,7 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->zs_l[1] = line_launch(nz, n[0], sizeof(float2), 16);
   }
   P->acc_d = reinterpret_cast<double*>(base + o_acc);
+  P->status_d = reinterpret_cast<int*>(base + o_status);
 
   // launch shapes
   const int nlines = n[1] * nz;
@@ -485,6 +497,10 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->z_ti[s] = ti;
     P->z_smem[s] = (size_t)ti * nz * es;
   }
+  // CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the TMA kernel
+  // cannot take fail instead of falling back (switches for comparisons and tests; the autotuner, when
+  // on, chooses between the two kernels by timing)
+  if (const char* ev = std::getenv("CANS_Z_TMA")) P->z_tma = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (o.autotune) {
     const int rc = autotune_plan(P);
     if (rc != CANS_OK) {
@@ -610,38 +626,36 @@ cudaError_t cans::set_smem(const void* fn, size_t bytes) {
   return cudaSuccess;
 }
 
-namespace {
-
-// Event pair around one pass launch when profiling is on.
 // Each pass is an NVTX range (seen by Nsight tools attached to the process; a no-op otherwise) and,
-// while cans_plan_profile is on, a pair of CUDA events on the solve's stream.
-const char* const kPassName[CANS_PASS_COUNT] = {"x_forward",          "y_forward",        "z_solve",
-                                                "y_inverse",          "x_inverse",        "x_forward_residual",
-                                                "x_inverse_update",   "residual_stencil", "z_solve_double_columns"};
+// while cans_plan_profile is on, a pair of CUDA events on the pass's stream.
+namespace {
+const char* const kPassName[CANS_PASS_COUNT] = {
+    "x_forward",        "y_forward",        "z_solve",          "y_inverse",  "x_inverse",
+    "x_forward_residual", "x_inverse_update", "residual_stencil", "z_solve_double_columns",
+    "momentum",         "divergence",       "correction",       "chkdt",      "forcing"};
+}  // namespace
 
-struct PassTimer {
-  cans_plan_s* P;
-  cudaStream_t st;
-  int rec = -1;
-  PassTimer(cans_plan_s* P_, int kind, cudaStream_t st_) : P(P_), st(st_) {
-    nvtxRangePushA(kPassName[kind]);
-    if (!P->profiling) return;
-    if ((size_t)(2 * P->ev_used + 2) > P->ev_pool.size()) {
-      for (int q = 0; q < 64; ++q) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return;
-        P->ev_pool.push_back(e);
-      }
+cans::PassTimer::PassTimer(cans_plan_s* P_, int kind, cudaStream_t st_) : P(P_), st(st_) {
+  nvtxRangePushA(kPassName[kind]);
+  if (!P->profiling) return;
+  if ((size_t)(2 * P->ev_used + 2) > P->ev_pool.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      P->ev_pool.push_back(e);
     }
-    rec = P->ev_used++;
-    P->ev_kind.push_back(kind);
-    cudaEventRecord(P->ev_pool[2 * rec], st);
   }
-  ~PassTimer() {
-    if (rec >= 0) cudaEventRecord(P->ev_pool[2 * rec + 1], st);
-    nvtxRangePop();
-  }
-};
+  rec = P->ev_used++;
+  P->ev_kind.push_back(kind);
+  cudaEventRecord(P->ev_pool[2 * rec], st);
+}
+
+cans::PassTimer::~PassTimer() {
+  if (rec >= 0) cudaEventRecord(P->ev_pool[2 * rec + 1], st);
+  nvtxRangePop();
+}
+
+namespace {
 
 #define CK(...)                                  \
   do {                                           \
@@ -690,9 +704,10 @@ bool tune_lookup(const std::string& key, std::vector<int>& v) {
   bool found = false;
   while (std::fgets(line, sizeof(line), fh)) {
     char k[400];
-    int a, b, cc, d;
-    if (std::sscanf(line, "%399s %d %d %d %d", k, &a, &b, &cc, &d) == 5 && key == k) {
-      v = {a, b, cc, d};
+    int a, b, cc, d, t = 0;
+    const int got = std::sscanf(line, "%399s %d %d %d %d %d", k, &a, &b, &cc, &d, &t);
+    if (got >= 5 && key == k) {
+      v = {a, b, cc, d, got == 6 ? t : 0};
       found = true;
     }
   }
@@ -708,7 +723,7 @@ void tune_store(const std::string& key, const std::vector<int>& v) {
   if (!path) return;
   FILE* fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%s %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3]);
+  std::fprintf(fh, "%s %d %d %d %d %d\n", key.c_str(), v[0], v[1], v[2], v[3], v[4]);
   std::fclose(fh);
 }
 
@@ -747,6 +762,7 @@ int autotune_plan(cans_plan_s* P) {
     } else {
       P->z_ti[s] = c[3];
       P->z_smem[s] = (size_t)c[3] * P->n[2] * (s ? 4 : 8);
+      if (s) P->z_tma = c[4];
     }
   };
   if (tune_lookup(key, v)) {
@@ -764,7 +780,7 @@ int autotune_plan(cans_plan_s* P) {
   }
   cudaMemset(f, 0, N * sizeof(double));
   cudaMemset(w, 0, wbytes);
-  std::vector<int> best = {P->x_l[s].nl, P->y_l[s].nl, P->zs_l[s].nl, P->z_ti[s]};
+  std::vector<int> best = {P->x_l[s].nl, P->y_l[s].nl, P->zs_l[s].nl, P->z_ti[s], 0};
   const int cand_nl[4] = {4, 8, 16, 32};
   const int cand_ti[3] = {s ? 8 : 4, s ? 16 : 8, s ? 32 : 16};
   const int nlines = P->n[1] * P->n[2];
@@ -786,6 +802,7 @@ int autotune_plan(cans_plan_s* P) {
     }
   }
   if (P->bc[2] != BC_P) {
+    P->z_tma = 0;
     for (int ti : cand_ti) {
       if ((size_t)ti * P->n[2] * (s ? 4 : 8) > (size_t)96 * 1024) continue;
       P->z_ti[s] = ti;
@@ -793,6 +810,11 @@ int autotune_plan(cans_plan_s* P) {
       const float tz = s ? time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); })
                          : time_best([&] { return launch_z<double>(P, (double*)w, nullptr, 0); });
       if (tz < bz) { bz = tz; best[3] = ti; }
+    }
+    if (s && ztma_feasible(P, w)) {  // the TMA-fed float kernel (its tile width is fixed)
+      P->z_tma = 1;
+      const float tz = time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); });
+      if (tz < bz) { bz = tz; best[4] = 1; }
     }
   }
   cudaFree(f);
@@ -817,10 +839,13 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     PassTimer tm_(P, kind, st);             \
     CK(__VA_ARGS__);                        \
   } while (0)
+  // the singular column's weighted sum before its projection (compatibility check of the status word)
+  double* compat = P->singular ? P->acc_d + P->nacc - 7 : nullptr;
   if (P->opts.prec == CANS_FP64) {
-    TIMED(CANS_PASS_XF, launch_xfwd<double, 0>(P, f, nullptr, nullptr, p, nullptr, st));
+    CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
+    TIMED(CANS_PASS_XF, launch_xfwd<double, 0>(P, f, nullptr, nullptr, p, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<double, 1>(P, p, st));
-    TIMED(CANS_PASS_Z, launch_z<double>(P, p, nullptr, st));
+    TIMED(CANS_PASS_Z, launch_z<double>(P, p, nullptr, st, -1, compat));
     TIMED(CANS_PASS_YI, launch_y<double, -1>(P, p, st));
     TIMED(CANS_PASS_XI, launch_xinv<double, 0>(P, p, p, nullptr, nullptr, inv_scale, nullptr, st));
   } else {
@@ -833,8 +858,8 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
     TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
-    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st, 0));
-    TIMED(CANS_PASS_ZD, launch_z<float>(P, W, nullptr, st, 1));
+    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st, 0, compat));
+    TIMED(CANS_PASS_ZD, launch_z<float>(P, W, nullptr, st, 1, compat));
     TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
     if (sweeps == 0) {
       TIMED(CANS_PASS_XI, launch_xinv<float, 0>(P, W, p, nullptr, nullptr, inv_scale, nullptr, st));
@@ -868,12 +893,20 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
       }
     }
   }
+  // the final residual (opts.verify, or a caller that asks for the norms; not for an in-place FP64
+  // solve, whose f is gone), then the status word's checks
+  double* acc2 = P->acc_d + P->nacc - 4;
+  const bool verify = (info != nullptr || P->opts.verify) && f != p;
+  if (verify) CK(launch_residual_norms(P, f, p, acc2, st));
+  CK(launch_solve_status(P, compat != nullptr, verify, st));
   if (info) {
-    double* acc2 = P->acc_d + P->nacc - 4;
-    CK(launch_residual_norms(P, f, p, acc2, st));
-    if (P->singular) CK(launch_weighted_sum(P, f, acc2 + 2, st));
+    if (P->singular && verify) CK(launch_weighted_sum(P, f, acc2 + 2, st));
     std::vector<double> h(P->nacc);
+    int word = CANS_OK;
+    const int zero = CANS_OK;
     CK(cudaMemcpyAsync(h.data(), P->acc_d, P->nacc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&word, P->status_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(P->status_d, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     const double rr = h[P->nacc - 4], ff = h[P->nacc - 3];
     const double fn = std::sqrt(ff);
@@ -885,9 +918,31 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
       info[0] = std::sqrt(rr) / fn;
       for (int s = 1; s < sweeps + 2; ++s) info[s] = info[0];
     }
+    if (!verify) {  // in place: f is gone, no residual to report (the device checks still ran)
+      for (int s = 0; s < sweeps + 2; ++s) info[s] = std::nan("");
+      return word;
+    }
     if (P->singular && std::fabs(h[P->nacc - 2]) > 1e-10 * h[P->nacc - 1]) return CANS_ERR_INCOMPATIBLE;
     if (P->opts.prec == CANS_MIXED && info[sweeps] > P->opts.tol) return CANS_ERR_NOT_CONVERGED;
+    if (word != CANS_OK) return word;
   }
+  return CANS_OK;
+}
+
+int cans_plan_status(cans_plan_t P, int* status) {
+  if (!P || !status) return CANS_ERR_ARG;
+  *status = CANS_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CANS_ERR_CUDA;
+  if (dev != P->device && cudaSetDevice(P->device) != cudaSuccess) return CANS_ERR_CUDA;
+  int word = CANS_OK;
+  const int zero = CANS_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&word, P->status_d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(P->status_d, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (dev != P->device) cudaSetDevice(dev);
+  if (e != cudaSuccess) return CANS_ERR_CUDA;
+  *status = word;
   return CANS_OK;
 }
 

@@ -322,25 +322,41 @@ int box_step(const cans_plan_s* P, double* u, double* v, double* w, double* p, c
   do {                                               \
     if ((__VA_ARGS__) != cudaSuccess) return CANS_ERR_CUDA; \
   } while (0)
-  BOX_CK(cudaMemsetAsync(dti, 0, sizeof(unsigned long long), st));
-  if (!(prm->dt > 0)) box_chkdt_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, u, v, w, dti);
+  cans_plan_t PM = const_cast<cans_plan_t>(P);  // the profile records live in the plan
   double dl = std::min(P->len[0] / P->n[0], P->len[1] / P->n[1]);
   for (int k = 0; k < P->n[2]; ++k) dl = std::min(dl, P->dzf_h[k]);
-  box_dt_kernel<<<1, 32, 0, st>>>(dti, dt, prm->cfl, prm->nu, dl, prm->dt);
-  BOX_CK(cudaGetLastError());
+  {
+    PassTimer tm(PM, CANS_PASS_CHKDT, st);
+    BOX_CK(cudaMemsetAsync(dti, 0, sizeof(unsigned long long), st));
+    if (!(prm->dt > 0)) box_chkdt_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, u, v, w, dti);
+    box_dt_kernel<<<1, 32, 0, st>>>(dti, dt, prm->cfl, prm->nu, dl, prm->dt);
+    BOX_CK(cudaGetLastError());
+  }
   double lz = 0;
   for (int k = 0; k < P->n[2]; ++k) lz += P->dzf_h[k];
   for (int s = 0; s < 3; ++s) {
     const double a = ALPHA[s], b = BETA[s], gm = a + b;
-    box_momentum_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, gm, dt);
-    box_divergence_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, f, gm, dt);
+    {
+      PassTimer tm(PM, CANS_PASS_MOMENTUM, st);
+      box_momentum_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, gm, dt);
+    }
+    {
+      PassTimer tm(PM, CANS_PASS_DIVERGENCE, st);
+      box_divergence_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, f, gm, dt);
+    }
     BOX_CK(cudaGetLastError());
-    const int rc = cans_poisson_solve(const_cast<cans_plan_t>(P), f, phi, pws, st, nullptr);
+    const int rc = cans_poisson_solve(PM, f, phi, pws, st, nullptr);
     if (rc != CANS_OK) return rc;
     double* bulk = prm->forcing ? small + 1 : nullptr;
-    if (bulk) BOX_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
-    box_correct_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gm, dt, bulk);
-    if (bulk) box_forcing_kernel<<<G, 256, 0, st>>>(N, u, bulk, 1.0 / ((double)g.n[0] * g.n[1] * lz), prm->ubulk);
+    {
+      PassTimer tm(PM, CANS_PASS_CORRECT, st);
+      if (bulk) BOX_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
+      box_correct_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gm, dt, bulk);
+    }
+    if (bulk) {
+      PassTimer tm(PM, CANS_PASS_FORCING, st);
+      box_forcing_kernel<<<G, 256, 0, st>>>(N, u, bulk, 1.0 / ((double)g.n[0] * g.n[1] * lz), prm->ubulk);
+    }
     BOX_CK(cudaGetLastError());
   }
 #undef BOX_CK

@@ -1,6 +1,6 @@
-// Reporting kernels (only run when the caller asks for residual norms): ||f - (L_h + shift) p||^2
-// in FP64 (Eq. poi with a non-uniform z) and the dzf-weighted sum of f for the compatibility check of a
-// singular problem.
+// Reporting kernels: ||f - (L_h + shift) p||^2 in FP64 (Eq. poi with a non-uniform z) and the
+// dzf-weighted sum of f for the compatibility check of a singular problem (when the caller asks for
+// residual norms, or verifies every solve), and the status word's check at the end of every solve.
 #include <algorithm>
 
 #include "plan.cuh"
@@ -74,6 +74,30 @@ cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* a
   cudaError_t e = cudaMemsetAsync(acc2, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   weighted_sum_kernel<<<148 * 4, 256, 0, st>>>(f, P->n[0], P->n[1], P->n[2], P->dzf_d, acc2);
+  return cudaGetLastError();
+}
+
+SolveCheck solve_check_args(const cans_plan_s* P, bool compat, bool verify) {
+  SolveCheck c;
+  c.nacc = P->nacc;
+  c.sweeps = (P->opts.prec == CANS_MIXED) ? P->opts.max_sweeps : 0;
+  c.compat = compat ? 1 : 0;
+  c.verify = verify ? 1 : 0;
+  c.tol = P->opts.tol;
+  c.compat_scale = P->compat_scale;
+  // the mixed path's singular column comes out of float transforms
+  c.compat_tol = (P->opts.prec == CANS_MIXED) ? 1e-5 : 1e-9;
+  return c;
+}
+
+__global__ void solve_status_kernel(const double* __restrict__ acc, SolveCheck c, int* status) {
+  if (threadIdx.x != 0) return;
+  const int code = solve_check(acc, c);
+  if (code != CANS_OK) atomicCAS(status, CANS_OK, code);
+}
+
+cudaError_t launch_solve_status(const cans_plan_s* P, bool compat, bool verify, cudaStream_t st) {
+  solve_status_kernel<<<1, 32, 0, st>>>(P->acc_d, solve_check_args(P, compat, verify), P->status_d);
   return cudaGetLastError();
 }
 

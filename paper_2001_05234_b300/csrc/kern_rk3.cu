@@ -406,18 +406,34 @@ int cans_rk3_step(cans_plan_t P, double* u, double* v, double* w, double* p, con
   double* small = reinterpret_cast<double*>(base + 8 * fb);  // [0] dt, [1] bulk sum, [2] dti bits
   void* pws = base + 8 * fb + 256;
   double* dt = dt_dev ? dt_dev : small;
-  RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt, st));
+  {
+    PassTimer tm(P, CANS_PASS_CHKDT, st);
+    RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt,
+                       st));
+  }
   for (int s = 0; s < 3; ++s) {
     NvtxRange substage(s == 0 ? "rk3_substage_1" : (s == 1 ? "rk3_substage_2" : "rk3_substage_3"));
     const double a = RK_ALPHA[s], b = RK_BETA[s], g = a + b;
-    RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, g, dt, st));
-    RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
+    {
+      PassTimer tm(P, CANS_PASS_MOMENTUM, st);
+      RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, g, dt, st));
+    }
+    {
+      PassTimer tm(P, CANS_PASS_DIVERGENCE, st);
+      RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
+    }
     int rc = cans_poisson_solve(P, f, phi, pws, cuda_stream, nullptr);
     if (rc != CANS_OK) return rc;
     double* bulk = prm->forcing ? small + 1 : nullptr;
-    if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
-    RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st));
-    if (bulk) RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
+    {
+      PassTimer tm(P, CANS_PASS_CORRECT, st);
+      if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
+      RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st));
+    }
+    if (bulk) {
+      PassTimer tm(P, CANS_PASS_FORCING, st);
+      RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
+    }
   }
   return CANS_OK;
 }
@@ -472,25 +488,41 @@ int cans_rk3_step_implicit(cans_plan_t P, cans_plan_t U, cans_plan_t W, double* 
   double* small = reinterpret_cast<double*>(base + 10 * fb);  // [0] dt, [1] bulk sum, [2] dti bits
   void* pws = base + 10 * fb + 256;
   double* dt = dt_dev ? dt_dev : small;
-  RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt, st));
+  {
+    PassTimer tm(P, CANS_PASS_CHKDT, st);
+    RK_CK(launch_chkdt(P, u, v, w, reinterpret_cast<unsigned long long*>(small + 2), dt, prm->cfl, prm->nu, prm->dt,
+                       st));
+  }
   for (int s = 0; s < 3; ++s) {
     NvtxRange substage(s == 0 ? "rk3_implicit_substage_1" : (s == 1 ? "rk3_implicit_substage_2" : "rk3_implicit_substage_3"));
     const double a = RK_ALPHA[s], b = RK_BETA[s], g = a + b;
     const double h = g * prm->nu * prm->dt / 2, sigma = -1.0 / h;
-    RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, fu, fv, fw, prm->nu, a, b, g, dt, st, sigma));
+    {
+      PassTimer tm(P, CANS_PASS_MOMENTUM, st);
+      RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, fu, fv, fw, prm->nu, a, b, g, dt, st, sigma));
+    }
     int rc = cans_helmholtz_solve(U, fu, us, sigma, pws, cuda_stream, nullptr);
     if (rc == CANS_OK) rc = cans_helmholtz_solve(U, fv, vs, sigma, pws, cuda_stream, nullptr);
     if (rc == CANS_OK) rc = cans_helmholtz_solve(W, fw, ws, sigma, pws, cuda_stream, nullptr);
     if (rc != CANS_OK) return rc;
-    RK_CK(cudaMemsetAsync(ws + (size_t)P->n[0] * P->n[1] * (P->n[2] - 1), 0,
-                          sizeof(double) * P->n[0] * P->n[1], st));  // the top wall face
-    RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
+    {
+      PassTimer tm(P, CANS_PASS_DIVERGENCE, st);
+      RK_CK(cudaMemsetAsync(ws + (size_t)P->n[0] * P->n[1] * (P->n[2] - 1), 0,
+                            sizeof(double) * P->n[0] * P->n[1], st));  // the top wall face
+      RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));
+    }
     rc = cans_poisson_solve(P, f, phi, pws, cuda_stream, nullptr);
     if (rc != CANS_OK) return rc;
     double* bulk = prm->forcing ? small + 1 : nullptr;
-    if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
-    RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st, -h));
-    if (bulk) RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
+    {
+      PassTimer tm(P, CANS_PASS_CORRECT, st);
+      if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
+      RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st, -h));
+    }
+    if (bulk) {
+      PassTimer tm(P, CANS_PASS_FORCING, st);
+      RK_CK(launch_forcing(P, u, bulk, prm->ubulk, st));
+    }
   }
   return CANS_OK;
 }
@@ -516,9 +548,13 @@ static int project_impl(cans_plan_t P, double* u, double* v, double* w, void* wo
   double* f = reinterpret_cast<double*>(base);
   double* phi = reinterpret_cast<double*>(base + fb);
   void* pws = base + 2 * fb;
-  RK_CK(launch_divergence(P, u, v, w, f, 1.0, nullptr, 1.0, adjoint, st));
+  {
+    PassTimer tm(P, CANS_PASS_DIVERGENCE, st);
+    RK_CK(launch_divergence(P, u, v, w, f, 1.0, nullptr, 1.0, adjoint, st));
+  }
   int rc = cans_poisson_solve(P, f, phi, pws, cuda_stream, nullptr);
   if (rc != CANS_OK) return rc;
+  PassTimer tm(P, CANS_PASS_CORRECT, st);
   RK_CK(launch_correct(P, u, v, w, phi, u, v, w, nullptr, 1.0, nullptr, adjoint, nullptr, st));
   return CANS_OK;
 }

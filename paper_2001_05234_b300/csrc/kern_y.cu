@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(512, 2) zspec_kernel(T* __restrict__ w, int nx
                                                        LineTab<T> tb, const T* __restrict__ mux,
                                                        const T* __restrict__ muy, const T* __restrict__ muz,
                                                        int singular, const double* gauge, double gauge_scale,
-                                                       T shift, WLay wl) {
+                                                       T shift, WLay wl, double* compat, double cw) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(512, 2) zspec_kernel(T* __restrict__ w, int nx
     const int i = i0 + l;
     if (i >= nx) continue;
     T v = bufT[L.r(s, l)];
-    if (singular && i == 0 && j == 0 && s == 0)
+    if (singular && i == 0 && j == 0 && s == 0) {
+      if (compat != nullptr) *compat = cw * (double)v;  // uniform z: sum_k dz d_k = dz * slot 0
       v = (gauge != nullptr) ? (T)(gauge_scale * (*gauge) * NZ) : (T)0;
+    }
     else
       v = v / (mux[i] + my + muz[s]);
     bufT[L.r(s, l)] = v;
@@ -235,7 +237,7 @@ template <> const LineTab<double>& tab_z<double>(const cans_plan_s* P) { return 
 template <> const LineTab<float>& tab_z<float>(const cans_plan_s* P) { return P->tz_f; }
 
 template <typename T, int MC>
-static cudaError_t zspec_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+static cudaError_t zspec_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, double* compat) {
   const Launch& L = P->zs_l[sizeof(T) == 8 ? 0 : 1];
   cudaError_t e = set_smem((const void*)zspec_kernel<T, MC>, L.smem);
   if (e != cudaSuccess) return e;
@@ -245,23 +247,24 @@ static cudaError_t zspec_m(const cans_plan_s* P, T* w, const double* gauge, cuda
   const T* muz = sizeof(T) == 8 ? (const T*)P->muz_d : (const T*)P->muz_f;
   zspec_kernel<T, MC><<<grid, L.threads, L.smem, st>>>(w, P->n[0], P->n[1], P->n[2], L.lognl, tab_z<T>(P), mux, muy,
                                                        muz, P->singular ? 1 : 0, gauge, P->gauge_scale,
-                                                       (T)P->shift, wlay(P, sizeof(T) == 4));
+                                                       (T)P->shift, wlay(P, sizeof(T) == 4), compat,
+                                                       P->dzf_h.empty() ? 0.0 : P->dzf_h[0]);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st) {
+cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, double* compat) {
   switch (P->dz.m) {
 #define CASE_M(MM) \
-  case MM: return zspec_m<T, MM>(P, w, gauge, st);
+  case MM: return zspec_m<T, MM>(P, w, gauge, st, compat);
     CANS_FOR_EACH_M(CASE_M)
 #undef CASE_M
-    default: return zspec_m<T, 0>(P, w, gauge, st);
+    default: return zspec_m<T, 0>(P, w, gauge, st, compat);
   }
 }
 
-template cudaError_t launch_zspec<double>(const cans_plan_s*, double*, const double*, cudaStream_t);
-template cudaError_t launch_zspec<float>(const cans_plan_s*, float*, const double*, cudaStream_t);
+template cudaError_t launch_zspec<double>(const cans_plan_s*, double*, const double*, cudaStream_t, double*);
+template cudaError_t launch_zspec<float>(const cans_plan_s*, float*, const double*, cudaStream_t, double*);
 
 template cudaError_t launch_y<double, 1>(const cans_plan_s*, double*, cudaStream_t);
 template cudaError_t launch_y<double, -1>(const cans_plan_s*, double*, cudaStream_t);

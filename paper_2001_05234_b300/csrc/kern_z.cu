@@ -3,7 +3,10 @@
 //   zpass_f64_kernel : double columns -- every column of the FP64 path, or the marked low-|mu|
 //                      columns of the mixed path (including the singular (0,0) mode), over the
 //                      bounding box of the marked columns only.
+#include <mutex>
+
 #include "plan.cuh"
+#include "tma.cuh"
 
 namespace cans {
 
@@ -86,14 +89,51 @@ __device__ __forceinline__ void tile_store(const T* tile, T* col0, size_t plane,
   }
 }
 
-// PAIR: x periodic, so x-slots 2q and 2q+1 (q >= 1) share their eigenvalue; a warp solves such a pair
-// with one factorisation (zsolve_pair) unless the plan marks one of the two as a double column.
+// The float columns of one staged tile (x-slots i0 .. i0+ncols-1 of y-slot j), one warp per column
+// or column pair.  PAIR: x periodic, so x-slots 2q and 2q+1 (q >= 1) share their eigenvalue; a warp
+// solves such a pair with one factorisation (zsolve_pair) unless the plan marks one of the two as a
+// double column.  Columns the plan marks are left for the double kernel.
+template <int MMAX, bool PAIR, typename ZS>
+__device__ __forceinline__ void solve_tile_f32(float* tile, const ZS& Z, const ZArgs& a, int i0, int j, int ncols,
+                                               const float* sa, const float* sb, const float* sc) {
+  constexpr bool CL = MMAX >= 4;  // lane-contiguous coefficient rows, four per 16-byte load
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float muy = a.muy_f[j] + (float)a.shift;
+  auto single = [&](int cidx) {
+    const int i = i0 + cidx;
+    if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) return;
+    if (a.nz == 32 * MMAX)
+      zsolve_column<MMAX, float, float, false, ZS, true, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc,
+                                                             nullptr, 0.f);
+    else
+      zsolve_column<MMAX, float, float, false, ZS, false, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc,
+                                                              nullptr, 0.f);
+  };
+  if constexpr (PAIR) {  // i0 and ncols are even (checked at launch)
+    for (int q = warp; 2 * q < ncols; q += nwarps) {
+      const int c0 = 2 * q, i = i0 + c0;
+      const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
+      const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
+      if (i == 0 || m0 || m1) {  // slots 0 and 1 (X_0, X_M) differ; a marked column goes to the double kernel
+        single(c0);
+        single(c0 + 1);
+      } else if (a.nz == 32 * MMAX) {
+        zsolve_pair<MMAX, float, float, ZS, true, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+      } else {
+        zsolve_pair<MMAX, float, float, ZS, false, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
+      }
+    }
+  } else {
+    for (int cidx = warp; cidx < ncols; cidx += nwarps) single(cidx);
+  }
+}
+
 template <int MMAX, int TIC, bool PAIR>
 __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf,
                                                                       int vec, WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
-  constexpr bool CL = MMAX >= 4;  // lane-contiguous coefficient rows, four per 16-byte load
+  constexpr bool CL = MMAX >= 4;
   const int rs = CL ? 32 * (m + 4) : 32 * m;
   float* sa = reinterpret_cast<float*>(smem_raw);
   float* sb = sa + rs;
@@ -107,38 +147,91 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   stage_zrows<CL>(sa, sb, sc, zf, a.nz, m);
   tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const float muy = a.muy_f[j] + (float)a.shift;
-  auto single = [&](int cidx) {
-    const int i = i0 + cidx;
-    if (a.mask != nullptr && a.mask[(size_t)j * a.nx + i]) return;
-    if (a.nz == 32 * MMAX)
-      zsolve_column<MMAX, float, float, false, decltype(Z), true, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
-                                                                      sc, nullptr, 0.f);
-    else
-      zsolve_column<MMAX, float, float, false, decltype(Z), false, CL>(tile, cidx, Z, a.nz, a.mux_f[i] + muy, sa, sb,
-                                                                       sc, nullptr, 0.f);
-  };
-  if constexpr (PAIR) {  // i0 and ncols are even (checked at launch)
-    for (int q = warp; 2 * q < ncols; q += nwarps) {
-      const int c0 = 2 * q, i = i0 + c0;
-      const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
-      const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
-      if (i == 0 || m0 || m1) {  // slots 0 and 1 (X_0, X_M) differ; a marked column goes to the double kernel
-        single(c0);
-        single(c0 + 1);
-      } else if (a.nz == 32 * MMAX) {
-        zsolve_pair<MMAX, float, float, decltype(Z), true, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb, sc);
-      } else {
-        zsolve_pair<MMAX, float, float, decltype(Z), false, CL>(tile, c0, c0 + 1, Z, a.nz, a.mux_f[i] + muy, sa, sb,
-                                                                 sc);
-      }
-    }
-  } else {
-    for (int cidx = warp; cidx < ncols; cidx += nwarps) single(cidx);
-  }
+  solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, ncols, sa, sb, sc);
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
+}
+
+// The float z pass fed by TMA, for full columns (Nz = 32 MMAX, MMAX >= 4) of a natural-layout work
+// field with Nx a multiple of 16.  Persistent CTAs (three per SM) walk tiles of 16 x-slots x Nz rows
+// of one y-slot, t = blockIdx.x, blockIdx.x + gridDim.x, ...  While the warps solve tile t, one
+// thread's tensor copy of tile t + gridDim.x lands in a raw staging buffer (its own mbarrier, bytes
+// counted), so each CTA always has its next 32 KB in flight; after the wait, the CTA moves the
+// staged rows into the bank-swizzled solve tile (ZSwz16), hands the staging buffer back to the copy
+// engine, solves, and stores the tile with 16-byte writes.  A copy that never lands (a bounded wait
+// running out) records CANS_ERR_TIMEOUT in the plan's status word and ends the CTA.
+template <int MMAX, bool PAIR>
+__global__ void __launch_bounds__(256, 3) zpass_tma_kernel(const __grid_constant__ CUtensorMap tm,
+                                                           float* __restrict__ w, ZArgs a, ZTab<float> zf, int ntx,
+                                                           int ntiles, unsigned wait_limit) {
+  constexpr int TI = 16, NZ = 32 * MMAX, BOXZ = NZ < 256 ? NZ : 256, NBOX = NZ / BOXZ;
+  constexpr uint32_t TILE_BYTES = TI * NZ * 4;
+  constexpr int LS = MMAX + 4;
+  static_assert(MMAX >= 4 && NZ % BOXZ == 0, "full columns of 128, 256 or 512 rows");
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 128 bytes by hand below
+  unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  float* stage = reinterpret_cast<float*>(base);
+  float* tile = reinterpret_cast<float*>(base + TILE_BYTES);
+  float* sa = tile + TI * NZ;
+  float* sb = sa + 32 * LS;
+  float* sc = sb + 32 * LS;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + 32 * LS);
+  const int tid = threadIdx.x;
+  if (tid == 0) mbar_init(bar, 1);
+  stage_zrows<true>(sa, sb, sc, zf, NZ, MMAX);
+  __syncthreads();
+  const ZSwz16<MMAX> Z;
+  auto issue = [&](int t) {
+    const int tx = t % ntx, j = t / ntx;
+    mbar_arrive_expect_tx(bar, TILE_BYTES);
+#pragma unroll
+    for (int b = 0; b < NBOX; ++b) tma_load_3d(stage + b * BOXZ * TI, &tm, tx * TI, j, b * BOXZ, bar);
+  };
+  int t = blockIdx.x;
+  if (tid == 0 && t < ntiles) issue(t);
+  const size_t plane = (size_t)a.nx * a.ny;
+  uint32_t parity = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int tx = t % ntx, j = t / ntx, i0 = tx * TI;
+    const bool landed = mbar_wait_bounded(bar, parity, wait_limit);
+    if (__syncthreads_or(!landed)) {
+      if (tid == 0) {
+        atomicCAS(a.status, CANS_OK, CANS_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, parity, wait_limit);  // give the copy in flight a last chance to land
+      }
+      return;
+    }
+    parity ^= 1u;
+    const float4* src = reinterpret_cast<const float4*>(stage);
+#pragma unroll 4
+    for (int e = tid; e < NZ * TI / 4; e += 256) {
+      const int k = e >> 2, q = (e & 3) << 2;
+      const float4 v = src[e];
+      tile[Z.at(k, q)] = v.x;
+      tile[Z.at(k, q + 1)] = v.y;
+      tile[Z.at(k, q + 2)] = v.z;
+      tile[Z.at(k, q + 3)] = v.w;
+    }
+    __syncthreads();
+    if (tid == 0 && t + (int)gridDim.x < ntiles) {
+      fence_async_smem();  // the staging reads above come before the next copy's writes
+      issue(t + gridDim.x);
+    }
+    solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, TI, sa, sb, sc);
+    __syncthreads();
+    float* col0 = w + (size_t)j * a.nx + i0;
+#pragma unroll 4
+    for (int e = tid; e < NZ * TI / 4; e += 256) {
+      const int k = e >> 2, q = (e & 3) << 2;
+      float4 v;
+      v.x = tile[Z.at(k, q)];
+      v.y = tile[Z.at(k, q + 1)];
+      v.z = tile[Z.at(k, q + 2)];
+      v.w = tile[Z.at(k, q + 3)];
+      *reinterpret_cast<float4*>(col0 + (size_t)k * plane + q) = v;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename T, int MMAX, int TIC>
@@ -172,7 +265,7 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
     const double mu = a.mux_d[i] + muy;
     if (a.singular && i == 0 && j == 0) {
       const double target = (a.gauge != nullptr) ? a.gauge_scale * (*a.gauge) : 0.0;
-      zsolve_column<MMAX, double, T, true>(tile, cidx, Z, a.nz, mu, sa, sb, sc, a.dzf, target);
+      zsolve_column<MMAX, double, T, true>(tile, cidx, Z, a.nz, mu, sa, sb, sc, a.dzf, target, a.compat);
     } else {
       zsolve_column<MMAX, double, T, false>(tile, cidx, Z, a.nz, mu, sa, sb, sc, nullptr, 0.0);
     }
@@ -195,8 +288,10 @@ __global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZA
   tile_store<T>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
 
-static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
+static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge, double* compat) {
   ZArgs a;
+  a.compat = compat;
+  a.status = P->status_d;
   a.nx = P->n[0];
   a.ny = P->n[1];
   a.nz = P->n[2];
@@ -220,16 +315,102 @@ static ZArgs zargs(const cans_plan_s* P, int ti, const double* gauge) {
   return a;
 }
 
+// ---- TMA-fed float z pass: host side ----------------------------------------------------------
+// The tensor-map encoder is a driver function; the runtime hands out its address, so the library
+// needs no link against the driver library.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  });
+  return fn;
+}
+
+// Shapes the TMA kernel takes: float natural-layout work field, Nx a multiple of 16 (16-slot tiles,
+// 64-byte box rows), full columns of 128, 256 or 512 rows, a 16-byte aligned field.
+bool ztma_feasible(const cans_plan_s* P, const void* w) {
+  return !P->wblk && P->n[0] % 16 == 0 && P->z_mmax >= 4 && P->n[2] == 32 * P->z_mmax &&
+         (reinterpret_cast<uintptr_t>(w) & 15) == 0 && encode_tiled() != nullptr;
+}
+
+constexpr unsigned kTmaWaitLimit = 1u << 20;  // polls of one copy's barrier (~0.3 s) before a timeout
+
+template <int MMAX>
+static cudaError_t ztma_m(const cans_plan_s* P, float* w, cudaStream_t st) {
+  constexpr int TI = 16, NZ = 32 * MMAX;
+  const int nx = P->n[0], ny = P->n[1];
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NZ};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {TI, 1, (cuuint32_t)(NZ < 256 ? NZ : 256)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, w, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  ZArgs a = zargs(P, TI, nullptr, nullptr);
+  a.mask = P->mask_d;
+  const bool pair = P->bc[0] == BC_P;  // Nx is even: every 16-slot tile holds whole Re / Im pairs
+  auto kern = pair ? zpass_tma_kernel<MMAX, true> : zpass_tma_kernel<MMAX, false>;
+  const size_t smem = 2 * (size_t)TI * NZ * 4 + 3 * 32 * (MMAX + 4) * 4 + 16 + 128;
+  cudaError_t e = set_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
+  // persistent grid: every resident CTA slot of the device (cached per device and kernel)
+  static std::mutex lock;
+  static int cached[16][2] = {};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  {
+    std::lock_guard<std::mutex> g(lock);
+    int& c = cached[dev & 15][pair ? 1 : 0];
+    if (c == 0) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, 256, smem)) != cudaSuccess) return e;
+      c = c < 1 ? 1 : c;
+    }
+    per_sm = c;
+  }
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int ntx = nx / TI, ntiles = ntx * ny;
+  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
+  kern<<<grid, 256, smem, st>>>(tm, w, a, P->zt_f, ntx, ntiles, kTmaWaitLimit);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_ztma(const cans_plan_s* P, float* w, cudaStream_t st) {
+  switch (P->z_mmax) {
+    case 4: return ztma_m<4>(P, w, st);
+    case 8: return ztma_m<8>(P, w, st);
+    default: return ztma_m<16>(P, w, st);
+  }
+}
+
 // part: -1 both kernels, 0 the float columns only, 1 the marked double columns only (mixed path)
 template <typename T, int MMAX, int TIC>
-static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
+static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part,
+                        double* compat) {
   const WLay wl = wlay(P, sizeof(T) == 4);
   const int vec = ((wl.blk || P->n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(w) & 15) == 0) ? 1 : 0;
   if (sizeof(T) == 4) {
     // float columns first, then the double columns of the marked bounding box
     cudaError_t e = cudaSuccess;
-    if (part != 1) {
-      ZArgs a = zargs(P, P->z_ti[1], gauge);
+    if (part != 1 && MMAX >= 4 && P->z_tma && ztma_feasible(P, w)) {
+      e = launch_ztma(P, reinterpret_cast<float*>(w), st);
+      if (e != cudaSuccess || part == 0) return e;
+    } else if (part != 1 && P->z_tma == 2) {
+      return cudaErrorNotSupported;  // the TMA kernel was required and cannot take this shape
+    } else if (part != 1) {
+      ZArgs a = zargs(P, P->z_ti[1], gauge, nullptr);
       a.mask = P->mask_d;
       const size_t smem = 3 * 32 * (a.m + 4) * sizeof(float) + P->z_smem[1];
       dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
@@ -242,7 +423,7 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
       e = cudaGetLastError();
       if (e != cudaSuccess || part == 0) return e;
     }
-    ZArgs b = zargs(P, P->z_ti[1], gauge);
+    ZArgs b = zargs(P, P->z_ti[1], gauge, compat);
     b.mask = P->mask_d;
     const size_t smem64 = 3 * 32 * b.m * sizeof(double) + P->z_smem[1];
     e = set_smem((const void*)zpass_f64_kernel<T, MMAX, TIC>, smem64);
@@ -251,7 +432,7 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
     if (grid64.x > 0 && grid64.y > 0) zpass_f64_kernel<T, MMAX, TIC><<<grid64, 256, smem64, st>>>(w, b, P->zt_d, vec, wl);
     return cudaGetLastError();
   }
-  ZArgs a = zargs(P, P->z_ti[0], gauge);
+  ZArgs a = zargs(P, P->z_ti[0], gauge, compat);
   const size_t smem = 3 * 32 * a.m * sizeof(double) + P->z_smem[0];
   cudaError_t e = set_smem((const void*)zpass_f64_kernel<T, MMAX, TIC>, smem);
   if (e != cudaSuccess) return e;
@@ -262,28 +443,28 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
 
 // compile-time tile widths for the common shapes (the z tile is TI x-slots wide, a power of two)
 template <typename T, int MMAX>
-static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
+static cudaError_t z_m(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part, double* compat) {
   switch (P->z_ti[sizeof(T) == 4 ? 1 : 0]) {
-    case 32: return z_mt<T, MMAX, 32>(P, w, gauge, st, part);
-    case 16: return z_mt<T, MMAX, 16>(P, w, gauge, st, part);
-    case 8: return z_mt<T, MMAX, 8>(P, w, gauge, st, part);
-    default: return z_mt<T, MMAX, 0>(P, w, gauge, st, part);
+    case 32: return z_mt<T, MMAX, 32>(P, w, gauge, st, part, compat);
+    case 16: return z_mt<T, MMAX, 16>(P, w, gauge, st, part, compat);
+    case 8: return z_mt<T, MMAX, 8>(P, w, gauge, st, part, compat);
+    default: return z_mt<T, MMAX, 0>(P, w, gauge, st, part, compat);
   }
 }
 
 template <typename T>
-cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part) {
-  if (P->bc[2] == BC_P) return (part == 1) ? cudaSuccess : launch_zspec<T>(P, w, gauge, st);
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part, double* compat) {
+  if (P->bc[2] == BC_P) return (part == 1) ? cudaSuccess : launch_zspec<T>(P, w, gauge, st, compat);
   switch (P->z_mmax) {
-    case 1: return z_m<T, 1>(P, w, gauge, st, part);
-    case 2: return z_m<T, 2>(P, w, gauge, st, part);
-    case 4: return z_m<T, 4>(P, w, gauge, st, part);
-    case 8: return z_m<T, 8>(P, w, gauge, st, part);
-    default: return z_m<T, 16>(P, w, gauge, st, part);
+    case 1: return z_m<T, 1>(P, w, gauge, st, part, compat);
+    case 2: return z_m<T, 2>(P, w, gauge, st, part, compat);
+    case 4: return z_m<T, 4>(P, w, gauge, st, part, compat);
+    case 8: return z_m<T, 8>(P, w, gauge, st, part, compat);
+    default: return z_m<T, 16>(P, w, gauge, st, part, compat);
   }
 }
 
-template cudaError_t launch_z<double>(const cans_plan_s*, double*, const double*, cudaStream_t, int);
-template cudaError_t launch_z<float>(const cans_plan_s*, float*, const double*, cudaStream_t, int);
+template cudaError_t launch_z<double>(const cans_plan_s*, double*, const double*, cudaStream_t, int, double*);
+template cudaError_t launch_z<float>(const cans_plan_s*, float*, const double*, cudaStream_t, int, double*);
 
 }  // namespace cans

@@ -8,10 +8,14 @@
 // from a fixed array that lives in the library itself.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the library holds it, at the
-// size below, until the process exits.  In host code its name is only a host-side stand-in, so the
-// device address is looked up with cudaGetSymbolAddress, once per device, with that device current,
-// on the first call made on it.  Every call shares the one array: calls that overlap on the GPU (two
-// streams, two threads) race on it and must be serialised by the caller.
+// size below, until the process exits.  Under CUDA's lazy module loading (the default) the memory is
+// committed when the first call on a device loads this part of the library, so a caller whose pool
+// will take the device's memory makes that first call before the pool does (and before any stream
+// capture).  In host code the array's name is only a host-side stand-in, so the device address is
+// looked up with cudaGetSymbolAddress, with that device current, on the first call made on it, and
+// kept; later calls check the kept address with cudaPointerGetAttributes (a host-side query) and look
+// it up again if the device was reset in between.  Every call shares the one array: calls that
+// overlap on the GPU (two streams, two threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,11 +33,21 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_lock;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_scratch on the current device (looked up on first use); nullptr on failure.
+// Device address of g_scratch on the current device (looked up on first use, and again when the kept
+// address no longer belongs to this device's live context, e.g. after cudaDeviceReset); nullptr on
+// failure.
 void* scratch_address() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> guard(g_lock);
+  if (g_scratch_ptr[dev] != nullptr) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, g_scratch_ptr[dev]) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+        attr.device != dev) {
+      cudaGetLastError();  // the failed query leaves no sticky error behind
+      g_scratch_ptr[dev] = nullptr;
+    }
+  }
   if (g_scratch_ptr[dev] == nullptr) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess) return nullptr;

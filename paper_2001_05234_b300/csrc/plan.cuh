@@ -69,6 +69,8 @@ struct ZArgs {
   double gauge_scale;
   int j_end, i_end;     // FP64-column kernel: bounding box of the columns it owns
   int xpairs;           // x periodic, even widths: column pairs of equal shift
+  double* compat;       // optional: sum_k dzf_k d_k of the singular column (before its projection)
+  int* status;          // plan status word (bounded waits record CANS_ERR_TIMEOUT here)
 };
 
 }  // namespace cans
@@ -105,11 +107,16 @@ struct cans_plan_s {
   const float *mux_f, *muy_f, *sa_hi, *sa_lo, *sc_hi, *sc_lo;
   const unsigned char* mask_d = nullptr;
   int mask_i_end = 0, mask_j_end = 0;  // bounding box of the double-precision columns (mixed)
-  double* acc_d = nullptr;             // [0] |f|^2, [1+s] |r_s|^2, [nacc-5] gauge sum, [nacc-4..] reports
+  double* acc_d = nullptr;             // [0] |f|^2, [1+s] |r_s|^2, [nacc-7] compatibility sum,
+                                       // [nacc-5] gauge sum, [nacc-4..] reports
   int nacc = 0;
+  int* status_d = nullptr;             // device status word (cans_plan_status)
+  double compat_scale = 0;             // sqrt(Nx Ny sum_k dzf_k^2): |sum w f| <= compat_scale ||f||_2
   double idx2, idy2;
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
+  int z_tma = 1;  // float z pass: 1 the TMA-fed persistent kernel where the shape allows it, 0 never,
+                  // 2 required (shapes it cannot take fail)
   size_t z_smem[2];
   int wblk = 0;  // mixed path: work field in the blocked layout
   // per-pass event records (cans_plan_profile)
@@ -120,6 +127,33 @@ struct cans_plan_s {
 };
 
 namespace cans {
+
+// The checks of a finished solve, from the norms it accumulated on the device (acc, laid out as the
+// plan's acc_d): CANS_ERR_INCOMPATIBLE when the singular column's removed weighted sum exceeds
+// compat_tol * compat_scale * ||f||_2; CANS_ERR_NOT_CONVERGED when a norm is not finite, when a
+// refinement sweep (from the second on) reduced a residual still above tol by less than half, or
+// (verify) when the final relative residual acc[nacc-4] / acc[nacc-3] exceeds tol^2; else CANS_OK.
+struct SolveCheck {
+  int nacc, sweeps;   // sweeps: refinement sweeps whose residual norms acc[1 .. sweeps] hold
+  int compat, verify; // compat: acc[nacc-7] holds the singular column's weighted sum
+  double tol, compat_scale, compat_tol;
+};
+
+__device__ __forceinline__ int solve_check(const double* acc, const SolveCheck& c) {
+  const double ff = acc[0];
+  if (c.compat && !(fabs(acc[c.nacc - 7]) <= c.compat_tol * c.compat_scale * sqrt(ff))) return CANS_ERR_INCOMPATIBLE;
+  if (!isfinite(ff)) return CANS_ERR_NOT_CONVERGED;
+  for (int s = 0; s < c.sweeps; ++s) {
+    const double r2 = acc[1 + s];
+    if (!isfinite(r2)) return CANS_ERR_NOT_CONVERGED;
+    if (s >= 1 && r2 > c.tol * c.tol * ff && r2 > 0.25 * acc[s]) return CANS_ERR_NOT_CONVERGED;
+  }
+  if (c.verify) {
+    const double rr = acc[c.nacc - 4], f2 = acc[c.nacc - 3];
+    if (!(rr <= c.tol * c.tol * f2)) return CANS_ERR_NOT_CONVERGED;
+  }
+  return CANS_OK;
+}
 
 // layout of the working field of this plan and precision (the FP64 path works in p: natural)
 inline WLay wlay(const cans_plan_s* P, bool working_float) {
@@ -141,10 +175,20 @@ cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Ph
 template <typename T, int DIR>
 cudaError_t launch_y(const cans_plan_s* P, T* w, cudaStream_t st);
 // part: -1 the whole z pass; in the mixed path 0 = the float columns, 1 = the marked double columns
+// compat (optional): receives sum_k dzf_k d_k of the singular column before its projection
 template <typename T>
-cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part = -1);
+cudaError_t launch_z(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, int part = -1,
+                     double* compat = nullptr);
+// the TMA-fed float z kernel takes this plan's shape and this work field (kern_z.cu)
+bool ztma_feasible(const cans_plan_s* P, const void* w);
 template <typename T>
-cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st);
+cudaError_t launch_zspec(const cans_plan_s* P, T* w, const double* gauge, cudaStream_t st, double* compat = nullptr);
+// Fold the checks of a finished solve into the plan's status word (cans_plan_status): one 32-thread
+// kernel on the solve's stream; the first error recorded stays until the word is read.  compat: the
+// singular column's weighted sum is in acc[nacc-7]; verify: acc[nacc-4], acc[nacc-3] hold ||r||^2,
+// ||f||^2 of the result.
+cudaError_t launch_solve_status(const cans_plan_s* P, bool compat, bool verify, cudaStream_t st);
+SolveCheck solve_check_args(const cans_plan_s* P, bool compat, bool verify);
 cudaError_t launch_residual_norms(const cans_plan_s* P, const double* f, const double* p, double* acc2, cudaStream_t st);
 cudaError_t launch_weighted_sum(const cans_plan_s* P, const double* f, double* acc2, cudaStream_t st);
 cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double* v, const double* w, const double* p,
@@ -183,6 +227,18 @@ cudaError_t launch_y_cols(const cans_plan_s* P, float* w, cudaStream_t st, bool*
 template <int MODE>
 cudaError_t launch_xinv_warp(const cans_plan_s* P, const float* src, double* p, float* Phi, float* Plo, double scale,
                              double* gauge, cudaStream_t st, bool* handled);
+
+// NVTX range and, while cans_plan_profile is on, a CUDA event pair on `st` around the launches made
+// during its lifetime, recorded as pass kind `kind` (a cans_pass).
+struct PassTimer {
+  cans_plan_s* P;
+  cudaStream_t st;
+  int rec = -1;
+  PassTimer(cans_plan_s* P, int kind, cudaStream_t st);
+  ~PassTimer();
+  PassTimer(const PassTimer&) = delete;
+  PassTimer& operator=(const PassTimer&) = delete;
+};
 
 // Opt a kernel into more than 48 KB of dynamic shared memory.  The attribute is set once per kernel
 // and size (remembered per device), so later launches -- including those inside a stream capture --

@@ -23,7 +23,8 @@ struct ZTab {
 };
 
 // Reciprocal: approximate (one MUFU op, ~1 ulp) for float columns -- the mixed path corrects the
-// float solve by refinement anyway -- and IEEE division for double columns.
+// float solve by refinement anyway.  Double columns (below) take the approximate reciprocal refined
+// by two Newton steps: within about 1 ulp, not correctly rounded.
 __device__ __forceinline__ float rcp_(float x) {
   float r;
   asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -60,6 +61,20 @@ struct ZSwz {
   __device__ __forceinline__ int at(int k, int i) const { return at(k, i, seg(k)); }
   static __host__ __device__ constexpr int ilog2_c(int x) { return x <= 1 ? 0 : 1 + ilog2_c(x / 2); }
 };
+// 16-wide tiles (the TMA-fed z pass): rows k and k+1 (k even) share one 32-word line, so the XOR
+// pattern spans all 32 banks -- a dense 16-word row alone could reach only 16.  Lanes reading one
+// column (rows lane*M + r) and the row-major copy phases (8 rows x 4 vectors per warp) both hit 32
+// distinct banks for M = 4, 8, 16 (checked by enumeration).
+template <int M_>
+struct ZSwz16 {
+  static constexpr int SH = M_ >= 16 ? 4 : (M_ >= 8 ? 3 : (M_ >= 4 ? 2 : (M_ >= 2 ? 1 : 0)));
+  __device__ __forceinline__ int ti() const { return 16; }
+  __device__ __forceinline__ int at(int k, int i, int sg) const {
+    return ((k >> 1) << 5) + ((((k & 1) << 4) | i) ^ ((sg ^ ((k >> 1) & 3)) & 31));
+  }
+  __device__ __forceinline__ int at(int k, int i) const { return at(k, i, k >> SH); }
+};
+
 template <int TI_ = 0, int M_ = 0>
 __device__ __forceinline__ ZSwz<TI_, M_> make_zswz(int TI, int m) {
   ZSwz<TI_, M_> s;
@@ -96,10 +111,12 @@ __device__ __forceinline__ float f4_get(const float4& v, int i) {
 // caller guarantees Nz = 32 MMAX (no identity rows), which removes every row-validity test.
 // mu is the x-y eigenvalue term of the mode.  SING: the singular Neumann mode -- the right-hand side
 // is first projected on the compatible subspace (sum_k dzf_k d_k = 0), the last row is replaced by
-// x = 0, and the result is shifted to the dzf-weighted mean `target`.
+// x = 0, and the result is shifted to the dzf-weighted mean `target`; the removed part
+// sum_k dzf_k d_k goes to *compat when compat is not NULL (the compatibility check of the status word).
 template <int MMAX, typename C, typename T, bool SING, typename ZS, bool FULL = false, bool CL = false>
 __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int Nz, C mu, const C* sa,
-                                              const C* sb, const C* sc, const double* weights, C target) {
+                                              const C* sb, const C* sc, const double* weights, C target,
+                                              double* compat = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr int m = MMAX;  // rows per lane (compile time: keeps the row arrays in registers)
   static_assert(!CL || (MMAX >= 4 && sizeof(C) == 4), "lane-contiguous rows: float, four rows per load");
@@ -140,6 +157,7 @@ __device__ __forceinline__ void zsolve_column(T* tile, int col, const ZS& Z, int
       swd += __shfl_xor_sync(full, swd, o);
     }
     proj = swd / sw;
+    if (compat != nullptr && lane == 0) *compat = (double)swd;
   }
   C cp[MMAX], dp[MMAX], lp[MMAX];
   C rr = 0;

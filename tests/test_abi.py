@@ -51,6 +51,15 @@ def test_status_strings(cans):
 def test_opts_defaults(cans):
     o = cans.cans_opts_default()
     assert o.prec == cans.CANS_FP64 and o.max_sweeps == 2 and o.tol == 1e-12 and abs(o.fp64_mode_fraction - 0.01) < 1e-15
+    assert o.verify == 0
+
+
+def test_plan_status_rejects_null_arguments(cans):
+    import ctypes
+
+    word = ctypes.c_int(5)
+    assert cans.lib().cans_plan_status(None, ctypes.byref(word)) == cans.CANS_ERR_ARG
+    assert cans.lib().cans_plan_status(None, None) == cans.CANS_ERR_ARG
 
 
 @pytest.mark.parametrize(

@@ -410,4 +410,5 @@ def test_autotuned_plan_matches_oracle(cans, tmp_path, monkeypatch):
         assert rel(host(pt), ref) <= (1e-12 if prec == 0 else 1e-11)
         cans.cans_plan_destroy(h)
     lines = cache.read_text().strip().splitlines()
-    assert len(lines) == 2 and all(len(l.split()) == 5 for l in lines)
+    # key, then lines per CTA of x and y, of the spectral z pass, the z tile width, the TMA z kernel flag
+    assert len(lines) == 2 and all(len(l.split()) == 6 for l in lines)

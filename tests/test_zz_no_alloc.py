@@ -3,7 +3,8 @@
 Collected last on purpose: if it fails, a run that stops at the first failure has already run every
 other test.  It compares cans_poisson_solve_noalloc, which takes its workspace from the library's
 fixed scratch array, with cans_poisson_solve given a caller-allocated workspace, on two calls in a
-row, and checks that a problem larger than the scratch array is refused.
+row (with a solve of another problem through the same scratch between them), and checks that a
+problem larger than the scratch array is refused.
 """
 import numpy as np
 import pytest
@@ -38,12 +39,22 @@ def test_noalloc_solve_matches_workspace_solve(prec):
     s = int(torch.cuda.current_stream().cuda_stream)
     ref = torch.empty_like(f)
     assert C.cans_poisson_solve(h, f.data_ptr(), ref.data_ptr(), wp, s, None) == 0
-    for _ in range(2):  # two calls in a row share the scratch array
+    # a problem of another shape and boundary conditions, solved through the same scratch between the
+    # compared calls, leaves different stale data in it: a solve that read a scratch word before
+    # writing it would no longer match
+    other = I.case_channel(n=(96, 64, 40))
+    g = torch.from_numpy(I.rhs_host(other)).cuda()
+    q = torch.empty_like(g)
+    h2 = _plan(C, other, 1)
+    for call in range(2):  # two calls in a row share the scratch array
         out = torch.full_like(f, float("nan"))
         assert C.cans_poisson_solve_noalloc(h, f.data_ptr(), out.data_ptr(), s, None) == 0
         torch.cuda.synchronize()
         err = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
         assert err <= 1e-12, err
+        if call == 0:
+            assert C.cans_poisson_solve_noalloc(h2, g.data_ptr(), q.data_ptr(), s, None) == 0
+    C.cans_plan_destroy(h2)
     C.cans_plan_destroy(h)
 
 
