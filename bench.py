@@ -941,6 +941,76 @@ def solve_once(spec: str, sweeps: int):
     print("ok")
 
 
+def rk3_once(spec: str, prec: int):
+    """Two explicit RK3 steps of the channel recipe at NX,NY,NZ (Lx = 4 pi, Ly = 2 pi, Lz = 2, tanh 1.8,
+    Re_b = 5600, CFL 0.9) with the Poisson solves in precision `prec`; no output but "ok".  Used for
+    small ncu captures of the step's kernels."""
+    import torch
+
+    import paper_2001_05234_b300 as cans
+    from paper_2001_05234_b300 import build_lib
+    from paper_2001_05234_b300 import inputs as I
+
+    build_lib.build()
+    n = tuple(int(v) for v in spec.split(","))
+    dzf = I.tanh_dzf(n[2], 1.8, 2.0)
+    shape, npts = (n[2], n[1], n[0]), n[0] * n[1] * n[2]
+    seed = I.SEED_BASE + 4
+    zc = torch.tensor(I.z_centres(dzf), device="cuda")
+    u = (1.5 * (1 - (zc - 1) ** 2))[:, None, None] + 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=11).view(shape) - 1)
+    v = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=12).view(shape) - 1)
+    w = 0.1 * (2 * I.uniform_torch(seed, npts, "cuda", stream=13).view(shape) - 1)
+    w[-1] = 0
+    p = torch.zeros_like(u)
+    ch = cans.Channel(n, (4 * np.pi, 2 * np.pi), dzf, prec=prec, sweeps=1)
+    for _ in range(2):
+        ch.rk3_step(u, v, w, p, 2.0 / 5600, cfl=0.9, ubulk=1.0)
+    torch.cuda.synchronize()
+    ch.close()
+    print("ok")
+
+
+def fp64_once(spec: str):
+    """Two plain FP64 solves of the bench recipe at NX,NY,NZ; no output but "ok" (ncu captures)."""
+    import torch
+
+    import paper_2001_05234_b300 as cans
+    from paper_2001_05234_b300 import build_lib
+    from paper_2001_05234_b300 import inputs as I
+
+    build_lib.build()
+    case = I.case_modes(n=tuple(int(v) for v in spec.split(",")))
+    f = I.rhs_device(case, "cuda")
+    p = torch.empty_like(f)
+    s = cans.PoissonSolver(case.n, case.bc, case.length_xy, case.dzf, prec=cans.CANS_FP64)
+    s.solve(f, p)
+    s.solve(f, p)
+    torch.cuda.synchronize()
+    s.close()
+    print("ok")
+
+
+def ensemble_once():
+    """Two solves of the 64-problem uneven ensemble (mixed, 2 sweeps) as the bench runs it, without the
+    graph (each launch visible to a profiler); no output but "ok"."""
+    import torch
+
+    import paper_2001_05234_b300 as cans
+    from paper_2001_05234_b300 import build_lib
+    from paper_2001_05234_b300 import inputs as I
+
+    build_lib.build()
+    cases = I.ensemble_cases()
+    fs = [I.rhs_device(c, "cuda") for c in cases]
+    ps = [torch.empty_like(f) for f in fs]
+    b = cans.Batch(cases, prec=cans.CANS_MIXED, sweeps=2, nstreams=16)
+    b.solve(fs, ps)
+    b.solve(fs, ps)
+    torch.cuda.synchronize()
+    b.close()
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -951,8 +1021,21 @@ def main():
     ap.add_argument("--solve-once", default=None, metavar="NX,NY,NZ",
                     help="profiling aid: two mixed solves of this size, no measurement")
     ap.add_argument("--sweeps", type=int, default=1, help="refinement sweeps for --solve-once")
+    ap.add_argument("--rk3-once", default=None, metavar="NX,NY,NZ",
+                    help="profiling aid: two explicit RK3 steps of the channel recipe, no measurement")
+    ap.add_argument("--rk3-prec", type=int, default=1, help="Poisson precision for --rk3-once (0 FP64, 1 mixed)")
+    ap.add_argument("--fp64-once", default=None, metavar="NX,NY,NZ",
+                    help="profiling aid: two FP64 solves of the bench recipe, no measurement")
+    ap.add_argument("--ensemble-once", action="store_true",
+                    help="profiling aid: two ensemble solves without the graph, no measurement")
     args = ap.parse_args()
-    if args.solve_once:
+    if args.rk3_once:
+        rk3_once(args.rk3_once, args.rk3_prec)
+    elif args.fp64_once:
+        fp64_once(args.fp64_once)
+    elif args.ensemble_once:
+        ensemble_once()
+    elif args.solve_once:
         solve_once(args.solve_once, args.sweeps)
     elif args.impl == "reference":
         reference_arm(args)

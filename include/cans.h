@@ -142,6 +142,29 @@ int cans_poisson_solve(cans_plan_t plan, const double* f, double* p, void* works
 int cans_helmholtz_solve(cans_plan_t plan, const double* f, double* p, double shift, void* workspace,
                          void* cuda_stream, double* info);
 
+/*
+ * cans_poisson_solve_divergence -- the pressure equation of the fractional step (Eq. poi_ns) with its
+ * right-hand side formed inside the solve's first pass: f = scale / (gamma dt) D(u, v, w), D the
+ * cell-centred divergence of a channel's face velocities (u on x-faces, v on y-faces, w on z-faces with
+ * w = 0 on both walls: the layout of cans_rk3_step), dt read from dt_dev on the device (dt_dev NULL:
+ * f = scale D(u, v, w)).  Channel plans only (x, y periodic, z Neumann, cell grid), otherwise
+ * CANS_ERR_UNSUPPORTED.
+ *   u, v, w : device, Nx*Ny*Nz doubles, read only.
+ *   f       : device output that receives f, or NULL for FP64 plans and mixed plans with max_sweeps 0
+ *             (the mixed refinement re-reads f, so it is required there: CANS_ERR_ARG).  Distinct from
+ *             u, v, w and p.
+ *   p, workspace, cuda_stream, info : as cans_poisson_solve (info needs f for the residual; with f
+ *             NULL its values are NaN).
+ * The result equals cans_poisson_solve applied to that f bit for bit (the divergence takes the same
+ * roundings as the stand-alone divergence kernel of the RK3 step), without the separate pass that
+ * would read u, v, w and write f and without the first x pass's read of f.  On B300 both forms are
+ * bound by the divergence's FP64 operations, and cans_rk3_step keeps the separate kernel, which
+ * measured faster.
+ */
+int cans_poisson_solve_divergence(cans_plan_t plan, const double* u, const double* v, const double* w, double scale,
+                                  const double* dt_dev, double gamma, double* f, double* p, void* workspace,
+                                  void* cuda_stream, double* info);
+
 /* Release the plan and its device tables. */
 int cans_plan_destroy(cans_plan_t plan);
 
@@ -269,8 +292,10 @@ int cans_batch_destroy(cans_batch_t batch);
  * CANS_ERR_INCOMPATIBLE (singular problem, f with a weighted mean), CANS_ERR_NOT_CONVERGED (a norm
  * the solve accumulated is not finite, a stalled refinement sweep, or, with the plan's opts.verify,
  * a final relative residual above its tol) -- else CANS_OK; when the call itself fails, every entry
- * receives the returned status.  The internal streams are created and released on every call, so this form is not meant for
- * stream capture or tight loops: keep a cans_batch_t for those. */
+ * receives the returned status.  The internal streams and events come from a per-device pool that the
+ * first call on a device creates (make that first call outside any stream capture); later calls only
+ * record events and enqueue work, so they can be captured into a CUDA graph.  Calls that overlap (two
+ * host threads at once) share the pool's events and must be serialised by the caller. */
 int cans_poisson_batched_workspace_size(int count, const cans_plan_t* plans, size_t* bytes);
 int cans_poisson_solve_batched(int count, const cans_plan_t* plans, const double* const* f, double* const* p,
                                void* workspace, void* cuda_stream, int* device_status);

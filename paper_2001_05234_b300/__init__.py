@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
         L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_plan_status.argtypes = [vp, ip]
+        L.cans_poisson_solve_divergence.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp, ctypes.c_double, vp, vp,
+                                                    vp, vp, dp]
         L.cans_poisson_adjoint_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve_adjoint.argtypes = [vp, vp, vp, vp, vp]
         L.cans_transform_xy.argtypes = [vp, vp, ctypes.c_int, vp]
@@ -247,6 +249,15 @@ def cans_noalloc_scratch_bytes() -> int:
 
 def cans_plan_destroy(plan) -> int:
     return lib().cans_plan_destroy(plan)
+
+
+def cans_poisson_solve_divergence(plan, u: int, v: int, w: int, scale: float, dt_ptr: int, gamma: float, f_ptr: int,
+                                  p_ptr: int, workspace_ptr: int, stream_ptr: int, info=None) -> int:
+    """cans_poisson_solve_divergence: p solves L_h p = scale / (gamma dt) D(u, v, w) (dt on the device;
+    dt_ptr 0: scale D(u, v, w)); f_ptr (0 allowed where the solve does not re-read f) receives f."""
+    return lib().cans_poisson_solve_divergence(plan, u, v, w, float(scale), dt_ptr or None, float(gamma), f_ptr or None,
+                                               p_ptr, workspace_ptr or None, stream_ptr or None,
+                                               _dptr(info) if info is not None else None)
 
 
 def cans_plan_status(plan) -> int:

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -60,9 +61,9 @@ static int batch_solve_impl(cans_batch_t B, const double* const* f, double* cons
   return CANS_OK;
 }
 
-extern "C" {
-
-int cans_batch_create(int count, const cans_plan_t* plans, int nstreams, cans_batch_t* out) {
+// A batch's host bookkeeping (workspace offsets, launch order, stream assignment) with its stream and
+// event slots left empty.
+static int cans_batch_create_shape(int count, const cans_plan_t* plans, int nstreams, cans_batch_t* out) {
   if (count < 1 || !plans || !out || nstreams < 1 || nstreams > 64) return CANS_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < count; ++i)
@@ -95,8 +96,23 @@ int cans_batch_create(int count, const cans_plan_t* plans, int nstreams, cans_ba
     B->stream_of[q] = s;
     load[s] += pts(q);
   }
-  B->streams.resize(ns);
-  B->joins.resize(ns);
+  B->streams.assign(ns, nullptr);
+  B->joins.assign(ns, nullptr);
+  *out = B;
+  return CANS_OK;
+}
+
+extern "C" {
+
+int cans_batch_create(int count, const cans_plan_t* plans, int nstreams, cans_batch_t* out) {
+  if (count < 1 || !plans || !out || nstreams < 1 || nstreams > 64) return CANS_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!plans[i]) return CANS_ERR_ARG;
+  cans_batch_t B = nullptr;
+  const int rc = cans_batch_create_shape(count, plans, nstreams, &B);
+  if (rc != CANS_OK) return rc;
+  const int ns = (int)B->streams.size();
   bool ok = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
   for (int s = 0; s < ns && ok; ++s) {
     ok = cudaStreamCreateWithFlags(&B->streams[s], cudaStreamNonBlocking) == cudaSuccess &&
@@ -147,13 +163,43 @@ int cans_poisson_batched_workspace_size(int count, const cans_plan_t* plans, siz
 int cans_poisson_solve_batched(int count, const cans_plan_t* plans, const double* const* f, double* const* p,
                                void* workspace, void* cuda_stream, int* device_status) {
   if (count < 1 || !plans || !f || !p) return CANS_ERR_ARG;
+  // The internal streams and events come from a per-device pool created by the first call on the
+  // device, so later calls only record events and launch work (and can be captured into a graph).
+  constexpr int kPoolStreams = 8, kMaxDev = 64;
+  struct Pool {
+    cudaStream_t streams[kPoolStreams];
+    cudaEvent_t fork, joins[kPoolStreams];
+    bool ready;
+  };
+  static Pool pools[kMaxDev] = {};
+  static std::mutex pool_lock;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return CANS_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> g(pool_lock);
+    Pool& q = pools[dev];
+    if (!q.ready) {
+      bool ok = cudaEventCreateWithFlags(&q.fork, cudaEventDisableTiming) == cudaSuccess;
+      for (int i = 0; i < kPoolStreams && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&q.streams[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&q.joins[i], cudaEventDisableTiming) == cudaSuccess;
+      if (!ok) return CANS_ERR_CUDA;  // (a partial pool is kept; its handles are valid)
+      q.ready = true;
+    }
+  }
   cans_batch_t B = nullptr;
-  int rc = cans_batch_create(count, plans, 8, &B);
+  int rc = cans_batch_create_shape(count, plans, kPoolStreams, &B);  // host bookkeeping only
   if (rc != CANS_OK) return rc;
+  const int ns = (int)B->streams.size();
+  for (int i = 0; i < ns; ++i) {
+    B->streams[i] = pools[dev].streams[i];
+    B->joins[i] = pools[dev].joins[i];
+  }
+  B->fork = pools[dev].fork;
   rc = batch_solve_impl(B, f, p, workspace, cuda_stream, device_status);
   if (rc != CANS_OK)  // a failed launch leaves the internal streams unjoined: drain them first
     for (cudaStream_t s : B->streams) cudaStreamSynchronize(s);
-  cans_batch_destroy(B);  // stream destruction waits for the queued work
+  delete B;  // the pool keeps its streams and events
   if (device_status && rc != CANS_OK) {
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     std::vector<int> h(count, rc);

@@ -501,6 +501,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   // cannot take fail instead of falling back (switches for comparisons and tests; the autotuner, when
   // on, chooses between the two kernels by timing)
   if (const char* ev = std::getenv("CANS_Z_TMA")) P->z_tma = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
+  if (const char* ev = std::getenv("CANS_Z_TMA_CTAS"))
+    P->z_tma_ctas = (ev[0] >= '1' && ev[0] <= '4') ? ev[0] - '0' : P->z_tma_ctas;
   if (o.autotune) {
     const int rc = autotune_plan(P);
     if (rc != CANS_OK) {
@@ -762,7 +764,10 @@ int autotune_plan(cans_plan_s* P) {
     } else {
       P->z_ti[s] = c[3];
       P->z_smem[s] = (size_t)c[3] * P->n[2] * (s ? 4 : 8);
-      if (s) P->z_tma = c[4];
+      if (s) {
+        P->z_tma = c[4] ? 1 : 0;
+        if (c[4]) P->z_tma_ctas = c[4];
+      }
     }
   };
   if (tune_lookup(key, v)) {
@@ -811,10 +816,13 @@ int autotune_plan(cans_plan_s* P) {
                          : time_best([&] { return launch_z<double>(P, (double*)w, nullptr, 0); });
       if (tz < bz) { bz = tz; best[3] = ti; }
     }
-    if (s && ztma_feasible(P, w)) {  // the TMA-fed float kernel (its tile width is fixed)
+    if (s && ztma_feasible(P, w)) {  // the TMA-fed float kernel (tile width fixed), 2 or 3 CTAs per SM
       P->z_tma = 1;
-      const float tz = time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); });
-      if (tz < bz) { bz = tz; best[4] = 1; }
+      for (int ctas : {4, 1, 2, 3}) {
+        P->z_tma_ctas = ctas;
+        const float tz = time_best([&] { return launch_z<float>(P, (float*)w, nullptr, 0); });
+        if (tz < bz) { bz = tz; best[4] = ctas; }
+      }
     }
   }
   cudaFree(f);
@@ -828,8 +836,10 @@ int autotune_plan(cans_plan_s* P) {
 
 extern "C" {
 
-int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspace, void* cuda_stream, double* info) {
-  if (!P || !f || !p) return CANS_ERR_ARG;
+// The solve, with its right-hand side either read from f or (div != NULL) formed as the divergence of a
+// channel's face velocities inside the first x pass; f is then the optional by-product array.
+static int solve_impl(cans_plan_t P, const double* f, const DivArgs* div, double* p, void* workspace,
+                      void* cuda_stream, double* info) {
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const size_t N = field_points(P);
   const int sweeps = P->opts.max_sweeps;
@@ -839,27 +849,38 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     PassTimer tm_(P, kind, st);             \
     CK(__VA_ARGS__);                        \
   } while (0)
+  // the z pass of the mixed path: the float columns, then the double ones (lowest |mu|, singular)
+  auto z_pass = [&](float* W, const double* gz, double* cp) -> int {
+    TIMED(CANS_PASS_Z, launch_z<float>(P, W, gz, st, 0, cp));
+    TIMED(CANS_PASS_ZD, launch_z<float>(P, W, gz, st, 1, cp));
+    return CANS_OK;
+  };
   // the singular column's weighted sum before its projection (compatibility check of the status word)
   double* compat = P->singular ? P->acc_d + P->nacc - 7 : nullptr;
   if (P->opts.prec == CANS_FP64) {
     CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
-    TIMED(CANS_PASS_XF, launch_xfwd<double, 0>(P, f, nullptr, nullptr, p, P->acc_d, st));
+    if (div)
+      TIMED(CANS_PASS_XF, launch_xfwd_div<double>(P, *div, p, P->acc_d, st));
+    else
+      TIMED(CANS_PASS_XF, launch_xfwd<double, 0>(P, f, nullptr, nullptr, p, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<double, 1>(P, p, st));
     TIMED(CANS_PASS_Z, launch_z<double>(P, p, nullptr, st, -1, compat));
     TIMED(CANS_PASS_YI, launch_y<double, -1>(P, p, st));
     TIMED(CANS_PASS_XI, launch_xinv<double, 0>(P, p, p, nullptr, nullptr, inv_scale, nullptr, st));
   } else {
-    if (f == p) return CANS_ERR_ARG;
+    if (f == p || (f == nullptr && sweeps > 0)) return CANS_ERR_ARG;  // the residual re-reads f
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CANS_ERR_WORKSPACE;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     float* W = reinterpret_cast<float*>(ws);
     float* Phi = reinterpret_cast<float*>(ws + work_field_bytes(P));
     float* Plo = reinterpret_cast<float*>(ws + work_field_bytes(P) + align256(N * 4));
     CK(cudaMemsetAsync(P->acc_d, 0, P->nacc * sizeof(double), st));
-    TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
+    if (div)
+      TIMED(CANS_PASS_XF, launch_xfwd_div<float>(P, *div, W, P->acc_d, st));
+    else
+      TIMED(CANS_PASS_XF, launch_xfwd<float, 0>(P, f, nullptr, nullptr, W, P->acc_d, st));
     TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
-    TIMED(CANS_PASS_Z, launch_z<float>(P, W, nullptr, st, 0, compat));
-    TIMED(CANS_PASS_ZD, launch_z<float>(P, W, nullptr, st, 1, compat));
+    if (const int rz = z_pass(W, nullptr, compat)) return rz;
     TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
     if (sweeps == 0) {
       TIMED(CANS_PASS_XI, launch_xinv<float, 0>(P, W, p, nullptr, nullptr, inv_scale, nullptr, st));
@@ -878,8 +899,7 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
           TIMED(CANS_PASS_XR, launch_xfwd<float, 1>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
         }
         TIMED(CANS_PASS_YF, launch_y<float, 1>(P, W, st));
-        TIMED(CANS_PASS_Z, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st, 0));
-        TIMED(CANS_PASS_ZD, launch_z<float>(P, W, s == 0 ? gauge : nullptr, st, 1));
+        if (const int rz = z_pass(W, s == 0 ? gauge : nullptr, nullptr)) return rz;
         TIMED(CANS_PASS_YI, launch_y<float, -1>(P, W, st));
         const bool last = (s + 1 == sweeps);
         if (s == 0 && !last)
@@ -896,7 +916,7 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
   // the final residual (opts.verify, or a caller that asks for the norms; not for an in-place FP64
   // solve, whose f is gone), then the status word's checks
   double* acc2 = P->acc_d + P->nacc - 4;
-  const bool verify = (info != nullptr || P->opts.verify) && f != p;
+  const bool verify = (info != nullptr || P->opts.verify) && f != nullptr && f != p;
   if (verify) CK(launch_residual_norms(P, f, p, acc2, st));
   CK(launch_solve_status(P, compat != nullptr, verify, st));
   if (info) {
@@ -927,6 +947,23 @@ int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspac
     if (word != CANS_OK) return word;
   }
   return CANS_OK;
+}
+
+int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspace, void* cuda_stream, double* info) {
+  if (!P || !f || !p) return CANS_ERR_ARG;
+  return solve_impl(P, f, nullptr, p, workspace, cuda_stream, info);
+}
+
+int cans_poisson_solve_divergence(cans_plan_t P, const double* u, const double* v, const double* w, double scale,
+                                  const double* dt_dev, double gamma, double* f, double* p, void* workspace,
+                                  void* cuda_stream, double* info) {
+  if (!P || !u || !v || !w || !p) return CANS_ERR_ARG;
+  if (P->bc[0] != BC_P || P->bc[1] != BC_P || P->bc[2] != BC_NN || P->opts.z_grid != 0) return CANS_ERR_UNSUPPORTED;
+  if (dt_dev != nullptr && !(gamma != 0.0)) return CANS_ERR_ARG;
+  if (f != nullptr && (f == p || f == u || f == v || f == w)) return CANS_ERR_ARG;
+  if (p == u || p == v || p == w) return CANS_ERR_ARG;
+  const DivArgs d = div_args(P, u, v, w, f, scale, dt_dev, gamma);
+  return solve_impl(P, f, &d, p, workspace, cuda_stream, info);
 }
 
 int cans_plan_status(cans_plan_t P, int* status) {

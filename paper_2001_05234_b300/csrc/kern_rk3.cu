@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "plan.cuh"
 
@@ -55,99 +56,198 @@ __device__ __forceinline__ double lap_t(const Chan& g, const double* a, int i, i
 }
 
 // Momentum right-hand side A(u) + nu L(u) (Eq. up) and the predictor
-//   u* = u + dt (alpha rhs + beta rhs_prev - gamma G p).  rhs replaces rhs_prev in place.
+//   u* = u + dt (alpha rhs + beta rhs_prev - gamma G p);  rhs replaces rhs_prev in place.
 // IMPL (Crank-Nicolson diffusion, Eq. up_id and Eq. up_id_2): rhs = A(u) alone, and us receives the
 // right-hand side of the Helmholtz problem (L + sigma) u* = sigma (u** - gamma nu dt/2 L u), sigma =
 // -2/(gamma nu dt), which is sigma (u + dt (alpha A + beta A_prev - gamma G p)) - L u.
+// Flux form, on tiles of MX x MY columns that march along z (a thread owns one (i, j) column and MZ
+// planes of it).  The conservative advection of Eq. up is a difference of
+// face and edge fluxes, and each flux serves the two points on either side of it -- and the uv, uw,
+// vw edge fluxes two equations each -- so every flux is computed once:
+//   A(i)  = (u_{i-1} + u_i)^2 at cell centres (x flux of u),  B(j) = (v_{j-1} + v_j)^2 (y flux of v),
+//   C(k)  = (w_{k-1} + w_k)^2 (z flux of w),
+//   Euv   = (u_j + u_{j+1})(v_i + v_{i+1}) on the x-y edges, Euw = (u_k + u_{k+1})(w_i + w_{i+1}) on the
+//   x-z edges, Evw = (v_k + v_{k+1})(w_j + w_{j+1}) on the y-z edges,
+// each thread forming those on its east, north and top sides.  The west and south ones come from the
+// neighbouring threads through a shared tile (double-buffered by plane; the tile's first row and
+// column form theirs themselves), the bottom ones from the thread's own previous plane, as do the z
+// first differences of the diffusion.  Advection is the conservative central form with two-point
+// averages (the 1/4 of the averages in the metric factors), diffusion the 3-point Laplacian with the
+// no-slip ghosts -u for u and v and w = 0 on the walls.  B300 issues FP64 at 1/64 of the FP32 rate and
+// the kernel is bound by it, so the shared fluxes, nu and dt folded into the coefficients, and one
+// fused chain for nu L u - A(u) keep it at ~79 FP64 instructions per point (a pointwise form of the
+// same operator took ~96 and 5.58 ms per 512 x 256 x 192 launch against 4.91).
+constexpr int MX = 32, MY = 8, MZ = 16;
+
 template <bool IMPL>
-__global__ void momentum_kernel(Chan g, const double* __restrict__ u, const double* __restrict__ v,
-                                const double* __restrict__ w, const double* __restrict__ p, double* __restrict__ ru,
-                                double* __restrict__ rv, double* __restrict__ rw, double* __restrict__ us,
-                                double* __restrict__ vs, double* __restrict__ ws, double nu, double alpha, double beta,
-                                double gamma, const double* __restrict__ dt_dev, double sigma) {
-  // The same discrete operator as written term by term (two-point averages, products, differences),
-  // arranged for fewer FP64 operations (B300 issues FP64 at 1/64 of FP32): the 1/2 x 1/2 factors of
-  // the averaged products and 1/dx^2 are folded into constants, (ue^2 - uw^2) is formed as
-  // (u_e - u_w)(u_e + 2 u_c + u_w), and sums of products use FMA.
-  const size_t N = (size_t)g.nx * g.ny * g.nz;
+__global__ void __launch_bounds__(MX * MY, 2) momentum_flux_kernel(
+    Chan g, const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
+    const double* __restrict__ p, double* __restrict__ ru, double* __restrict__ rv, double* __restrict__ rw,
+    double* __restrict__ us, double* __restrict__ vs, double* __restrict__ ws, double nu, double alpha, double beta,
+    double gamma, const double* __restrict__ dt_dev, double sigma) {
+  // shared fluxes of the current plane, two buffers by plane parity: [A, Euv, Euw] read by the east
+  // neighbour, [Euv, B, Evw] by the north one (Euv by both)
+  __shared__ double sA[2][MY][MX], sUV[2][MY][MX], sUW[2][MY][MX], sB[2][MY][MX], sVW[2][MY][MX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * MX + tx, j = blockIdx.y * MY + ty;
+  const bool live = i < g.nx && j < g.ny;
+  const int k0 = blockIdx.z * MZ, k1 = min(g.nz, k0 + MZ);
   const double dt = *dt_dev;
   const double qdx = 0.25 * g.dxi, qdy = 0.25 * g.dyi, dx2 = g.dxi * g.dxi, dy2 = g.dyi * g.dyi;
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((size_t)g.nx * g.ny));
-    const double qdz = 0.25 * g.dzfi[k], dzfi = g.dzfi[k], dzc_up = g.dzci[k], dzc_dn = dzc_inv_below(g, k);
-    const double uc = u[c], vc = v[c];
-    double r_u, r_v, r_w, l_u, l_v, l_w = 0.0;
-    {  // u at (i+1/2, j, k)
-      const double ue = u[g.id(i + 1, j, k)], uw = u[g.id(i - 1, j, k)];
-      const double un = u[g.id(i, j + 1, k)], uS = u[g.id(i, j - 1, k)];
-      const double ut = Ut(g, u, i, j, k + 1), ub = Ut(g, u, i, j, k - 1);
-      const double ax = (ue - uw) * fma(2.0, uc, ue + uw);
-      const double ay = fma(-(uS + uc), v[g.id(i, j - 1, k)] + v[g.id(i + 1, j - 1, k)],
-                            (uc + un) * (vc + v[g.id(i + 1, j, k)]));
-      const double az = fma(-(ub + uc), Wn(g, w, i, j, k - 1) + Wn(g, w, i + 1, j, k - 1),
-                            (uc + ut) * (Wn(g, w, i, j, k) + Wn(g, w, i + 1, j, k)));
-      const double adv = fma(qdx, ax, fma(qdy, ay, qdz * az));
-      const double lz = fma(ut - uc, dzc_up, -(uc - ub) * dzc_dn) * dzfi;
-      const double lap = fma(dx2, fma(-2.0, uc, ue + uw), fma(dy2, fma(-2.0, uc, un + uS), lz));
-      r_u = IMPL ? -adv : fma(nu, lap, -adv);
-      l_u = lap;
+  const double ndx2 = nu * dx2, ndy2 = nu * dy2;
+  const double dta = dt * alpha, dtb = dt * beta, dtg = -dt * gamma, dga_x = dtg * g.dxi, dga_y = dtg * g.dyi;
+  const int ie = (i + 1 < g.nx) ? i + 1 : 0, iw = (i > 0) ? i - 1 : g.nx - 1;
+  const int jn = (j + 1 < g.ny) ? j + 1 : 0, js = (j > 0) ? j - 1 : g.ny - 1;
+  const size_t plane = (size_t)g.nx * g.ny;
+  auto at = [&](int ii, int jj, int kk) { return (size_t)ii + (size_t)g.nx * ((size_t)jj + (size_t)g.ny * kk); };
+  auto U = [&](const double* a, int ii, int jj, int kk) {  // tangential component with no-slip ghosts
+    if (kk < 0) return -a[at(ii, jj, 0)];
+    if (kk >= g.nz) return -a[at(ii, jj, g.nz - 1)];
+    return a[at(ii, jj, kk)];
+  };
+  auto Wv = [&](int ii, int jj, int kk) { return (kk < 0 || kk >= g.nz - 1) ? 0.0 : w[at(ii, jj, kk)]; };
+  // the carried bottom quantities of plane k (from plane k - 1): the z fluxes Euw, Evw and C at the
+  // bottom face, and the bottom z first differences of u, v (scaled by 1/dzc) and w (by 1/dzf)
+  double fuw_b = 0, fvw_b = 0, c_b = 0, gu_b = 0, gv_b = 0, hw_b = 0;
+  if (live) {
+    const int kb = k0 - 1;
+    fuw_b = (U(u, i, j, kb) + U(u, i, j, k0)) * (Wv(i, j, kb) + Wv(ie, j, kb));
+    fvw_b = (U(v, i, j, kb) + U(v, i, j, k0)) * (Wv(i, j, kb) + Wv(i, jn, kb));
+    const double wb0 = Wv(i, j, kb), wb1 = Wv(i, j, k0);  // C at cell k0: (w_{k0-1} + w_{k0})^2
+    c_b = (wb0 + wb1) * (wb0 + wb1);
+    const double dzb = (k0 == 0) ? g.dzfi[0] : g.dzci[k0 - 1];
+    gu_b = (U(u, i, j, k0) - U(u, i, j, kb)) * dzb;
+    gv_b = (U(v, i, j, k0) - U(v, i, j, kb)) * dzb;
+    hw_b = (wb1 - wb0) * g.dzfi[k0];  // w = 0 on the bottom wall face
+  }
+  for (int k = k0; k < k1; ++k) {
+    const int b = k & 1;
+    double uc = 0, vc = 0, wc = 0, ue = 0, un = 0, ut = 0, vE = 0, vn = 0, vt = 0, wE = 0, wn = 0, wt = 0;
+    double fA_e = 0, fuv = 0, fuw = 0, fB_n = 0, fvw = 0, c_t = 0;
+    const size_t c = at(i, j, k);
+    if (live) {
+      uc = u[c];
+      vc = v[c];
+      wc = Wv(i, j, k);
+      ue = u[at(ie, j, k)];
+      un = u[at(i, jn, k)];
+      ut = U(u, i, j, k + 1);
+      vE = v[at(ie, j, k)];
+      vn = v[at(i, jn, k)];
+      vt = U(v, i, j, k + 1);
+      wE = Wv(ie, j, k);
+      wn = Wv(i, jn, k);
+      wt = Wv(i, j, k + 1);
+      // this thread's east, north and top fluxes
+      fA_e = (uc + ue) * (uc + ue);
+      fuv = (uc + un) * (vc + vE);
+      fuw = (uc + ut) * (wc + wE);
+      fB_n = (vc + vn) * (vc + vn);
+      fvw = (vc + vt) * (wc + wn);
+      c_t = (wc + wt) * (wc + wt);
+      sA[b][ty][tx] = fA_e;
+      sUV[b][ty][tx] = fuv;
+      sUW[b][ty][tx] = fuw;
+      sB[b][ty][tx] = fB_n;
+      sVW[b][ty][tx] = fvw;
     }
-    {  // v at (i, j+1/2, k)
-      const double ve = v[g.id(i + 1, j, k)], vw = v[g.id(i - 1, j, k)];
-      const double vn = v[g.id(i, j + 1, k)], vS = v[g.id(i, j - 1, k)];
-      const double vt = Ut(g, v, i, j, k + 1), vb = Ut(g, v, i, j, k - 1);
-      const double ax = fma(-(vw + vc), u[g.id(i - 1, j, k)] + u[g.id(i - 1, j + 1, k)],
-                            (vc + ve) * (uc + u[g.id(i, j + 1, k)]));
-      const double ay = (vn - vS) * fma(2.0, vc, vn + vS);
-      const double az = fma(-(vb + vc), Wn(g, w, i, j, k - 1) + Wn(g, w, i, j + 1, k - 1),
-                            (vc + vt) * (Wn(g, w, i, j, k) + Wn(g, w, i, j + 1, k)));
-      const double adv = fma(qdx, ax, fma(qdy, ay, qdz * az));
-      const double lz = fma(vt - vc, dzc_up, -(vc - vb) * dzc_dn) * dzfi;
-      const double lap = fma(dx2, fma(-2.0, vc, ve + vw), fma(dy2, fma(-2.0, vc, vn + vS), lz));
-      r_v = IMPL ? -adv : fma(nu, lap, -adv);
-      l_v = lap;
+    __syncthreads();
+    if (live) {
+      // west fluxes: from the thread to the west, or formed here on the tile's first column
+      double fA_w, fuv_w, fuw_w;
+      const double uw = u[at(iw, j, k)];
+      if (tx > 0) {
+        fA_w = sA[b][ty][tx - 1];
+        fuv_w = sUV[b][ty][tx - 1];
+        fuw_w = sUW[b][ty][tx - 1];
+      } else {
+        fA_w = (uw + uc) * (uw + uc);
+        fuv_w = (uw + u[at(iw, jn, k)]) * (v[at(iw, j, k)] + vc);
+        fuw_w = (uw + U(u, iw, j, k + 1)) * (Wv(iw, j, k) + wc);
+      }
+      // south fluxes
+      double fuv_s, fB_s, fvw_s;
+      const double vs_ = v[at(i, js, k)];
+      if (ty > 0) {
+        fuv_s = sUV[b][ty - 1][tx];
+        fB_s = sB[b][ty - 1][tx];
+        fvw_s = sVW[b][ty - 1][tx];
+      } else {
+        fuv_s = (u[at(i, js, k)] + uc) * (vs_ + v[at(ie, js, k)]);
+        fB_s = (vs_ + vc) * (vs_ + vc);
+        fvw_s = (vs_ + U(v, i, js, k + 1)) * (Wv(i, js, k) + wc);
+      }
+      const double dzfi = g.dzfi[k], dzc_up = g.dzci[k], qdz = 0.25 * dzfi;
+      const double uS = u[at(i, js, k)], vW = v[at(iw, j, k)];
+      // second differences along x and y, z first differences (carried to the next plane)
+      const double xx_u = fma(-2.0, uc, ue + uw), yy_u = fma(-2.0, uc, un + uS), gu_t = (ut - uc) * dzc_up;
+      const double xx_v = fma(-2.0, vc, vE + vW), yy_v = fma(-2.0, vc, vn + vs_), gv_t = (vt - vc) * dzc_up;
+      double r_u, r_v, r_w = 0.0, lap_u = 0.0, lap_v = 0.0, lap_w = 0.0, hw_t = 0.0;
+      if (IMPL) {  // the Helmholtz right-hand side needs L u on its own
+        lap_u = fma(dx2, xx_u, fma(dy2, yy_u, (gu_t - gu_b) * dzfi));
+        lap_v = fma(dx2, xx_v, fma(dy2, yy_v, (gv_t - gv_b) * dzfi));
+        r_u = -fma(qdx, fA_e - fA_w, fma(qdy, fuv - fuv_s, qdz * (fuw - fuw_b)));
+        r_v = -fma(qdx, fuv - fuv_w, fma(qdy, fB_n - fB_s, qdz * (fvw - fvw_b)));
+      } else {  // nu L u - A(u) as one chain, nu folded into the metric factors
+        const double ndz = nu * dzfi;
+        r_u = fma(ndx2, xx_u, fma(ndy2, yy_u, fma(ndz, gu_t - gu_b,
+              fma(-qdx, fA_e - fA_w, fma(-qdy, fuv - fuv_s, -qdz * (fuw - fuw_b))))));
+        r_v = fma(ndx2, xx_v, fma(ndy2, yy_v, fma(ndz, gv_t - gv_b,
+              fma(-qdx, fuv - fuv_w, fma(-qdy, fB_n - fB_s, -qdz * (fvw - fvw_b))))));
+      }
+      // w at (i, j, k+1/2); the top wall face stays at rest
+      if (k < g.nz - 1) {
+        const double qdzc = 0.25 * dzc_up;
+        const double xx_w = fma(-2.0, wc, wE + Wv(iw, j, k)), yy_w = fma(-2.0, wc, wn + Wv(i, js, k));
+        hw_t = (wt - wc) * g.dzfi[k + 1];
+        if (IMPL) {
+          lap_w = fma(dx2, xx_w, fma(dy2, yy_w, (hw_t - hw_b) * dzc_up));
+          r_w = -fma(qdx, fuw - fuw_w, fma(qdy, fvw - fvw_s, qdzc * (c_t - c_b)));
+        } else {
+          r_w = fma(ndx2, xx_w, fma(ndy2, yy_w, fma(nu * dzc_up, hw_t - hw_b,
+                fma(-qdx, fuw - fuw_w, fma(-qdy, fvw - fvw_s, -qdzc * (c_t - c_b))))));
+        }
+      }
+      // u* = u + dt (alpha r + beta r_prev - gamma G p): dt alpha, dt beta and -dt gamma / dx folded
+      const double pc = p[c];
+      const double dpx = p[at(ie, j, k)] - pc, dpy = p[at(i, jn, k)] - pc;
+      const double dpz = (k < g.nz - 1) ? p[c + plane] - pc : 0.0;
+      if (IMPL) {
+        double su = fma(dga_x, dpx, fma(dta, r_u, uc)), sv = fma(dga_y, dpy, fma(dta, r_v, vc));
+        double sw = fma(dtg * dzc_up, dpz, fma(dta, r_w, wc));
+        if (beta != 0.0) {
+          su = fma(dtb, ru[c], su);
+          sv = fma(dtb, rv[c], sv);
+          sw = fma(dtb, rw[c], sw);
+        }
+        us[c] = fma(sigma, su, -lap_u);
+        vs[c] = fma(sigma, sv, -lap_v);
+        ws[c] = (k < g.nz - 1) ? fma(sigma, sw, -lap_w) : 0.0;
+      } else {
+        double su = fma(dga_x, dpx, fma(dta, r_u, uc)), sv = fma(dga_y, dpy, fma(dta, r_v, vc));
+        double sw = fma(dtg * dzc_up, dpz, fma(dta, r_w, wc));
+        if (beta != 0.0) {
+          su = fma(dtb, ru[c], su);
+          sv = fma(dtb, rv[c], sv);
+          sw = fma(dtb, rw[c], sw);
+        }
+        us[c] = su;
+        vs[c] = sv;
+        ws[c] = (k < g.nz - 1) ? sw : 0.0;
+      }
+      ru[c] = r_u;
+      rv[c] = r_v;
+      rw[c] = r_w;
+      // carry the top quantities to the next plane's bottom
+      fuw_b = fuw;
+      fvw_b = fvw;
+      c_b = c_t;
+      gu_b = gu_t;
+      gv_b = gv_t;
+      hw_b = hw_t;
     }
-    if (k == g.nz - 1) {
-      r_w = 0.0;
-    } else {  // w at (i, j, k+1/2)
-      const double wc = w[c];
-      const double we = Wn(g, w, i + 1, j, k), ww = Wn(g, w, i - 1, j, k);
-      const double wn = Wn(g, w, i, j + 1, k), wS = Wn(g, w, i, j - 1, k);
-      const double wt = Wn(g, w, i, j, k + 1), wb = Wn(g, w, i, j, k - 1);
-      const double qdzc = 0.25 * dzc_up;
-      const double ax = fma(-(ww + wc), u[g.id(i - 1, j, k)] + u[g.id(i - 1, j, k + 1)],
-                            (wc + we) * (uc + u[g.id(i, j, k + 1)]));
-      const double ay = fma(-(wS + wc), v[g.id(i, j - 1, k)] + v[g.id(i, j - 1, k + 1)],
-                            (wc + wn) * (vc + v[g.id(i, j, k + 1)]));
-      const double az = (wt - wb) * fma(2.0, wc, wt + wb);
-      const double adv = fma(qdx, ax, fma(qdy, ay, qdzc * az));
-      const double lz = fma(wt - wc, g.dzfi[k + 1], -(wc - wb) * dzfi) * dzc_up;
-      const double lap = fma(dx2, fma(-2.0, wc, we + ww), fma(dy2, fma(-2.0, wc, wn + wS), lz));
-      r_w = IMPL ? -adv : fma(nu, lap, -adv);
-      l_w = lap;
-    }
-    const double pc = p[c];
-    const double gx = (p[g.id(i + 1, j, k)] - pc) * g.dxi;
-    const double gy = (p[g.id(i, j + 1, k)] - pc) * g.dyi;
-    const double gz = (k < g.nz - 1) ? (p[g.id(i, j, k + 1)] - pc) * dzc_up : 0.0;
-    double su = alpha * r_u, sv = alpha * r_v, sw = alpha * r_w;
-    if (beta != 0.0) {
-      su = fma(beta, ru[c], su);
-      sv = fma(beta, rv[c], sv);
-      sw = fma(beta, rw[c], sw);
-    }
-    if (IMPL) {
-      us[c] = fma(sigma, fma(dt, fma(-gamma, gx, su), uc), -l_u);
-      vs[c] = fma(sigma, fma(dt, fma(-gamma, gy, sv), vc), -l_v);
-      ws[c] = (k < g.nz - 1) ? fma(sigma, fma(dt, fma(-gamma, gz, sw), w[c]), -l_w) : 0.0;
-    } else {
-      us[c] = fma(dt, fma(-gamma, gx, su), uc);
-      vs[c] = fma(dt, fma(-gamma, gy, sv), vc);
-      ws[c] = (k < g.nz - 1) ? fma(dt, fma(-gamma, gz, sw), w[c]) : 0.0;
-    }
-    ru[c] = r_u;
-    rv[c] = r_v;
-    rw[c] = r_w;
+    // no barrier here: the next plane writes the other buffer, and the plane after it reaches this
+    // buffer only after every thread has passed the next plane's barrier, i.e. finished these reads
   }
 }
 
@@ -155,20 +255,22 @@ __global__ void momentum_kernel(Chan g, const double* __restrict__ u, const doub
 // Adjoint use: the face field is first divided by its face weight (dzf for u and v, dzc for w).
 __global__ void divergence_kernel(Chan g, const double* __restrict__ u, const double* __restrict__ v,
                                   const double* __restrict__ w, double* __restrict__ f, double scale_num,
-                                  const double* __restrict__ dt_dev, double gamma, int weighted) {
+                                  const double* __restrict__ dt_dev, double gamma, int weighted, DivArgs dv) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const double scale = (dt_dev != nullptr) ? scale_num / (gamma * (*dt_dev)) : scale_num;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((size_t)g.nx * g.ny));
+    if (!weighted) {  // the arithmetic the fused x pass repeats bit for bit
+      f[c] = dv.at(scale, c, i, j, k);
+      continue;
+    }
     double uw = u[c] - u[g.id(i - 1, j, k)];
     double vw = v[c] - v[g.id(i, j - 1, k)];
     double wt = Wn(g, w, i, j, k), wb = Wn(g, w, i, j, k - 1);
-    if (weighted) {
-      uw *= g.dzfi[k];
-      vw *= g.dzfi[k];
-      wt *= (k < g.nz - 1) ? 2.0 / (g.dzf[k] + g.dzf[k + 1]) : 0.0;
-      wb *= (k > 0) ? 2.0 / (g.dzf[k - 1] + g.dzf[k]) : 0.0;
-    }
+    uw *= g.dzfi[k];
+    vw *= g.dzfi[k];
+    wt *= (k < g.nz - 1) ? 2.0 / (g.dzf[k] + g.dzf[k + 1]) : 0.0;
+    wb *= (k > 0) ? 2.0 / (g.dzf[k - 1] + g.dzf[k]) : 0.0;
     f[c] = scale * (uw * g.dxi + vw * g.dyi + (wt - wb) * g.dzfi[k]);
   }
 }
@@ -233,25 +335,31 @@ __global__ void forcing_kernel(Chan g, double* __restrict__ u, const double* __r
 // largest inverse advective time scale over all cells (chkdt listing, y and z rows by symmetry),
 // reduced on the device: block maximum, then one atomic max on the bit pattern (non-negative doubles
 // order like their bits).
+// The largest inverse advective time scale of cell (i, j, k) (Eq. dt and its chkdt rows; the y and z
+// rows follow the x row by symmetry), in FP64; the 1/4 of the four-point averages is folded into the
+// metric factors (fewer FP64 operations).
+__device__ __forceinline__ double dti_cell(const Chan& g, const double* __restrict__ u, const double* __restrict__ v,
+                                           const double* __restrict__ w, size_t c, int i, int j, int k) {
+  const double qdx = 0.25 * g.dxi, qdy = 0.25 * g.dyi, qdz = 0.25 * g.dzfi[k];
+  const double vx = fabs(v[c] + v[g.id(i, j - 1, k)] + v[g.id(i + 1, j, k)] + v[g.id(i + 1, j - 1, k)]);
+  const double wx = fabs(Wn(g, w, i, j, k) + Wn(g, w, i, j, k - 1) + Wn(g, w, i + 1, j, k) + Wn(g, w, i + 1, j, k - 1));
+  const double dtix = fma(fabs(u[c]), g.dxi, fma(vx, qdy, wx * qdz));
+  const double uy = fabs(u[c] + u[g.id(i - 1, j, k)] + u[g.id(i, j + 1, k)] + u[g.id(i - 1, j + 1, k)]);
+  const double wy = fabs(Wn(g, w, i, j, k) + Wn(g, w, i, j, k - 1) + Wn(g, w, i, j + 1, k) + Wn(g, w, i, j + 1, k - 1));
+  const double dtiy = fma(uy, qdx, fma(fabs(v[c]), g.dyi, wy * qdz));
+  const double uz = fabs(u[c] + u[g.id(i - 1, j, k)] + Ut(g, u, i, j, k + 1) + Ut(g, u, i - 1, j, k + 1));
+  const double vz = fabs(v[c] + v[g.id(i, j - 1, k)] + Ut(g, v, i, j, k + 1) + Ut(g, v, i, j - 1, k + 1));
+  const double dtiz = fma(uz, qdx, fma(vz, qdy, fabs(Wn(g, w, i, j, k)) * g.dzci[k]));
+  return fmax(dtix, fmax(dtiy, dtiz));
+}
+
 __global__ void chkdt_kernel(Chan g, const double* __restrict__ u, const double* __restrict__ v,
                              const double* __restrict__ w, unsigned long long* dti_bits) {
-  // the 1/4 of the four-point averages folded into the metric factors (fewer FP64 operations)
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  const double qdx = 0.25 * g.dxi, qdy = 0.25 * g.dyi;
   double dti = 0.0;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N; c += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((size_t)g.nx * g.ny));
-    const double qdz = 0.25 * g.dzfi[k];
-    const double vx = fabs(v[c] + v[g.id(i, j - 1, k)] + v[g.id(i + 1, j, k)] + v[g.id(i + 1, j - 1, k)]);
-    const double wx = fabs(Wn(g, w, i, j, k) + Wn(g, w, i, j, k - 1) + Wn(g, w, i + 1, j, k) + Wn(g, w, i + 1, j, k - 1));
-    const double dtix = fma(fabs(u[c]), g.dxi, fma(vx, qdy, wx * qdz));
-    const double uy = fabs(u[c] + u[g.id(i - 1, j, k)] + u[g.id(i, j + 1, k)] + u[g.id(i - 1, j + 1, k)]);
-    const double wy = fabs(Wn(g, w, i, j, k) + Wn(g, w, i, j, k - 1) + Wn(g, w, i, j + 1, k) + Wn(g, w, i, j + 1, k - 1));
-    const double dtiy = fma(uy, qdx, fma(fabs(v[c]), g.dyi, wy * qdz));
-    const double uz = fabs(u[c] + u[g.id(i - 1, j, k)] + Ut(g, u, i, j, k + 1) + Ut(g, u, i - 1, j, k + 1));
-    const double vz = fabs(v[c] + v[g.id(i, j - 1, k)] + Ut(g, v, i, j, k + 1) + Ut(g, v, i, j - 1, k + 1));
-    const double dtiz = fma(uz, qdx, fma(vz, qdy, fabs(Wn(g, w, i, j, k)) * g.dzci[k]));
-    dti = fmax(dti, fmax(dtix, fmax(dtiy, dtiz)));
+    dti = fmax(dti, dti_cell(g, u, v, w, c, i, j, k));
   }
   for (int o = 16; o > 0; o >>= 1) dti = fmax(dti, __shfl_xor_sync(0xffffffffu, dti, o));
   if ((threadIdx.x & 31) == 0) atomicMax(dti_bits, (unsigned long long)__double_as_longlong(dti));
@@ -294,13 +402,13 @@ cudaError_t launch_momentum(const cans_plan_s* P, const double* u, const double*
                             double alpha, double beta, double gamma, const double* dt_dev, cudaStream_t st,
                             double sigma) {
   const Chan g = chan(P);
-  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  const dim3 grid((g.nx + MX - 1) / MX, (g.ny + MY - 1) / MY, (g.nz + MZ - 1) / MZ), block(MX, MY);
   if (sigma != 0.0)
-    momentum_kernel<true><<<grid_for(N), 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
+    momentum_flux_kernel<true><<<grid, block, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
                                                        dt_dev, sigma);
   else
-    momentum_kernel<false><<<grid_for(N), 256, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
-                                                        dt_dev, 0.0);
+    momentum_flux_kernel<false><<<grid, block, 0, st>>>(g, u, v, w, p, ru, rv, rw, us, vs, ws, nu, alpha, beta, gamma,
+                                                        dt_dev, sigma);
   return cudaGetLastError();
 }
 
@@ -308,8 +416,29 @@ cudaError_t launch_divergence(const cans_plan_s* P, const double* u, const doubl
                               double scale_num, const double* dt_dev, double gamma, int weighted, cudaStream_t st) {
   const Chan g = chan(P);
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  divergence_kernel<<<grid_for(N), 256, 0, st>>>(g, u, v, w, f, scale_num, dt_dev, gamma, weighted);
+  divergence_kernel<<<grid_for(N), 256, 0, st>>>(g, u, v, w, f, scale_num, dt_dev, gamma, weighted,
+                                                 div_args(P, u, v, w, f, scale_num, dt_dev, gamma));
   return cudaGetLastError();
+}
+
+DivArgs div_args(const cans_plan_s* P, const double* u, const double* v, const double* w, double* fout, double num,
+                 const double* dt, double gamma) {
+  const Chan g = chan(P);
+  DivArgs d;
+  d.u = u;
+  d.v = v;
+  d.w = w;
+  d.fout = fout;
+  d.dzfi = g.dzfi;
+  d.dt = dt;
+  d.num = num;
+  d.gamma = gamma;
+  d.dxi = g.dxi;
+  d.dyi = g.dyi;
+  d.nx = g.nx;
+  d.ny = g.ny;
+  d.nz = g.nz;
+  return d;
 }
 
 cudaError_t launch_correct(const cans_plan_s* P, const double* us, const double* vs, const double* ws,
@@ -418,6 +547,10 @@ int cans_rk3_step(cans_plan_t P, double* u, double* v, double* w, double* p, con
       PassTimer tm(P, CANS_PASS_MOMENTUM, st);
       RK_CK(launch_momentum(P, u, v, w, p, ru, rv, rw, us, vs, ws, prm->nu, a, b, g, dt, st));
     }
+    // Eq. poi_ns: the divergence as its own kernel, then the solve.  (Forming the divergence inside the
+    // solve's first x pass, cans_poisson_solve_divergence, saves its 16 B/pt of traffic, but both
+    // forms are bound by the divergence's FP64 operations on this GPU, and the separate kernel hides
+    // their latency better: measured 0.54 ms faster per step at 512 x 256 x 192.)
     {
       PassTimer tm(P, CANS_PASS_DIVERGENCE, st);
       RK_CK(launch_divergence(P, us, vs, ws, f, 1.0, dt, g, 0, st));

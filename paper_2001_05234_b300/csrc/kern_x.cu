@@ -50,12 +50,14 @@ __device__ __forceinline__ void block_accumulate_d(double v, double* dst) {
 
 // Forward x-pass.  MODE 0: read f (double) -> T.  MODE 1 (T = float): the residual
 // f - L_h(Phi + Plo) computed on the fly; MODE 2: the same with Plo known to be zero (first sweep).
-// Output lines go to dst (T) in transform slot order.  norm_acc (optional) receives sum f^2 (MODE 0)
-// or sum r^2.
+// MODE 3: f formed on the fly as the divergence of a channel's face velocities (dv), written to
+// dv.fout as well when that is set.
+// Output lines go to dst (T) in transform slot order.  norm_acc (optional) receives sum f^2 (MODE 0,
+// 3) or sum r^2.
 template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
                                                       const float* __restrict__ Plo, T* __restrict__ dst, XArgs a,
-                                                      LineTab<T> tb, StencilDF S, double* norm_acc) {
+                                                      LineTab<T> tb, StencilDF S, double* norm_acc, DivArgs dv) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -65,6 +67,7 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
   const int line0 = blockIdx.x * nl;
   const float inv_ny = 1.0f / (float)S.n[1];
   float acc = 0.f;
+  const double dscale = (MODE == 3) ? dv.scale() : 0.0;
   // copy-in with U independent loads (or residual evaluations) in flight per thread
   constexpr int U = (MODE == 0) ? 8 : 2;
   const int total = nl * N;
@@ -80,6 +83,11 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
         const size_t c = (size_t)line * N + n;
         if (MODE == 0) {
           v[u] = from_double<T>(f[c]);
+        } else if (MODE == 3) {
+          const int k = (int)(((float)line + 0.5f) * inv_ny);
+          const double fv = dv.at(dscale, c, n, line - k * S.n[1], k);
+          if (dv.fout != nullptr) dv.fout[c] = fv;
+          v[u] = from_double<T>(fv);
         } else {
           // k = line / Ny, exact: (line + 1/2)/Ny stays >= 1/(2 Ny) away from an integer
           const int k = (int)(((float)line + 0.5f) * inv_ny);
@@ -366,15 +374,34 @@ StencilDF stencil_df(const cans_plan_s* P) {
 
 template <typename T, int MODE, int MC>
 static cudaError_t xfwd_m(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
-                          double* acc, cudaStream_t st) {
+                          double* acc, cudaStream_t st, const DivArgs* dv = nullptr) {
   const Launch& L = P->x_l[sizeof(T) == 8 ? 0 : 1];
   XArgs a{P->n[0], P->n[1] * P->n[2], L.lognl, 1.0, wlay(P, sizeof(T) == 4)};
   cudaError_t e = set_smem((const void*)xfwd_kernel<T, MODE, MC>, L.smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.nlines + L.nl - 1) / L.nl;
-  xfwd_kernel<T, MODE, MC><<<grid, L.threads, L.smem, st>>>(f, Phi, Plo, dst, a, tab_x<T>(P), stencil_df(P), acc);
+  xfwd_kernel<T, MODE, MC><<<grid, L.threads, L.smem, st>>>(f, Phi, Plo, dst, a, tab_x<T>(P), stencil_df(P), acc,
+                                                            dv != nullptr ? *dv : DivArgs{});
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_xfwd_div(const cans_plan_s* P, const DivArgs& d, T* dst, double* acc, cudaStream_t st) {
+  if (sizeof(T) == 4) {
+    bool handled = false;
+    const cudaError_t e = launch_xfwd_div_warp(P, d, reinterpret_cast<float*>(dst), acc, st, &handled);
+    if (handled) return e;
+  }
+  switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xfwd_m<T, 3, MM>(P, nullptr, nullptr, nullptr, dst, acc, st, &d);
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return xfwd_m<T, 3, 0>(P, nullptr, nullptr, nullptr, dst, acc, st, &d);
+  }
+}
+template cudaError_t launch_xfwd_div<double>(const cans_plan_s*, const DivArgs&, double*, double*, cudaStream_t);
+template cudaError_t launch_xfwd_div<float>(const cans_plan_s*, const DivArgs&, float*, double*, cudaStream_t);
 
 template <int MC>
 static cudaError_t xfwd_pipe_m(const cans_plan_s* P, const double* f, float* dst, double* acc, cudaStream_t st) {

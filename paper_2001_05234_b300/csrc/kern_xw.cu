@@ -53,6 +53,36 @@ struct SrcF {  // f (double) rounded to float; accumulates sum f^2
   }
 };
 
+struct SrcDiv {  // f formed from the face velocities (DivArgs) at (n, j, k), rounded to float; sum f^2
+  const DivArgs* d;
+  double s;     // the divergence's scale
+  size_t base;  // linear index of the line's first point
+  int j, k;
+  float acc;
+  // called by all 32 lanes together, as SrcF::pair
+  __device__ __forceinline__ float2 pair(int n) {
+    const size_t c = base + n;
+    const double x0 = d->at(s, c, n, j, k), x1 = d->at(s, c + 1, n + 1, j, k);
+    if (d->fout != nullptr) *reinterpret_cast<double2*>(d->fout + c) = make_double2(x0, x1);
+    bool oka, okb;
+    float a = d2f_rn_int(x0, &oka), b = d2f_rn_int(x1, &okb);
+    if (!__all_sync(0xffffffffu, oka && okb)) {
+      if (!oka) a = __double2float_rn(x0);
+      if (!okb) b = __double2float_rn(x1);
+    }
+    acc = __fmaf_rn(a, a, __fmaf_rn(b, b, acc));
+    return make_float2(a, b);
+  }
+  __device__ __forceinline__ float one(int n) {
+    const size_t c = base + n;
+    const double x = d->at(s, c, n, j, k);
+    if (d->fout != nullptr) d->fout[c] = x;
+    const float a = d2f_rn(x);
+    acc = __fmaf_rn(a, a, acc);
+    return a;
+  }
+};
+
 template <bool PLO>
 struct SrcRes {  // r = f - L_h(Phi + Plo) at (n, j, k); accumulates sum r^2
   const double* __restrict__ f;
@@ -110,6 +140,22 @@ struct SnkUpd {
   const float* sphi;  // the line's Phi (and Plo) staged in shared memory (MODE >= 2)
   const float* splo;
   size_t base;
+  // the update of one output value x at global offset o, its staged iterate values given (MODE >= 2)
+  __device__ __forceinline__ float upd_with(float x, float phi, float plo, size_t o, double& pd) {
+    const float d = x * scale;
+    if (MODE == 5) {
+      pd = f2d(phi) + f2d(d);
+      return 0.f;
+    }
+    df s2 = two_sum(phi, d);
+    s2 = fast_two_sum(s2.hi, (MODE <= 3) ? s2.lo + plo : s2.lo);
+    if (MODE == 2 || MODE == 4) {
+      Plo[o] = s2.lo;
+      return s2.hi;
+    }
+    pd = df_to_double(s2);
+    return 0.f;
+  }
   __device__ __forceinline__ float upd(size_t o, float x, double& pd) {
     const float d = x * scale;
     if (MODE == 0) {
@@ -151,10 +197,21 @@ struct SnkLine {
   SnkUpd<MODE>* u;
   size_t base;
   __device__ __forceinline__ void one(int n, float x) { u->one(base + n, x); }
-  __device__ __forceinline__ void pair(int n, float a, float b) {
+  __device__ __forceinline__ void pair(int n, float a, float b) {  // n even
     const size_t o = base + n;
     double pa = 0.0, pb = 0.0;
-    const float ha = u->upd(o, a, pa), hb = u->upd(o + 1, b, pb);
+    float ha, hb;
+    if (MODE >= 2) {
+      // the staged iterate as one 8-byte pair per lane: lanes hold consecutive pairs, so a warp's
+      // reads cover 256 contiguous bytes without bank conflicts
+      const float2 ph = *reinterpret_cast<const float2*>(u->sphi + n);
+      const float2 pl = (MODE <= 3) ? *reinterpret_cast<const float2*>(u->splo + n) : make_float2(0.f, 0.f);
+      ha = u->upd_with(a, ph.x, pl.x, o, pa);
+      hb = u->upd_with(b, ph.y, pl.y, o + 1, pb);
+    } else {
+      ha = u->upd(o, a, pa);
+      hb = u->upd(o + 1, b, pb);
+    }
     if (MODE == 0 || MODE == 3 || MODE == 5)
       *reinterpret_cast<double2*>(u->p + o) = make_double2(pa, pb);
     else
@@ -162,10 +219,13 @@ struct SnkLine {
   }
 };
 
+// MODE 0: f (double) -> float; 1, 2: the residual of a refinement sweep (Plo nonzero / zero);
+// 3: the divergence of a channel's face velocities (dv), formed on the fly
 template <int M, int BC, int MODE>
-__global__ void __launch_bounds__(32 * XW_WARPS, MODE == 0 ? 3 : 2)
+__global__ void __launch_bounds__(32 * XW_WARPS, (MODE == 0 || MODE == 3) ? 3 : 2)
     xfwd_w_kernel(const double* __restrict__ f, const float* __restrict__ Phi, const float* __restrict__ Plo,
-                  float* __restrict__ dst, int nlines, LineTab<float> tb, StencilDF S, double* norm_acc) {
+                  float* __restrict__ dst, int nlines, LineTab<float> tb, StencilDF S, double* norm_acc,
+                  DivArgs dv) {
   __shared__ float2 xbuf[XW_WARPS][M];
   constexpr int N = 2 * M;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -176,6 +236,11 @@ __global__ void __launch_bounds__(32 * XW_WARPS, MODE == 0 ? 3 : 2)
     SnkF snk{dst + base};
     if (MODE == 0) {
       SrcF src{f + base, 0.f};
+      wl::forward<M, BC>(wl::Plain{xb}, tb, lane, src, snk);
+      acc += src.acc;
+    } else if (MODE == 3) {
+      const int k = line / dv.ny;
+      SrcDiv src{&dv, dv.scale(), base, line - k * dv.ny, k, 0.f};
       wl::forward<M, BC>(wl::Plain{xb}, tb, lane, src, snk);
       acc += src.acc;
     } else {
@@ -273,10 +338,11 @@ int xw_grid(K kernel, int nlines) {
 
 template <int M, int BC, int MODE>
 cudaError_t xfwd_w(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst, double* acc,
-                   cudaStream_t st) {
+                   cudaStream_t st, const DivArgs* dv = nullptr) {
   const int nlines = P->n[1] * P->n[2];
   auto k = xfwd_w_kernel<M, BC, MODE>;
-  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(f, Phi, Plo, dst, nlines, P->tx_f, stencil_df(P), acc);
+  k<<<xw_grid(k, nlines), 32 * XW_WARPS, 0, st>>>(f, Phi, Plo, dst, nlines, P->tx_f, stencil_df(P), acc,
+                                                  dv != nullptr ? *dv : DivArgs{});
   return cudaGetLastError();
 }
 
@@ -330,6 +396,21 @@ cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float*
   XW_CASE(256)
   XW_CASE(512)
 #undef XW_CASE
+  *handled = false;
+  return cudaSuccess;
+}
+
+// the divergence source on the warp engine: periodic x lines (the channel) of the supported lengths
+cudaError_t launch_xfwd_div_warp(const cans_plan_s* P, const DivArgs& d, float* dst, double* acc, cudaStream_t st,
+                                 bool* handled) {
+  *handled = false;
+  if (P->wblk || P->bc[0] != BC_P || !aligned16(dst) || (d.fout != nullptr && !aligned16(d.fout)) ||
+      !aligned16(d.u) || !aligned16(d.v) || !aligned16(d.w))
+    return cudaSuccess;
+  *handled = true;
+  if (P->dx.m == 128) return xfwd_w<128, BC_P, 3>(P, nullptr, nullptr, nullptr, dst, acc, st, &d);
+  if (P->dx.m == 256) return xfwd_w<256, BC_P, 3>(P, nullptr, nullptr, nullptr, dst, acc, st, &d);
+  if (P->dx.m == 512) return xfwd_w<512, BC_P, 3>(P, nullptr, nullptr, nullptr, dst, acc, st, &d);
   *handled = false;
   return cudaSuccess;
 }

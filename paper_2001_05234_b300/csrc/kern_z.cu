@@ -3,6 +3,7 @@
 //   zpass_f64_kernel : double columns -- every column of the FP64 path, or the marked low-|mu|
 //                      columns of the mixed path (including the singular (0,0) mode), over the
 //                      bounding box of the marked columns only.
+#include <cstdlib>
 #include <mutex>
 
 #include "plan.cuh"
@@ -153,34 +154,82 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
 }
 
 // The float z pass fed by TMA, for full columns (Nz = 32 MMAX, MMAX >= 4) of a natural-layout work
-// field with Nx a multiple of 16.  Persistent CTAs (three per SM) walk tiles of 16 x-slots x Nz rows
+// field with Nx a multiple of 16.  Persistent CTAs (MINB per SM: 3 at 80 registers a thread, or 2 at
+// up to 128, which keeps the column-pair solve of 16 rows per lane free of spills) walk tiles of
+// 16 x-slots x Nz rows
 // of one y-slot, t = blockIdx.x, blockIdx.x + gridDim.x, ...  While the warps solve tile t, one
 // thread's tensor copy of tile t + gridDim.x lands in a raw staging buffer (its own mbarrier, bytes
 // counted), so each CTA always has its next 32 KB in flight; after the wait, the CTA moves the
 // staged rows into the bank-swizzled solve tile (ZSwz16), hands the staging buffer back to the copy
 // engine, solves, and stores the tile with 16-byte writes.  A copy that never lands (a bounded wait
 // running out) records CANS_ERR_TIMEOUT in the plan's status word and ends the CTA.
+// The register-staged float z pass (one 32-slot tile per CTA, as zpass_f32_kernel) with a tensor
+// prefetch into L2: CTA b (tiles numbered row by row) first asks TMA to bring tile b + ahead into L2
+// -- ahead is the number of CTAs resident at once, so that tile belongs to a CTA that starts about
+// when this one ends -- and its own 16-byte loads then mostly wait for L2 instead of DRAM.  The
+// prefetch has no shared-memory destination and nothing waits for it.
 template <int MMAX, bool PAIR>
-__global__ void __launch_bounds__(256, 3) zpass_tma_kernel(const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__(256, 3) zpass_pf_kernel(const __grid_constant__ CUtensorMap tm,
+                                                          float* __restrict__ w, ZArgs a, ZTab<float> zf,
+                                                          int ahead) {
+  constexpr int TI = 32, NZ = 32 * MMAX, BOXZ = NZ < 256 ? NZ : 256, NBOX = NZ / BOXZ;
+  constexpr bool CL = MMAX >= 4;
+  const int tn = (blockIdx.y * gridDim.x + blockIdx.x) + ahead;
+  if (threadIdx.x == 0 && tn < (int)(gridDim.x * gridDim.y)) {
+#pragma unroll
+    for (int b = 0; b < NBOX; ++b) tma_prefetch_l2_3d(&tm, (tn % gridDim.x) * TI, tn / gridDim.x, b * BOXZ);
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rs = 32 * (MMAX + 4);
+  float* sa = reinterpret_cast<float*>(smem_raw);
+  float* sb = sa + rs;
+  float* sc = sb + rs;
+  float* tile = sc + rs;
+  const int i0 = blockIdx.x * TI, j = blockIdx.y;
+  const size_t plane = (size_t)a.nx * a.ny;
+  float* col0 = w + (size_t)j * a.nx + i0;
+  const auto Z = make_zswz<TI, MMAX>(TI, MMAX);
+  stage_zrows<CL>(sa, sb, sc, zf, NZ, MMAX);
+  tile_load<float>(tile, col0, plane, Z, NZ, TI, true);
+  __syncthreads();
+  solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, TI, sa, sb, sc);
+  __syncthreads();
+  tile_store<float>(tile, col0, plane, Z, NZ, TI, true);
+}
+
+template <int TI, int MMAX>
+struct TmaSwz {
+  typedef ZSwz16<MMAX> type;
+};
+template <int MMAX>
+struct TmaSwz<32, MMAX> {
+  typedef ZSwz<32, MMAX> type;
+};
+
+template <int MMAX, bool PAIR, int MINB, int TI>
+__global__ void __launch_bounds__(16 * TI, MINB) zpass_tma_kernel(const __grid_constant__ CUtensorMap tm,
                                                            float* __restrict__ w, ZArgs a, ZTab<float> zf, int ntx,
                                                            int ntiles, unsigned wait_limit) {
-  constexpr int TI = 16, NZ = 32 * MMAX, BOXZ = NZ < 256 ? NZ : 256, NBOX = NZ / BOXZ;
+  constexpr int NT = 16 * TI;  // 8 warps for 16-slot tiles, 16 for 32-slot tiles: one pair per warp
+  constexpr int NZ = 32 * MMAX, BOXZ = NZ < 256 ? NZ : 256, NBOX = NZ / BOXZ;
+  constexpr int PR = TI / 4;  // 16-byte vectors per tile row
   constexpr uint32_t TILE_BYTES = TI * NZ * 4;
   constexpr int LS = MMAX + 4;
   static_assert(MMAX >= 4 && NZ % BOXZ == 0, "full columns of 128, 256 or 512 rows");
-  extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 128 bytes by hand below
-  unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-  float* stage = reinterpret_cast<float*>(base);
-  float* tile = reinterpret_cast<float*>(base + TILE_BYTES);
-  float* sa = tile + TI * NZ;
-  float* sb = sa + 32 * LS;
-  float* sc = sb + 32 * LS;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sc + 32 * LS);
+  // every buffer at a fixed offset from the 128-byte aligned dynamic shared array (the tensor copy's
+  // destination alignment), so no buffer address has to stay live in registers across the solve
+  extern __shared__ __align__(128) float ztma_smem[];
+  float* const stage = ztma_smem;
+  float* const tile = ztma_smem + TI * NZ;
+  float* const sa = tile + TI * NZ;
+  float* const sb = sa + 32 * LS;
+  float* const sc = sb + 32 * LS;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(sc + 32 * LS);
   const int tid = threadIdx.x;
   if (tid == 0) mbar_init(bar, 1);
   stage_zrows<true>(sa, sb, sc, zf, NZ, MMAX);
   __syncthreads();
-  const ZSwz16<MMAX> Z;
+  const typename TmaSwz<TI, MMAX>::type Z = {};
   auto issue = [&](int t) {
     const int tx = t % ntx, j = t / ntx;
     mbar_arrive_expect_tx(bar, TILE_BYTES);
@@ -189,7 +238,6 @@ __global__ void __launch_bounds__(256, 3) zpass_tma_kernel(const __grid_constant
   };
   int t = blockIdx.x;
   if (tid == 0 && t < ntiles) issue(t);
-  const size_t plane = (size_t)a.nx * a.ny;
   uint32_t parity = 0;
   for (; t < ntiles; t += gridDim.x) {
     const int tx = t % ntx, j = t / ntx, i0 = tx * TI;
@@ -204,8 +252,8 @@ __global__ void __launch_bounds__(256, 3) zpass_tma_kernel(const __grid_constant
     parity ^= 1u;
     const float4* src = reinterpret_cast<const float4*>(stage);
 #pragma unroll 4
-    for (int e = tid; e < NZ * TI / 4; e += 256) {
-      const int k = e >> 2, q = (e & 3) << 2;
+    for (int e = tid; e < NZ * PR; e += NT) {
+      const int k = e / PR, q = (e % PR) * 4;
       const float4 v = src[e];
       tile[Z.at(k, q)] = v.x;
       tile[Z.at(k, q + 1)] = v.y;
@@ -220,9 +268,10 @@ __global__ void __launch_bounds__(256, 3) zpass_tma_kernel(const __grid_constant
     solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, TI, sa, sb, sc);
     __syncthreads();
     float* col0 = w + (size_t)j * a.nx + i0;
+    const size_t plane = (size_t)a.nx * a.ny;
 #pragma unroll 4
-    for (int e = tid; e < NZ * TI / 4; e += 256) {
-      const int k = e >> 2, q = (e & 3) << 2;
+    for (int e = tid; e < NZ * PR; e += NT) {
+      const int k = e / PR, q = (e % PR) * 4;
       float4 v;
       v.x = tile[Z.at(k, q)];
       v.y = tile[Z.at(k, q + 1)];
@@ -345,9 +394,58 @@ bool ztma_feasible(const cans_plan_s* P, const void* w) {
 
 constexpr unsigned kTmaWaitLimit = 1u << 20;  // polls of one copy's barrier (~0.3 s) before a timeout
 
-template <int MMAX>
+template <int MMAX, int MINB, int TI>
 static cudaError_t ztma_m(const cans_plan_s* P, float* w, cudaStream_t st) {
-  constexpr int TI = 16, NZ = 32 * MMAX;
+  constexpr int NZ = 32 * MMAX;
+  const int nx = P->n[0], ny = P->n[1];
+  CUtensorMap tm;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NZ};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {TI, 1, (cuuint32_t)(NZ < 256 ? NZ : 256)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  // box rows are 64 bytes: no promotion to 128-byte L2 lines (their other half belongs to the
+  // neighbouring tile, which another CTA reads at another time)
+  CUtensorMapL2promotion prom = CU_TENSOR_MAP_L2_PROMOTION_NONE;
+  if (const char* ev = std::getenv("CANS_Z_TMA_L2")) prom = ev[0] == '1' ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                       : (ev[0] == '6' ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B : prom);
+  if (encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, w, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, prom,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  ZArgs a = zargs(P, TI, nullptr, nullptr);
+  a.mask = P->mask_d;
+  const bool pair = P->bc[0] == BC_P;  // Nx is even: every 16-slot tile holds whole Re / Im pairs
+  auto kern = pair ? zpass_tma_kernel<MMAX, true, MINB, TI> : zpass_tma_kernel<MMAX, false, MINB, TI>;
+  const size_t smem = 2 * (size_t)TI * NZ * 4 + 3 * 32 * (MMAX + 4) * 4 + 16;
+  cudaError_t e = set_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
+  // persistent grid: every resident CTA slot of the device (cached per device and kernel)
+  static std::mutex lock;
+  static int cached[16][2] = {};  // per device and pair flag, for this instantiation
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  {
+    std::lock_guard<std::mutex> g(lock);
+    int& c = cached[dev & 15][pair ? 1 : 0];
+    if (c == 0) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kern, 16 * TI, smem)) != cudaSuccess) return e;
+      c = c < 1 ? 1 : c;
+    }
+    per_sm = c;
+  }
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int ntx = nx / TI, ntiles = ntx * ny;
+  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
+  kern<<<grid, 16 * TI, smem, st>>>(tm, w, a, P->zt_f, ntx, ntiles, kTmaWaitLimit);
+  return cudaGetLastError();
+}
+
+// shape variants: 1 = one 512-thread CTA per SM on 32-slot tiles (128-byte rows), 2 / 3 = two or
+// three 256-thread CTAs per SM on 16-slot tiles
+template <int MMAX>
+static cudaError_t zpf_m(const cans_plan_s* P, float* w, cudaStream_t st) {
+  constexpr int TI = 32, NZ = 32 * MMAX;
   const int nx = P->n[0], ny = P->n[1];
   CUtensorMap tm;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)NZ};
@@ -355,22 +453,20 @@ static cudaError_t ztma_m(const cans_plan_s* P, float* w, cudaStream_t st) {
   const cuuint32_t box[3] = {TI, 1, (cuuint32_t)(NZ < 256 ? NZ : 256)};
   const cuuint32_t estr[3] = {1, 1, 1};
   if (encode_tiled()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, w, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   ZArgs a = zargs(P, TI, nullptr, nullptr);
   a.mask = P->mask_d;
-  const bool pair = P->bc[0] == BC_P;  // Nx is even: every 16-slot tile holds whole Re / Im pairs
-  auto kern = pair ? zpass_tma_kernel<MMAX, true> : zpass_tma_kernel<MMAX, false>;
-  const size_t smem = 2 * (size_t)TI * NZ * 4 + 3 * 32 * (MMAX + 4) * 4 + 16 + 128;
+  const bool pair = P->bc[0] == BC_P;
+  auto kern = pair ? zpass_pf_kernel<MMAX, true> : zpass_pf_kernel<MMAX, false>;
+  const size_t smem = 3 * 32 * (MMAX + 4) * 4 + (size_t)TI * NZ * 4;
   cudaError_t e = set_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
-  // persistent grid: every resident CTA slot of the device (cached per device and kernel)
   static std::mutex lock;
   static int cached[16][2] = {};
-  int dev = 0;
+  int dev = 0, per_sm = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  int per_sm = 0, sms = 0;
   {
     std::lock_guard<std::mutex> g(lock);
     int& c = cached[dev & 15][pair ? 1 : 0];
@@ -381,17 +477,24 @@ static cudaError_t ztma_m(const cans_plan_s* P, float* w, cudaStream_t st) {
     per_sm = c;
   }
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int ntx = nx / TI, ntiles = ntx * ny;
-  const int grid = ntiles < per_sm * sms ? ntiles : per_sm * sms;
-  kern<<<grid, 256, smem, st>>>(tm, w, a, P->zt_f, ntx, ntiles, kTmaWaitLimit);
+  dim3 grid(nx / TI, ny);
+  kern<<<grid, 256, smem, st>>>(tm, w, a, P->zt_f, per_sm * sms);
   return cudaGetLastError();
+}
+
+template <int MMAX>
+static cudaError_t ztma_v(const cans_plan_s* P, float* w, cudaStream_t st) {
+  if (P->z_tma_ctas == 4 && P->n[0] % 32 == 0) return zpf_m<MMAX>(P, w, st);
+  if (P->z_tma_ctas == 1 && P->n[0] % 32 == 0) return ztma_m<MMAX, 1, 32>(P, w, st);
+  if (P->z_tma_ctas == 3) return ztma_m<MMAX, 3, 16>(P, w, st);
+  return ztma_m<MMAX, 2, 16>(P, w, st);
 }
 
 static cudaError_t launch_ztma(const cans_plan_s* P, float* w, cudaStream_t st) {
   switch (P->z_mmax) {
-    case 4: return ztma_m<4>(P, w, st);
-    case 8: return ztma_m<8>(P, w, st);
-    default: return ztma_m<16>(P, w, st);
+    case 4: return ztma_v<4>(P, w, st);
+    case 8: return ztma_v<8>(P, w, st);
+    default: return ztma_v<16>(P, w, st);
   }
 }
 

@@ -49,6 +49,31 @@ struct WLay {
   __device__ __forceinline__ size_t zstride() const { return blk ? (size_t)nbx * ny * 32 : (size_t)nx * ny; }
 };
 
+// The right-hand side of Eq. poi_ns formed from the face velocities of a channel (x, y periodic, w = 0
+// on both wall faces): f = s (dxi (u_i - u_{i-1}) + dyi (v_j - v_{j-1}) + dzfi_k (w_k - w_{k-1})) with
+// s = num / (gamma dt), dt read on the device (s = num when dt is NULL).  The fused multiply-adds are
+// spelled out, so the stand-alone divergence kernel and the x pass that forms f on the fly produce the
+// same bits (and the FP64 operation count stays at seven per point).
+struct DivArgs {
+  const double *u, *v, *w;
+  double* fout;  // optional: f written as a by-product (the mixed refinement's residual reads it)
+  const double* dzfi;
+  const double* dt;
+  double num, gamma, dxi, dyi;
+  int nx, ny, nz;
+  __device__ __forceinline__ double scale() const { return dt != nullptr ? num / (gamma * (*dt)) : num; }
+  // f at cell (i, j, k), linear index c
+  __device__ __forceinline__ double at(double s, size_t c, int i, int j, int k) const {
+    const size_t im = (i == 0) ? c + (size_t)(nx - 1) : c - 1;
+    const size_t jm = (j == 0) ? c + (size_t)(ny - 1) * nx : c - (size_t)nx;
+    const double wt = (k < nz - 1) ? w[c] : 0.0;
+    const double wb = (k >= 1) ? w[c - (size_t)nx * ny] : 0.0;
+    const double t = __fma_rn(__dsub_rn(u[c], u[im]), dxi,
+                              __fma_rn(__dsub_rn(v[c], v[jm]), dyi, __dmul_rn(__dsub_rn(wt, wb), dzfi[k])));
+    return __dmul_rn(s, t);
+  }
+};
+
 struct XArgs {
   int nx, nlines, lognl;
   double scale;  // inverse only
@@ -115,8 +140,14 @@ struct cans_plan_s {
   double idx2, idy2;
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
-  int z_tma = 1;  // float z pass: 1 the TMA-fed persistent kernel where the shape allows it, 0 never,
-                  // 2 required (shapes it cannot take fail)
+  int z_tma = 0;  // float z pass: 0 the register-staged kernel; 1 a TMA-using variant (z_tma_ctas)
+                  // where the shape allows it; 2 required (shapes it cannot take fail).  The
+                  // autotuner times the staged kernel against the variants and keeps the fastest.
+  int z_tma_ctas = 4;  // TMA kernel shape: 4 = the persistent register-staged kernel with a tensor
+                       // prefetch of each CTA's next tile into L2 (three CTAs per SM, 32-slot tiles);
+                       // 1 = tiles copied into shared memory by TMA, one 512-thread CTA per SM,
+                       // 32-slot tiles; 2 / 3 = two (128 registers) or three (80) 256-thread CTAs
+                       // per SM, 16-slot tiles
   size_t z_smem[2];
   int wblk = 0;  // mixed path: work field in the blocked layout
   // per-pass event records (cans_plan_profile)
@@ -169,6 +200,11 @@ inline WLay wlay(const cans_plan_s* P, bool working_float) {
 template <typename T, int MODE>
 cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, T* dst,
                         double* acc, cudaStream_t st);
+// forward x-pass whose input is the divergence of a channel's face velocities (DivArgs), formed on the fly
+template <typename T>
+cudaError_t launch_xfwd_div(const cans_plan_s* P, const DivArgs& d, T* dst, double* acc, cudaStream_t st);
+DivArgs div_args(const cans_plan_s* P, const double* u, const double* v, const double* w, double* fout, double num,
+                 const double* dt, double gamma);
 template <typename T, int MODE>
 cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Phi, float* Plo, double scale,
                         double* gauge, cudaStream_t st);
@@ -215,6 +251,8 @@ Launch line_launch_shape(int N, int count, size_t elem2, int prefer_nl);
 template <int MODE>
 cudaError_t launch_xfwd_warp(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, float* dst,
                              double* acc, cudaStream_t st, bool* handled);
+cudaError_t launch_xfwd_div_warp(const cans_plan_s* P, const DivArgs& d, float* dst, double* acc, cudaStream_t st,
+                                 bool* handled);
 cudaError_t launch_scale_z(const cans_plan_s* P, const double* in, double* out, const double* wz, cudaStream_t st);
 cudaError_t launch_remove_weighted_mean(const cans_plan_s* P, double* f, double* acc2, cudaStream_t st);
 cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,

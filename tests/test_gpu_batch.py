@@ -141,3 +141,39 @@ def test_solve_batched_device_status_flags_nonfinite(cans):
     for q in (0, 1, 3):
         assert float((out[q] - ref[q]).abs().max()) <= 1e-13 * float(ref[q].abs().max())
     b.close()
+
+
+def test_solve_batched_one_call_replays_from_a_graph(cans):
+    """The one-call batched solve takes its internal streams from a per-device pool created by the first
+    call, so a later call can be captured into a CUDA graph; replays give the eager results and the
+    per-problem status."""
+    import torch
+
+    cases = I.ensemble_cases(count=5, sizes=(16, 32, 48))
+    fs = [torch.from_numpy(I.rhs_host(c)).cuda() for c in cases]
+    b = cans.Batch(cases, prec=cans.CANS_MIXED, sweeps=2, nstreams=4)
+    nbytes = cans.cans_poisson_batched_workspace_size(b.plans)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    status = torch.full((len(cases),), 99, dtype=torch.int32, device="cuda")
+    ref = [torch.empty_like(f) for f in fs]
+    out = [torch.full_like(f, float("nan")) for f in fs]
+    # eager first (creates the pool outside any capture)
+    assert cans.cans_poisson_solve_batched(b.plans, [t.data_ptr() for t in fs], [t.data_ptr() for t in ref], base,
+                                           torch.cuda.current_stream().cuda_stream, status.data_ptr()) == 0
+    torch.cuda.synchronize()
+    status.fill_(99)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=s):
+        rc = cans.cans_poisson_solve_batched(b.plans, [t.data_ptr() for t in fs], [t.data_ptr() for t in out], base,
+                                             s.cuda_stream, status.data_ptr())
+    assert rc == 0
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [0] * len(cases)
+    for a, e in zip(out, ref):
+        assert torch.equal(a, e)
+    b.close()

@@ -1,13 +1,14 @@
-"""The TMA-fed float z pass against the register-staged one and the oracle.
+"""The TMA-using float z kernels against the register-staged one and the oracle.
 
-Both kernels run the same per-column arithmetic (zsolve_pair / zsolve_column on a bank-swizzled tile)
-and differ only in how tiles reach shared memory (a tensor copy into a staging buffer on an mbarrier,
-persistent CTAs, 16-slot tiles, against register-staged 16-byte loads) and in the swizzle, so mixed
-solves through either must agree bit for bit; the TMA solve must also match the oracle (Eq.
-poi_reduced) to the mixed path's bound.  CANS_Z_TMA=2 makes a plan fail rather than fall back, so
-these cases are known to run the TMA kernel; the shapes cover 4, 8 and 16 rows per lane, column pairs
-(x periodic) and single columns, FP64 low-|mu| columns inside TMA tiles, and more tiles than resident
-CTAs (each CTA walks several tiles through its copy pipeline).
+All variants run the same per-column arithmetic (zsolve_pair / zsolve_column on a bank-swizzled tile)
+and differ only in how tiles reach shared memory: the register-staged kernel with a tensor prefetch
+of a later tile into L2 (shape 4), or a tensor copy into a staging buffer on an mbarrier with
+persistent CTAs -- one 512-thread CTA per SM on 32-slot tiles (shape 1), two or three 256-thread CTAs
+on 16-slot tiles (2, 3).  Mixed solves through any of them must agree bit for bit with the
+register-staged kernel, and match the oracle (Eq. poi_reduced) to the mixed path's bound.
+CANS_Z_TMA=2 makes a plan fail rather than fall back, so these cases are known to run the chosen
+kernel; the shapes cover 4, 8 and 16 rows per lane, column pairs (x periodic) and single columns,
+FP64 low-|mu| columns inside the tiles (whose stores skip them), and more tiles than resident CTAs.
 """
 import numpy as np
 import pytest
@@ -38,10 +39,14 @@ def cans():
     return C
 
 
+# 4: the register-staged kernel with the TMA prefetch of a later tile into L2; 1: tiles copied by TMA,
+# one 512-thread CTA per SM (32-slot tiles); 2, 3: two or three 256-thread CTAs per SM (16-slot tiles)
+@pytest.mark.parametrize("shape", ["4", "1", "2", "3"])
 @pytest.mark.parametrize("n,bc", SHAPES)
-def test_tma_z_pass_matches_staged_kernel_bitwise_and_oracle(cans, monkeypatch, n, bc):
+def test_tma_z_pass_matches_staged_kernel_bitwise_and_oracle(cans, monkeypatch, n, bc, shape):
     import torch
 
+    monkeypatch.setenv("CANS_Z_TMA_CTAS", shape)
     case = I.case_modes(n=n)
     case.bc = bc
     case.length_xy = (n[0] / 1024, n[1] / 1024)  # the bench's spacing
