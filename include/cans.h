@@ -398,6 +398,37 @@ int cans_project_adjoint(cans_plan_t plan, double* u, double* v, double* w, void
 int cans_poisson_solve_noalloc(cans_plan_t plan, const double* f, double* p, void* cuda_stream, double* info);
 size_t cans_noalloc_scratch_bytes(void);
 
+/*
+ * z-slab decomposition of one solve over several GPUs (the paper's Implementation section distributes
+ * the grid over GPUs).  Rank r of P owns the z rows z0 .. z1-1 of the whole problem (all of x and y):
+ * its x-y transforms are local (cans_transform_xy with a plan of the slab's shape), and only the
+ * tridiagonal systems along z (Eq. poi_reduced) cross the slab boundaries:
+ *   1. cans_zslab_eliminate: Thomas' forward sweep over the slab, each interior row expressed through
+ *      the previous slab's last unknown and the slab's own last one; per (x, y) column 10 numbers go to
+ *      `iface` (ncol x 10 doubles), and the slab's part of the singular (0,0) column to `col00` (nzs
+ *      doubles, used when the problem is singular).
+ *   2. the caller gathers every rank's `iface` (rank-major: P x ncol x 10 doubles) and `col00` (the
+ *      slabs' parts in rank order: Nz doubles) on every rank (an all-gather; NCCL for GPUs).
+ *   3. cans_zslab_finish: the reduced tridiagonal system of the P slabs' last rows (one per column, the
+ *      system the warp-level partitioned solve forms across lanes), solved on every rank, then the
+ *      slab's back substitution, the result times `scale` (1/(Nx Ny) undoes the transforms' factor);
+ *      the singular column is solved whole from the gathered right-hand side, with the compatible
+ *      projection and zero weighted mean of cans_poisson_solve.
+ *   plan   : the whole problem's FP64 plan (Neumann, Dirichlet or mixed z walls; z_grid 0; a periodic
+ *            or mixed-precision plan gives CANS_ERR_UNSUPPORTED).  Kept by the caller.
+ *   field  : the slab's transformed field, Nx*Ny*(z1-z0) doubles, solved in place.
+ *   workspace : cans_zslab_sizes() bytes, 256-byte aligned, kept between the two calls.
+ * Asynchronous on cuda_stream.  All in FP64; P <= 64.
+ */
+typedef struct cans_zslab_s* cans_zslab_t;
+int cans_zslab_create(cans_plan_t plan, int z0, int z1, cans_zslab_t* out);
+int cans_zslab_sizes(cans_zslab_t slab, size_t* workspace_bytes, size_t* iface_doubles, size_t* col00_doubles);
+int cans_zslab_eliminate(cans_zslab_t slab, double* field, double* iface, double* col00, void* workspace,
+                         void* cuda_stream);
+int cans_zslab_finish(cans_zslab_t slab, double* field, const double* iface_all, const double* col00_all, int nranks,
+                      int rank, double scale, void* workspace, void* cuda_stream);
+int cans_zslab_destroy(cans_zslab_t slab);
+
 /* Host copies of the per-slot eigenvalue terms lam_x(i)/dx^2 (length Nx) and lam_y(j)/dy^2
  * (length Ny) the plan uses; either pointer may be NULL. */
 int cans_plan_eigenvalues(cans_plan_t plan, double* mu_x, double* mu_y);

@@ -64,6 +64,12 @@ def lib() -> ctypes.CDLL:
         L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_plan_status.argtypes = [vp, ip]
+        L.cans_zslab_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
+        L.cans_zslab_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t)]
+        L.cans_zslab_eliminate.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.cans_zslab_finish.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp]
+        L.cans_zslab_destroy.argtypes = [vp]
         L.cans_poisson_solve_divergence.argtypes = [vp, vp, vp, vp, ctypes.c_double, vp, ctypes.c_double, vp, vp,
                                                     vp, vp, dp]
         L.cans_poisson_adjoint_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -258,6 +264,32 @@ def cans_poisson_solve_divergence(plan, u: int, v: int, w: int, scale: float, dt
     return lib().cans_poisson_solve_divergence(plan, u, v, w, float(scale), dt_ptr or None, float(gamma), f_ptr or None,
                                                p_ptr, workspace_ptr or None, stream_ptr or None,
                                                _dptr(info) if info is not None else None)
+
+
+def cans_zslab_create(plan, z0: int, z1: int):
+    h = ctypes.c_void_p()
+    _check(lib().cans_zslab_create(plan, int(z0), int(z1), ctypes.byref(h)), "cans_zslab_create")
+    return h
+
+
+def cans_zslab_sizes(slab):
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().cans_zslab_sizes(slab, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "cans_zslab_sizes")
+    return int(a.value), int(b.value), int(c.value)
+
+
+def cans_zslab_eliminate(slab, field: int, iface: int, col00: int, workspace: int, stream_ptr: int) -> int:
+    return lib().cans_zslab_eliminate(slab, field, iface, col00, workspace, stream_ptr or None)
+
+
+def cans_zslab_finish(slab, field: int, iface_all: int, col00_all: int, nranks: int, rank: int, scale: float,
+                      workspace: int, stream_ptr: int) -> int:
+    return lib().cans_zslab_finish(slab, field, iface_all, col00_all or None, int(nranks), int(rank), float(scale),
+                                   workspace, stream_ptr or None)
+
+
+def cans_zslab_destroy(slab) -> int:
+    return lib().cans_zslab_destroy(slab)
 
 
 def cans_plan_status(plan) -> int:
