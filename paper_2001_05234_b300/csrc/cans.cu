@@ -420,6 +420,12 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   const size_t o_acc = B.add(zeros.data(), P->nacc * 8);
   const int status0 = CANS_OK;
   const size_t o_status = B.add(&status0, sizeof(int));
+  // slots of the reproducible block sums (gauge, bulk velocity): every grid that sums has at most one
+  // block per x line, or at most 148 * 16 blocks
+  P->dsum_nslots = std::max<size_t>((size_t)n[1] * n[2], (size_t)148 * 16);
+  const size_t o_dsum = B.add(std::vector<double>(P->dsum_nslots, 0.0).data(), P->dsum_nslots * sizeof(double));
+  const unsigned count0 = 0;
+  const size_t o_dcount = B.add(&count0, sizeof(unsigned));
   {
     double w2 = 0;
     for (int k = 0; k < nz; ++k) w2 += dz[k] * dz[k];
@@ -478,6 +484,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
   }
   P->acc_d = reinterpret_cast<double*>(base + o_acc);
   P->status_d = reinterpret_cast<int*>(base + o_status);
+  P->dsum_slots = reinterpret_cast<double*>(base + o_dsum);
+  P->dsum_count = reinterpret_cast<unsigned*>(base + o_dcount);
 
   // launch shapes
   const int nlines = n[1] * nz;
@@ -497,9 +505,11 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->z_ti[s] = ti;
     P->z_smem[s] = (size_t)ti * nz * es;
   }
-  // CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the TMA kernel
-  // cannot take fail instead of falling back (switches for comparisons and tests; the autotuner, when
-  // on, chooses between the two kernels by timing)
+  // CANS_RES_PTS=1/2/4 sets the residual stencil's points per thread (a switch for comparisons and
+  // tests).  CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the
+  // TMA kernel cannot take fail instead of falling back (switches for comparisons and tests; the
+  // autotuner, when on, chooses between the two kernels by timing)
+  if (const char* ev = std::getenv("CANS_RES_PTS")) P->res_pts = (ev[0] == '1') ? 1 : (ev[0] == '2' ? 2 : 4);
   if (const char* ev = std::getenv("CANS_Z_TMA")) P->z_tma = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_Z_TMA_CTAS"))
     P->z_tma_ctas = (ev[0] >= '1' && ev[0] <= '4') ? ev[0] - '0' : P->z_tma_ctas;

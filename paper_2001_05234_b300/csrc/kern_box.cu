@@ -220,7 +220,7 @@ __global__ void box_correct_kernel(BoxG g, const double* __restrict__ us, const 
                                    const double* __restrict__ ws, const double* __restrict__ phi,
                                    double* __restrict__ u, double* __restrict__ v, double* __restrict__ w,
                                    double* __restrict__ p, double gamma, const double* __restrict__ dt_dev,
-                                   double* bulk) {
+                                   DetSum bulk) {
   const size_t N = (size_t)g.n[0] * g.n[1] * g.n[2];
   const double f = gamma * (*dt_dev);
   double acc = 0.0;
@@ -243,10 +243,7 @@ __global__ void box_correct_kernel(BoxG g, const double* __restrict__ us, const 
     p[c] += phi[c];
     acc += g.dzf[k] * un;
   }
-  if (bulk != nullptr) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(bulk, acc);
-  }
+  if (bulk.out != nullptr) det_sum_finish(block_sum_d(acc), bulk);
 }
 
 template <int WX, int WY, int WZ>
@@ -350,8 +347,8 @@ int box_step(const cans_plan_s* P, double* u, double* v, double* w, double* p, c
     double* bulk = prm->forcing ? small + 1 : nullptr;
     {
       PassTimer tm(PM, CANS_PASS_CORRECT, st);
-      if (bulk) BOX_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
-      box_correct_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gm, dt, bulk);
+      if ((size_t)G > PM->dsum_nslots) return CANS_ERR_CUDA;
+      box_correct_kernel<WX, WY, WZ><<<G, 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gm, dt, plan_sum(PM, bulk));
     }
     if (bulk) {
       PassTimer tm(PM, CANS_PASS_FORCING, st);

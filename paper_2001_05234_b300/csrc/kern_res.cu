@@ -334,10 +334,192 @@ __global__ void __launch_bounds__(R2X * R2Y, 3) res2_kernel(const double* __rest
   }
 }
 
+// Four x-consecutive points per thread (nx a multiple of 4, f 16-byte and the float fields 16-byte
+// aligned): Phi, Plo, r and the y neighbours move as float4, f as two double2; the address, loop and
+// ghost work of a plane is shared by four points.  Same arithmetic per point as res_kernel.
+constexpr int R4X = 32, R4Y = 8;  // threads of a CTA; a thread owns points i .. i + 3
+
+template <int PM, int BX, int BY, int BZ>
+__global__ void __launch_bounds__(R4X * R4Y, 2) res4_kernel(const double* __restrict__ f, const float* __restrict__ Phi,
+                                                         const float* __restrict__ Plo, float* __restrict__ r,
+                                                         StencilDF S, int kchunk, double* norm_acc) {
+  constexpr bool PLO = (PM & 1) != 0, SHIFT = (PM & 2) != 0;
+  __shared__ float4 zc[64];  // (c_k hi, c_k lo, a_k hi, a_k lo) of the chunk's planes
+  const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
+  const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
+  for (int q = threadIdx.y * R4X + threadIdx.x; q < k1 - k0; q += R4X * R4Y)
+    zc[q] = make_float4(S.sc_hi[k0 + q], S.sc_lo[k0 + q], S.sa_hi[k0 + q], S.sa_lo[k0 + q]);
+  __syncthreads();
+  const int i = 4 * (blockIdx.x * R4X + threadIdx.x), j = blockIdx.y * R4Y + threadIdx.y;
+  float acc = 0.f;
+  if (i < nx && j < ny) {  // nx is a multiple of 4, so i + 3 < nx as well
+    const int sz = nx * ny;
+    const int im = (i == 0) ? nx - 1 : i - 1, ip = (i + 4 == nx) ? 0 : i + 4;  // outer x neighbours
+    const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+    const bool gxm = BX != BC_P && i == 0, gxp = BX != BC_P && i + 4 == nx;
+    const bool gym = BY != BC_P && j == 0, gyp = BY != BC_P && j == ny - 1;
+    const float sxm = (BX == BC_NN) ? 1.f : (BX == BC_DD) ? -1.f : ((S.xlo == BC_NN) ? 1.f : -1.f);
+    const float sxp = (BX == BC_NN) ? 1.f : (BX == BC_DD) ? -1.f : ((S.xhi == BC_NN) ? 1.f : -1.f);
+    const float sym = (BY == BC_NN) ? 1.f : (BY == BC_DD) ? -1.f : ((S.ylo == BC_NN) ? 1.f : -1.f);
+    const float syp = (BY == BC_NN) ? 1.f : (BY == BC_DD) ? -1.f : ((S.yhi == BC_NN) ? 1.f : -1.f);
+    const float zsl = (BZ == BC_NN) ? 1.f : (BZ == BC_DD) ? -1.f : ((S.zlo == BC_NN) ? 1.f : -1.f);
+    const float zsh = (BZ == BC_NN) ? 1.f : (BZ == BC_DD) ? -1.f : ((S.zhi == BC_NN) ? 1.f : -1.f);
+    const int c0 = j * nx + i;
+    const int dxm = im - i, dxp = ip - i, dym = (jm - j) * nx, dyp = (jp - j) * nx;
+    const int kprev = (k0 == 0) ? nz - 1 : k0 - 1;
+    const float* pp = Phi + (size_t)k0 * sz + c0;
+    const double* fp = f + (size_t)k0 * sz + c0;
+    float* rp = r + (size_t)k0 * sz + c0;
+    auto ld4 = [](const float* a) { return *reinterpret_cast<const float4*>(a); };
+    float4 p_cur = ld4(pp);
+    const bool zwall0 = BZ != BC_P && k0 == 0;
+    df dm[4];
+    {
+      const float4 pv = ld4(Phi + (size_t)kprev * sz + c0);
+      const float pvs[4] = {pv.x, pv.y, pv.z, pv.w}, pcs[4] = {p_cur.x, p_cur.y, p_cur.z, p_cur.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dm[e] = two_sum(zwall0 ? zsl * pcs[e] : pvs[e], -pcs[e]);  // Phi_{k-1} - Phi_k
+    }
+    const float* qp = PLO ? Plo + (size_t)k0 * sz + c0 : nullptr;
+    float4 q_prev = make_float4(0.f, 0.f, 0.f, 0.f), q_cur = q_prev;
+    if (PLO) {
+      q_prev = ld4(Plo + (size_t)kprev * sz + c0);
+      q_cur = ld4(qp);
+    }
+    // ring of the next PF planes' f and Phi_{k+1} (loads issued PF planes ahead of their use)
+    constexpr int PF = 2;
+    double2 fa[PF], fb[PF];
+    float4 pr[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int k = k0 + u;
+      if (k < k1) {
+        fa[u] = *reinterpret_cast<const double2*>(fp + (size_t)u * sz);
+        fb[u] = *reinterpret_cast<const double2*>(fp + (size_t)u * sz + 2);
+        pr[u] = (k == nz - 1) ? ld4(Phi + c0) : ld4(pp + (size_t)(u + 1) * sz);  // periodic wrap
+      }
+    }
+    float nxm = pp[dxm], nxp = pp[dxp];
+    float4 nym = ld4(pp + dym), nyp = ld4(pp + dyp);
+    // r at one point from its six neighbours (Phi part, double-float); dm: Phi_{k-1} - Phi_k in,
+    // Phi_k - Phi_{k+1} out
+    auto point = [&](float xm, float xp, float ym, float yp, float pc, float zp, df& dmv, const float4& co,
+                     double fk) {
+      const df dp = two_sum(zp, -pc);
+      df L;
+      if (S.iso) {
+        const df sx = two_sum(xm, xp);
+        const df sy = two_sum(ym, yp);
+        const df s2 = two_sum(sx.hi, sy.hi);
+        const df d = two_sum(s2.hi, -4.f * pc);
+        L = df_prod(S.idx2, df_make(d.hi, __fadd_rn(d.lo, __fadd_rn(s2.lo, __fadd_rn(sx.lo, sy.lo)))));
+      } else {
+        L = df_prod(S.idx2, second_difference(xm, xp, pc));
+        L = df_add_prod(L, S.idy2, second_difference(ym, yp, pc));
+      }
+      L = df_add_prod(L, df_make(co.x, co.y), dp);
+      L = df_add_prod(L, df_make(co.z, co.w), dmv);
+      if (SHIFT) L = df_add_prod(L, S.shift, df_make(pc, 0.f));
+      const df fs = df_split_rz(fk);
+      dmv = df_make(-dp.hi, -dp.lo);
+      return __fadd_rn(__fsub_rn(fs.hi, L.hi), __fsub_rn(fs.lo, L.lo));
+    };
+    for (int kb = k0; kb < k1; kb += PF) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int k = kb + u;
+        if (k < k1) {
+          const bool top = (k == nz - 1);
+          const float4 p_next = pr[u];
+          const double2 f01 = fa[u], f23 = fb[u];
+          if (k + PF < k1) {
+            fa[u] = *reinterpret_cast<const double2*>(fp + (size_t)PF * sz);
+            fb[u] = *reinterpret_cast<const double2*>(fp + (size_t)PF * sz + 2);
+            pr[u] = (k + PF == nz - 1) ? ld4(Phi + c0) : ld4(pp + (size_t)(PF + 1) * sz);
+          }
+          const float pcs[4] = {p_cur.x, p_cur.y, p_cur.z, p_cur.w};
+          const float yms[4] = {nym.x, nym.y, nym.z, nym.w}, yps[4] = {nyp.x, nyp.y, nyp.z, nyp.w};
+          const float zps[4] = {p_next.x, p_next.y, p_next.z, p_next.w};
+          const float xl = gxm ? sxm * p_cur.x : nxm;
+          const float xr = gxp ? sxp * p_cur.w : nxp;
+          if (k + 1 < k1) {
+            nxm = pp[sz + dxm];
+            nxp = pp[sz + dxp];
+            nym = ld4(pp + sz + dym);
+            nyp = ld4(pp + sz + dyp);
+          }
+          const bool ztop = BZ != BC_P && top;
+          const float4 co = zc[k - k0];
+          const double fks[4] = {f01.x, f01.y, f23.x, f23.y};
+          float rr[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float c = pcs[e];
+            const float xm = (e == 0) ? xl : pcs[(e + 3) & 3];
+            const float xp = (e == 3) ? xr : pcs[(e + 1) & 3];
+            const float ym = gym ? sym * c : yms[e];
+            const float yp = gyp ? syp * c : yps[e];
+            const float zp = ztop ? zsh * c : zps[e];
+            rr[e] = point(xm, xp, ym, yp, c, zp, dm[e], co, fks[e]);
+          }
+          if (PLO) {
+            const long long dzp = top ? -(long long)(nz - 1) * sz : (long long)sz;
+            const float4 q_next = ld4(qp + dzp);
+            const float4 qym4 = ld4(qp + dym), qyp4 = ld4(qp + dyp);
+            const float qcs[4] = {q_cur.x, q_cur.y, q_cur.z, q_cur.w};
+            const float qyms[4] = {qym4.x, qym4.y, qym4.z, qym4.w}, qyps[4] = {qyp4.x, qyp4.y, qyp4.z, qyp4.w};
+            const float qzms[4] = {q_prev.x, q_prev.y, q_prev.z, q_prev.w};
+            const float qzps[4] = {q_next.x, q_next.y, q_next.z, q_next.w};
+            const float qxl = gxm ? sxm * q_cur.x : qp[dxm];
+            const float qxr = gxp ? sxp * q_cur.w : qp[dxp];
+            const bool zbot = BZ != BC_P && k == 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float c = qcs[e];
+              const float qxm = (e == 0) ? qxl : qcs[(e + 3) & 3];
+              const float qxp = (e == 3) ? qxr : qcs[(e + 1) & 3];
+              const float qym = gym ? sym * c : qyms[e];
+              const float qyp = gyp ? syp * c : qyps[e];
+              const float qzm = zbot ? zsl * c : qzms[e];
+              const float qzp = ztop ? zsh * c : qzps[e];
+              rr[e] -= S.idx2.hi * (qxm + qxp - 2.f * c) + S.idy2.hi * (qym + qyp - 2.f * c) + co.x * (qzp - c) +
+                       co.z * (qzm - c) + (SHIFT ? S.shift.hi * c : 0.f);
+            }
+            q_prev = q_cur;
+            q_cur = q_next;
+            qp += sz;
+          }
+          *reinterpret_cast<float4*>(rp) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+          acc = __fmaf_rn(rr[0], rr[0], __fmaf_rn(rr[1], rr[1], __fmaf_rn(rr[2], rr[2], __fmaf_rn(rr[3], rr[3], acc))));
+          p_cur = p_next;
+          pp += sz;
+          fp += sz;
+          rp += sz;
+        }
+      }
+    }
+  }
+  if (norm_acc != nullptr) {
+    __shared__ float red[R4X * R4Y / 32];
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+    const int t = threadIdx.y * R4X + threadIdx.x;
+    if ((t & 31) == 0) red[t >> 5] = acc;
+    __syncthreads();
+    if (t == 0) {
+      float s = 0.f;
+      for (int w = 0; w < R4X * R4Y / 32; ++w) s += red[w];
+      atomicAdd(norm_acc, (double)s);
+    }
+  }
+}
+
 template <int PLO, int BX, int BY, int BZ>
 cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi, const float* Plo, float* r,
-                       const StencilDF& S, int kchunk, double* acc, cudaStream_t st, bool pairs) {
-  if (pairs)
+                       const StencilDF& S, int kchunk, double* acc, cudaStream_t st, int pts) {
+  if (pts == 4)
+    res4_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
+  else if (pts == 2)
     res2_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
   else
     res_kernel<PLO, BX, BY, BZ><<<grid, block, 0, st>>>(f, Phi, Plo, r, S, kchunk, acc);
@@ -346,7 +528,7 @@ cudaError_t res_launch(dim3 grid, dim3 block, const double* f, const float* Phi,
 
 template <int PLO, int BX, int BY>
 cudaError_t res_bz(int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
-                   const StencilDF& S, int kc, double* acc, cudaStream_t st, bool pr) {
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st, int pr) {
   if (bz == BC_P) return res_launch<PLO, BX, BY, BC_P>(g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (bz == BC_NN) return res_launch<PLO, BX, BY, BC_NN>(g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (bz == BC_DD) return res_launch<PLO, BX, BY, BC_DD>(g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
@@ -354,7 +536,7 @@ cudaError_t res_bz(int bz, dim3 g, dim3 b, const double* f, const float* Phi, co
 }
 template <int PLO, int BX>
 cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
-                   const StencilDF& S, int kc, double* acc, cudaStream_t st, bool pr) {
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st, int pr) {
   if (by == BC_P) return res_bz<PLO, BX, BC_P>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (by == BC_NN) return res_bz<PLO, BX, BC_NN>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (by == BC_DD) return res_bz<PLO, BX, BC_DD>(bz, g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
@@ -362,7 +544,7 @@ cudaError_t res_by(int by, int bz, dim3 g, dim3 b, const double* f, const float*
 }
 template <int PLO>
 cudaError_t res_bx(const int* bc, dim3 g, dim3 b, const double* f, const float* Phi, const float* Plo, float* r,
-                   const StencilDF& S, int kc, double* acc, cudaStream_t st, bool pr) {
+                   const StencilDF& S, int kc, double* acc, cudaStream_t st, int pr) {
   if (bc[0] == BC_P) return res_by<PLO, BC_P>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (bc[0] == BC_NN) return res_by<PLO, BC_NN>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
   if (bc[0] == BC_DD) return res_by<PLO, BC_DD>(bc[1], bc[2], g, b, f, Phi, Plo, r, S, kc, acc, st, pr);
@@ -377,21 +559,29 @@ cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* 
   const int kchunk = std::min(nz, 64);  // at most the 64 planes whose z coefficients a CTA stages
   dim3 grid((nx + RX - 1) / RX, (ny + RY - 1) / RY, (nz + kchunk - 1) / kchunk);
   dim3 block(RX, RY);
-  // two points per thread where nx is even and the vector accesses are aligned
-  const bool pairs = nx % 2 == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0 &&
-                     ((reinterpret_cast<uintptr_t>(Phi) | reinterpret_cast<uintptr_t>(r) |
-                       (plo ? reinterpret_cast<uintptr_t>(Plo) : 0)) & 7) == 0;
-  if (pairs) {
+  // four (or two) points per thread where nx allows and the vector accesses are aligned
+  const uintptr_t fl = reinterpret_cast<uintptr_t>(Phi) | reinterpret_cast<uintptr_t>(r) |
+                       (plo ? reinterpret_cast<uintptr_t>(Plo) : 0);
+  const bool f16 = (reinterpret_cast<uintptr_t>(f) & 15) == 0;
+  int pts = 1;
+  if (P->res_pts >= 4 && nx % 4 == 0 && f16 && (fl & 15) == 0)
+    pts = 4;
+  else if (P->res_pts >= 2 && nx % 2 == 0 && f16 && (fl & 7) == 0)
+    pts = 2;
+  if (pts == 4) {
+    grid.x = (nx / 4 + R4X - 1) / R4X;
+    block = dim3(R4X, R4Y);
+  } else if (pts == 2) {
     grid.x = (nx / 2 + R2X - 1) / R2X;
     block = dim3(R2X, R2Y);
   }
   const StencilDF S = stencil_df(P);
   const int pm = (plo ? 1 : 0) | (S.shift.hi != 0.f ? 2 : 0);
   switch (pm) {
-    case 0: return res_bx<0>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pairs);
-    case 1: return res_bx<1>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pairs);
-    case 2: return res_bx<2>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pairs);
-    default: return res_bx<3>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pairs);
+    case 0: return res_bx<0>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pts);
+    case 1: return res_bx<1>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pts);
+    case 2: return res_bx<2>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pts);
+    default: return res_bx<3>(P->bc, grid, block, f, Phi, Plo, r, S, kchunk, norm_acc, st, pts);
   }
 }
 

@@ -276,14 +276,14 @@ __global__ void divergence_kernel(Chan g, const double* __restrict__ u, const do
 }
 
 // u = u* - gamma dt G Phi (Eq. poi_ns correction), p += Phi when p != nullptr, and the dzf-weighted
-// sum of the new u into *bulk (for the constant-flow-rate forcing).  Adjoint use (weighted): the
+// sum of the new u into *bulk.out (for the constant-flow-rate forcing; a reproducible block sum).  Adjoint use (weighted): the
 // gradient is multiplied by the face weight.
 // Crank-Nicolson diffusion (Eq. up_id_2): p += Phi + lcoef L_p Phi with lcoef = -gamma nu dt/2 and L_p
 // the pressure Laplacian (periodic x, y; Neumann walls).
 __global__ void correct_kernel(Chan g, const double* __restrict__ us, const double* __restrict__ vs,
                                const double* __restrict__ ws, const double* __restrict__ phi, double* __restrict__ u,
                                double* __restrict__ v, double* __restrict__ w, double* __restrict__ p, double gamma,
-                               const double* __restrict__ dt_dev, int weighted, double* bulk, double lcoef) {
+                               const double* __restrict__ dt_dev, int weighted, DetSum bulk, double lcoef) {
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   const double f = (dt_dev != nullptr) ? gamma * (*dt_dev) : 1.0;
   double acc = 0.0;
@@ -317,10 +317,7 @@ __global__ void correct_kernel(Chan g, const double* __restrict__ us, const doub
     }
     acc += g.dzf[k] * un;
   }
-  if (bulk != nullptr) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(bulk, acc);
-  }
+  if (bulk.out != nullptr) det_sum_finish(block_sum_d(acc), bulk);
 }
 
 // u += ubulk - <u>_V with <u>_V = bulk / (Nx Ny sum dzf)
@@ -446,7 +443,10 @@ cudaError_t launch_correct(const cans_plan_s* P, const double* us, const double*
                            const double* dt_dev, int weighted, double* bulk, cudaStream_t st, double lcoef) {
   const Chan g = chan(P);
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  correct_kernel<<<grid_for(N), 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gamma, dt_dev, weighted, bulk, lcoef);
+  const int grid = grid_for(N);
+  if ((size_t)grid > P->dsum_nslots) return cudaErrorInvalidConfiguration;
+  correct_kernel<<<grid, 256, 0, st>>>(g, us, vs, ws, phi, u, v, w, p, gamma, dt_dev, weighted, plan_sum(P, bulk),
+                                       lcoef);
   return cudaGetLastError();
 }
 
@@ -560,7 +560,6 @@ int cans_rk3_step(cans_plan_t P, double* u, double* v, double* w, double* p, con
     double* bulk = prm->forcing ? small + 1 : nullptr;
     {
       PassTimer tm(P, CANS_PASS_CORRECT, st);
-      if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
       RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st));
     }
     if (bulk) {
@@ -649,7 +648,6 @@ int cans_rk3_step_implicit(cans_plan_t P, cans_plan_t U, cans_plan_t W, double* 
     double* bulk = prm->forcing ? small + 1 : nullptr;
     {
       PassTimer tm(P, CANS_PASS_CORRECT, st);
-      if (bulk) RK_CK(cudaMemsetAsync(bulk, 0, sizeof(double), st));
       RK_CK(launch_correct(P, us, vs, ws, phi, u, v, w, p, g, dt, 0, bulk, st, -h));
     }
     if (bulk) {

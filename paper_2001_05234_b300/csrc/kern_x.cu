@@ -32,22 +32,6 @@ __device__ __forceinline__ void block_accumulate(float v, double* dst) {
   }
 }
 
-__device__ __forceinline__ void block_accumulate_d(double v, double* dst) {
-  __shared__ double redd[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) redd[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    v = (lane < (int)(blockDim.x >> 5)) ? redd[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) atomicAdd(dst, v);
-  }
-}
-
 // Forward x-pass.  MODE 0: read f (double) -> T.  MODE 1 (T = float): the residual
 // f - L_h(Phi + Plo) computed on the fly; MODE 2: the same with Plo known to be zero (first sweep).
 // MODE 3: f formed on the fly as the divergence of a channel's face velocities (dv), written to
@@ -126,14 +110,15 @@ __global__ void __launch_bounds__(512, 2) xfwd_kernel(const double* __restrict__
 }
 
 // Inverse x-pass.  MODE 0: p (double) = scale * x.  MODE 1: Phi = scale * x (the iterate's tail Plo
-// is implicitly zero), and (when gauge != nullptr) sum_c dzf_k Phi_c into *gauge.
+// is implicitly zero), and (when gauge.out != nullptr) sum_c dzf_k Phi_c into *gauge.out (a reproducible
+// block sum).
 // MODE 2: (Phi, Plo) += scale * x (double-float).  MODE 3: p = Phi + Plo + scale * x (double).
 // MODE 4, 5: as 2, 3 with the old Plo known to be zero (first sweep).
 template <typename T, int MODE, int MC>
 __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src, double* __restrict__ p,
                                                       float* __restrict__ Phi, float* __restrict__ Plo, XArgs a,
                                                       LineTab<T> tb, const float* __restrict__ wz,
-                                                      const float* __restrict__ wz_lo, int ny, double* gauge) {
+                                                      const float* __restrict__ wz_lo, int ny, DetSum gauge) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -186,7 +171,7 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
     } else if (MODE == 1) {
       const float ph = (float)v * (float)a.scale;
       Phi[o] = ph;
-      if (gauge != nullptr) {
+      if (gauge.out != nullptr) {
         const int k = line / ny;
         df t = two_prod(ph, wz[k]);  // ph * dzf_k with dzf_k = wz + wz_lo (double-float weight)
         t.lo = __fmaf_rn(ph, wz_lo[k], t.lo);
@@ -204,7 +189,7 @@ __global__ void __launch_bounds__(512, 2) xinv_kernel(const T* __restrict__ src,
       }
     }
   }
-  if (MODE == 1 && gauge != nullptr) block_accumulate_d((double)gacc.hi + (double)gacc.lo, gauge);
+  if (MODE == 1 && gauge.out != nullptr) det_sum_finish(block_sum_d((double)gacc.hi + (double)gacc.lo), gauge);
 }
 
 // ---- pipelined x-passes -------------------------------------------------------------------------
@@ -277,7 +262,7 @@ __global__ void __launch_bounds__(512, 2) xinv_pipe_kernel(const T* __restrict__
                                                            float* __restrict__ Phi, float* __restrict__ Plo,
                                                            int nlines, int lognl, double scale, LineTab<T> tb,
                                                            const float* __restrict__ wz,
-                                                           const float* __restrict__ wz_lo, int ny, double* gauge) {
+                                                           const float* __restrict__ wz_lo, int ny, DetSum gauge) {
   typedef typename V2<T>::t C;
   constexpr int N = 2 * MC, PAD = 16 / sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -313,7 +298,7 @@ __global__ void __launch_bounds__(512, 2) xinv_pipe_kernel(const T* __restrict__
       } else if (MODE == 1) {
         const float ph = (float)v * fscale;
         Phi[o] = ph;
-        if (gauge != nullptr) {
+        if (gauge.out != nullptr) {
           const int k = line / ny;
           df tt = two_prod(ph, wz[k]);
           tt.lo = __fmaf_rn(ph, wz_lo[k], tt.lo);
@@ -334,7 +319,7 @@ __global__ void __launch_bounds__(512, 2) xinv_pipe_kernel(const T* __restrict__
     line_inverse_fused<MAXV, T, MC, true>(buf, L, lognl, tb, loadslot, store);
     __syncthreads();
   }
-  if (MODE == 1 && gauge != nullptr) block_accumulate_d((double)gacc.hi + (double)gacc.lo, gauge);
+  if (MODE == 1 && gauge.out != nullptr) det_sum_finish(block_sum_d((double)gacc.hi + (double)gacc.lo), gauge);
 }
 
 template <typename K>
@@ -428,7 +413,9 @@ cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi,
         launch_xfwd_warp<MODE>(P, f, Phi, Plo, reinterpret_cast<float*>(dst), acc, st, &handled);
     if (handled) return e;
   }
-  if (MODE == 0 && sizeof(T) == 4 && !P->wblk) {
+  // the pipelined kernel stages f with 16-byte copies: f must be 16-byte aligned (lines of N doubles
+  // with N even then all are); a double array that is only 8-byte aligned takes the kernel below
+  if (MODE == 0 && sizeof(T) == 4 && !P->wblk && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
     switch (P->dx.m) {
 #define CASE_M(MM) \
   case MM: return xfwd_pipe_m<MM>(P, f, reinterpret_cast<float*>(dst), acc, st);
@@ -454,8 +441,9 @@ static cudaError_t xinv_m(const cans_plan_s* P, const T* src, double* p, float* 
   cudaError_t e = set_smem((const void*)xinv_kernel<T, MODE, MC>, L.smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.nlines + L.nl - 1) / L.nl;
+  if ((size_t)grid > P->dsum_nslots) return cudaErrorInvalidConfiguration;
   xinv_kernel<T, MODE, MC><<<grid, L.threads, L.smem, st>>>(src, p, Phi, Plo, a, tab_x<T>(P), P->dzf_f,
-                                                            P->dzf_flo, P->n[1], gauge);
+                                                            P->dzf_flo, P->n[1], plan_sum(P, gauge));
   return cudaGetLastError();
 }
 
@@ -473,8 +461,9 @@ static cudaError_t xinv_pipe_m(const cans_plan_s* P, const T* src, double* p, fl
   if (e != cudaSuccess) return e;
   const int nlines = P->n[1] * P->n[2];
   const int grid = persistent_grid(xinv_pipe_kernel<T, MODE, MC>, L.threads, smem, (nlines + L.nl - 1) / L.nl);
+  if ((size_t)grid > P->dsum_nslots) return cudaErrorInvalidConfiguration;
   xinv_pipe_kernel<T, MODE, MC><<<grid, L.threads, smem, st>>>(src, p, Phi, Plo, nlines, L.lognl, scale, tab_x<T>(P),
-                                                               P->dzf_f, P->dzf_flo, P->n[1], gauge);
+                                                               P->dzf_f, P->dzf_flo, P->n[1], plan_sum(P, gauge));
   return cudaGetLastError();
 }
 
@@ -487,7 +476,9 @@ cudaError_t launch_xinv(const cans_plan_s* P, const T* src, double* p, float* Ph
                                                  st, &handled);
     if (handled) return e;
   }
-  if (!(sizeof(T) == 4 && P->wblk)) {
+  // the pipelined kernel stages src with 16-byte copies (src is the caller's p in place on the FP64
+  // path, which may be only 8-byte aligned)
+  if (!(sizeof(T) == 4 && P->wblk) && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
     switch (P->dx.m) {
 #define CASE_M(MM) \
   case MM: return xinv_pipe_m<T, MODE, MM>(P, src, p, Phi, Plo, scale, gauge, st);

@@ -279,17 +279,17 @@ template <int M, int BC, int MODE>
 __global__ void __launch_bounds__(32 * XW_WARPS, upd_reads<MODE>() == 2 ? 2 : 3)
     xinv_w_kernel(const float* __restrict__ src, double* __restrict__ p, float* __restrict__ Phi,
                   float* __restrict__ Plo, int nlines, float scale, LineTab<float> tb, const float* __restrict__ wz,
-                  const float* __restrict__ wz_lo, int ny, double* gauge) {
+                  const float* __restrict__ wz_lo, int ny, DetSum gauge) {
   constexpr int N = 2 * M, NR = upd_reads<MODE>();
   extern __shared__ __align__(16) unsigned char xw_smem[];  // [XW_WARPS][M] float2, then [XW_WARPS][NR N] float
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float2* xb = reinterpret_cast<float2*>(xw_smem) + wid * M;
   float* stg = reinterpret_cast<float*>(xw_smem + (size_t)XW_WARPS * M * sizeof(float2)) + (size_t)wid * NR * N;
-  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge != nullptr, df_make(0.f, 0.f), df_make(0.f, 0.f),
+  SnkUpd<MODE> u{p, Phi, Plo, scale, df_make(0.f, 0.f), gauge.out != nullptr, df_make(0.f, 0.f), df_make(0.f, 0.f),
                  stg, stg + (NR == 2 ? N : 0), 0};
   for (int line = blockIdx.x * XW_WARPS + wid; line < nlines; line += gridDim.x * XW_WARPS) {
     const size_t base = (size_t)line * N;
-    if (MODE == 1 && gauge != nullptr) {
+    if (MODE == 1 && gauge.out != nullptr) {
       const int k = line / ny;
       u.gw = df_make(wz[k], wz_lo[k]);
     }
@@ -306,24 +306,12 @@ __global__ void __launch_bounds__(32 * XW_WARPS, upd_reads<MODE>() == 2 ? 2 : 3)
     SnkLine<MODE> out{&u, base};
     wl::inverse<M, BC, true>(wl::Plain{xb}, tb, lane, in, out);
     if (NR > 0) __syncwarp();  // the staged iterate is read before the next line overwrites it
-    if (MODE == 1 && gauge != nullptr) {  // the line's dzf_k-weighted share of the gauge sum
+    if (MODE == 1 && gauge.out != nullptr) {  // the line's dzf_k-weighted share of the gauge sum
       u.gacc = df_add(u.gacc, df_mul(u.lacc, u.gw));
       u.lacc = df_make(0.f, 0.f);
     }
   }
-  if (MODE == 1 && gauge != nullptr) {
-    __shared__ double red[XW_WARPS];
-    double v = (double)u.gacc.hi + (double)u.gacc.lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < XW_WARPS; ++w) s += red[w];
-      atomicAdd(gauge, s);
-    }
-  }
+  if (MODE == 1 && gauge.out != nullptr) det_sum_finish(block_sum_d((double)u.gacc.hi + (double)u.gacc.lo), gauge);
 }
 
 template <typename K>
@@ -359,8 +347,9 @@ cudaError_t xinv_w(const cans_plan_s* P, const float* src, double* p, float* Phi
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::max(1, std::min((nlines + XW_WARPS - 1) / XW_WARPS, std::max(per_sm, 1) * sms));
+  if ((size_t)grid > P->dsum_nslots) return cudaErrorInvalidConfiguration;
   k<<<grid, 32 * XW_WARPS, smem, st>>>(src, p, Phi, Plo, nlines, (float)scale, P->tx_f, P->dzf_f, P->dzf_flo, P->n[1],
-                                        gauge);
+                                        plan_sum(P, gauge));
   return cudaGetLastError();
 }
 

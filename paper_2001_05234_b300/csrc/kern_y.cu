@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(512, 2) ypass_pipe_kernel(T* __restrict__ w, i
       for (int e = threadIdx.x; e < NY * nl; e += blockDim.x) {
         const int n = e >> lognl, l = e & (nl - 1);
         if (i0 + l < nx)
-          cp_async4(dst + e, plane + (size_t)n * rs + l);
+          cp_async_elem(dst + e, plane + (size_t)n * rs + l);
         else
           dst[e] = (T)0;
       }

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "cans.h"
+#include "detsum.cuh"
 #include "dfloat.cuh"
 #include "lines.cuh"
 #include "zsolve.cuh"
@@ -136,10 +137,14 @@ struct cans_plan_s {
                                        // [nacc-5] gauge sum, [nacc-4..] reports
   int nacc = 0;
   int* status_d = nullptr;             // device status word (cans_plan_status)
+  double* dsum_slots = nullptr;        // per-block slots of the reproducible sums (detsum.cuh) ...
+  unsigned* dsum_count = nullptr;      // ... and their arrival counter
+  size_t dsum_nslots = 0;              // slots: one per x line, at least 148 * 16 (every grid that sums)
   double compat_scale = 0;             // sqrt(Nx Ny sum_k dzf_k^2): |sum w f| <= compat_scale ||f||_2
   double idx2, idy2;
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
+  int res_pts = 4;  // residual stencil: points per thread (4, 2 or 1; fewer where nx or alignment demand)
   int z_tma = 0;  // float z pass: 0 the register-staged kernel; 1 a TMA-using variant (z_tma_ctas)
                   // where the shape allows it; 2 required (shapes it cannot take fail).  The
                   // autotuner times the staged kernel against the variants and keeps the fastest.
@@ -194,6 +199,15 @@ inline WLay wlay(const cans_plan_s* P, bool working_float) {
   w.ny = P->n[1];
   w.nbx = (P->n[0] + 31) / 32;
   return w;
+}
+
+// The plan's reproducible block sum (detsum.cuh) into *out (nullptr: no sum).
+inline DetSum plan_sum(const cans_plan_s* P, double* out) {
+  DetSum d;
+  d.slots = P->dsum_slots;
+  d.count = P->dsum_count;
+  d.out = out;
+  return d;
 }
 
 // pass launchers (each in its own translation unit)
