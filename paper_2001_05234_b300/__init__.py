@@ -600,12 +600,13 @@ class Batch:
     """Many independent Poisson problems solved in one asynchronous call (cans_batch_*).
     cases: objects with .n, .bc, .length_xy, .dzf (e.g. inputs.PoissonCase)."""
 
-    def __init__(self, cases, prec=CANS_MIXED, sweeps=2, nstreams=8):
+    def __init__(self, cases, prec=CANS_MIXED, sweeps=2, nstreams=8, autotune=False):
         self.cases = list(cases)
         self.plans = []
         for c in self.cases:
             o = cans_opts_default()
             o.prec, o.max_sweeps = int(prec), int(sweeps)
+            o.autotune = 1 if autotune else 0
             self.plans.append(cans_poisson_plan(c.n, c.length_xy, c.bc, c.dzf, o)[1])
         self.batch = cans_batch_create(self.plans, nstreams)
         self._ws_buf, self._ws = _aligned_workspace(cans_batch_workspace_size(self.batch))
