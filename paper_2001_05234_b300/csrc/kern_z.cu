@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <mutex>
 
+#include "async.cuh"
 #include "plan.cuh"
 #include "tma.cuh"
 
@@ -151,6 +152,65 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, ncols, sa, sb, sc);
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
+}
+
+// The float z pass on pair-granular tiles (ZSwzP) for a periodic x direction: full columns
+// (Nz = 32 MMAX, MMAX >= 4), tiles of 32 x-slots of a natural-layout field.  The tile arrives by
+// 8-byte cp.async copies straight into its swizzled place -- a CTA has all 64 KB of its tile in
+// flight at once and holds no registers for it -- and each column pair is solved by zsolve_pair2,
+// with both right-hand sides of a row in one 8-byte word.  Same arithmetic per column as
+// zpass_f32_kernel (bit-identical results); slot 0 and 1 of x and the columns the plan marks for the
+// double kernel are handled as there.
+template <int MMAX>
+__global__ void __launch_bounds__(256, 3) zpass_p2_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, WLay wl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TI = 32, rs = 32 * (MMAX + 4);
+  float* sa = reinterpret_cast<float*>(smem_raw);
+  float* sb = sa + rs;
+  float* sc = sb + rs;
+  float* tile = sc + rs;
+  const int i0 = blockIdx.x * TI, j = blockIdx.y;
+  const size_t plane = wl.zstride();
+  float* col0 = w + wl.zbase(i0, j);
+  const ZSwzP<MMAX> Z;
+  {  // thread t copies pair t & 15 of rows (t >> 4) + 16 u
+    const int p2 = 2 * (threadIdx.x & 15);
+    for (int k = threadIdx.x >> 4; k < 32 * MMAX; k += blockDim.x >> 4)
+      cp_async8(tile + Z.at(k, p2), col0 + (size_t)k * plane + p2);
+    cp_async_commit();
+  }
+  stage_zrows<true>(sa, sb, sc, zf, a.nz, MMAX);
+  cp_async_wait<0>();
+  __syncthreads();
+  {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float muy = a.muy_f[j] + (float)a.shift;
+    for (int q = warp; q < TI / 2; q += nwarps) {
+      const int c0 = 2 * q, i = i0 + c0;
+      const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
+      const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
+      if (i == 0 || m0 || m1) {  // slots 0 and 1 (X_0, X_M) differ; a marked column goes to the double kernel
+        if (!m0)
+          zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0, Z, a.nz, a.mux_f[i] + muy, sa,
+                                                                            sb, sc, nullptr, 0.f);
+        if (!m1)
+          zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0 + 1, Z, a.nz,
+                                                                            a.mux_f[i + 1] + muy, sa, sb, sc,
+                                                                            nullptr, 0.f);
+      } else {
+        zsolve_pair2<MMAX>(tile, c0, Z, a.mux_f[i] + muy, sa, sb, sc);
+      }
+    }
+  }
+  __syncthreads();
+  {  // thread t writes floats 4 (t & 7) .. 4 (t & 7) + 3 of rows (t >> 3) + 32 u
+    const int q = 4 * (threadIdx.x & 7);
+    for (int k = threadIdx.x >> 3; k < 32 * MMAX; k += blockDim.x >> 3) {
+      const float2 lo = *reinterpret_cast<const float2*>(tile + Z.at(k, q));
+      const float2 hi = *reinterpret_cast<const float2*>(tile + Z.at(k, q + 2));
+      *reinterpret_cast<float4*>(col0 + (size_t)k * plane + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+  }
 }
 
 // The float z pass fed by TMA, for full columns (Nz = 32 MMAX, MMAX >= 4) of a natural-layout work
@@ -512,6 +572,20 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
       if (e != cudaSuccess || part == 0) return e;
     } else if (part != 1 && P->z_tma == 2) {
       return cudaErrorNotSupported;  // the TMA kernel was required and cannot take this shape
+    } else if (part != 1 && MMAX >= 4 && TIC == 32 && P->z_p2 && P->bc[0] == BC_P && P->n[2] == 32 * MMAX &&
+               P->n[0] % 32 == 0 && !wl.blk && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+      // pair-granular tiles fetched by cp.async (periodic x, full columns, whole 32-slot tiles)
+      if constexpr (MMAX >= 4) {
+        ZArgs a = zargs(P, 32, gauge, nullptr);
+        a.mask = P->mask_d;
+        const size_t smem = 3 * 32 * (MMAX + 4) * sizeof(float) + (size_t)32 * 32 * MMAX * sizeof(float);
+        e = set_smem((const void*)zpass_p2_kernel<MMAX>, smem);
+        if (e != cudaSuccess) return e;
+        zpass_p2_kernel<MMAX><<<dim3(P->n[0] / 32, P->n[1]), 256, smem, st>>>(reinterpret_cast<float*>(w), a,
+                                                                              P->zt_f, wl);
+        e = cudaGetLastError();
+        if (e != cudaSuccess || part == 0) return e;
+      }
     } else if (part != 1) {
       ZArgs a = zargs(P, P->z_ti[1], gauge, nullptr);
       a.mask = P->mask_d;

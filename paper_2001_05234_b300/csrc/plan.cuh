@@ -145,6 +145,7 @@ struct cans_plan_s {
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
   int res_pts = 4;  // residual stencil: points per thread (4, 2 or 1; fewer where nx or alignment demand)
+  int z_p2 = 1;    // float z pass of a periodic x on full columns: pair-granular cp.async tiles (0: off)
   int z_tma = 0;  // float z pass: 0 the register-staged kernel; 1 a TMA-using variant (z_tma_ctas)
                   // where the shape allows it; 2 required (shapes it cannot take fail).  The
                   // autotuner times the staged kernel against the variants and keeps the fastest.

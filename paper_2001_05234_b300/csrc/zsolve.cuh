@@ -75,6 +75,21 @@ struct ZSwz16 {
   __device__ __forceinline__ int at(int k, int i) const { return at(k, i, k >> SH); }
 };
 
+// Pair-granular 32-wide tiles (the column pairs 2p, 2p+1 of a periodic x direction stay adjacent: one
+// 8-byte word per row and pair).  The pair index is XOR-ed with the low four bits of the owning lane's
+// segment and with k & 3, so the 16 lanes of each half-warp's 8-byte accesses of one pair reach 16
+// distinct bank pairs; a 4-byte access of one column from all 32 lanes meets 2-way conflicts (lanes l
+// and l + 16).  M_ rows per lane (a power of two).
+template <int M_>
+struct ZSwzP {
+  static constexpr int SH = ZSwz<>::ilog2_c(M_);
+  __device__ __forceinline__ int ti() const { return 32; }
+  __device__ __forceinline__ int at(int k, int i, int sg) const {
+    return k * 32 + ((((i >> 1) ^ ((sg ^ (k & 3)) & 15)) << 1) | (i & 1));
+  }
+  __device__ __forceinline__ int at(int k, int i) const { return at(k, i, k >> SH); }
+};
+
 template <int TI_ = 0, int M_ = 0>
 __device__ __forceinline__ ZSwz<TI_, M_> make_zswz(int TI, int m) {
   ZSwz<TI_, M_> s;
@@ -480,6 +495,156 @@ __device__ __forceinline__ void zsolve_pair(T* tile, int col0, int col1, const Z
       tile[Z.at(k0 + r, col0, lane)] = cvt<T>(x0);
       t1(k0 + r) = cvt<T>(x1);
     }
+  }
+}
+
+// zsolve_pair on the pair-granular layout (ZSwzP), float, full columns (Nz = 32 MMAX, MMAX >= 4,
+// lane-contiguous coefficient rows): the two right-hand sides of a row move as one 8-byte word, and
+// both columns' forward values go back into the tile, so only the pivot and spike sequences stay in
+// registers.  The arithmetic is zsolve_pair's, operation for operation.
+template <int MMAX, typename ZS>
+__device__ __forceinline__ void zsolve_pair2(float* tile, int col0, const ZS& Z, float mu, const float* sa,
+                                             const float* sb, const float* sc) {
+  const int lane = threadIdx.x & 31;
+  constexpr int m = MMAX;
+  static_assert(MMAX >= 4, "four or more rows per lane");
+  constexpr int LS = MMAX + 4;
+  float4 A4, B4, C4;
+  auto coefs = [&](int r, float& a, float& b, float& c) {
+    if ((r & 3) == 0) {
+      A4 = *reinterpret_cast<const float4*>(sa + lane * LS + r);
+      B4 = *reinterpret_cast<const float4*>(sb + lane * LS + r);
+      C4 = *reinterpret_cast<const float4*>(sc + lane * LS + r);
+    }
+    a = f4_get(A4, r & 3);
+    b = f4_get(B4, r & 3);
+    c = f4_get(C4, r & 3);
+  };
+  const int k0 = lane * m;
+  const unsigned full = 0xffffffffu;
+  auto row = [&](int k) -> float2* { return reinterpret_cast<float2*>(tile + Z.at(k, col0, lane)); };
+  float cp[MMAX], lp[MMAX];
+  float rr = 0.f, cprev = 0.f, lprev = 0.f, d0prev = 0.f, d1prev = 0.f;
+#pragma unroll
+  for (int r = 0; r < m - 1; ++r) {
+    const int k = k0 + r;
+    float a, b, c;
+    coefs(r, a, b, c);
+    b += mu;
+    const float2 d = *row(k);
+    const float inv = rcp_(b - a * cprev);
+    const bool last_inner = (r == m - 2);
+    cp[r] = last_inner ? 0.f : c * inv;
+    if (last_inner) rr = -c * inv;
+    const float dp0r = (d.x - a * d0prev) * inv;
+    const float dp1r = (d.y - a * d1prev) * inv;
+    *row(k) = make_float2(dp0r, dp1r);
+    lp[r] = ((r == 0) ? -a : -a * lprev) * inv;
+    cprev = c * inv;
+    d0prev = dp0r;
+    d1prev = dp1r;
+    lprev = lp[r];
+  }
+  float Dl0, Dl1, Vl, Wl, Df0, Df1, Vf, Wf;
+  {
+    float D0 = 0.f, D1 = 0.f, V = 0.f, W = 0.f;
+#pragma unroll
+    for (int r = m - 2; r >= 0; --r) {
+      const float2 dr = *row(k0 + r);
+      if (r == m - 2) {
+        D0 = dr.x;
+        D1 = dr.y;
+        V = lp[r];
+        W = rr;
+        Dl0 = D0;
+        Dl1 = D1;
+        Vl = V;
+        Wl = W;
+      } else {
+        D0 = dr.x - cp[r] * D0;
+        D1 = dr.y - cp[r] * D1;
+        V = lp[r] - cp[r] * V;
+        W = -cp[r] * W;
+      }
+    }
+    Df0 = D0;
+    Df1 = D1;
+    Vf = V;
+    Wf = W;
+  }
+  const int kl = k0 + m - 1;
+  constexpr int rl = m - 1;
+  float al, bl, cl;
+  if ((rl & 3) != 0) {  // the last row's group of four was loaded by the forward loop
+    al = f4_get(A4, rl & 3);
+    bl = f4_get(B4, rl & 3);
+    cl = f4_get(C4, rl & 3);
+  } else {
+    coefs(rl, al, bl, cl);
+  }
+  bl += mu;
+  const float2 dl = *row(kl);
+  const float Dfn0 = __shfl_down_sync(full, Df0, 1);
+  const float Dfn1 = __shfl_down_sync(full, Df1, 1);
+  const float Vfn = __shfl_down_sync(full, Vf, 1);
+  const float Wfn = __shfl_down_sync(full, Wf, 1);
+  const bool hasn = lane < 31;
+  float alpha = (lane == 0) ? 0.f : al * Vl;
+  float beta = bl + al * Wl + (hasn ? cl * Vfn : 0.f);
+  float gamma = hasn ? cl * Wfn : 0.f;
+  float delta0 = dl.x - al * Dl0 - (hasn ? cl * Dfn0 : 0.f);
+  float delta1 = dl.y - al * Dl1 - (hasn ? cl * Dfn1 : 0.f);
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    float am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
+    float gm = __shfl_up_sync(full, gamma, s);
+    float dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
+    float ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
+    float gp = __shfl_down_sync(full, gamma, s);
+    float dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
+    if (lane < s) {
+      am = 0.f;
+      bm = 1.f;
+      gm = 0.f;
+      dm0 = 0.f;
+      dm1 = 0.f;
+    }
+    if (lane + s > 31) {
+      ap = 0.f;
+      bp = 1.f;
+      gp = 0.f;
+      dq0 = 0.f;
+      dq1 = 0.f;
+    }
+    const float k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
+    const float na = -am * k1, ng = -gp * k2;
+    const float nb = beta - gm * k1 - ap * k2;
+    delta0 = delta0 - dm0 * k1 - dq0 * k2;
+    delta1 = delta1 - dm1 * k1 - dq1 * k2;
+    alpha = na;
+    beta = nb;
+    gamma = ng;
+  }
+  const float ib = rcp_(beta);
+  const float E0 = delta0 * ib, E1 = delta1 * ib;
+  float Ep0 = __shfl_up_sync(full, E0, 1), Ep1 = __shfl_up_sync(full, E1, 1);
+  if (lane == 0) {
+    Ep0 = 0.f;
+    Ep1 = 0.f;
+  }
+  *row(kl) = make_float2(E0, E1);
+  float x0 = E0, x1 = E1;
+#pragma unroll
+  for (int r = m - 2; r >= 0; --r) {
+    const float2 dr = *row(k0 + r);
+    if (r == m - 2) {
+      x0 = dr.x + lp[r] * Ep0 + rr * E0;
+      x1 = dr.y + lp[r] * Ep1 + rr * E1;
+    } else {
+      x0 = dr.x + lp[r] * Ep0 - cp[r] * x0;
+      x1 = dr.y + lp[r] * Ep1 - cp[r] * x1;
+    }
+    *row(k0 + r) = make_float2(x0, x1);
   }
 }
 
