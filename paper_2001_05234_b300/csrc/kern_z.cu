@@ -154,6 +154,55 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
 
+// Per-warp values of the two column pairs a warp solves in a pair-granular tile (x-slots i0 .. i0 + 31 of
+// y-slot j; 8 warps, pairs q = warp and warp + 8): read from global memory before the tile barrier.
+struct PairMu {
+  float mu[2][2];
+  bool skip[2][2];  // the column is the double kernel's
+  bool single[2];   // solve the two columns one by one (slots 0, 1 of x, or a marked column)
+};
+__device__ __forceinline__ PairMu pair_mu(const ZArgs& a, int i0, int j) {
+  PairMu v;
+  const int warp = threadIdx.x >> 5;
+  const float muy = a.muy_f[j] + (float)a.shift;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = i0 + 2 * (warp + 8 * h);
+    const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
+    const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
+    v.mu[h][0] = a.mux_f[i] + muy;
+    v.mu[h][1] = a.mux_f[i + 1] + muy;
+    v.skip[h][0] = m0;
+    v.skip[h][1] = m1;
+    v.single[h] = i == 0 || m0 || m1;
+  }
+  return v;
+}
+
+// The column pairs of one pair-granular tile, one warp per pair (256 threads): slots 0 and 1 of x
+// (X_0, X_M: different eigenvalues) as single columns, a column the plan marks for the double kernel
+// skipped, every other pair by zsolve_pair2.
+template <int MMAX>
+__device__ __forceinline__ void solve_tile_p2(float* tile, const ZArgs& a, const PairMu& v, const float* sa,
+                                              const float* sb, const float* sc) {
+  const ZSwzP<MMAX> Z;
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c0 = 2 * (warp + 8 * h);
+    if (v.single[h]) {
+      if (!v.skip[h][0])
+        zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0, Z, a.nz, v.mu[h][0], sa, sb, sc,
+                                                                          nullptr, 0.f);
+      if (!v.skip[h][1])
+        zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0 + 1, Z, a.nz, v.mu[h][1], sa, sb,
+                                                                          sc, nullptr, 0.f);
+    } else {
+      zsolve_pair2<MMAX>(tile, c0, Z, v.mu[h][0], sa, sb, sc);
+    }
+  }
+}
+
 // The float z pass on pair-granular tiles (ZSwzP) for a periodic x direction: full columns
 // (Nz = 32 MMAX, MMAX >= 4), tiles of 32 x-slots of a natural-layout field.  The tile arrives by
 // 8-byte cp.async copies straight into its swizzled place -- a CTA has all 64 KB of its tile in
@@ -175,33 +224,16 @@ __global__ void __launch_bounds__(256, 3) zpass_p2_kernel(float* __restrict__ w,
   const ZSwzP<MMAX> Z;
   {  // thread t copies pair t & 15 of rows (t >> 4) + 16 u
     const int p2 = 2 * (threadIdx.x & 15);
-    for (int k = threadIdx.x >> 4; k < 32 * MMAX; k += blockDim.x >> 4)
+    for (int k = threadIdx.x >> 4; k < 32 * MMAX; k += blockDim.x >> 4) {
       cp_async8(tile + Z.at(k, p2), col0 + (size_t)k * plane + p2);
+    }
     cp_async_commit();
   }
   stage_zrows<true>(sa, sb, sc, zf, a.nz, MMAX);
+  const PairMu v = pair_mu(a, i0, j);  // global reads in flight with the tile copy
   cp_async_wait<0>();
   __syncthreads();
-  {
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const float muy = a.muy_f[j] + (float)a.shift;
-    for (int q = warp; q < TI / 2; q += nwarps) {
-      const int c0 = 2 * q, i = i0 + c0;
-      const bool m0 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i];
-      const bool m1 = a.mask != nullptr && a.mask[(size_t)j * a.nx + i + 1];
-      if (i == 0 || m0 || m1) {  // slots 0 and 1 (X_0, X_M) differ; a marked column goes to the double kernel
-        if (!m0)
-          zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0, Z, a.nz, a.mux_f[i] + muy, sa,
-                                                                            sb, sc, nullptr, 0.f);
-        if (!m1)
-          zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0 + 1, Z, a.nz,
-                                                                            a.mux_f[i + 1] + muy, sa, sb, sc,
-                                                                            nullptr, 0.f);
-      } else {
-        zsolve_pair2<MMAX>(tile, c0, Z, a.mux_f[i] + muy, sa, sb, sc);
-      }
-    }
-  }
+  solve_tile_p2<MMAX>(tile, a, v, sa, sb, sc);
   __syncthreads();
   {  // thread t writes floats 4 (t & 7) .. 4 (t & 7) + 3 of rows (t >> 3) + 32 u
     const int q = 4 * (threadIdx.x & 7);

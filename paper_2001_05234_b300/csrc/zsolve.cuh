@@ -594,28 +594,18 @@ __device__ __forceinline__ void zsolve_pair2(float* tile, int col0, const ZS& Z,
   float gamma = hasn ? cl * Wfn : 0.f;
   float delta0 = dl.x - al * Dl0 - (hasn ? cl * Dfn0 : 0.f);
   float delta1 = dl.y - al * Dl1 - (hasn ? cl * Dfn1 : 0.f);
+  // Cyclic reduction without boundary selects: at stride s, alpha is already zero on lanes < s and
+  // gamma on lanes > 31 - s (lane 0 has no left and lane 31 no right coupling, and each step keeps
+  // zeros within twice the stride), so k1, k2 vanish exactly where the shuffles return the lane's own
+  // values, and every nonzero result equals the selected form's.
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
-    float am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
-    float gm = __shfl_up_sync(full, gamma, s);
-    float dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
-    float ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
-    float gp = __shfl_down_sync(full, gamma, s);
-    float dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
-    if (lane < s) {
-      am = 0.f;
-      bm = 1.f;
-      gm = 0.f;
-      dm0 = 0.f;
-      dm1 = 0.f;
-    }
-    if (lane + s > 31) {
-      ap = 0.f;
-      bp = 1.f;
-      gp = 0.f;
-      dq0 = 0.f;
-      dq1 = 0.f;
-    }
+    const float am = __shfl_up_sync(full, alpha, s), bm = __shfl_up_sync(full, beta, s);
+    const float gm = __shfl_up_sync(full, gamma, s);
+    const float dm0 = __shfl_up_sync(full, delta0, s), dm1 = __shfl_up_sync(full, delta1, s);
+    const float ap = __shfl_down_sync(full, alpha, s), bp = __shfl_down_sync(full, beta, s);
+    const float gp = __shfl_down_sync(full, gamma, s);
+    const float dq0 = __shfl_down_sync(full, delta0, s), dq1 = __shfl_down_sync(full, delta1, s);
     const float k1 = alpha * rcp_(bm), k2 = gamma * rcp_(bp);
     const float na = -am * k1, ng = -gp * k2;
     const float nb = beta - gm * k1 - ap * k2;
