@@ -193,6 +193,18 @@ int cans_plan_destroy(cans_plan_t plan);
 int cans_plan_status(cans_plan_t plan, int* status);
 
 /*
+ * cans_check_bounded_wait -- exercises the failure path of the bounded device-side waits (the
+ * transaction-barrier waits of the TMA-fed z kernels) without a fault: one thread waits, with the same
+ * bounded wait, on a shared-memory barrier whose phase either completes at once (complete != 0: the
+ * thread's own arrival announces 0 bytes) or never completes (complete == 0: it announces 16 bytes that
+ * no copy delivers; no copy is in flight).  A wait that runs out after `polls` polls (each a hardware
+ * suspend of bounded length, later ones followed by a ~0.25 us sleep) records CANS_ERR_TIMEOUT in the
+ * plan's status word, read with cans_plan_status.  polls: 1 .. 2^20.  Asynchronous on cuda_stream;
+ * CANS_ERR_ARG for a NULL plan or polls out of range.
+ */
+int cans_check_bounded_wait(cans_plan_t plan, unsigned polls, int complete, void* cuda_stream);
+
+/*
  * cans_poisson_solve_adjoint -- q = S^T g, the transpose (plain Euclidean inner product) of the solve
  * operator S: f -> p of cans_poisson_solve with this plan (the backward pass of a differentiable
  * solve; projection-adjoint reading R10).  With D = diag(dzf_k) along z, D A_z is symmetric, so S is

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_plan_status.argtypes = [vp, ip]
+        L.cans_check_bounded_wait.argtypes = [vp, ctypes.c_uint, ctypes.c_int, vp]
         L.cans_zslab_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
         L.cans_zslab_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_size_t)]
@@ -290,6 +291,13 @@ def cans_zslab_finish(slab, field: int, iface_all: int, col00_all: int, nranks: 
 
 def cans_zslab_destroy(slab) -> int:
     return lib().cans_zslab_destroy(slab)
+
+
+def cans_check_bounded_wait(plan, polls: int, complete: bool, stream=None) -> None:
+    """Run the bounded device-side wait on a barrier that completes (complete) or never does
+    (cans_check_bounded_wait): a wait that runs out records CANS_ERR_TIMEOUT in the plan's status word."""
+    _check(lib().cans_check_bounded_wait(plan, int(polls), 1 if complete else 0, _stream_ptr(stream) or None),
+           "cans_check_bounded_wait")
 
 
 def cans_plan_status(plan) -> int:

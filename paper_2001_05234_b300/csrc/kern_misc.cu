@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "plan.cuh"
+#include "tma.cuh"
 
 namespace cans {
 
@@ -147,7 +148,26 @@ __global__ void split_f64_kernel(const double* __restrict__ x, size_t n, float* 
   }
 }
 
+// One thread waits, with the bounded wait of the TMA-fed z kernels, on a shared-memory transaction
+// barrier whose phase completes when its one expected arrival has come and the announced bytes have
+// landed.  complete != 0: the thread arrives announcing 0 bytes (the phase completes at once);
+// complete == 0: it announces 16 bytes that no copy delivers, so the wait runs out after `polls` polls
+// and records CANS_ERR_TIMEOUT in the status word.  No copy is ever in flight.
+__global__ void bounded_wait_kernel(int* status, unsigned polls, int complete) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_arrive_expect_tx(&bar, complete ? 0u : 16u);
+  if (!mbar_wait_bounded(&bar, 0, polls)) atomicCAS(status, CANS_OK, CANS_ERR_TIMEOUT);
+}
+
 }  // namespace cans
+
+extern "C" int cans_check_bounded_wait(cans_plan_t plan, unsigned polls, int complete, void* cuda_stream) {
+  if (!plan || polls == 0 || polls > (1u << 20)) return CANS_ERR_ARG;
+  cans::bounded_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(cuda_stream)>>>(plan->status_d, polls, complete);
+  return cudaGetLastError() == cudaSuccess ? CANS_OK : CANS_ERR_CUDA;
+}
 
 extern "C" int cans_split_f64(const double* x, size_t n, float* rn, float* hi, float* lo, double* back,
                               void* cuda_stream) {

@@ -62,6 +62,14 @@ def test_plan_status_rejects_null_arguments(cans):
     assert cans.lib().cans_plan_status(None, None) == cans.CANS_ERR_ARG
 
 
+def test_bounded_wait_check_rejects_bad_arguments(cans):
+    """Refused before any launch: a NULL plan, no polls, more than 2^20 polls."""
+    assert cans.lib().cans_check_bounded_wait(None, 100, 0, None) == cans.CANS_ERR_ARG
+    fake = 1  # never dereferenced: the poll count is checked first
+    assert cans.lib().cans_check_bounded_wait(fake, 0, 0, None) == cans.CANS_ERR_ARG
+    assert cans.lib().cans_check_bounded_wait(fake, (1 << 20) + 1, 0, None) == cans.CANS_ERR_ARG
+
+
 @pytest.mark.parametrize(
     "n,L,bc,dzf,want",
     [

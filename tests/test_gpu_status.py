@@ -3,7 +3,8 @@ without `info`, including from solves replayed out of a CUDA graph, and ordinary
 clear.
 
 Failures are made on the host side of the inputs only (a right-hand side with a mean on a singular
-problem, a tolerance no refinement can reach, a NaN in f); nothing here faults or hangs the GPU.
+problem, a tolerance no refinement can reach, a NaN in f), or, for the bounded device-side waits, by a
+transaction barrier whose announced bytes no copy delivers; nothing here faults or hangs the GPU.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from paper_2001_05234_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 P, NN, DD = 0, 1, 2
-OK, INCOMPATIBLE, NOT_CONVERGED = 0, -5, -6
+OK, INCOMPATIBLE, NOT_CONVERGED, TIMEOUT = 0, -5, -6, -7
 
 
 @pytest.fixture(scope="module")
@@ -196,3 +197,34 @@ def test_batched_device_status_flags_unreached_tolerance(cans):
     assert status.cpu().tolist() == [OK, NOT_CONVERGED, OK]
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_bounded_wait_that_runs_out_records_timeout(cans, graph):
+    """The bounded wait of the TMA-fed z kernels on a barrier that never completes (16 bytes announced,
+    none delivered, no copy in flight) gives up after its polls and leaves CANS_ERR_TIMEOUT in the
+    plan's status word -- also from a graph replay; a barrier that completes leaves the word clear."""
+    import torch
+
+    n = (32, 24, 16)
+    s = cans.PoissonSolver(n, (P, P, NN), (1.0, 1.0), I.tanh_dzf(16, 1.5), prec=1)
+    assert s.status() == OK
+    cans.cans_check_bounded_wait(s.plan, 200, complete=True)
+    assert s.status() == OK
+    if graph:
+        st = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            cans.cans_check_bounded_wait(s.plan, 200, complete=False, stream=st)
+        assert s.status() == OK  # capture launches nothing
+        g.replay()
+    else:
+        cans.cans_check_bounded_wait(s.plan, 200, complete=False)
+    torch.cuda.synchronize()
+    assert s.status() == TIMEOUT
+    assert s.status() == OK  # read and cleared
+    # the plan still solves after a recorded timeout
+    f = torch.from_numpy(_rhs(n, (P, P, NN), I.tanh_dzf(16, 1.5))).cuda()
+    s.solve(f)
+    assert s.status() == OK
+    s.close()
