@@ -506,11 +506,13 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->z_smem[s] = (size_t)ti * nz * es;
   }
   // CANS_RES_PTS=1/2/4 sets the residual stencil's points per thread, CANS_Z_P2=0 keeps a periodic-x
-  // float z pass on the staged kernel (switches for comparisons and tests).  CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the
+  // float z pass on the staged kernel, CANS_RES_SPLIT=0 / 2 keeps the sweep residual of CTA-engine x lines
+  // fused into the x pass / splits it at every size (switches for comparisons and tests).  CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the
   // TMA kernel cannot take fail instead of falling back (switches for comparisons and tests; the
   // autotuner, when on, chooses between the two kernels by timing)
   if (const char* ev = std::getenv("CANS_RES_PTS")) P->res_pts = (ev[0] == '1') ? 1 : (ev[0] == '2' ? 2 : 4);
   if (const char* ev = std::getenv("CANS_Z_P2")) P->z_p2 = (ev[0] == '0') ? 0 : 1;
+  if (const char* ev = std::getenv("CANS_RES_SPLIT")) P->res_split = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_Z_TMA")) P->z_tma = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_Z_TMA_CTAS"))
     P->z_tma_ctas = (ev[0] >= '1' && ev[0] <= '4') ? ev[0] - '0' : P->z_tma_ctas;
@@ -904,6 +906,11 @@ static int solve_impl(cans_plan_t P, const double* f, const DivArgs* div, double
         if (xres_warp_ok(P, W)) {
           TIMED(CANS_PASS_RS, launch_residual(P, f, Phi, Plo, s > 0, W, P->acc_d + 1 + s, st));
           TIMED(CANS_PASS_XR, launch_xfwd32_warp(P, W, st));
+        } else if ((P->res_split == 2 || (P->res_split == 1 && N >= ((size_t)1 << 24))) && xres_cta_ok(P, W)) {
+          // large fields: the stencil + a float x pass (measured 2.04 vs 2.23 ms at 192x512x512);
+          // small ones keep the fused pass, one launch fewer on their latency-bound chain
+          TIMED(CANS_PASS_RS, launch_residual(P, f, Phi, Plo, s > 0, W, P->acc_d + 1 + s, st));
+          TIMED(CANS_PASS_XR, launch_xfwd32_cta(P, W, st));
         } else if (s == 0) {
           TIMED(CANS_PASS_XR, launch_xfwd<float, 2>(P, f, Phi, Plo, W, P->acc_d + 1 + s, st));
         } else {

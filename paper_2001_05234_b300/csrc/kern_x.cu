@@ -215,35 +215,42 @@ __device__ __forceinline__ void stage_lines(S* dst, const S* src, int nl, int N,
   cp_async_commit();
 }
 
-template <int MC>
-__global__ void __launch_bounds__(512, 2) xfwd_pipe_kernel(const double* __restrict__ f, float* __restrict__ dst,
-                                                           int nlines, int lognl, LineTab<float> tb, double* norm_acc) {
+// S = double: f -> float lines (the first pass of a mixed solve).  S = float: a float field transformed
+// in place (src == dst: each tile's lines are staged whole before the tile writes them back, and tiles
+// share no lines), the residual of a refinement sweep written by the streaming stencil.
+template <typename S, int MC>
+__global__ void __launch_bounds__(512, 2) xfwd_pipe_kernel(const S* f, float* dst, int nlines, int lognl,
+                                                           LineTab<float> tb, double* norm_acc) {
   typedef float2 C;
-  constexpr int N = 2 * MC, PAD = 2;
+  constexpr int N = 2 * MC, PAD = 16 / sizeof(S);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nl = 1 << lognl;
-  double* raw = reinterpret_cast<double*>(smem_raw);  // [2][nl][N + PAD]
-  C* buf = reinterpret_cast<C*>(smem_raw + 2 * (size_t)nl * (N + PAD) * sizeof(double));
+  S* raw = reinterpret_cast<S*>(smem_raw);  // [2][nl][N + PAD]
+  C* buf = reinterpret_cast<C*>(smem_raw + 2 * (size_t)nl * (N + PAD) * sizeof(S));
   const Lay L{nl};
   const int ntiles = (nlines + nl - 1) / nl;
   float acc = 0.f;
   int t = blockIdx.x;
-  if (t < ntiles) stage_lines<double>(raw, f + (size_t)t * nl * N, nl, N, PAD, min(nl, nlines - t * nl));
+  if (t < ntiles) stage_lines<S>(raw, f + (size_t)t * nl * N, nl, N, PAD, min(nl, nlines - t * nl));
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
     const int slot = it & 1;
     const int tn = t + gridDim.x;
     if (tn < ntiles) {
-      stage_lines<double>(raw + (size_t)(slot ^ 1) * nl * (N + PAD), f + (size_t)tn * nl * N, nl, N, PAD,
-                          min(nl, nlines - tn * nl));
+      stage_lines<S>(raw + (size_t)(slot ^ 1) * nl * (N + PAD), f + (size_t)tn * nl * N, nl, N, PAD,
+                     min(nl, nlines - tn * nl));
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const double* src = raw + (size_t)slot * nl * (N + PAD);
+    const S* src = raw + (size_t)slot * nl * (N + PAD);
     const int line0 = t * nl;
     auto load = [&](int l, int n) -> float {
-      const float v = d2f_rn(src[l * (N + PAD) + n]);
+      float v;
+      if constexpr (sizeof(S) == 8)
+        v = d2f_rn(src[l * (N + PAD) + n]);
+      else
+        v = src[l * (N + PAD) + n];
       acc += v * v;
       return v;
     };
@@ -388,20 +395,45 @@ cudaError_t launch_xfwd_div(const cans_plan_s* P, const DivArgs& d, T* dst, doub
 template cudaError_t launch_xfwd_div<double>(const cans_plan_s*, const DivArgs&, double*, double*, cudaStream_t);
 template cudaError_t launch_xfwd_div<float>(const cans_plan_s*, const DivArgs&, float*, double*, cudaStream_t);
 
-template <int MC>
-static cudaError_t xfwd_pipe_m(const cans_plan_s* P, const double* f, float* dst, double* acc, cudaStream_t st) {
+template <typename S, int MC>
+static cudaError_t xfwd_pipe_m(const cans_plan_s* P, const S* f, float* dst, double* acc, cudaStream_t st) {
+  constexpr int PAD = 16 / sizeof(S);
   Launch L = P->x_l[1];
-  size_t smem = L.smem + 2 * (size_t)L.nl * (2 * MC + 2) * sizeof(double);
+  size_t smem = L.smem + 2 * (size_t)L.nl * (2 * MC + PAD) * sizeof(S);
   while (smem > (size_t)110 * 1024 && L.nl > 1) {  // keep two CTAs per SM
     L = line_launch_shape(2 * MC, P->n[1] * P->n[2], sizeof(float2), L.nl / 2);
-    smem = L.smem + 2 * (size_t)L.nl * (2 * MC + 2) * sizeof(double);
+    smem = L.smem + 2 * (size_t)L.nl * (2 * MC + PAD) * sizeof(S);
   }
-  cudaError_t e = set_smem((const void*)xfwd_pipe_kernel<MC>, smem);
+  cudaError_t e = set_smem((const void*)xfwd_pipe_kernel<S, MC>, smem);
   if (e != cudaSuccess) return e;
   const int nlines = P->n[1] * P->n[2];
-  const int grid = persistent_grid(xfwd_pipe_kernel<MC>, L.threads, smem, (nlines + L.nl - 1) / L.nl);
-  xfwd_pipe_kernel<MC><<<grid, L.threads, smem, st>>>(f, dst, nlines, L.lognl, P->tx_f, acc);
+  const int grid = persistent_grid(xfwd_pipe_kernel<S, MC>, L.threads, smem, (nlines + L.nl - 1) / L.nl);
+  xfwd_pipe_kernel<S, MC><<<grid, L.threads, smem, st>>>(f, dst, nlines, L.lognl, P->tx_f, acc);
   return cudaGetLastError();
+}
+
+// The CTA-wide forward x pass of a float field in place (the sweep residual the streaming stencil
+// wrote), for x lengths with a compile-time engine, a natural-layout field, 16-byte aligned.
+bool xres_cta_ok(const cans_plan_s* P, const float* W) {
+  if (P->wblk || (reinterpret_cast<uintptr_t>(W) & 15) != 0) return false;
+  switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM:         \
+    return true;
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return false;
+  }
+}
+
+cudaError_t launch_xfwd32_cta(const cans_plan_s* P, float* W, cudaStream_t st) {
+  switch (P->dx.m) {
+#define CASE_M(MM) \
+  case MM: return xfwd_pipe_m<float, MM>(P, W, W, nullptr, st);
+    CANS_FOR_EACH_M(CASE_M)
+#undef CASE_M
+    default: return cudaErrorNotSupported;
+  }
 }
 
 template <typename T, int MODE>
@@ -418,7 +450,7 @@ cudaError_t launch_xfwd(const cans_plan_s* P, const double* f, const float* Phi,
   if (MODE == 0 && sizeof(T) == 4 && !P->wblk && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
     switch (P->dx.m) {
 #define CASE_M(MM) \
-  case MM: return xfwd_pipe_m<MM>(P, f, reinterpret_cast<float*>(dst), acc, st);
+  case MM: return xfwd_pipe_m<double, MM>(P, f, reinterpret_cast<float*>(dst), acc, st);
       CANS_FOR_EACH_M(CASE_M)
 #undef CASE_M
       default: break;

@@ -144,6 +144,8 @@ struct cans_plan_s {
   double idx2, idy2;
   cans::Launch x_l[2], y_l[2];  // [0] double storage, [1] float storage
   int z_ti[2], z_m, z_mmax;
+  int res_split = 1;  // CTA-engine x lines: the sweep residual as the streaming stencil + an x pass from
+                      // 2^24 points on (1), never (0), always (2); fused into the x pass otherwise
   int res_pts = 4;  // residual stencil: points per thread (4, 2 or 1; fewer where nx or alignment demand)
   int z_p2 = 1;    // float z pass of a periodic x on full columns: pair-granular cp.async tiles (0: off)
   int z_tma = 0;  // float z pass: 0 the register-staged kernel; 1 a TMA-using variant (z_tma_ctas)
@@ -273,6 +275,8 @@ cudaError_t launch_remove_weighted_mean(const cans_plan_s* P, double* f, double*
 cudaError_t launch_residual(const cans_plan_s* P, const double* f, const float* Phi, const float* Plo, bool plo,
                             float* r, double* norm_acc, cudaStream_t st);
 bool xres_warp_ok(const cans_plan_s* P, const float* W);
+bool xres_cta_ok(const cans_plan_s* P, const float* W);
+cudaError_t launch_xfwd32_cta(const cans_plan_s* P, float* W, cudaStream_t st);
 cudaError_t launch_xfwd32_warp(const cans_plan_s* P, float* W, cudaStream_t st);
 // y-pass with the x-slots across the lanes (kern_yc.cu): taken first where the shape allows it
 template <int DIR>

@@ -93,3 +93,36 @@ def test_misaligned_f_falls_back_to_one_point_per_thread(cans, monkeypatch):
     ref = oracle.poisson_solve(f, bc, length_xy, dzf, nthreads=8)
     rel = float(np.linalg.norm(p4[0] - ref) / np.linalg.norm(ref))
     assert rel <= 1e-10, (rel, msg)
+
+
+CTA_CASES = [
+    # x lengths of the CTA-wide engine: the sweep residual as the streaming stencil + the float x pass
+    ((96, 48, 40), (P, P, NN), (1.0, 1.0), 0.0, 2),
+    ((48, 64, 32), (NN, DD, DD), (1.0, 0.5), -20.0, 2),
+    ((192, 24, 16), (DD, NN, P), (1.0, 1.0), 0.0, 3),
+    ((64, 32, 30), (ND, P, NN), (1.0, 1.0), 0.0, 2),
+]
+
+
+@pytest.mark.parametrize("n,bc,length_xy,shift,sweeps", CTA_CASES)
+def test_split_residual_on_cta_engine_lines(cans, monkeypatch, n, bc, length_xy, shift, sweeps):
+    """CTA-engine x lines: the split residual (stencil + in-place float x pass; CANS_RES_SPLIT=2 takes it
+    at every size, by default only large fields do) against the oracle, and against the residual fused
+    into the x pass (CANS_RES_SPLIT=0; the two round differently)."""
+    import torch
+
+    dzf = I.uniform_dzf(n[2]) if bc[2] == P else I.tanh_dzf(n[2], 1.6)
+    case = I.PoissonCase("res", n, bc, length_xy, dzf, 4245, "uniform")
+    f = I.rhs_host(case)
+    ft = torch.from_numpy(f).cuda()
+    got = {}
+    for flag in ("2", "0"):  # split at every size / fused
+        monkeypatch.setenv("CANS_RES_SPLIT", flag)
+        got[flag] = _solve(cans, monkeypatch, "4", n, bc, length_xy, dzf, shift, sweeps, ft)
+    ps, info, st = got["2"]
+    assert st == 0, info
+    ref = oracle.helmholtz_solve(f, bc, length_xy, dzf, shift=shift, nthreads=8)
+    rel = float(np.linalg.norm(ps - ref) / np.linalg.norm(ref))
+    assert rel <= 1e-10, rel
+    pf = got["0"][0]
+    assert float(np.linalg.norm(ps - pf) / np.linalg.norm(pf)) <= 1e-10
