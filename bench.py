@@ -116,8 +116,8 @@ NCU_DRAM_BYTES_PER_POINT = {
     "y_forward": 7.18,
     "y_inverse": 7.21,
     "x_inverse_update": 15.28,
-    "residual_stencil": 15.90,
-    "z_solve": 6.25,
+    "residual_stencil": 15.87,  # res4_kernel
+    "z_solve": 6.21,  # zpass_p2_kernel: (134.37 + 74.05) MB / 33.55 M points
 }
 
 
