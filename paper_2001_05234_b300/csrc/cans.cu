@@ -505,8 +505,8 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->z_ti[s] = ti;
     P->z_smem[s] = (size_t)ti * nz * es;
   }
-  // CANS_RES_PTS=1/2/4 sets the residual stencil's points per thread, CANS_Z_P2=0 keeps a periodic-x
-  // float z pass on the staged kernel, CANS_RES_SPLIT=0 / 2 keeps the sweep residual of CTA-engine x lines
+  // CANS_RES_PTS=1/2/4 sets the residual stencil's points per thread, CANS_Z_P2=0 keeps the float z pass of
+  // full columns on the staged kernel, CANS_RES_SPLIT=0 / 2 keeps the sweep residual of CTA-engine x lines
   // fused into the x pass / splits it at every size (switches for comparisons and tests).  CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the
   // TMA kernel cannot take fail instead of falling back (switches for comparisons and tests; the
   // autotuner, when on, chooses between the two kernels by timing)

@@ -182,7 +182,9 @@ __device__ __forceinline__ PairMu pair_mu(const ZArgs& a, int i0, int j) {
 // The column pairs of one pair-granular tile, one warp per pair (256 threads): slots 0 and 1 of x
 // (X_0, X_M: different eigenvalues) as single columns, a column the plan marks for the double kernel
 // skipped, every other pair by zsolve_pair2.
-template <int MMAX>
+// PAIR false (x not periodic): every column is solved on its own (zsolve_column; its 4-byte accesses
+// of the pair-granular tile meet 2-way bank conflicts, lanes l and l + 16).
+template <int MMAX, bool PAIR>
 __device__ __forceinline__ void solve_tile_p2(float* tile, const ZArgs& a, const PairMu& v, const float* sa,
                                               const float* sb, const float* sc) {
   const ZSwzP<MMAX> Z;
@@ -190,7 +192,7 @@ __device__ __forceinline__ void solve_tile_p2(float* tile, const ZArgs& a, const
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int c0 = 2 * (warp + 8 * h);
-    if (v.single[h]) {
+    if (!PAIR || v.single[h]) {
       if (!v.skip[h][0])
         zsolve_column<MMAX, float, float, false, ZSwzP<MMAX>, true, true>(tile, c0, Z, a.nz, v.mu[h][0], sa, sb, sc,
                                                                           nullptr, 0.f);
@@ -210,7 +212,7 @@ __device__ __forceinline__ void solve_tile_p2(float* tile, const ZArgs& a, const
 // with both right-hand sides of a row in one 8-byte word.  Same arithmetic per column as
 // zpass_f32_kernel (bit-identical results); slot 0 and 1 of x and the columns the plan marks for the
 // double kernel are handled as there.
-template <int MMAX>
+template <int MMAX, bool PAIR>
 __global__ void __launch_bounds__(256, 3) zpass_p2_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf, WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int TI = 32, rs = 32 * (MMAX + 4);
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(256, 3) zpass_p2_kernel(float* __restrict__ w,
   const PairMu v = pair_mu(a, i0, j);  // global reads in flight with the tile copy
   cp_async_wait<0>();
   __syncthreads();
-  solve_tile_p2<MMAX>(tile, a, v, sa, sb, sc);
+  solve_tile_p2<MMAX, PAIR>(tile, a, v, sa, sb, sc);
   __syncthreads();
   {  // thread t writes floats 4 (t & 7) .. 4 (t & 7) + 3 of rows (t >> 3) + 32 u
     const int q = 4 * (threadIdx.x & 7);
@@ -604,17 +606,18 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
       if (e != cudaSuccess || part == 0) return e;
     } else if (part != 1 && P->z_tma == 2) {
       return cudaErrorNotSupported;  // the TMA kernel was required and cannot take this shape
-    } else if (part != 1 && MMAX >= 4 && TIC == 32 && P->z_p2 && P->bc[0] == BC_P && P->n[2] == 32 * MMAX &&
-               P->n[0] % 32 == 0 && !wl.blk && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
-      // pair-granular tiles fetched by cp.async (periodic x, full columns, whole 32-slot tiles)
+    } else if (part != 1 && MMAX >= 4 && TIC == 32 && P->z_p2 && P->n[2] == 32 * MMAX && P->n[0] % 32 == 0 &&
+               !wl.blk && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+      // pair-granular tiles fetched by cp.async (full columns, whole 32-slot tiles; the column pairs of a
+      // periodic x share their factorisation)
       if constexpr (MMAX >= 4) {
         ZArgs a = zargs(P, 32, gauge, nullptr);
         a.mask = P->mask_d;
         const size_t smem = 3 * 32 * (MMAX + 4) * sizeof(float) + (size_t)32 * 32 * MMAX * sizeof(float);
-        e = set_smem((const void*)zpass_p2_kernel<MMAX>, smem);
+        auto kern = P->bc[0] == BC_P ? zpass_p2_kernel<MMAX, true> : zpass_p2_kernel<MMAX, false>;
+        e = set_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        zpass_p2_kernel<MMAX><<<dim3(P->n[0] / 32, P->n[1]), 256, smem, st>>>(reinterpret_cast<float*>(w), a,
-                                                                              P->zt_f, wl);
+        kern<<<dim3(P->n[0] / 32, P->n[1]), 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, wl);
         e = cudaGetLastError();
         if (e != cudaSuccess || part == 0) return e;
       }

@@ -1,7 +1,8 @@
 """The float z pass on pair-granular tiles against the staged kernel and the oracle.
 
 For a periodic x direction the Re / Im slots of one wavenumber share their z system (Eq. poi_reduced
-with equal mu).  The pair-granular kernel keeps the two columns of a pair side by side, fetches its
+with equal mu); with walls in x every column has its own.  The pair-granular kernel keeps the columns
+2p and 2p + 1 side by side, fetches its
 tiles with 8-byte cp.async copies and solves each pair with both right-hand sides of a row in one
 8-byte word; the arithmetic per column is the staged kernel's, so mixed solves through either must
 agree bit for bit (CANS_Z_P2=0 selects the staged kernel), and both must match the oracle.  The shapes
@@ -24,6 +25,11 @@ CASES = [
     ((128, 64, 256), (P, DD, NN), (1.0, 1.0), 0.0),               # 8 rows per lane
     ((64, 48, 128), (P, NN, DD), (1.0, 0.5), 0.0),                # 4 rows per lane, Dirichlet z
     ((96, 24, 512), (P, ND, NN), (1.0, 1.0), -30.0),              # mixed y walls, shift, three tiles in x
+    # walled x: every column solved on its own from the pair-granular tile
+    ((128, 48, 512), (NN, P, NN), (1.0, 1.0), 0.0),               # singular
+    ((64, 32, 256), (DD, DD, NN), (1.0, 1.0), 0.0),
+    ((96, 24, 128), (ND, NN, DD), (1.0, 0.5), -10.0),             # quarter-wave x, shift
+    ((32, 48, 512), (4, P, NN), (32 / 1024, 48 / 1024), 0.0),     # quarter-wave x (Dirichlet first), one tile
 ]
 
 
