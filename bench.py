@@ -250,11 +250,12 @@ def gpu_arm(args):
     _, info64, _ = s64.solve(f, p, info=True)
     s64.close()
 
-    # end to end through the C ABI with host buffers: every step copies its f from pinned host memory,
-    # solves, and copies its p back.  Steps are pipelined the way a production loop runs them: step
-    # k+1's upload and step k-1's download (separate copy streams; PCIe is full duplex) overlap step
-    # k's solve, with double device buffers and events guarding their reuse.  All copies of all steps
-    # lie inside the timed region.
+    # end to end through the C ABI with host buffers (cans_poisson_solve_host): every step's call uploads
+    # its f from pinned host memory, solves, and downloads its p.  Steps are pipelined the way a
+    # production loop runs them: the call orders its upload (copy-in stream), solve (compute stream) and
+    # download (copy-out stream) by events, so step k+1's upload and step k-1's download (PCIe is full
+    # duplex) overlap step k's solve; double device buffers, and events here guarding their reuse
+    # across steps.  All copies of all steps lie inside the timed region.
     fh = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
     fh.copy_(f)
     ph = [torch.empty_like(fh, pin_memory=True) for _ in range(2)]
@@ -263,26 +264,17 @@ def gpu_arm(args):
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     e2e_steps = max(4, min(args.steps, 10))  # the pipeline's fill and drain are spread over the steps
     ev = lambda: torch.cuda.Event()  # noqa: E731
-    ev_in, ev_done, ev_out = [ev() for _ in range(e2e_steps)], [ev() for _ in range(e2e_steps)], \
-        [ev() for _ in range(e2e_steps)]
+    ev_done, ev_out = [ev() for _ in range(e2e_steps)], [ev() for _ in range(e2e_steps)]
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         b = k % 2
-        with torch.cuda.stream(s_in):
-            if k >= 2:
-                s_in.wait_event(ev_done[k - 2])  # the solve two steps back has read fd[b]
-            fd[b].copy_(fh, non_blocking=True)
-            ev_in[k].record(s_in)
-        stream.wait_event(ev_in[k])
         if k >= 2:
-            stream.wait_event(ev_out[k - 2])  # pd[b] has been copied out
-        solver.solve(fd[b], pd[b], stream=stream)
+            s_in.wait_event(ev_done[k - 2])  # the solve two steps back has read fd[b]
+            stream.wait_event(ev_out[k - 2])  # and its p has left pd[b]
+        solver.solve_host(fh, ph[b], fd[b], pd[b], copy_in=s_in, compute=stream, copy_out=s_out)
         ev_done[k].record(stream)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_done[k])
-            ph[b].copy_(pd[b], non_blocking=True)
-            ev_out[k].record(s_out)
+        ev_out[k].record(s_out)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_check = float(torch.linalg.vector_norm(ph[(e2e_steps - 1) % 2].cuda() - pd[(e2e_steps - 1) % 2]))
@@ -357,6 +349,7 @@ def gpu_arm(args):
         "cpu_fft_comparator": cpu_fft,
         "e2e": {"value": npts / (e2e_ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": npts * 8, "d2h_bytes_per_step": npts * 8, "steps": e2e_steps,
+                "api": "cans_poisson_solve_host (upload, solve, download in one C-ABI call)",
                 "pipelined": "upload of step k+1 and download of step k-1 overlap the solve of step k",
                 "last_copy_check": e2e_check},
         "gpu_launches": kernels_per_solve * args.steps,

@@ -166,6 +166,23 @@ int cans_poisson_solve_divergence(cans_plan_t plan, const double* u, const doubl
                                   void* cuda_stream, double* info);
 
 /* Release the plan and its device tables. */
+/*
+ * cans_poisson_solve_host -- the solve of cans_poisson_solve from and to host memory: the upload of f
+ * (host -> f_dev) on copy_in_stream, the solve (f_dev -> p_dev, workspace as for cans_poisson_solve) on
+ * compute_stream once the upload is done, and the download of p (p_dev -> p_host) on copy_out_stream
+ * once the solve is done, ordered by two events the plan owns.  All asynchronous; p_host holds p when
+ * copy_out_stream has passed the call.  Each stream waits only for what it consumes, so consecutive calls
+ * with alternating device buffers (and separate host buffers) overlap one call's download and the next
+ * call's upload with the solves; the solves themselves stay one at a time on compute_stream (a plan
+ * serves one solve at a time).  The three streams may be the same stream.
+ *   f_host, p_host : host arrays of Nx Ny Nz doubles (page-locked for the copies to be asynchronous).
+ *   f_dev, p_dev   : caller-owned device arrays of Nx Ny Nz doubles, distinct (f_dev is overwritten by
+ *                    the upload, p_dev by the solve); in place (f_dev == p_dev) is refused.
+ * Errors: CANS_ERR_ARG for a NULL argument or f_dev == p_dev, CANS_ERR_WORKSPACE as cans_poisson_solve
+ * (before anything is enqueued), CANS_ERR_CUDA when a copy, event or launch cannot be enqueued.
+ */
+int cans_poisson_solve_host(cans_plan_t plan, const double* f_host, double* p_host, double* f_dev, double* p_dev,
+                            void* workspace, void* copy_in_stream, void* compute_stream, void* copy_out_stream);
 int cans_plan_destroy(cans_plan_t plan);
 
 /*

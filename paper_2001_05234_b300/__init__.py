@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         L.cans_poisson_plan.argtypes = [ip, dp, ip, dp, ctypes.POINTER(cans_opts), ctypes.POINTER(vp)]
         L.cans_poisson_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_poisson_solve.argtypes = [vp, vp, vp, vp, vp, dp]
+        L.cans_poisson_solve_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.cans_helmholtz_solve.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, dp]
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_plan_status.argtypes = [vp, ip]
@@ -416,6 +417,20 @@ class PoissonSolver:
         if st != CANS_OK and not (info and st in (-5, -6)):
             raise CansError(st, "cans_helmholtz_solve" if shift is not None else "cans_poisson_solve")
         return (out, buf, st) if info else out
+
+    def solve_host(self, f_host, p_host, f_dev, p_dev, copy_in=None, compute=None, copy_out=None):
+        """cans_poisson_solve_host: upload f_host into f_dev on copy_in, solve into p_dev on compute,
+        download into p_host on copy_out (torch streams; None = the current stream), all asynchronous."""
+        import torch
+
+        for t, dev in ((f_host, False), (p_host, False), (f_dev, True), (p_dev, True)):
+            assert t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == self.shape
+            assert t.is_cuda == dev
+        _check(lib().cans_poisson_solve_host(self.plan, f_host.data_ptr(), p_host.data_ptr(), f_dev.data_ptr(),
+                                             p_dev.data_ptr(), self._ws_ptr, _stream_ptr(copy_in),
+                                             _stream_ptr(compute), _stream_ptr(copy_out)),
+               "cans_poisson_solve_host")
+        return p_host
 
     def status(self) -> int:
         """The plan's device status word since the last read (cans_plan_status; synchronises)."""

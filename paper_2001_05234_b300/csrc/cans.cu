@@ -572,6 +572,8 @@ int cans_poisson_solve_adjoint(cans_plan_t P, const double* g, double* q, void* 
 int cans_plan_destroy(cans_plan_t P) {
   if (!P) return CANS_ERR_ARG;
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->host_ev)
+    if (e) cudaEventDestroy(e);
   if (P->dtab) cudaFree(P->dtab);
   delete P;
   return CANS_OK;
@@ -970,6 +972,29 @@ static int solve_impl(cans_plan_t P, const double* f, const DivArgs* div, double
 int cans_poisson_solve(cans_plan_t P, const double* f, double* p, void* workspace, void* cuda_stream, double* info) {
   if (!P || !f || !p) return CANS_ERR_ARG;
   return solve_impl(P, f, nullptr, p, workspace, cuda_stream, info);
+}
+
+int cans_poisson_solve_host(cans_plan_t P, const double* f_host, double* p_host, double* f_dev, double* p_dev,
+                            void* workspace, void* copy_in_stream, void* compute_stream, void* copy_out_stream) {
+  if (!P || !f_host || !p_host || !f_dev || !p_dev || f_dev == p_dev) return CANS_ERR_ARG;
+  if (P->opts.prec == CANS_MIXED && (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+    return CANS_ERR_WORKSPACE;  // refused before the upload is enqueued
+  cudaStream_t sin = static_cast<cudaStream_t>(copy_in_stream), sc = static_cast<cudaStream_t>(compute_stream),
+               sout = static_cast<cudaStream_t>(copy_out_stream);
+  for (cudaEvent_t& e : P->host_ev)
+    if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return CANS_ERR_CUDA;
+  const size_t bytes = field_points(P) * sizeof(double);
+  // upload on copy_in, solve on compute after it, download on copy_out after the solve: each stream
+  // waits only for what it consumes, so consecutive calls with other device buffers overlap
+  if (cudaMemcpyAsync(f_dev, f_host, bytes, cudaMemcpyHostToDevice, sin) != cudaSuccess ||
+      cudaEventRecord(P->host_ev[0], sin) != cudaSuccess || cudaStreamWaitEvent(sc, P->host_ev[0], 0) != cudaSuccess)
+    return CANS_ERR_CUDA;
+  const int rc = solve_impl(P, f_dev, nullptr, p_dev, workspace, compute_stream, nullptr);
+  if (rc != CANS_OK) return rc;
+  if (cudaEventRecord(P->host_ev[1], sc) != cudaSuccess || cudaStreamWaitEvent(sout, P->host_ev[1], 0) != cudaSuccess ||
+      cudaMemcpyAsync(p_host, p_dev, bytes, cudaMemcpyDeviceToHost, sout) != cudaSuccess)
+    return CANS_ERR_CUDA;
+  return CANS_OK;
 }
 
 int cans_poisson_solve_divergence(cans_plan_t P, const double* u, const double* v, const double* w, double scale,

@@ -161,6 +161,7 @@ struct cans_plan_s {
   // per-pass event records (cans_plan_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t host_ev[2] = {nullptr, nullptr};  // cans_poisson_solve_host: upload done, solve done
   std::vector<int> ev_kind;  // pass kind of record r (events 2r, 2r+1)
   int ev_used = 0;
 };
