@@ -35,6 +35,17 @@ METRIC = "Poisson solve Gpts/s (mixed precision refined to 1e-12 relative residu
 WORKLOAD = "poisson_1024x1024x512_P-P-NN_tanh1.8_modes64"
 
 
+_FP64_PEAK = []
+
+
+def fp64_peak_tflops(cans) -> float:
+    """The FP64 FMA rate of this GPU in TFLOP/s, measured once per run with the library's probe kernel
+    (cans_fp64_fma_probe: independent FMA chains on every SM, CUDA-event timed, best of 3)."""
+    if not _FP64_PEAK:
+        _FP64_PEAK.append(cans.fp64_fma_tflops())
+    return _FP64_PEAK[0]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -359,6 +370,9 @@ def gpu_arm(args):
         "rk3_step": rk3,
         "ensemble": ens,
         "config2_channel": cfg2,
+        "fp64_fma_peak": {"tflops": fp64_peak_tflops(cans),
+                          "how": "cans_fp64_fma_probe: 8 independent FP64 FMA chains per thread, 8 blocks "
+                                 "of 256 threads per SM, CUDA events, best of 3"},
     }
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -448,11 +462,13 @@ def config2_measure(cans, I, args):
     npts = nx * ny * nz
     hbm, _ = _peaks()
     # FP64 flop model: ~2.5 log2 N flops per point per real transform direction and pass (4 passes)
-    # plus ~6 for the Makhoul twiddles and ~9 for the z elimination; FP64 peak 1.13 TFLOP/s (the
-    # measured 0.57 T FMA/s of this GPU)
+    # plus ~6 for the Makhoul twiddles and ~9 for the z elimination, against the FP64 FMA rate measured
+    # on this GPU in the same run
     flops = npts * (2 * (2.5 * np.log2(nx) + 6) + 2 * (2.5 * np.log2(ny) + 6) + 9)
+    peak64 = fp64_peak_tflops(cans)
     out_frac = {"hbm_frac_80B_model": 80.0 * npts / (ms_lib * 1e-3) / 1e9 / hbm,
-                "fp64_flop_frac": flops / (ms_lib * 1e-3) / 1.13e12}
+                "fp64_flop_frac": flops / (ms_lib * 1e-3) / (peak64 * 1e12),
+                "fp64_peak_tflops_measured": peak64}
     return {"workload": "poisson_channel_1024x512x256_P-DD-NN_tanh1.8_fp64", "unit": "ms/solve",
             "fp64": ms_lib, "fp64_gpts": npts / (ms_lib * 1e-3) / 1e9, **out_frac,
             "cufft_comparator": ms_cufft, "cufft_comparator_gpts": npts / (ms_cufft * 1e-3) / 1e9,
@@ -674,6 +690,7 @@ def rk3_breakdown(cans, ch, step, npts, ms_step):
                    "share_of_step": ms / ms_step}
             if nm == "momentum":
                 ent["fp64_tflops"] = MOMENTUM_FP64_FLOPS * npts / (per_launch * 1e-3) / 1e12
+                ent["fp64_frac_of_measured"] = ent["fp64_tflops"] / fp64_peak_tflops(cans)
             out[nm] = ent
         else:
             solve_ms += tot / reps

@@ -222,6 +222,15 @@ int cans_plan_status(cans_plan_t plan, int* status);
 int cans_check_bounded_wait(cans_plan_t plan, unsigned polls, int complete, void* cuda_stream);
 
 /*
+ * cans_fp64_fma_probe -- measures the GPU's FP64 fused multiply-add rate (the bound of the FP64 solve
+ * path and of the RK3 momentum kernel): eight 256-thread blocks per SM, each thread running 8
+ * independent FMA chains for `iters` steps and storing one double to out[thread].  Asynchronous on
+ * cuda_stream; *flops receives the FP64 operations the launch performs (2 per FMA), to be divided by
+ * the launch's CUDA-event time.  out: device, n_out >= SMs x 2048 doubles (else CANS_ERR_ARG).
+ */
+int cans_fp64_fma_probe(double* out, size_t n_out, unsigned iters, void* cuda_stream, size_t* flops);
+
+/*
  * cans_poisson_solve_adjoint -- q = S^T g, the transpose (plain Euclidean inner product) of the solve
  * operator S: f -> p of cans_poisson_solve with this plan (the backward pass of a differentiable
  * solve; projection-adjoint reading R10).  With D = diag(dzf_k) along z, D A_z is symmetric, so S is

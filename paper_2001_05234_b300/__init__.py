@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         L.cans_plan_destroy.argtypes = [vp]
         L.cans_plan_status.argtypes = [vp, ip]
         L.cans_check_bounded_wait.argtypes = [vp, ctypes.c_uint, ctypes.c_int, vp]
+        L.cans_fp64_fma_probe.argtypes = [vp, ctypes.c_size_t, ctypes.c_uint, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.cans_zslab_create.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]
         L.cans_zslab_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                        ctypes.POINTER(ctypes.c_size_t)]
@@ -299,6 +300,26 @@ def cans_check_bounded_wait(plan, polls: int, complete: bool, stream=None) -> No
     (cans_check_bounded_wait): a wait that runs out records CANS_ERR_TIMEOUT in the plan's status word."""
     _check(lib().cans_check_bounded_wait(plan, int(polls), 1 if complete else 0, _stream_ptr(stream) or None),
            "cans_check_bounded_wait")
+
+
+def fp64_fma_tflops(iters: int = 20000, reps: int = 3) -> float:
+    """The GPU's FP64 FMA rate in TFLOP/s (cans_fp64_fma_probe timed with CUDA events, best of reps)."""
+    import torch
+
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    out = torch.empty(props.multi_processor_count * 2048, dtype=torch.float64, device="cuda")
+    flops = ctypes.c_size_t(0)
+    st = torch.cuda.current_stream()
+    best = 0.0
+    for _ in range(reps + 1):  # the first launch warms up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib().cans_fp64_fma_probe(out.data_ptr(), out.numel(), int(iters), _stream_ptr(st),
+                                         ctypes.byref(flops)), "cans_fp64_fma_probe")
+        e1.record(st)
+        e1.synchronize()
+        best = max(best, flops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
 
 
 def cans_plan_status(plan) -> int:

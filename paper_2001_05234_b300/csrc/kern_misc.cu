@@ -161,7 +161,39 @@ __global__ void bounded_wait_kernel(int* status, unsigned polls, int complete) {
   if (!mbar_wait_bounded(&bar, 0, polls)) atomicCAS(status, CANS_OK, CANS_ERR_TIMEOUT);
 }
 
+// FP64 fused multiply-add throughput: every thread runs 8 independent chains x <- x * m + c for
+// `iters` steps (|m| < 1, so the values stay finite and normal) and stores their sum, which keeps the
+// compiler from dropping the work.  2 * 8 * iters FP64 operations per thread.
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double* __restrict__ out, unsigned iters) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = 1.0 + 1e-3 * (double)(q + (t & 7));
+  const double m = 0.999999, c = 1e-6;
+  for (unsigned i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  out[t] = s;
+}
+
 }  // namespace cans
+
+extern "C" int cans_fp64_fma_probe(double* out, size_t n_out, unsigned iters, void* cuda_stream, size_t* flops) {
+  int dev = 0, sms = 0;
+  if (!out || !flops || iters == 0) return CANS_ERR_ARG;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CANS_ERR_CUDA;
+  const size_t threads = (size_t)sms * 8 * 256;  // eight 256-thread blocks per SM
+  if (n_out < threads) return CANS_ERR_ARG;
+  cans::fp64_fma_kernel<<<sms * 8, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(out, iters);
+  *flops = threads * 16 * (size_t)iters;
+  return cudaGetLastError() == cudaSuccess ? CANS_OK : CANS_ERR_CUDA;
+}
 
 extern "C" int cans_check_bounded_wait(cans_plan_t plan, unsigned polls, int complete, void* cuda_stream) {
   if (!plan || polls == 0 || polls > (1u << 20)) return CANS_ERR_ARG;

@@ -101,3 +101,4 @@ def test_pageable_host_memory_and_argument_checks(cans):
     assert L.cans_poisson_solve_host(sm.plan, fh.data_ptr(), ph.data_ptr(), fd.data_ptr(), pd.data_ptr(), None, None,
                                      None, None) == cans.CANS_ERR_WORKSPACE  # mixed needs its workspace
     sm.close()
+
