@@ -2,8 +2,9 @@
 stream, the solve on a compute stream, the download on a copy-out stream, ordered by the plan's
 events).  Its result equals the device-to-device solve of the same plan bit for bit, on one stream and
 on three; pipelined calls with alternating device buffers (the loop bench.py times) give each step its
-own right-hand side's solution; pageable host memory works (synchronously) as well; bad arguments are
-refused before anything is enqueued."""
+own right-hand side's solution; the three streams captured into one CUDA graph replay correctly;
+pageable host memory works (synchronously) as well; bad arguments are refused before anything is
+enqueued."""
 import numpy as np
 import pytest
 
@@ -102,3 +103,39 @@ def test_pageable_host_memory_and_argument_checks(cans):
                                      None, None) == cans.CANS_ERR_WORKSPACE  # mixed needs its workspace
     sm.close()
 
+
+
+def test_host_solve_captured_in_a_cuda_graph(cans):
+    """Upload, solve and download on three streams captured into one CUDA graph (the plan's events
+    become the graph's edges); replays with a new right-hand side in the pinned input buffer give its
+    solution."""
+    import torch
+
+    n = (128, 32, 24)
+    dzf = I.tanh_dzf(24, 1.5)
+    s = cans.PoissonSolver(n, (P, P, NN), (1.0, 1.0), dzf, prec=1, sweeps=2)
+    fs = [I.rhs_host(I.PoissonCase("g", n, (P, P, NN), (1.0, 1.0), dzf, 4300 + k, "uniform")) for k in range(2)]
+    want = [s.solve(torch.from_numpy(f).cuda()).cpu().numpy() for f in fs]
+    fh = torch.from_numpy(fs[0].copy()).pin_memory()
+    ph = torch.zeros_like(fh).pin_memory()
+    fd = torch.empty(fs[0].shape, dtype=torch.float64, device="cuda")
+    pd = torch.empty_like(fd)
+    s.solve_host(fh, ph, fd, pd)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    cap, s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        ev = torch.cuda.Event()
+        ev.record(cap)
+        s_in.wait_event(ev)  # fork the copy streams from the capture
+        s_out.wait_event(ev)
+        s.solve_host(fh, ph, fd, pd, copy_in=s_in, compute=cap, copy_out=s_out)
+        done = torch.cuda.Event()
+        done.record(s_out)
+        cap.wait_event(done)  # join
+    for k in range(2):
+        fh.copy_(torch.from_numpy(fs[k]))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(ph.numpy(), want[k])
+    s.close()
