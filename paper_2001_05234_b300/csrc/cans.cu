@@ -506,12 +506,14 @@ int cans_poisson_plan(const int n[3], const double len_xy[2], const int bc[3], c
     P->z_smem[s] = (size_t)ti * nz * es;
   }
   // CANS_RES_PTS=1/2/4 sets the residual stencil's points per thread, CANS_Z_P2=0 keeps the float z pass of
-  // full columns on the staged kernel, CANS_RES_SPLIT=0 / 2 keeps the sweep residual of CTA-engine x lines
+  // full columns on the staged kernel, CANS_Z_FUSE64=0 / 2 keeps the marked columns of short ones in the
+  // separate double kernel / fuses them at every field size, CANS_RES_SPLIT=0 / 2 keeps the sweep residual of CTA-engine x lines
   // fused into the x pass / splits it at every size (switches for comparisons and tests).  CANS_Z_TMA=0 keeps the float z pass on the register-staged kernel, =2 makes a shape the
   // TMA kernel cannot take fail instead of falling back (switches for comparisons and tests; the
   // autotuner, when on, chooses between the two kernels by timing)
   if (const char* ev = std::getenv("CANS_RES_PTS")) P->res_pts = (ev[0] == '1') ? 1 : (ev[0] == '2' ? 2 : 4);
   if (const char* ev = std::getenv("CANS_Z_P2")) P->z_p2 = (ev[0] == '0') ? 0 : 1;
+  if (const char* ev = std::getenv("CANS_Z_FUSE64")) P->z_fuse64 = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_RES_SPLIT")) P->res_split = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_Z_TMA")) P->z_tma = (ev[0] == '0') ? 0 : (ev[0] == '2' ? 2 : 1);
   if (const char* ev = std::getenv("CANS_Z_TMA_CTAS"))

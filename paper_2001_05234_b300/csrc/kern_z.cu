@@ -130,9 +130,46 @@ __device__ __forceinline__ void solve_tile_f32(float* tile, const ZS& Z, const Z
   }
 }
 
-template <int MMAX, int TIC, bool PAIR>
+// The marked (low-|mu|, singular) columns of a staged float tile solved in FP64 in place: the body of
+// zpass_f64_kernel on a tile already in shared memory (double coefficient rows in sa .. sc).
+template <int MMAX, typename ZS>
+__device__ __forceinline__ void solve_tile_marked_f64(float* tile, const ZS& Z, const ZArgs& a, int i0, int j,
+                                                      int ncols, const double* sa, const double* sb,
+                                                      const double* sc) {
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const double muy = a.muy_d[j] + a.shift;
+  auto marked = [&](int i) { return a.mask[(size_t)j * a.nx + i] != 0; };
+  auto single = [&](int cidx) {
+    const int i = i0 + cidx;
+    if (!marked(i)) return;
+    const double mu = a.mux_d[i] + muy;
+    if (a.singular && i == 0 && j == 0) {
+      const double target = (a.gauge != nullptr) ? a.gauge_scale * (*a.gauge) : 0.0;
+      zsolve_column<MMAX, double, float, true>(tile, cidx, Z, a.nz, mu, sa, sb, sc, a.dzf, target, a.compat);
+    } else {
+      zsolve_column<MMAX, double, float, false>(tile, cidx, Z, a.nz, mu, sa, sb, sc, nullptr, 0.0);
+    }
+  };
+  if (MMAX >= 2 && a.xpairs) {
+    for (int q = warp; 2 * q < ncols; q += nwarps) {
+      const int c0 = 2 * q, i = i0 + c0;
+      if (i == 0 || !marked(i) || !marked(i + 1)) {
+        single(c0);
+        single(c0 + 1);
+      } else if constexpr (MMAX >= 2) {
+        zsolve_pair<MMAX, double, float, ZS, false, false>(tile, c0, c0 + 1, Z, a.nz, a.mux_d[i] + muy, sa, sb, sc);
+      }
+    }
+  } else {
+    for (int cidx = warp; cidx < ncols; cidx += nwarps) single(cidx);
+  }
+}
+
+// F64: the tile's marked columns are solved here in FP64 as well (short columns, MMAX <= 4), so the
+// separate double kernel is not launched; sd holds their double coefficient rows.
+template <int MMAX, int TIC, bool PAIR, bool F64 = false>
 __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w, ZArgs a, ZTab<float> zf,
-                                                                      int vec, WLay wl) {
+                                                                      int vec, WLay wl, ZTab<double> zd = {}) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
   constexpr bool CL = MMAX >= 4;
@@ -147,9 +184,19 @@ __global__ void __launch_bounds__(256, 3) zpass_f32_kernel(float* __restrict__ w
   const int ncols = min(TI, a.nx - i0);
   const auto Z = make_zswz<TIC, MMAX>(TI, m);
   stage_zrows<CL>(sa, sb, sc, zf, a.nz, m);
+  // the double rows after the tile (8-byte aligned: the tile holds TI * Nz floats, TI even)
+  double* da = reinterpret_cast<double*>(tile + (size_t)TI * a.nz + ((TI * a.nz) & 1));
+  bool any64 = false;
+  if constexpr (F64) {  // does the tile hold a marked column? (a vote, uniform over the CTA)
+    any64 = __syncthreads_or((int)threadIdx.x < ncols && a.mask[(size_t)j * a.nx + i0 + threadIdx.x] != 0) != 0;
+    if (any64) stage_zrows<false>(da, da + 32 * m, da + 64 * m, zd, a.nz, m);
+  }
   tile_load<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
   __syncthreads();
   solve_tile_f32<MMAX, PAIR>(tile, Z, a, i0, j, ncols, sa, sb, sc);
+  if constexpr (F64) {
+    if (any64) solve_tile_marked_f64<MMAX>(tile, Z, a, i0, j, ncols, da, da + 32 * m, da + 64 * m);
+  }
   __syncthreads();
   tile_store<float>(tile, col0, plane, Z, a.nz, ncols, vec != 0);
 }
@@ -601,40 +648,53 @@ static cudaError_t z_mt(const cans_plan_s* P, T* w, const double* gauge, cudaStr
   if (sizeof(T) == 4) {
     // float columns first, then the double columns of the marked bounding box
     cudaError_t e = cudaSuccess;
-    if (part != 1 && MMAX >= 4 && P->z_tma && ztma_feasible(P, w)) {
-      e = launch_ztma(P, reinterpret_cast<float*>(w), st);
-      if (e != cudaSuccess || part == 0) return e;
-    } else if (part != 1 && P->z_tma == 2) {
-      return cudaErrorNotSupported;  // the TMA kernel was required and cannot take this shape
-    } else if (part != 1 && MMAX >= 4 && TIC == 32 && P->z_p2 && P->n[2] == 32 * MMAX && P->n[0] % 32 == 0 &&
-               !wl.blk && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
-      // pair-granular tiles fetched by cp.async (full columns, whole 32-slot tiles; the column pairs of a
-      // periodic x share their factorisation)
-      if constexpr (MMAX >= 4) {
-        ZArgs a = zargs(P, 32, gauge, nullptr);
+    const bool tma = MMAX >= 4 && P->z_tma && ztma_feasible(P, w);
+    const bool p2 = !tma && MMAX >= 4 && TIC == 32 && P->z_p2 && P->n[2] == 32 * MMAX && P->n[0] % 32 == 0 &&
+                    !wl.blk && (reinterpret_cast<uintptr_t>(w) & 15) == 0;
+    // short columns on the staged kernel of a tiny field: the marked columns are solved in FP64 inside it,
+    // one launch fewer per z pass on a latency-bound chain (32^3 mixed with 2 sweeps: 139 -> 130 us); on
+    // larger fields the separate double kernel overlaps better with other work (64-problem ensemble
+    // 4.63 ms separate, 4.70 fused), so z_fuse64 = 1 fuses up to 2^16 points only, 2 always
+    const size_t npts = (size_t)P->n[0] * P->n[1] * P->n[2];
+    const bool fuse = !tma && !p2 && P->z_tma != 2 && MMAX <= 4 && P->mask_d != nullptr &&
+                      (P->z_fuse64 == 2 || (P->z_fuse64 == 1 && npts <= ((size_t)1 << 16)));
+    if (part != 1) {
+      if (tma) {
+        e = launch_ztma(P, reinterpret_cast<float*>(w), st);
+      } else if (P->z_tma == 2) {
+        return cudaErrorNotSupported;  // the TMA kernel was required and cannot take this shape
+      } else if (p2) {
+        // pair-granular tiles fetched by cp.async (full columns, whole 32-slot tiles; the column pairs of
+        // a periodic x share their factorisation)
+        if constexpr (MMAX >= 4) {
+          ZArgs a = zargs(P, 32, gauge, nullptr);
+          a.mask = P->mask_d;
+          const size_t smem = 3 * 32 * (MMAX + 4) * sizeof(float) + (size_t)32 * 32 * MMAX * sizeof(float);
+          auto kern = P->bc[0] == BC_P ? zpass_p2_kernel<MMAX, true> : zpass_p2_kernel<MMAX, false>;
+          e = set_smem((const void*)kern, smem);
+          if (e != cudaSuccess) return e;
+          kern<<<dim3(P->n[0] / 32, P->n[1]), 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, wl);
+          e = cudaGetLastError();
+        }
+      } else {
+        ZArgs a = zargs(P, P->z_ti[1], gauge, fuse ? compat : nullptr);
         a.mask = P->mask_d;
-        const size_t smem = 3 * 32 * (MMAX + 4) * sizeof(float) + (size_t)32 * 32 * MMAX * sizeof(float);
-        auto kern = P->bc[0] == BC_P ? zpass_p2_kernel<MMAX, true> : zpass_p2_kernel<MMAX, false>;
+        const size_t smem = 3 * 32 * (a.m + 4) * sizeof(float) + P->z_smem[1] +
+                            (fuse ? 3 * 32 * (size_t)a.m * sizeof(double) + sizeof(double) : 0);
+        dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
+        // pairs of equal eigenvalues: periodic x, every tile an even number of whole pairs
+        const bool pair = MMAX >= 4 && P->bc[0] == BC_P && a.nx % 2 == 0 && a.ti % 2 == 0;
+        constexpr bool F64 = MMAX <= 4;  // the fused variant exists for short columns only
+        auto kern = pair ? (fuse ? zpass_f32_kernel<MMAX, TIC, (MMAX >= 4), F64> : zpass_f32_kernel<MMAX, TIC, (MMAX >= 4)>)
+                         : (fuse ? zpass_f32_kernel<MMAX, TIC, false, F64> : zpass_f32_kernel<MMAX, TIC, false>);
         e = set_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<dim3(P->n[0] / 32, P->n[1]), 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, wl);
+        kern<<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl, P->zt_d);
         e = cudaGetLastError();
-        if (e != cudaSuccess || part == 0) return e;
       }
-    } else if (part != 1) {
-      ZArgs a = zargs(P, P->z_ti[1], gauge, nullptr);
-      a.mask = P->mask_d;
-      const size_t smem = 3 * 32 * (a.m + 4) * sizeof(float) + P->z_smem[1];
-      dim3 grid((a.nx + a.ti - 1) / a.ti, a.ny);
-      // pairs of equal eigenvalues: periodic x, every tile an even number of whole pairs
-      const bool pair = MMAX >= 4 && P->bc[0] == BC_P && a.nx % 2 == 0 && a.ti % 2 == 0;
-      auto kern = pair ? zpass_f32_kernel<MMAX, TIC, (MMAX >= 4)> : zpass_f32_kernel<MMAX, TIC, false>;
-      e = set_smem((const void*)kern, smem);
-      if (e != cudaSuccess) return e;
-      kern<<<grid, 256, smem, st>>>(reinterpret_cast<float*>(w), a, P->zt_f, vec, wl);
-      e = cudaGetLastError();
       if (e != cudaSuccess || part == 0) return e;
     }
+    if (fuse) return cudaSuccess;  // the marked columns were solved with the float ones
     ZArgs b = zargs(P, P->z_ti[1], gauge, compat);
     b.mask = P->mask_d;
     const size_t smem64 = 3 * 32 * b.m * sizeof(double) + P->z_smem[1];

@@ -147,6 +147,8 @@ struct cans_plan_s {
   int res_split = 1;  // CTA-engine x lines: the sweep residual as the streaming stencil + an x pass from
                       // 2^24 points on (1), never (0), always (2); fused into the x pass otherwise
   int res_pts = 4;  // residual stencil: points per thread (4, 2 or 1; fewer where nx or alignment demand)
+  int z_fuse64 = 1;  // staged float z kernel, <= 4 rows per lane: marked columns solved in it (1: fields of
+                     // up to 2^16 points, 2: always, 0: never)
   int z_p2 = 1;    // float z pass on full columns: pair-granular cp.async tiles (0: the staged kernel)
   int z_tma = 0;  // float z pass: 0 the register-staged kernel; 1 a TMA-using variant (z_tma_ctas)
                   // where the shape allows it; 2 required (shapes it cannot take fail).  The
