@@ -325,7 +325,8 @@ def gpu_arm(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 transforms + f64 low-mode z-solves + double-float residual (mixed)",
+        "dtype": "f32+f64",
+        "precision": "f32 transforms + f64 low-mode z-solves + double-float residual (mixed)",
         "data": "synthetic (seeded SplitMix64; 64 random Fourier modes + N(0,1e-3) noise)",
         "config": {
             "workload": WORKLOAD,
