@@ -424,8 +424,11 @@ __global__ void __launch_bounds__(16 * TI, MINB) zpass_tma_kernel(const __grid_c
   }
 }
 
+// Two CTAs per SM for a double tile (the FP64 path: its dependent FP64 chains hide each other better,
+// 1024x1024x512 FP64 solve 97.9 -> 95.1 ms, despite register spills at 128 registers), one for a float
+// tile (the mixed path's marked columns: 0.22 ms against 0.25 with two).
 template <typename T, int MMAX, int TIC>
-__global__ void __launch_bounds__(256, 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 1) zpass_f64_kernel(T* __restrict__ w, ZArgs a, ZTab<double> zd, int vec,
                                                            WLay wl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TI = TIC > 0 ? TIC : a.ti, m = a.m;
